@@ -1,0 +1,95 @@
+"""Pins for the oracle ray caster (Algorithm 4): closed-form compositing and shading cases.
+
+Beyond these cases the ray caster is parity-unpinned: its remaining behaviour is the
+reading of Algorithm 4 stated in the module docstring, checked only against the GPU.
+"""
+
+import numpy as np
+
+import synth
+from oracle import raycast
+
+
+def _volume(B, n, fill):
+    """B^3 bricks of n^3 nodes; fill(gx, gy, gz) -> (f, f_u, f_v, f_w) per node (global node coords)."""
+    table = np.arange(B ** 3, dtype=np.int32).reshape(B, B, B)
+    cache = np.zeros((B ** 3, n, n, n, 4))
+    for bz in range(B):
+        for by in range(B):
+            for bx in range(B):
+                k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+                cache[table[bz, by, bx]] = fill(bx * n + i, by * n + j, bz * n + k)
+    return cache, table
+
+
+def _const_tf(rgba, n=16):
+    return np.tile(np.asarray(rgba, dtype=np.float32), (n, 1))
+
+
+def _axis_view(eye, up=(0.0, 1.0, 0.0), **kw):
+    return synth.default_view(width=5, height=5, eye=eye, target=(0.0, 0.0, 0.0), up=up, **kw)
+
+
+def test_constant_field_closed_form():
+    B, n = 2, 8
+    N = B * n
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, 0.5), 0 * x, 0 * x, 0 * x], -1))
+    alpha = float(np.float32(0.05))  # the transfer function is stored in FP32
+    rgb = np.array([0.2, 0.4, 0.8], dtype=np.float32).astype(np.float64)
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=1.0)
+    img = raycast.raycast(cache, table, n, view, _const_tf([*rgb, alpha]))
+    _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
+    assert K[2, 2] == N - 1  # box depth 2 at one sample per voxel spacing 2/(N-1)
+    A = 1 - (1 - alpha) ** K[2, 2]
+    assert abs(img[2, 2, 3] - A) < 1e-12
+    assert np.max(np.abs(img[2, 2, :3] - rgb * A)) < 1e-12  # zero gradient: unshaded colour
+
+
+def test_early_termination_closed_form():
+    B, n = 2, 8
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, 0.5), 0 * x, 0 * x, 0 * x], -1))
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=0.99)
+    img = raycast.raycast(cache, table, n, view, _const_tf([1.0, 1.0, 1.0, 0.5]))
+    # A_k = 1 - 2^-k first exceeds 0.99 at k = 7
+    assert abs(img[2, 2, 3] - (1 - 2.0 ** -7)) < 1e-15
+    assert abs(img[2, 2, 0] - (1 - 2.0 ** -7)) < 1e-15
+
+
+def test_headlight_shading_closed_form():
+    """Linear field along x: a ray along z sees n . d = 0 (ambient only), a ray along x sees |n . d| = 1."""
+    B, n = 2, 8
+    N = B * n
+    slope = 0.01
+    cache, table = _volume(B, n, lambda x, y, z: np.stack(
+        [0.3 + slope * x, np.full(x.shape, slope * (n - 1)), 0 * x, 0 * x], -1))
+    alpha = float(np.float32(0.04))
+    rgb = np.array([0.9, 0.5, 0.1], dtype=np.float32).astype(np.float64)
+    tf = _const_tf([*rgb, alpha])
+    ka, kd, ks = (float(np.float32(x)) for x in (0.3, 0.6, 0.3))
+    for eye, up, d in [((0.0, 0.0, 3.0), (0.0, 1.0, 0.0), 0.0), ((3.0, 0.0, 0.0), (0.0, 1.0, 0.0), 1.0)]:
+        view = _axis_view(eye, up=up, opacity_max=1.0, ka=ka, kd=kd, ks=ks, shininess=20.0)
+        img = raycast.raycast(cache, table, n, view, tf)
+        _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
+        A = 1 - (1 - alpha) ** K[2, 2]
+        c = rgb * (ka + kd * d) + ks * d ** 20
+        assert abs(img[2, 2, 3] - A) < 1e-12
+        assert np.max(np.abs(img[2, 2, :3] - c * A)) < 1e-9
+
+
+def test_absent_bricks_and_misses_are_black():
+    B, n = 2, 8
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, 0.5), 0 * x, 0 * x, 0 * x], -1))
+    tf = _const_tf([1.0, 1.0, 1.0, 0.3])
+    tf[0] = 0.0  # value 0 (an absent brick's nodes) is fully transparent
+    view = _axis_view((0.0, 0.0, 3.0))
+    img = raycast.raycast(cache, np.full_like(table, -1), n, view, tf)
+    assert np.all(img == 0)
+    away = synth.default_view(width=4, height=4, eye=(0.0, 0.0, 3.0), target=(0.0, 0.0, 6.0))
+    assert np.all(raycast.raycast(cache, table, n, away, tf) == 0)
+
+
+def test_center_pixel_ray_is_view_direction():
+    view = synth.default_view(width=7, height=5)
+    d, _, _, _, _ = raycast.ray_setup(view, (64, 64, 64))
+    fwd = -np.array(view["eye"]) / np.linalg.norm(view["eye"])
+    assert np.max(np.abs(d[2, 3] - fwd)) < 1e-6
