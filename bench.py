@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the micro-model hot path on the 512^3 / 4096-block workload.
+
+One step = one pass of every stage of the path over the batch, all in the library's kernels:
+  least-squares encode of the 4096 sample blocks (FP64 class set-up + FP32 fit + FP64 RMSE),
+  decode of every block to the value+gradient cache, a 1024x1024 ray cast of the cache, and the
+  adjoint of the fit residual (gradient of 0.5*||decode(P) - D||^2 at the fitted P).
+The headline is decoded voxels per second of whole step (Gvoxel/s). Inputs are resident in HBM
+and larger than L2 (512 MB of samples, 2.15 GB of cache), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mfa|reference]
+
+Under torchrun each rank runs its own replica of the workload (blocks are independent; there is
+no data-path collective): weak scaling, value = voxels of all ranks / max step time over ranks.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+N_FIELD, BRICK, NCP, DEGREE = 512, 32, 12, 2
+IMG = 1024
+METRIC = "Gvoxel/s MFA decode (value+grad), % roofline, max err vs FP64 oracle"
+WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degree 2, 12^3 control points: "
+            "LS encode + value/gradient decode + 1024^2 ray cast (1 sample/voxel, 256-entry TF) + adjoint")
+# dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by the
+# sha256 of the kernel source it was taken on; reported as null once the source changes.
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def src_sha(name):
+    path = os.path.join(ROOT, "paper_2409_00184_b300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+class Workload:
+    def __init__(self, mfa, ctx, seed):
+        self.mfa, self.ctx = mfa, ctx
+        B = (N_FIELD // BRICK) ** 3
+        self.B, self.vox = B, BRICK ** 3
+        field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+        self.D = synth.blocks_from_field(field, BRICK).contiguous().view(B, self.vox)
+        del field
+        zero = np.zeros((NCP, NCP, NCP))
+        self.bs = synth.make_block_set([(NCP,) * 3] * B, [(DEGREE,) * 3] * B, [(BRICK,) * 3] * B, [zero] * B)
+        self.blk = mfa.DeviceBlocks(self.bs)
+        self.plan = mfa.EncodePlan(ctx, self.blk)
+        self.cache = torch.empty(B * self.vox * 4, device="cuda")
+        nb = N_FIELD // BRICK
+        self.table = torch.arange(B, dtype=torch.int32, device="cuda").view(nb, nb, nb)
+        self.tf = torch.from_numpy(synth.transfer_function(seed)).cuda()
+        self.view = synth.default_view(IMG, IMG)
+        self.image = torch.empty(IMG, IMG, 4, device="cuda")
+        self.grad = torch.empty(self.blk.cps_len, device="cuda")
+        self.rmse = torch.empty(B, dtype=torch.float64, device="cuda")
+
+    def step(self, ev=None, D=None):
+        m, c, blk, v = self.mfa, self.ctx, self.blk, self.vox
+        D = self.D if D is None else D
+        if ev:
+            ev[0].record()
+        m.encode_blocks(c, self.plan, D, v, self.B, blk.cps, self.rmse)
+        if ev:
+            ev[1].record()
+        m.decode_blocks(c, blk, self.cache, v, self.B)
+        if ev:
+            ev[2].record()
+        m.raycast(c, self.cache, v, self.B, self.table, BRICK, self.view, self.tf, self.image)
+        if ev:
+            ev[3].record()
+        m.adjoint_blocks(c, blk, D, v, self.B, self.grad, cps=blk.cps)
+        if ev:
+            ev[4].record()
+
+
+def algorithmic_bytes(B):
+    """Bytes each kernel must move at minimum per launch on this workload."""
+    vox, cp = BRICK ** 3, NCP ** 3
+    return {
+        "encode": B * (vox * 4 + cp * 4 + 8),          # read samples, write control points + RMSE
+        "decode": B * (vox * 16 + cp * 4 + 72),        # write float4 per voxel, read control points + descriptor
+        "raycast": IMG * IMG * 16,                      # image write; cache reads are counted as traffic, not here
+        "adjoint": B * (vox * 4 + 2 * cp * 4 + 72),    # read samples and control points, write gradient
+    }
+
+
+def check_against_oracle(w, nblocks=12, nvox=400, seed=5):
+    """Max error of the GPU encode+decode against the FP64 oracle's fit+decode of the same sample blocks."""
+    from oracle import decode as odec
+    from oracle import encode as oenc
+    g = synth.rng(seed)
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
+    cache = w.cache.view(w.B, w.vox, 4)
+    cps = w.blk.cps.view(w.B, NCP ** 3)
+    got, want, cperr = [], [], 0.0
+    for b in g.choice(w.B, nblocks, replace=False):
+        Db = w.D[b].view(BRICK, BRICK, BRICK).double().cpu().numpy()
+        P = oenc.fit_separable(Db, knots, (DEGREE,) * 3)
+        cperr = max(cperr, float(np.abs(cps[b].cpu().numpy().reshape(P.shape) - P).max() / (P.max() - P.min())))
+        kji = g.integers(0, BRICK, size=(nvox, 3))
+        lin = torch.as_tensor((kji[:, 0] * BRICK + kji[:, 1]) * BRICK + kji[:, 2], device="cuda")
+        got.append(cache[b][lin].cpu().numpy())
+        want.append(odec.decode_voxels(P, knots, (DEGREE,) * 3, (BRICK,) * 3, kji))
+    got, want = np.concatenate(got).astype(np.float64), np.concatenate(want)
+    vr = want[:, 0].max() - want[:, 0].min()
+    gm = np.abs(want[:, 1:]).max()
+    return {"value": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
+            "grad": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm),
+            "cps": cperr, "blocks": nblocks, "voxels_per_block": nvox,
+            "normalisation": "value: max|df|/range(f); grad: max|d grad|/max|grad|; cps: max|dP|/range(P)"}
+
+
+def oracle_sample_time(D_blocks):
+    """Times the FP64 oracle (fit + decode + adjoint) on the given host sample blocks, one thread."""
+    from threadpoolctl import threadpool_limits
+    from oracle import adjoint as oadj
+    from oracle import decode as odec
+    from oracle import encode as oenc
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
+    deg, ns, nc = (DEGREE,) * 3, (BRICK,) * 3, (NCP,) * 3
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        for Db in D_blocks:
+            P = oenc.fit_separable(Db, knots, deg)
+            f = odec.decode_block(P, knots, deg, ns)
+            oadj.adjoint_block(f[..., 0] - Db, knots, deg, nc)
+        return time.perf_counter() - t0
+
+
+def host_sample(seed, nblocks):
+    """The first `nblocks` blocks of the workload's field, generated on the host."""
+    field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+    blocks = synth.blocks_from_field(field, BRICK)
+    idx = synth.rng(seed + 1).choice(blocks.shape[0], nblocks, replace=False)
+    out = [blocks[int(i)].double().cpu().numpy() for i in idx]
+    del field, blocks
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    seed = synth.BASE_SEED + 2
+    budget = 150.0  # seconds for the whole run
+    per_step = budget / max(1, args.steps + args.warmup)
+    probe = host_sample(seed, 2)
+    t1 = oracle_sample_time(probe) / 2
+    nb = max(1, int(per_step / t1))
+    sample = host_sample(seed, nb)
+    for _ in range(args.warmup):
+        oracle_sample_time(sample)
+    times = [oracle_sample_time(sample) for _ in range(args.steps)]
+    dt = sum(times) / len(times)
+    value = nb * BRICK ** 3 / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "blocks": (N_FIELD // BRICK) ** 3, "sample_blocks_per_step": nb},
+            "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks per step "
+                                       "(ray cast not in the sample)"},
+            "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_00184_b300 import mfa
+    ctx = mfa.Context(local)
+    seed = synth.BASE_SEED + 2 + rank
+    w = Workload(mfa, ctx, seed)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        w.step()
+    st = ctx.device_status()
+    if st:
+        raise RuntimeError(f"device status {st:#x} after warm-up")
+
+    # ---- timed region: K steps, per-stage events on the launching stream ----
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    n0 = ctx.launch_count()
+    start.record(stream)
+    for k in range(K):
+        w.step(evs[k])
+    end.record(stream)
+    barrier()
+    launches = ctx.launch_count() - n0
+    clk = clocks.stop()
+    ms = start.elapsed_time(end) / K
+    names = ["encode", "decode", "raycast", "adjoint"]
+    per = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)) for i, n in enumerate(names)}
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = ctx.device_status()
+    if st:
+        raise RuntimeError(f"device status {st:#x} after the timed steps")
+    voxels = w.B * w.vox
+    value = ws * voxels / (ms * 1e-3) / 1e9
+
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    algo = algorithmic_bytes(w.B)
+    kernels = {n: {"ms": per[n], "GB_s": algo[n] / (per[n] * 1e-3) / 1e9} for n in names}
+    kernels["decode"]["Gvoxel_s"] = voxels / (per["decode"] * 1e-3) / 1e9
+    dom = max(names, key=lambda n: per[n])
+    achieved = algo[dom] / (per[dom] * 1e-3) / 1e9
+    src = {"encode": "encode.cu", "decode": "decode_fp32.cu", "raycast": "raycast.cu", "adjoint": "adjoint.cu"}[dom]
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr["src_sha"] == src_sha(src) else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"}
+
+    # ---- end to end: host samples in pinned memory -> step -> image back to the host ----
+    e2e = None
+    if not args.no_e2e:
+        hostD = torch.empty(w.D.shape, dtype=torch.float32, pin_memory=True)
+        hostD.copy_(w.D)
+        hostImg = torch.empty(w.image.shape, dtype=torch.float32, pin_memory=True)
+        Ddev = torch.empty_like(w.D)
+        Ke = max(3, min(K, 10))
+        barrier()
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(Ke):
+            Ddev.copy_(hostD, non_blocking=True)
+            w.step(D=Ddev)
+            hostImg.copy_(w.image, non_blocking=True)
+        e2.record(stream)
+        barrier()
+        ms_e2e = s2.elapsed_time(e2) / Ke
+        e2e = {"value": ws * voxels / (ms_e2e * 1e-3) / 1e9, "unit": "Gvoxel/s",
+               "h2d_bytes_per_step": hostD.numel() * 4, "d2h_bytes_per_step": hostImg.numel() * 4,
+               "ms_per_step": ms_e2e}
+
+    err = None if args.no_check or rank != 0 else check_against_oracle(w)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        nb = 64
+        sample = [w.D[int(b)].view(BRICK, BRICK, BRICK).double().cpu().numpy()
+                  for b in synth.rng(seed + 1).choice(w.B, nb, replace=False)]
+        t = oracle_sample_time(sample)
+        cpu = {"value": nb * w.vox / t / 1e9, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks ({nb * w.vox} voxels, "
+                         f"{t:.1f} s, one thread); the ray-cast stage is not in the sample"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": K,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
+                           "l2": "inputs larger than L2 (512 MB samples, 2.15 GB cache); no flush",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

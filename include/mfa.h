@@ -1,0 +1,206 @@
+/*
+ * mfa.h - C ABI of the B300 micro-model library (Adaptive-FAM hot path, arxiv 2409.00184).
+ *
+ * A micro-model (Sec. 4.2, Fig. "Micro-model storage layout") is one micro-block of a
+ * volume encoded as a clamped trivariate tensor-product B-spline: per axis a degree p,
+ * a control-point count C (the paper's NCP) and a knot vector of C + p + 1 values, plus
+ * C_x*C_y*C_z control points. The library
+ *
+ *   - decodes batches of micro-models into a device voxel cache of value and gradient
+ *     (the queries valueMicroModel / gradientMicroModel of Algorithm 4, evaluated on
+ *     each block's regular sample grid instead of per ray sample),
+ *   - ray-casts that cache front to back with early termination (Algorithm 4),
+ *   - fits micro-models to sample blocks by least squares (the model(NCP, degree) call
+ *     of Algorithm 1), and
+ *   - applies the transposed decode (adjoint) that turns that fit into a gradient method.
+ *
+ * Conventions for every entry point
+ *   - Plain C types only. "d_" pointers are CUDA device pointers the CALLER allocates and
+ *     owns; "h_" pointers are host memory. The library allocates device memory only in
+ *     mfa_ctx_create and mfa_encode_plan_create, and frees it in the matching destroy.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream). Calls enqueue work on it
+ *     and return without synchronising, except mfa_ctx_device_status (documented there).
+ *   - Return value: MFA_OK (0) or a negative MFA_ERR_* code. Arguments are checked on the
+ *     host before anything is enqueued; nothing is enqueued when a call fails.
+ *   - Checks that need device data (descriptor contents, knot order, list entries) run
+ *     in the kernels: a block that fails them is skipped (its output is left untouched)
+ *     and a bit is OR-ed into the context's device status word (MFA_DEV_* below), which
+ *     mfa_ctx_device_status reads.
+ *   - A context is not thread-safe; use one per host thread (or serialise calls).
+ *
+ * Layouts
+ *   - knots: float32; a block's axis-a vector is knots[knot_off[a] .. knot_off[a]+C_a+p_a].
+ *   - control points: float32, cps[cp_off + a + C_x*(b + C_y*c)] = P_abc (x fastest).
+ *   - sample grid of a block: n_x*n_y*n_z samples at parameters u_i = i/(n-1) (FP32
+ *     quotient), stored [z][y][x] (x fastest) in the block's slot:
+ *     base + slot*slot_stride_voxels.
+ *   - decoded cache voxel: 4 floats (f, df/du, df/dv, df/dw); gradients are with respect
+ *     to the block parameters u, v, w in [0, 1] (divide by n-1 for per-voxel units).
+ */
+#ifndef MFA_H
+#define MFA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (return values) -------------------------------------------------- */
+#define MFA_OK               0
+#define MFA_ERR_INVALID_ARG -1   /* null/misaligned pointer, size out of range, bad enum */
+#define MFA_ERR_UNSUPPORTED -2   /* valid request this build does not implement          */
+#define MFA_ERR_CUDA        -3   /* a CUDA runtime call failed (launch, copy, malloc)    */
+#define MFA_ERR_TIMEOUT     -4   /* a bounded device wait gave up (see MFA_DEV_TIMEOUT)   */
+#define MFA_ERR_CAPACITY    -5   /* request exceeds a fixed library limit                */
+#define MFA_ERR_DEVICE      -6   /* the device status word holds error bits              */
+
+/* ---- device status word bits (mfa_ctx_device_status) -------------------------------- */
+#define MFA_DEV_BAD_DESC   0x1u  /* degree/ncp/nsamp outside the launch bounds or limits */
+#define MFA_DEV_BAD_KNOTS  0x2u  /* knot vector decreasing, or t_p >= t_C (empty domain) */
+#define MFA_DEV_BAD_RANGE  0x4u  /* knot/cp offset or slot outside the stated lengths    */
+#define MFA_DEV_BAD_LIST   0x8u  /* a list entry outside [0, nblocks), or count > length */
+#define MFA_DEV_TIMEOUT    0x10u /* a bounded wait (mbarrier/TMA/MMA) gave up            */
+#define MFA_DEV_NOT_SPD    0x20u /* an N^T N Cholesky pivot was not positive (C > n?)    */
+
+/* ---- precisions of the decode contractions ------------------------------------------ */
+#define MFA_PREC_FP32        0   /* FP32 FMA on the CUDA cores, banded (p+1 terms)       */
+#define MFA_PREC_BF16        1   /* tensor cores, BF16 operands, FP32 accumulation       */
+#define MFA_PREC_FP16        2   /* tensor cores, FP16 operands, FP32 accumulation       */
+#define MFA_PREC_SPLIT_BF16  3   /* tensor cores, hi+lo BF16 split (3 products), FP32 acc */
+
+/* ---- decode flags ------------------------------------------------------------------- */
+#define MFA_DECODE_VALUE_ONLY  0x1u /* write f only: 1 float per voxel instead of 4       */
+#define MFA_DECODE_LIST_SLOTS  0x2u /* with a list: item m goes to slot m (not desc.slot) */
+
+/* ---- fixed limits -------------------------------------------------------------------- */
+#define MFA_MAX_DEGREE 3
+#define MFA_MAX_NCP    32
+#define MFA_MAX_NSAMP  64
+
+/* One micro-block (72 bytes, 8-byte aligned). Axis order everywhere is x, y, z. */
+typedef struct {
+  int32_t degree[3];   /* p per axis, 1 <= p <= MFA_MAX_DEGREE                         */
+  int32_t ncp[3];      /* C per axis (the paper's NCP), p+1 <= C <= MFA_MAX_NCP          */
+  int32_t nsamp[3];    /* n per axis, 2 <= n <= MFA_MAX_NSAMP                            */
+  int32_t slot;        /* slot of the block's sample grid / cache entry                  */
+  int64_t knot_off[3]; /* first knot of each axis in the knots array                     */
+  int64_t cp_off;      /* first control point in the cps array                           */
+} mfa_block_desc;
+
+/* Upper bounds of a batch, stated by the caller; they size shared memory and select the
+ * kernel instance. Every block must satisfy degree <= max_degree, ncp <= max_ncp and
+ * nsamp <= max_nsamp on every axis (else MFA_DEV_BAD_DESC and the block is skipped). */
+typedef struct {
+  int32_t max_degree;
+  int32_t max_ncp;
+  int32_t max_nsamp;
+} mfa_bounds;
+
+typedef struct mfa_ctx mfa_ctx;
+
+/* Create a context on CUDA device `device`: queries the device, allocates the device
+ * status word and work-queue counters. Returns MFA_ERR_UNSUPPORTED on a device that is
+ * not compute capability 10.3 (this library is built for sm_103a only). */
+int  mfa_ctx_create(mfa_ctx** out, int device);
+void mfa_ctx_destroy(mfa_ctx* ctx);
+const char* mfa_status_string(int status);
+
+/* Synchronise `stream`, copy the device status word to *status and, if `clear`, reset
+ * it to 0. Returns MFA_OK, or MFA_ERR_CUDA if the stream reported an error. */
+int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* stream);
+
+/* Number of kernels this context launched since creation (all entry points). */
+int64_t mfa_ctx_launch_count(const mfa_ctx* ctx);
+
+/* Eq. 2: the size in bytes of one micro-model file, 1 + ((NCP + degree)*3 + NCP^3)*4.
+ * Returns -1 for NCP < 1 or degree < 0. */
+int64_t mfa_model_bytes(int32_t ncp, int32_t degree);
+
+/* ---- decode (Algorithm 4's value and gradient queries, batched on sample grids) ----- */
+/* Decodes blocks into the cache: for each selected block b and sample (i, j, k),
+ *   f   = sum_{a,b,c} N_a(u_i) N_b(v_j) N_c(w_k) P_abc,  and f_u, f_v, f_w with N' in the
+ * corresponding factor. Selection: if d_list is NULL every block 0..nblocks-1 is decoded;
+ * otherwise the items d_list[0 .. count) where count = *d_count (device int32, read by
+ * the kernel, so the call can be replayed from a CUDA graph) or list_len if d_count is
+ * NULL; count must be <= list_len. Destination: slot desc.slot, or slot m for item m
+ * with MFA_DECODE_LIST_SLOTS. Output per voxel: 4 floats (f, f_u, f_v, f_w), or 1 float
+ * with MFA_DECODE_VALUE_ONLY, at d_cache + (slot*slot_stride_voxels + voxel)*width.
+ * d_cache must be 16-byte aligned. knots_len / cps_len are the array lengths (floats),
+ * used for the range checks. precision: MFA_PREC_*. */
+int mfa_decode_blocks(mfa_ctx* ctx,
+                      const mfa_block_desc* d_desc, int32_t nblocks,
+                      const int32_t* d_list, int32_t list_len, const int32_t* d_count,
+                      const float* d_knots, int64_t knots_len,
+                      const float* d_cps, int64_t cps_len,
+                      float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                      const mfa_bounds* bounds, int32_t precision, uint32_t flags,
+                      void* stream);
+
+/* Fills per-axis basis tables for one block, for testing the span search and the
+ * Cox-de Boor recurrence on their own: for each axis a and sample i, span[a*MAXN + i]
+ * (int32) and N, N' at the p+1 nonzero functions, basis[((a*MAXN + i)*2 + {0,1})*4 + r]
+ * (float32, r < p+1; unused entries 0), MAXN = MFA_MAX_NSAMP. d_desc points at one
+ * descriptor. */
+int mfa_basis_tables(mfa_ctx* ctx, const mfa_block_desc* d_desc,
+                     const float* d_knots, int64_t knots_len,
+                     int32_t* d_span, float* d_basis, void* stream);
+
+/* ---- adjoint (transposed decode) ----------------------------------------------------- */
+/* For each block b: dP_abc = sum_{i,j,k} R_b[k][j][i] N_a(u_i) N_b(v_j) N_c(w_k), with R_b
+ * the block's residual grid at d_residual + slot*slot_stride_voxels (1 float per sample).
+ * Written to d_grad_cps at the block's cp_off (same layout as the control points);
+ * overwrites, does not accumulate. With d_cps non-NULL the residual is formed in the
+ * kernel instead: R = decode_value(d_cps) - d_residual (d_residual then holds the data
+ * samples D), which is the gradient of 0.5*||decode(P) - D||^2. */
+int mfa_adjoint_blocks(mfa_ctx* ctx,
+                       const mfa_block_desc* d_desc, int32_t nblocks,
+                       const float* d_knots, int64_t knots_len,
+                       const float* d_residual, int64_t slot_stride_voxels, int64_t nslots,
+                       const float* d_cps, float* d_grad_cps, int64_t cps_len,
+                       const mfa_bounds* bounds, int32_t precision, void* stream);
+
+/* ---- least-squares encode (Algorithm 1's model(NCP, degree)) ------------------------- */
+/* A plan validates a batch on the host, copies its descriptors and knots to the device
+ * and groups the axes into classes of equal (knots, p, C, n). Executing it computes, per
+ * class, M = N^T N and its Cholesky factor in FP64 and the pseudo-inverse (N^T N)^-1 N^T,
+ * then fits every block: P = D x_1 N_x^+ x_2 N_y^+ x_3 N_z^+ (the exact least-squares
+ * solution of the Kronecker system), and optionally its RMSE over the samples in FP64
+ * (Table 1's error metric). Requires p+1 <= C <= n per axis. */
+typedef struct mfa_encode_plan mfa_encode_plan;
+int  mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out,
+                            const mfa_block_desc* h_desc, int32_t nblocks,
+                            const float* h_knots, int64_t knots_len, int64_t cps_len);
+void mfa_encode_plan_destroy(mfa_encode_plan* plan);
+int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
+                       const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
+                       float* d_cps_out, double* d_rmse /* nullable, one per block */,
+                       void* stream);
+
+/* ---- ray casting (Algorithm 4) -------------------------------------------------------- */
+typedef struct {
+  float eye[3], target[3], up[3];
+  float fov_y_deg;
+  int32_t width, height;
+  float step_voxels;   /* sample spacing in voxels of the longest axis (1 = one per voxel) */
+  float opacity_max;   /* early termination once accumulated opacity exceeds this          */
+  float ka, kd, ks, shininess;  /* headlight Blinn-Phong coefficients                     */
+  float vmin, vmax;    /* value range mapped onto the transfer function                   */
+} mfa_view;
+
+/* Renders width*height premultiplied RGBA floats (row 0 at the top) into d_image from a
+ * decoded cache of bricks of brick_n^3 voxels. d_brick_table[(bz*By + by)*Bx + bx] is the
+ * slot of brick (bx, by, bz) or -1 if absent (its nodes read as zero); brick_dims =
+ * {Bx, By, Bz}. The volume of B_a*brick_n nodes per axis maps onto [-1, 1]^3. The
+ * transfer function is tf_n RGBA float entries over [vmin, vmax]. */
+int mfa_raycast(mfa_ctx* ctx,
+                const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                const mfa_view* view, const float* d_tf, int32_t tf_n,
+                float* d_image, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFA_H */

@@ -81,3 +81,13 @@ def select_ncp(errors, bound):
     """
     ok = [c for c, e in errors.items() if e < bound]
     return min(ok) if ok else None
+
+
+def fit_separable_batch(Dblocks, knots, degrees):
+    """:func:`fit_separable` for a stack of blocks that share knots and degrees: (B, n_z, n_y, n_x) -> (B, C_z, C_y, C_x)."""
+    D = np.asarray(Dblocks, dtype=np.float64)
+    _, nz, ny, nx = D.shape
+    Px = pseudo_inverse(collocation(knots[0], degrees[0], nx))
+    Py = pseudo_inverse(collocation(knots[1], degrees[1], ny))
+    Pz = pseudo_inverse(collocation(knots[2], degrees[2], nz))
+    return np.einsum("ck,bj,ai,nkji->ncba", Pz, Py, Px, D, optimize=True)

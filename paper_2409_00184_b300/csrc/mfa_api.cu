@@ -1,0 +1,245 @@
+// C-ABI entry points: context, host-side argument checks, dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace mfa;
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool bounds_ok(const mfa_bounds* b) {
+  return b && b->max_degree >= 1 && b->max_degree <= MFA_MAX_DEGREE && b->max_ncp >= 2 &&
+         b->max_ncp <= MFA_MAX_NCP && b->max_nsamp >= 2 && b->max_nsamp <= MFA_MAX_NSAMP &&
+         b->max_ncp >= b->max_degree + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mfa_ctx_create(mfa_ctx** out, int device) {
+  if (!out) return MFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) return MFA_ERR_CUDA;
+  if (device < 0 || device >= ndev) return MFA_ERR_INVALID_ARG;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MFA_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return MFA_ERR_UNSUPPORTED;
+  if (cudaSetDevice(device) != cudaSuccess) return MFA_ERR_CUDA;
+  mfa_ctx* c = new (std::nothrow) mfa_ctx();
+  if (!c) return MFA_ERR_CUDA;
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_counters, kNumCounters * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(c->d_counters, 0, kNumCounters * sizeof(uint32_t)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(c->d_status);
+    cudaFree(c->d_counters);
+    delete c;
+    return MFA_ERR_CUDA;
+  }
+  *out = c;
+  return MFA_OK;
+}
+
+void mfa_ctx_destroy(mfa_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_counters);
+  delete ctx;
+}
+
+const char* mfa_status_string(int status) {
+  switch (status) {
+    case MFA_OK: return "ok";
+    case MFA_ERR_INVALID_ARG: return "invalid argument";
+    case MFA_ERR_UNSUPPORTED: return "unsupported";
+    case MFA_ERR_CUDA: return "CUDA runtime error";
+    case MFA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MFA_ERR_CAPACITY: return "request exceeds a library limit";
+    case MFA_ERR_DEVICE: return "device status word holds error bits";
+    default: return "unknown status";
+  }
+}
+
+int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* stream) {
+  if (!ctx || !status) return MFA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MFA_ERR_CUDA;
+  if (cudaMemcpy(status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  if (clear && cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return MFA_ERR_CUDA;
+  return MFA_OK;
+}
+
+int64_t mfa_ctx_launch_count(const mfa_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int64_t mfa_model_bytes(int32_t ncp, int32_t degree) {
+  if (ncp < 1 || degree < 0) return -1;
+  const int64_t c = ncp;
+  return 1 + ((c + degree) * 3 + c * c * c) * 4;
+}
+
+int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
+                      const int32_t* d_list, int32_t list_len, const int32_t* d_count,
+                      const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
+                      float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                      const mfa_bounds* bounds, int32_t precision, uint32_t flags, void* stream) {
+  if (!ctx || !bounds_ok(bounds)) return MFA_ERR_INVALID_ARG;
+  if (nblocks < 0 || list_len < 0 || knots_len < 0 || cps_len < 0 || slot_stride_voxels < 1 || nslots < 0)
+    return MFA_ERR_INVALID_ARG;
+  if (flags & ~(MFA_DECODE_VALUE_ONLY | MFA_DECODE_LIST_SLOTS)) return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_DECODE_LIST_SLOTS) && !d_list) return MFA_ERR_INVALID_ARG;
+  if (precision < MFA_PREC_FP32 || precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
+  const int items = d_list ? list_len : nblocks;
+  if (items == 0 && !d_count) return MFA_OK;
+  if (!d_desc || !d_knots || !d_cps || !d_cache || nblocks == 0) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_cps, 4) || !aligned(d_cache, 16) ||
+      (d_list && !aligned(d_list, 4)) || (d_count && !aligned(d_count, 4)))
+    return MFA_ERR_INVALID_ARG;
+  if (precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
+  // work units (item x z-slab) are counted by a 32-bit queue counter
+  if ((int64_t)items * MFA_MAX_NSAMP >= (int64_t)1 << 30) return MFA_ERR_CAPACITY;
+  DecodeParams prm;
+  prm.desc = d_desc;
+  prm.nblocks = nblocks;
+  prm.list = d_list;
+  prm.list_len = list_len;
+  prm.count = d_count;
+  prm.knots = d_knots;
+  prm.knots_len = knots_len;
+  prm.cps = d_cps;
+  prm.cps_len = cps_len;
+  prm.cache = d_cache;
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.bounds = *bounds;
+  prm.flags = flags;
+  prm.status = ctx->d_status;
+  prm.counter = ctx->d_counters + kDecodeQueue;
+  prm.ks = 0;
+  prm.slabs = 0;
+  DecodeTuning tune;
+  return decode_fp32(ctx, prm, tune, static_cast<cudaStream_t>(stream));
+}
+
+int mfa_basis_tables(mfa_ctx* ctx, const mfa_block_desc* d_desc, const float* d_knots, int64_t knots_len,
+                     int32_t* d_span, float* d_basis, void* stream) {
+  if (!ctx || !d_desc || !d_knots || !d_span || !d_basis || knots_len < 1) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_desc, 8)) return MFA_ERR_INVALID_ARG;
+  return basis_tables(ctx, d_desc, d_knots, knots_len, d_span, d_basis, static_cast<cudaStream_t>(stream));
+}
+
+int mfa_adjoint_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
+                       const float* d_knots, int64_t knots_len,
+                       const float* d_residual, int64_t slot_stride_voxels, int64_t nslots,
+                       const float* d_cps, float* d_grad_cps, int64_t cps_len,
+                       const mfa_bounds* bounds, int32_t precision, void* stream) {
+  if (!ctx || !bounds_ok(bounds)) return MFA_ERR_INVALID_ARG;
+  if (nblocks < 0 || knots_len < 0 || cps_len < 0 || slot_stride_voxels < 1 || nslots < 0)
+    return MFA_ERR_INVALID_ARG;
+  if (precision < MFA_PREC_FP32 || precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
+  if (nblocks == 0) return MFA_OK;
+  if (nblocks >= (1 << 30)) return MFA_ERR_CAPACITY;
+  if (!d_desc || !d_knots || !d_residual || !d_grad_cps) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_residual, 4) || !aligned(d_grad_cps, 4) ||
+      (d_cps && !aligned(d_cps, 4)))
+    return MFA_ERR_INVALID_ARG;
+  if (precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
+  AdjointParams prm;
+  prm.desc = d_desc;
+  prm.nblocks = nblocks;
+  prm.knots = d_knots;
+  prm.knots_len = knots_len;
+  prm.residual = d_residual;
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.cps = d_cps;
+  prm.grad = d_grad_cps;
+  prm.cps_len = cps_len;
+  prm.bounds = *bounds;
+  prm.status = ctx->d_status;
+  prm.counter = ctx->d_counters + kAdjointQueue;
+  return adjoint(ctx, prm, static_cast<cudaStream_t>(stream));
+}
+
+int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
+  if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
+    return MFA_ERR_INVALID_ARG;
+  if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
+    return MFA_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
+  if (view->width < 1 || view->height < 1 || view->width > 16384 || view->height > 16384) return MFA_ERR_INVALID_ARG;
+  if (!(view->fov_y_deg > 0.f && view->fov_y_deg < 180.f) || !(view->step_voxels > 0.f) ||
+      !(view->vmax > view->vmin))
+    return MFA_ERR_INVALID_ARG;
+
+  // Camera frame in FP64, rounded once to FP32 (the per-pixel set-up then runs in FP32).
+  const double ex = view->eye[0], ey = view->eye[1], ez = view->eye[2];
+  double f[3] = {(double)view->target[0] - ex, (double)view->target[1] - ey, (double)view->target[2] - ez};
+  const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  if (!(fl > 0.0)) return MFA_ERR_INVALID_ARG;
+  for (double& v : f) v = v / fl;
+  const double u[3] = {view->up[0], view->up[1], view->up[2]};
+  double r[3] = {f[1] * u[2] - f[2] * u[1], f[2] * u[0] - f[0] * u[2], f[0] * u[1] - f[1] * u[0]};
+  const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(rl > 0.0)) return MFA_ERR_INVALID_ARG;
+  for (double& v : r) v = v / rl;
+  const double up[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  const double tan_h = std::tan((double)view->fov_y_deg * M_PI / 360.0);
+  const double tan_w = tan_h * view->width / view->height;
+
+  RaycastParams prm;
+  prm.cache = reinterpret_cast<const float4*>(d_cache);
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.table = d_brick_table;
+  int nmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    prm.B[a] = brick_dims[a];
+    const int N = brick_dims[a] * brick_n;
+    nmax = N > nmax ? N : nmax;
+    prm.half[a] = (float)((N - 1) / 2.0);
+    prm.gscale[a] = (float)((N - 1) / 2.0 / (brick_n - 1));
+    prm.eye[a] = view->eye[a];
+    prm.fwd[a] = (float)f[a];
+    prm.right[a] = (float)r[a];
+    prm.up[a] = (float)up[a];
+  }
+  prm.brick_n = brick_n;
+  prm.tf = reinterpret_cast<const float4*>(d_tf);
+  prm.tf_n = tf_n;
+  prm.image = reinterpret_cast<float4*>(d_image);
+  prm.W = view->width;
+  prm.H = view->height;
+  prm.tan_w = (float)tan_w;
+  prm.tan_h = (float)tan_h;
+  prm.dt = (float)((double)view->step_voxels * 2.0 / (nmax - 1));
+  const double max_samples = 2.0 * std::sqrt(3.0) / prm.dt + 2.0;
+  if (!(prm.dt > 0.f) || max_samples > (double)(1 << 24)) return MFA_ERR_INVALID_ARG;
+  prm.max_samples = (int)max_samples;
+  prm.step_voxels = view->step_voxels;
+  prm.opacity_max = view->opacity_max;
+  prm.ka = view->ka;
+  prm.kd = view->kd;
+  prm.ks = view->ks;
+  prm.shininess = view->shininess;
+  prm.vmin = view->vmin;
+  prm.vmax = view->vmax;
+  return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

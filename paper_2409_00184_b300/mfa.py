@@ -1,0 +1,269 @@
+"""Python binding of libmfa.so (the C ABI declared in include/mfa.h): argument marshalling only.
+
+Every function here forwards device pointers (torch tensors on the CUDA device), sizes and a
+CUDA stream to the library; all arithmetic runs in the library's kernels. Importing this module
+fails loudly if the compiled library is missing: there is no CPU or framework fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmfa.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVICE = -1, -2, -3, -4, -5, -6
+DEV_BAD_DESC, DEV_BAD_KNOTS, DEV_BAD_RANGE, DEV_BAD_LIST, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4, 8, 16, 32
+PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
+DECODE_VALUE_ONLY, DECODE_LIST_SLOTS = 1, 2
+MAX_DEGREE, MAX_NCP, MAX_NSAMP = 3, 32, 64
+
+
+class BlockDesc(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32 * 3), ("ncp", ctypes.c_int32 * 3), ("nsamp", ctypes.c_int32 * 3),
+                ("slot", ctypes.c_int32), ("knot_off", ctypes.c_int64 * 3), ("cp_off", ctypes.c_int64)]
+
+
+class Bounds(ctypes.Structure):
+    _fields_ = [("max_degree", ctypes.c_int32), ("max_ncp", ctypes.c_int32), ("max_nsamp", ctypes.c_int32)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fov_y_deg", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("step_voxels", ctypes.c_float), ("opacity_max", ctypes.c_float), ("ka", ctypes.c_float),
+                ("kd", ctypes.c_float), ("ks", ctypes.c_float), ("shininess", ctypes.c_float),
+                ("vmin", ctypes.c_float), ("vmax", ctypes.c_float)]
+
+
+DESC_DTYPE = np.dtype({"names": ["degree", "ncp", "nsamp", "slot", "knot_off", "cp_off"],
+                       "formats": [("<i4", 3), ("<i4", 3), ("<i4", 3), "<i4", ("<i8", 3), "<i8"],
+                       "offsets": [0, 12, 24, 36, 40, 64], "itemsize": 72})
+assert ctypes.sizeof(BlockDesc) == DESC_DTYPE.itemsize == 72
+
+SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
+           "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
+           "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
+           "mfa_raycast"]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libmfa.so not found at {_LIB_PATH}: build it with "
+                          "`python -m paper_2409_00184_b300.build` (no fallback path exists)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "mfa_ctx_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int]),
+        "mfa_ctx_destroy": (None, [P]),
+        "mfa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mfa_ctx_device_status": (ctypes.c_int, [P, ctypes.POINTER(U32), ctypes.c_int, P]),
+        "mfa_ctx_launch_count": (I64, [P]),
+        "mfa_model_bytes": (I64, [I32, I32]),
+        "mfa_decode_blocks": (ctypes.c_int, [P, P, I32, P, I32, P, P, I64, P, I64, P, I64, I64,
+                                             ctypes.POINTER(Bounds), I32, U32, P]),
+        "mfa_basis_tables": (ctypes.c_int, [P, P, P, I64, P, P, P]),
+        "mfa_adjoint_blocks": (ctypes.c_int, [P, P, I32, P, I64, P, I64, I64, P, P, I64,
+                                              ctypes.POINTER(Bounds), I32, P]),
+        "mfa_encode_plan_create": (ctypes.c_int, [P, ctypes.POINTER(P), P, I32, P, I64, I64]),
+        "mfa_encode_plan_destroy": (None, [P]),
+        "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
+        "mfa_raycast": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
+                                       ctypes.POINTER(View), P, I32, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class MfaError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {lib.mfa_status_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code != OK:
+        raise MfaError(code, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, n, what):
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call touches {n}")
+
+
+def model_bytes(ncp, degree):
+    """Eq. 2 model size in bytes."""
+    return int(lib.mfa_model_bytes(ncp, degree))
+
+
+class Context:
+    """An mfa_ctx on one CUDA device."""
+
+    def __init__(self, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.init()
+        self.device = dev
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.mfa_ctx_create(ctypes.byref(h), dev.index), "mfa_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib.mfa_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_status(self, clear=True, stream=None):
+        st = ctypes.c_uint32()
+        _check(lib.mfa_ctx_device_status(self.handle, ctypes.byref(st), int(clear), _stream(stream)),
+               "mfa_ctx_device_status")
+        return st.value
+
+    def launch_count(self):
+        return int(lib.mfa_ctx_launch_count(self.handle))
+
+
+def pack_descriptors(bs):
+    """numpy structured array (72-byte records) of a synth.BlockSet's descriptors."""
+    d = np.zeros(len(bs), dtype=DESC_DTYPE)
+    d["degree"], d["ncp"], d["nsamp"] = bs.degree, bs.ncp, bs.nsamp
+    d["slot"], d["knot_off"], d["cp_off"] = bs.slot, bs.knot_off, bs.cp_off
+    return d
+
+
+def bounds_of(bs):
+    return Bounds(int(np.max(bs.degree)), int(np.max(bs.ncp)), int(np.max(bs.nsamp)))
+
+
+class DeviceBlocks:
+    """A batch of micro-models resident on the device: descriptors, knots, control points."""
+
+    def __init__(self, bs, device="cuda", cps=None):
+        self.n = len(bs)
+        self.host_desc = pack_descriptors(bs)
+        self.desc = torch.from_numpy(self.host_desc.view(np.uint8).copy()).to(device)
+        self.host_knots = np.ascontiguousarray(bs.knots, dtype=np.float32)
+        self.knots = torch.from_numpy(self.host_knots).to(device)
+        self.cps = cps if cps is not None else torch.from_numpy(np.ascontiguousarray(bs.cps, np.float32)).to(device)
+        self.bounds = bounds_of(bs)
+        self.slot_voxels = int(np.max(np.prod(bs.nsamp.astype(np.int64), axis=1)))
+        self.nslots = int(np.max(bs.slot)) + 1 if self.n else 0
+        self.cps_len = int(np.sum(np.prod(bs.ncp.astype(np.int64), axis=1)))
+
+
+def decode_blocks(ctx, blocks, cache, slot_stride, nslots, precision=PREC_FP32, flags=0, cps=None,
+                  list_=None, count=None, bounds=None, stream=None):
+    """mfa_decode_blocks on a DeviceBlocks batch; cache: float32 CUDA tensor."""
+    cps = blocks.cps if cps is None else cps
+    width = 1 if flags & DECODE_VALUE_ONLY else 4
+    _need(cache, nslots * slot_stride * width, "cache")
+    _need(cps, blocks.cps_len, "cps")
+    _check(lib.mfa_decode_blocks(ctx.handle, _ptr(blocks.desc), blocks.n,
+                                 _ptr(list_), 0 if list_ is None else list_.numel(), _ptr(count),
+                                 _ptr(blocks.knots), blocks.knots.numel(), _ptr(cps), cps.numel(),
+                                 _ptr(cache), slot_stride, nslots, ctypes.byref(bounds or blocks.bounds),
+                                 precision, flags, _stream(stream)), "mfa_decode_blocks")
+
+
+def basis_tables(ctx, desc_one, knots, stream=None):
+    """mfa_basis_tables for one descriptor (uint8 CUDA tensor of 72 bytes): (span (3, 64), basis (3, 64, 2, 4))."""
+    span = torch.zeros(3 * MAX_NSAMP, dtype=torch.int32, device=knots.device)
+    basis = torch.zeros(3 * MAX_NSAMP * 2 * 4, dtype=torch.float32, device=knots.device)
+    _check(lib.mfa_basis_tables(ctx.handle, _ptr(desc_one), _ptr(knots), knots.numel(), _ptr(span), _ptr(basis),
+                                _stream(stream)), "mfa_basis_tables")
+    return span.view(3, MAX_NSAMP), basis.view(3, MAX_NSAMP, 2, 4)
+
+
+def adjoint_blocks(ctx, blocks, residual, slot_stride, nslots, grad, cps=None, precision=PREC_FP32,
+                   bounds=None, stream=None):
+    """mfa_adjoint_blocks: grad <- N^T residual per block (or N^T (decode(cps) - residual) with cps)."""
+    _need(residual, nslots * slot_stride, "residual")
+    _need(grad, blocks.cps_len, "grad")
+    if cps is not None:
+        _need(cps, blocks.cps_len, "cps")
+    _check(lib.mfa_adjoint_blocks(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
+                                  _ptr(residual), slot_stride, nslots, _ptr(cps), _ptr(grad), grad.numel(),
+                                  ctypes.byref(bounds or blocks.bounds), precision, _stream(stream)),
+           "mfa_adjoint_blocks")
+
+
+class EncodePlan:
+    """mfa_encode_plan for a DeviceBlocks batch (validated and grouped into axis classes on the host)."""
+
+    def __init__(self, ctx, blocks):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        desc = np.ascontiguousarray(blocks.host_desc)
+        _check(lib.mfa_encode_plan_create(ctx.handle, ctypes.byref(h), desc.ctypes.data_as(ctypes.c_void_p),
+                                          blocks.n, blocks.host_knots.ctypes.data_as(ctypes.c_void_p),
+                                          blocks.host_knots.size, blocks.cps_len), "mfa_encode_plan_create")
+        self.handle = h
+        self.cps_len, self.nblocks = blocks.cps_len, blocks.n
+
+    def close(self):
+        if self.handle:
+            lib.mfa_encode_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode_blocks(ctx, plan, data, slot_stride, nslots, cps_out, rmse=None, stream=None):
+    """mfa_encode_blocks: least-squares control points (and FP64 RMSE per block) from sample grids."""
+    _need(data, nslots * slot_stride, "data")
+    _need(cps_out, plan.cps_len, "cps_out")
+    if rmse is not None:
+        _need(rmse, plan.nblocks, "rmse")
+    _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
+                                 _ptr(rmse), _stream(stream)), "mfa_encode_blocks")
+
+
+def make_view(v):
+    return View((ctypes.c_float * 3)(*v["eye"]), (ctypes.c_float * 3)(*v["target"]),
+                (ctypes.c_float * 3)(*v["up"]), v["fov_y_deg"], int(v["width"]), int(v["height"]),
+                v.get("step_voxels", 1.0), v["opacity_max"], v["ka"], v["kd"], v["ks"], v["shininess"],
+                v["vmin"], v["vmax"])
+
+
+def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None):
+    """mfa_raycast: table is an int32 (Bz, By, Bx) CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
+    Bz, By, Bx = table.shape
+    _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
+    _need(cache, nslots * slot_stride * 4, "cache")
+    dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
+    vw = make_view(view)
+    _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims), brick_n,
+                           ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)), "mfa_raycast")

@@ -41,13 +41,13 @@ def clamped_uniform_knots(C, p):
 
 
 def random_clamped_knots(C, p, generator, min_gap=0.02):
-    """Clamped knot vector with seeded non-uniform interior knots (sorted, at least ``min_gap`` apart)."""
-    m = C - p - 1
-    while True:
-        inner = np.sort(generator.uniform(0.0, 1.0, size=m))
-        pts = np.concatenate([[0.0], inner, [1.0]])
-        if m == 0 or np.min(np.diff(pts)) >= min_gap:
-            break
+    """Clamped knot vector with seeded non-uniform interior knots: the C-p spans get widths
+    min_gap + (1 - (C-p) min_gap) * (a Dirichlet(1, ..., 1) draw)."""
+    m = C - p  # number of non-empty spans
+    gap = min(min_gap, 0.5 / m)
+    w = generator.dirichlet(np.ones(m))
+    widths = gap + (1.0 - m * gap) * w
+    inner = np.cumsum(widths)[:-1]
     return np.concatenate([np.zeros(p + 1), inner, np.ones(p + 1)])
 
 
@@ -313,7 +313,7 @@ def make_block_set(ncp, degree, nsamp, cps_list, knots_list=None, slots=None, or
 
 
 def random_block_set(B, seed, ncp_choices=(4, 6, 8, 12), degree_choices=(1, 2, 3), nsamp_choices=(5, 8, 13, 32),
-                     nonuniform=False, anisotropic=True):
+                     nonuniform=False, anisotropic=True, min_gap=0.02):
     """Small mixed batch for parity tests: random per-axis (C, p, n) with p+1 <= C <= n, random CPs in [-1, 1]."""
     g = rng(seed)
     ncp, deg, ns, cps, knots = [], [], [], [], []
@@ -326,7 +326,7 @@ def random_block_set(B, seed, ncp_choices=(4, 6, 8, 12), degree_choices=(1, 2, 3
             opts = [c for c in ncp_choices if p + 1 <= c <= n] or [p + 1]
             C = int(g.choice(opts))
             d3.append(p), c3.append(C), n3.append(n)
-            t3.append(random_clamped_knots(C, p, g) if nonuniform else clamped_uniform_knots(C, p))
+            t3.append(random_clamped_knots(C, p, g, min_gap) if nonuniform else clamped_uniform_knots(C, p))
         ncp.append(c3), deg.append(d3), ns.append(n3), knots.append(t3)
         cps.append(g.uniform(-1.0, 1.0, size=(c3[2], c3[1], c3[0])))
     return make_block_set(ncp, deg, ns, cps, knots)

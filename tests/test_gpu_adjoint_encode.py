@@ -1,0 +1,121 @@
+"""GPU adjoint (mfa_adjoint_blocks) and least-squares encode (mfa_encode_blocks) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import gm_blocks_fitted
+from oracle import adjoint as oadj
+from oracle import decode, encode
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    from paper_2409_00184_b300 import mfa as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mfa):
+    c = mfa.Context(0)
+    yield c
+    c.close()
+
+
+def _grids(bs, seed):
+    g = synth.rng(seed)
+    stride = int(np.max(np.prod(bs.nsamp.astype(np.int64), axis=1)))
+    grids = np.zeros((len(bs), stride), np.float32)
+    for b in range(len(bs)):
+        nx, ny, nz = bs.nsamp[b]
+        grids[bs.slot[b], : nx * ny * nz] = g.uniform(-1, 1, nx * ny * nz)
+    return grids, stride
+
+
+def _block_grid(grids, bs, b):
+    nx, ny, nz = bs.nsamp[b]
+    return grids[bs.slot[b], : nx * ny * nz].reshape(nz, ny, nx).astype(np.float64)
+
+
+@pytest.mark.parametrize("seed", [301, 302])
+def test_adjoint_matches_oracle(mfa, ctx, seed):
+    bs = synth.random_block_set(16, seed, nsamp_choices=(5, 13, 32, 64), ncp_choices=(4, 6, 8, 12, 20),
+                                nonuniform=seed % 2 == 0)
+    blk = mfa.DeviceBlocks(bs)
+    R, stride = _grids(bs, seed)
+    grad = torch.full((blk.cps_len,), float("nan"), device="cuda")
+    mfa.adjoint_blocks(ctx, blk, torch.from_numpy(R.ravel()).cuda(), stride, len(bs), grad)
+    assert ctx.device_status() == 0
+    G = grad.cpu().numpy()
+    for b in range(len(bs)):
+        want = oadj.adjoint_block(_block_grid(R, bs, b), bs.block_knots(b), bs.degree[b], bs.ncp[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = G[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max(), b
+
+
+def test_fused_residual_gradient(mfa, ctx):
+    bs = synth.random_block_set(12, 303, nsamp_choices=(8, 13, 32), ncp_choices=(4, 6, 8))
+    blk = mfa.DeviceBlocks(bs)
+    D, stride = _grids(bs, 303)
+    grad = torch.zeros(blk.cps_len, device="cuda")
+    mfa.adjoint_blocks(ctx, blk, torch.from_numpy(D.ravel()).cuda(), stride, len(bs), grad, cps=blk.cps)
+    assert ctx.device_status() == 0
+    G = grad.cpu().numpy()
+    for b in range(len(bs)):
+        knots, deg, nsamp = bs.block_knots(b), bs.degree[b], bs.nsamp[b]
+        r = decode.decode_block(bs.block_cps(b), knots, deg, nsamp)[..., 0] - _block_grid(D, bs, b)
+        want = oadj.adjoint_block(r, knots, deg, bs.ncp[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = G[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max(), b
+
+
+def _encode(mfa, ctx, bs, D, stride):
+    blk = mfa.DeviceBlocks(bs)
+    plan = mfa.EncodePlan(ctx, blk)
+    out = torch.full((blk.cps_len,), float("nan"), device="cuda")
+    rmse = torch.full((len(bs),), float("nan"), dtype=torch.float64, device="cuda")
+    mfa.encode_blocks(ctx, plan, torch.from_numpy(np.ascontiguousarray(D).ravel()).cuda(), stride, len(bs), out, rmse)
+    assert ctx.device_status() == 0
+    plan.close()
+    return out.cpu().numpy(), rmse.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed,nonuniform", [(311, False), (312, True)])
+def test_encode_matches_oracle_least_squares(mfa, ctx, seed, nonuniform):
+    # non-uniform knots keep every span at least one sample spacing wide (a well-posed fit)
+    bs = synth.random_block_set(16, seed, nsamp_choices=(13, 32, 64), ncp_choices=(3, 4, 6, 8, 12) if nonuniform
+                                else (3, 4, 6, 8, 12, 16, 24), nonuniform=nonuniform, min_gap=0.085)
+    D, stride = _grids(bs, seed)
+    P, rm = _encode(mfa, ctx, bs, D, stride)
+    for b in range(len(bs)):
+        Db = _block_grid(D, bs, b)
+        want = encode.fit_separable(Db, bs.block_knots(b), bs.degree[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = P[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(got - want).max() <= 1e-5 * max(1.0, np.abs(want).max()), b
+        want_rmse = encode.rmse(want, Db, bs.block_knots(b), bs.degree[b])
+        assert abs(rm[b] - want_rmse) <= 1e-5 * (Db.max() - Db.min()), (b, rm[b], want_rmse)
+
+
+def test_encode_config2_reduced(mfa, ctx):
+    bs, blocks = gm_blocks_fitted(128, 32, 12, 2, synth.BASE_SEED + 2)
+    D = blocks.reshape(len(bs), -1)
+    P, rm = _encode(mfa, ctx, bs, D, 32 ** 3)
+    want = bs.cps.astype(np.float64)  # the oracle's least-squares control points
+    rng_p = want.max() - want.min()
+    assert np.abs(P - want).max() <= 1e-5 * rng_p
+    assert np.all(rm > 0) and np.all(rm < 0.05)
+
+
+def test_encode_plan_rejects_bad_batches(mfa, ctx):
+    bs = synth.random_block_set(2, 313, ncp_choices=(12,), nsamp_choices=(8,), degree_choices=(2,))
+    bs.ncp[:] = 12  # C > n: not a least-squares problem with a unique solution
+    blk = mfa.DeviceBlocks(bs)
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.EncodePlan(ctx, blk)
+    assert e.value.code == mfa.ERR_INVALID_ARG

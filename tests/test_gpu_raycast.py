@@ -1,0 +1,106 @@
+"""GPU ray caster (mfa_raycast) against the oracle's Algorithm 4 on the same FP32 cache."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import gm_blocks_fitted, oracle_decode_set
+from oracle import raycast as ocast
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    from paper_2409_00184_b300 import mfa as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mfa):
+    c = mfa.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def volume():
+    """64^3 nodes = 4^3 bricks of 16^3, fitted with C = 8, degree 2; cache = oracle decode rounded to FP32."""
+    bs, _ = gm_blocks_fitted(64, 16, 8, 2, synth.BASE_SEED + 12)
+    cache = np.stack(oracle_decode_set(bs)).astype(np.float32)  # (64, 16, 16, 16, 4)
+    return cache, 16
+
+
+def _run(mfa, ctx, cache, table, n, view, tf):
+    dev_cache = torch.from_numpy(cache.reshape(-1)).cuda()
+    dev_table = torch.from_numpy(table.astype(np.int32)).cuda()
+    dev_tf = torch.from_numpy(tf).cuda()
+    img = torch.full((view["height"], view["width"], 4), float("nan"), device="cuda")
+    mfa.raycast(ctx, dev_cache, n ** 3, cache.shape[0], dev_table, n, view, dev_tf, img)
+    assert ctx.device_status() == 0
+    return img.cpu().numpy()
+
+
+def _tables(nb):
+    ident = np.arange(nb ** 3, dtype=np.int32).reshape(nb, nb, nb)
+    g = synth.rng(3)
+    perm = g.permutation(nb ** 3).astype(np.int32)
+    holes = ident.copy()
+    holes[g.random(holes.shape) < 0.3] = -1
+    return ident, perm, holes
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_raycast_no_early_termination(mfa, ctx, volume, which):
+    cache, n = volume
+    ident, perm, holes = _tables(4)
+    table = [ident, perm, holes][which]
+    if which == 1:  # permuted slots: the cache holds brick b at slot perm[b]
+        c2 = np.empty_like(cache)
+        c2[perm.reshape(-1)] = cache
+        cache = c2
+        table = perm.reshape(4, 4, 4)
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=64, height=48, opacity_max=1.0)
+    got = _run(mfa, ctx, cache, table, n, view, tf)
+    want = ocast.raycast(cache, table, n, view, tf)
+    assert np.max(np.abs(got - want)) <= 1e-4
+
+
+def test_raycast_early_termination_bound(mfa, ctx, volume):
+    cache, n = volume
+    ident, _, _ = _tables(4)
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    tf[:, 3] = np.clip(tf[:, 3] * 6, 0, 1)  # dense enough that most rays terminate early
+    view = synth.default_view(width=64, height=64, opacity_max=0.99)
+    got = _run(mfa, ctx, cache, ident, n, view, tf)
+    want = ocast.raycast(cache, ident, n, view, tf)
+    d = np.max(np.abs(got - want), axis=-1)
+    assert (want[..., 3] > 0.99).mean() > 0.2
+    assert d.max() <= 1e-2
+    assert (d <= 1e-4).mean() >= 0.999
+
+
+def test_raycast_constant_field_closed_form(mfa, ctx):
+    n, B = 8, 2
+    cache = np.zeros((B ** 3, n, n, n, 4), np.float32)
+    cache[..., 0] = 0.5
+    table = np.arange(B ** 3, dtype=np.int32).reshape(B, B, B)
+    alpha = np.float32(0.05)
+    tf = np.tile(np.array([0.2, 0.4, 0.8, alpha], np.float32), (16, 1))
+    view = synth.default_view(width=5, height=5, eye=(0.0, 0.0, 3.0), opacity_max=1.0)
+    got = _run(mfa, ctx, cache, table, n, view, tf)
+    _, _, _, K, _ = ocast.ray_setup(view, (B * n,) * 3)
+    assert K[2, 2] == B * n - 1
+    A = 1 - (1 - np.float64(alpha)) ** K[2, 2]
+    assert abs(got[2, 2, 3] - A) < 2e-6
+
+
+def test_raycast_argument_checks(mfa, ctx, volume):
+    cache, n = volume
+    ident, _, _ = _tables(4)
+    tf = synth.transfer_function(1)
+    view = synth.default_view(width=8, height=8, vmin=1.0, vmax=1.0)
+    with pytest.raises(mfa.MfaError):
+        _run(mfa, ctx, cache, ident, n, view, tf)
