@@ -26,12 +26,12 @@ struct BlockGeom {
   int64_t cp_off;
 };
 
-// Reads and checks one descriptor against the launch bounds and array lengths.
-// Returns 0 or the MFA_DEV_* bit that failed.
+// Reads and checks one descriptor against the launch bounds and array lengths (the slot field
+// only when check_slot). Returns 0 or the MFA_DEV_* bit that failed.
 __device__ __forceinline__ uint32_t load_desc(const mfa_block_desc* d, const mfa_bounds& bd,
                                               int64_t knots_len, int64_t cps_len,
                                               int64_t nslots, int64_t slot_stride,
-                                              BlockGeom& g) {
+                                              BlockGeom& g, bool check_slot = true) {
   for (int a = 0; a < 3; ++a) {
     g.p[a] = d->degree[a];
     g.C[a] = d->ncp[a];
@@ -50,7 +50,8 @@ __device__ __forceinline__ uint32_t load_desc(const mfa_block_desc* d, const mfa
     ncps *= g.C[a];
   }
   if (g.cp_off < 0 || g.cp_off + ncps > cps_len) return MFA_DEV_BAD_RANGE;
-  if (g.slot < 0 || g.slot >= nslots || vox > slot_stride) return MFA_DEV_BAD_RANGE;
+  if (vox > slot_stride) return MFA_DEV_BAD_RANGE;
+  if (check_slot && (g.slot < 0 || g.slot >= nslots)) return MFA_DEV_BAD_RANGE;
   return 0;
 }
 

@@ -77,10 +77,11 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
         const int item = (int)(unit / prm.slabs);
         b = prm.list ? prm.list[item] : item;
         uint32_t bad = 0;
+        const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
         if (b < 0 || b >= prm.nblocks) bad = MFA_DEV_BAD_LIST;
         else bad = load_desc(prm.desc + b, prm.bounds, prm.knots_len, prm.cps_len, prm.nslots,
-                             prm.slot_stride, s_g);
-        if (!bad && (prm.flags & MFA_DECODE_LIST_SLOTS)) {
+                             prm.slot_stride, s_g, !list_slots);
+        if (!bad && list_slots) {
           if (item >= prm.nslots) bad = MFA_DEV_BAD_RANGE;
           s_g.slot = item;
         }

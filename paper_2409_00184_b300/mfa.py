@@ -184,6 +184,8 @@ def decode_blocks(ctx, blocks, cache, slot_stride, nslots, precision=PREC_FP32, 
                   list_=None, count=None, bounds=None, stream=None):
     """mfa_decode_blocks on a DeviceBlocks batch; cache: float32 CUDA tensor."""
     cps = blocks.cps if cps is None else cps
+    if list_ is not None and list_.numel() == 0:
+        return  # an empty list selects nothing (a NULL list would mean every block)
     width = 1 if flags & DECODE_VALUE_ONLY else 4
     _need(cache, nslots * slot_stride * width, "cache")
     _need(cps, blocks.cps_len, "cps")

@@ -70,7 +70,7 @@ _GRADS = torch.tensor([
 
 def _hash3(ix, iy, iz, seed):
     """Integer lattice hash (int64 multiply-xorshift mix); identical on every device."""
-    h = ix * 73856093 + iy * 19349663 + iz * 83492791 + seed * 2654435761
+    h = ix * 73856093 + iy * 19349663 + iz * 83492791 + ((seed * 2654435761) & 0xFFFFFFFF)
     h = h & 0xFFFFFFFF
     h = (h ^ (h >> 16)) * 0x45D9F3B & 0xFFFFFFFF
     h = (h ^ (h >> 16)) * 0x45D9F3B & 0xFFFFFFFF
