@@ -113,6 +113,19 @@ int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* strea
 /* Number of kernels this context launched since creation (all entry points). */
 int64_t mfa_ctx_launch_count(const mfa_ctx* ctx);
 
+/* Tile shape of the FP32 decode for one batch class: `ks` z-planes per work unit and at most
+ * `ctas_per_sm` resident CTAs of the persistent grid (0 = library default for either field).
+ * A context holds up to 64 entries keyed by (max_degree, max_ncp, max_nsamp) of the call's
+ * mfa_bounds; mfa_decode_blocks uses the matching entry, else the defaults. Setting an entry
+ * again replaces it; ks is clamped to max_nsamp and lowered when shared memory requires it.
+ * Used by the autotuner (paper_2409_00184_b300/autotune.py), which times candidate shapes. */
+typedef struct {
+  int32_t ks;
+  int32_t ctas_per_sm;
+} mfa_decode_tiling;
+int mfa_ctx_set_decode_tiling(mfa_ctx* ctx, const mfa_bounds* key, const mfa_decode_tiling* tiling);
+int mfa_ctx_get_decode_tiling(const mfa_ctx* ctx, const mfa_bounds* key, mfa_decode_tiling* tiling);
+
 /* Eq. 2: the size in bytes of one micro-model file, 1 + ((NCP + degree)*3 + NCP^3)*4.
  * Returns -1 for NCP < 1 or degree < 0. */
 int64_t mfa_model_bytes(int32_t ncp, int32_t degree);

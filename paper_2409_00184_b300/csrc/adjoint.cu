@@ -1,4 +1,6 @@
 // Adjoint of the micro-model decode: dP_abc = sum_{k,j,i} R[k][j][i] N_a(u_i) N_b(v_j) N_c(w_k).
+// (Entry point; the common case runs on the dense contraction kernel of contract3.cu. The banded
+// gather kernel below is the general path for shapes beyond that kernel's shared memory.)
 //
 // The gradient of 0.5*||decode(P) - D||^2 with respect to the control points, i.e. the transposed
 // contraction that makes the least-squares encode of Algorithm 1's model() a gradient method.
@@ -11,6 +13,7 @@
 // recomputed from the knots in every CTA rather than stored. With control points given, R is
 // formed in the kernel as decode_value(P) - D, slab by slab, without an HBM round trip.
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -225,6 +228,31 @@ cudaError_t launch_adj(mfa_ctx* ctx, const AdjointParams& prm, const AdjSmem& L,
 }  // namespace
 
 int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream) {
+  // the dense contraction kernel first (N^T R, or M P - N^T D for the fused gradient); this banded
+  // gather kernel only serves block shapes whose buffers do not fit that kernel's shared memory
+  {
+    ContractParams c;
+    std::memset(&c, 0, sizeof(c));
+    c.mode = prm.cps ? kGradient : kAdjoint;
+    c.nblocks = prm.nblocks;
+    c.desc = prm.desc;
+    c.knots = prm.knots;
+    c.knots_len = prm.knots_len;
+    c.bounds = prm.bounds;
+    c.cps = prm.cps;
+    c.x = prm.residual;
+    c.slot_stride = prm.slot_stride;
+    c.nslots = prm.nslots;
+    c.out = prm.grad;
+    c.cps_len = prm.cps_len;
+    c.status = prm.status;
+    c.counter = prm.counter;
+    c.maxC = prm.bounds.max_ncp;
+    c.maxN = prm.bounds.max_nsamp;
+    c.pmax = prm.bounds.max_degree;
+    const int rc = contract3(ctx, c, stream);
+    if (rc != MFA_ERR_CAPACITY) return rc;
+  }
   const int maxN = prm.bounds.max_nsamp, maxC = prm.bounds.max_ncp, pmax = prm.bounds.max_degree;
   int ks = std::min(8, maxN);
   AdjSmem L = adj_layout(pmax, maxC, maxN, ks);

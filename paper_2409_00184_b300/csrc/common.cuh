@@ -6,12 +6,19 @@
 
 #include "mfa.h"
 
+struct mfa_tiling_entry {
+  mfa_bounds key;
+  mfa_decode_tiling tiling;
+};
+
 struct mfa_ctx {
   int device = 0;
   int num_sms = 0;
   uint32_t* d_status = nullptr;   // device status word (MFA_DEV_* bits)
   uint32_t* d_counters = nullptr; // work-queue counters, one per concurrent launch kind
   int64_t launches = 0;           // kernels enqueued through this context
+  int ntilings = 0;
+  mfa_tiling_entry tilings[64];   // decode tile shapes keyed by batch bounds (autotuner)
 };
 
 namespace mfa {

@@ -240,7 +240,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
 }
 
 template <int PMAX, bool VO>
-static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const DecodeSmem& L, int grid_cap,
+static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const DecodeSmem& L, int ctas_per_sm,
                               cudaStream_t stream) {
   auto kern = decode_fp32_kernel<PMAX, VO>;
   const size_t smem = (size_t)L.total * 4;
@@ -250,9 +250,8 @@ static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const Decod
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDecodeThreads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  int grid = ctx->num_sms * occ;
-  if (grid_cap > 0) grid = std::min(grid, grid_cap);
-  grid = std::max(grid, 1);
+  if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
+  const int grid = std::max(1, ctx->num_sms * occ);
   kern<<<grid, kDecodeThreads, smem, stream>>>(prm, L);
   ctx->launches++;
   return cudaGetLastError();
@@ -273,9 +272,9 @@ int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaSt
   const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
   cudaError_t e;
   switch (pmax) {
-    case 1: e = vo ? launch_one<1, true>(ctx, prm, L, tune.grid, stream) : launch_one<1, false>(ctx, prm, L, tune.grid, stream); break;
-    case 2: e = vo ? launch_one<2, true>(ctx, prm, L, tune.grid, stream) : launch_one<2, false>(ctx, prm, L, tune.grid, stream); break;
-    case 3: e = vo ? launch_one<3, true>(ctx, prm, L, tune.grid, stream) : launch_one<3, false>(ctx, prm, L, tune.grid, stream); break;
+    case 1: e = vo ? launch_one<1, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<1, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;
+    case 2: e = vo ? launch_one<2, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<2, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;
+    case 3: e = vo ? launch_one<3, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<3, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;
     default: return MFA_ERR_INVALID_ARG;
   }
   return e == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;

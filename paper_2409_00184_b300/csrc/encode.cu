@@ -2,13 +2,12 @@
 //
 // With samples on a regular grid the design matrix is N_z (x) N_y (x) N_x, so the least-squares
 // control points are P = D x_1 N_x^+ x_2 N_y^+ x_3 N_z^+ with N^+ = (N^T N)^{-1} N^T per axis.
-//   class kernel (FP64): one CTA per distinct axis class (knots, p, C, n): collocation matrix N,
-//     M = N^T N, Cholesky M = L L^T (pivots checked), N^+ by two triangular solves per sample,
-//     stored transposed (n x C) in FP32, plus the FP32 span/basis table the RMSE pass decodes with.
-//   fit kernel (FP32): one CTA per block (persistent queue), z-slabs of the sample grid through
-//     shared memory: dense x-, y- and z-contractions with N_x^+, N_y^+, N_z^+; then, optionally, a
-//     banded value decode of the fitted model against the samples with the squared error summed
-//     in FP64 (Table 1's RMSE).
+//   plan (host): validates the batch and groups its axes into classes of equal (knots, p, C, n).
+//   class kernel (FP64): one CTA per class: collocation matrix N, M = N^T N, Cholesky M = L L^T
+//     (pivots checked), N^+ by two triangular solves per sample, stored transposed (n x C) in
+//     FP32, plus the FP32 span/basis table the RMSE pass decodes with.
+//   fit: the shared three-axis contraction kernel (contract3.cu, mode kFit) applies the three
+//     pseudo-inverses to every block and sums the squared fitting error in FP64.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -22,28 +21,6 @@ namespace mfa {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kKnotMax = MFA_MAX_NCP + MFA_MAX_DEGREE + 1;
-
-struct EncClass {
-  int p, C, n;
-  int pinv_off;  // floats into the pseudo-inverse pool: n x C, [i][a]
-  int tab_off;   // entries into the basis-table pool: n entries
-  int pad;
-  float t[kKnotMax];
-};
-
-struct EncItem {
-  int cls[3];
-  int slot;
-  int64_t cp_off;
-};
-
-// Basis-table entry for the RMSE decode: first nonzero index and the p+1 values.
-struct TabEntry {
-  int off;
-  float N[MFA_MAX_DEGREE + 1];
-};
-
 __global__ void __launch_bounds__(kThreads) encode_class_kernel(const EncClass* classes, float* pinv,
                                                                 TabEntry* tabs, uint32_t* status) {
   __shared__ double s_t[kKnotMax];
@@ -114,134 +91,6 @@ __global__ void __launch_bounds__(kThreads) encode_class_kernel(const EncClass* 
       x[r] = v / s_L[r * C + r];
     }
     for (int r = 0; r < C; ++r) pinv[k.pinv_off + tid * C + r] = (float)x[r];
-  }
-}
-
-struct FitSmem {
-  int pinv[3], tab[3], P, D, W1, W2, total;  // offsets in 4-byte words
-};
-
-FitSmem fit_layout(int maxC, int maxN, int ks) {
-  FitSmem L;
-  int o = 0;
-  for (int a = 0; a < 3; ++a) { L.pinv[a] = o; o += maxN * maxC; }
-  for (int a = 0; a < 3; ++a) { L.tab[a] = o; o += maxN * (int)(sizeof(TabEntry) / 4); }
-  o = (o + 3) & ~3;
-  L.P = o;  o += maxC * maxC * maxC;
-  L.D = o;  o += maxN * maxN * ks;
-  L.W1 = o; o += maxN * maxC * ks;  // [kl][j][a]; U0 of the RMSE decode
-  L.W2 = o; o += maxC * maxC * ks;  // [kl][b][a]; T0 of the RMSE decode
-  L.total = o;
-  return L;
-}
-
-__global__ void __launch_bounds__(kThreads)
-encode_fit_kernel(const EncItem* items, int nblocks, const EncClass* classes, const float* pinv,
-                  const TabEntry* tabs, const float* data, int64_t slot_stride, float* cps, double* rmse,
-                  uint32_t* counter, FitSmem L, int ks) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ int s_item;
-  __shared__ double s_red[kThreads / 32];
-  const int tid = threadIdx.x;
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) s_item = atomicAdd(counter, 1u);
-    __syncthreads();
-    const int b = s_item;
-    if (b >= nblocks) break;
-    const EncItem it = items[b];
-    const EncClass& cx = classes[it.cls[0]];
-    const EncClass& cy = classes[it.cls[1]];
-    const EncClass& cz = classes[it.cls[2]];
-    const int Cx = cx.C, Cy = cy.C, Cz = cz.C, nx = cx.n, ny = cy.n, nz = cz.n;
-    const EncClass* cl[3] = {&cx, &cy, &cz};
-    for (int a = 0; a < 3; ++a) {
-      const int len = cl[a]->C * cl[a]->n;
-      for (int e = tid; e < len; e += blockDim.x) sm[L.pinv[a] + e] = pinv[cl[a]->pinv_off + e];
-      TabEntry* tb = reinterpret_cast<TabEntry*>(sm + L.tab[a]);
-      for (int e = tid; e < cl[a]->n; e += blockDim.x) tb[e] = tabs[cl[a]->tab_off + e];
-    }
-    float* s_P = sm + L.P;
-    float* s_D = sm + L.D;
-    float* s_W1 = sm + L.W1;
-    float* s_W2 = sm + L.W2;
-    const float* Px = sm + L.pinv[0];
-    const float* Py = sm + L.pinv[1];
-    const float* Pz = sm + L.pinv[2];
-    const int ncps = Cx * Cy * Cz, plane = Cx * Cy;
-    for (int e = tid; e < ncps; e += blockDim.x) s_P[e] = 0.f;
-    const float* src = data + (int64_t)it.slot * slot_stride;
-    __syncthreads();
-    for (int k0 = 0; k0 < nz; k0 += ks) {
-      const int kc = min(ks, nz - k0);
-      for (int e = tid; e < nx * ny * kc; e += blockDim.x) s_D[e] = src[(int64_t)k0 * nx * ny + e];
-      __syncthreads();
-      for (int e = tid; e < Cx * ny * kc; e += blockDim.x) {  // x: W1[kl][j][a] = sum_i Px[i][a] D[kl][j][i]
-        const int a = e % Cx, r = e / Cx;
-        const float* drow = s_D + r * nx;
-        float acc = 0.f;
-        for (int i = 0; i < nx; ++i) acc = fmaf(Px[i * Cx + a], drow[i], acc);
-        s_W1[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < plane * kc; e += blockDim.x) {  // y: W2[kl][b][a] = sum_j Py[j][b] W1[kl][j][a]
-        const int a = e % Cx, r = e / Cx, bb = r % Cy, kl = r / Cy;
-        float acc = 0.f;
-        for (int j = 0; j < ny; ++j) acc = fmaf(Py[j * Cy + bb], s_W1[(kl * ny + j) * Cx + a], acc);
-        s_W2[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < ncps; e += blockDim.x) {  // z: P[c][b][a] += sum_kl Pz[k0+kl][c] W2[kl][b][a]
-        const int ab = e % plane, c = e / plane;
-        float acc = s_P[e];
-        for (int kl = 0; kl < kc; ++kl) acc = fmaf(Pz[(k0 + kl) * Cz + c], s_W2[kl * plane + ab], acc);
-        s_P[e] = acc;
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < ncps; e += blockDim.x) cps[it.cp_off + e] = s_P[e];
-    if (!rmse) continue;
-    // RMSE: banded value decode of the fitted model against the samples, squares summed in FP64
-    const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
-    const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
-    const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
-    double sq = 0.0;
-    for (int k0 = 0; k0 < nz; k0 += ks) {
-      const int kc = min(ks, nz - k0);
-      for (int e = tid; e < plane * kc; e += blockDim.x) {
-        const int kl = e / plane, ab = e - kl * plane;
-        const TabEntry te = tz[k0 + kl];
-        float acc = 0.f;
-        for (int d = 0; d <= cz.p; ++d) acc = fmaf(s_P[(te.off + d) * plane + ab], te.N[d], acc);
-        s_W2[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < Cx * ny * kc; e += blockDim.x) {
-        const int a = e % Cx, r = e / Cx, j = r % ny, kl = r / ny;
-        const TabEntry te = ty[j];
-        float acc = 0.f;
-        for (int d = 0; d <= cy.p; ++d) acc = fmaf(s_W2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
-        s_W1[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < nx * ny * kc; e += blockDim.x) {
-        const int i = e % nx, r = e / nx;
-        const TabEntry te = tx[i];
-        float f = 0.f;
-        for (int d = 0; d <= cx.p; ++d) f = fmaf(s_W1[r * Cx + te.off + d], te.N[d], f);
-        const double diff = (double)f - (double)src[(int64_t)k0 * nx * ny + e];
-        sq += diff * diff;
-      }
-      __syncthreads();
-    }
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if ((tid & 31) == 0) s_red[tid >> 5] = sq;
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += s_red[w];
-      rmse[b] = sqrt(tot / ((double)nx * ny * nz));
-    }
   }
 }
 
@@ -360,27 +209,25 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
   encode_class_kernel<<<plan->nclasses, kThreads, 0, s>>>(plan->d_classes, plan->d_pinv, plan->d_tabs, ctx->d_status);
   ctx->launches++;
   if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
-  int ks = std::min(8, plan->maxN);
-  FitSmem L = fit_layout(plan->maxC, plan->maxN, ks);
-  while ((size_t)L.total * 4 > kMaxDynSmem && ks > 1) {
-    ks = std::max(1, ks / 2);
-    L = fit_layout(plan->maxC, plan->maxN, ks);
-  }
-  if ((size_t)L.total * 4 > kMaxDynSmem) return MFA_ERR_CAPACITY;
-  const size_t smem = (size_t)L.total * 4;
-  if (cudaFuncSetAttribute(encode_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MFA_ERR_CUDA;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, encode_fit_kernel, kThreads, smem) != cudaSuccess || occ < 1)
-    return MFA_ERR_CUDA;
-  uint32_t* counter = ctx->d_counters + kEncodeQueue;
-  if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), s) != cudaSuccess) return MFA_ERR_CUDA;
-  const int grid = std::max(1, std::min(ctx->num_sms * occ, plan->nblocks));
-  encode_fit_kernel<<<grid, kThreads, smem, s>>>(plan->d_items, plan->nblocks, plan->d_classes, plan->d_pinv,
-                                                 plan->d_tabs, d_data, slot_stride_voxels, d_cps_out, d_rmse,
-                                                 counter, L, ks);
-  ctx->launches++;
-  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+  ContractParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.mode = kFit;
+  prm.nblocks = plan->nblocks;
+  prm.items = plan->d_items;
+  prm.classes = plan->d_classes;
+  prm.pinv = plan->d_pinv;
+  prm.tabs = plan->d_tabs;
+  prm.rmse = d_rmse;
+  prm.x = d_data;
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.out = d_cps_out;
+  prm.status = ctx->d_status;
+  prm.counter = ctx->d_counters + kEncodeQueue;
+  prm.maxC = plan->maxC;
+  prm.maxN = plan->maxN;
+  prm.pmax = MFA_MAX_DEGREE;
+  return contract3(ctx, prm, s);
 }
 
 }  // extern "C"

@@ -35,8 +35,8 @@ struct DecodeParams {
 };
 
 struct DecodeTuning {
-  int ks = 0;    // 0 = default
-  int grid = 0;  // 0 = one wave of resident CTAs
+  int ks = 0;           // 0 = default
+  int ctas_per_sm = 0;  // 0 = as many as fit
 };
 
 int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaStream_t stream);
@@ -51,6 +51,7 @@ struct RaycastParams {
   const int32_t* table;
   int B[3];
   int brick_n;
+  int log2n;  // log2(brick_n) when brick_n is a power of two, else -1
   const float4* tf;
   int tf_n;
   float4* image;
@@ -84,5 +85,60 @@ struct AdjointParams {
 };
 
 int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream);
+
+// ---- least-squares encode: per-class tables built by the plan, consumed by the contraction ----
+constexpr int kKnotMax = MFA_MAX_NCP + MFA_MAX_DEGREE + 1;
+
+struct EncClass {
+  int p, C, n;
+  int pinv_off;  // floats into the pseudo-inverse pool: n x C, [i][a]
+  int tab_off;   // entries into the basis-table pool: n entries
+  int pad;
+  float t[kKnotMax];
+};
+
+struct EncItem {
+  int cls[3];
+  int slot;
+  int64_t cp_off;
+};
+
+// Basis-table entry: first nonzero basis index at a sample and the p+1 values there.
+struct TabEntry {
+  int off;
+  float N[MFA_MAX_DEGREE + 1];
+};
+
+// Transposed three-axis contraction Y[c][b][a] = sum X[k][j][i] Ax[i][a] Ay[j][b] Az[k][c] per block.
+enum ContractMode { kFit = 0, kAdjoint = 1, kGradient = 2 };
+
+struct ContractParams {
+  int mode;
+  int nblocks;
+  // kFit: items + classes + pools from an encode plan
+  const EncItem* items;
+  const EncClass* classes;
+  const float* pinv;
+  const TabEntry* tabs;
+  double* rmse;          // kFit, nullable
+  // kAdjoint / kGradient: descriptors and knots
+  const mfa_block_desc* desc;
+  const float* knots;
+  int64_t knots_len;
+  mfa_bounds bounds;
+  const float* cps;      // kGradient: control points P
+  // all modes
+  const float* x;        // sample grids (slot-addressed)
+  int64_t slot_stride;
+  int64_t nslots;
+  float* out;            // control-point-shaped output
+  int64_t cps_len;
+  uint32_t* status;
+  uint32_t* counter;
+  int maxC, maxN, pmax;
+};
+
+// Returns MFA_ERR_CAPACITY (without launching) when the block shapes do not fit shared memory.
+int contract3(mfa_ctx* ctx, ContractParams prm, cudaStream_t stream);
 
 }  // namespace mfa

@@ -83,6 +83,38 @@ int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* strea
 
 int64_t mfa_ctx_launch_count(const mfa_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+static bool same_key(const mfa_bounds& a, const mfa_bounds& b) {
+  return a.max_degree == b.max_degree && a.max_ncp == b.max_ncp && a.max_nsamp == b.max_nsamp;
+}
+
+int mfa_ctx_set_decode_tiling(mfa_ctx* ctx, const mfa_bounds* key, const mfa_decode_tiling* tiling) {
+  if (!ctx || !key || !tiling || !bounds_ok(key) || tiling->ks < 0 || tiling->ctas_per_sm < 0 ||
+      tiling->ks > MFA_MAX_NSAMP || tiling->ctas_per_sm > 32)
+    return MFA_ERR_INVALID_ARG;
+  for (int i = 0; i < ctx->ntilings; ++i)
+    if (same_key(ctx->tilings[i].key, *key)) {
+      ctx->tilings[i].tiling = *tiling;
+      return MFA_OK;
+    }
+  if (ctx->ntilings >= 64) return MFA_ERR_CAPACITY;
+  ctx->tilings[ctx->ntilings].key = *key;
+  ctx->tilings[ctx->ntilings].tiling = *tiling;
+  ctx->ntilings++;
+  return MFA_OK;
+}
+
+int mfa_ctx_get_decode_tiling(const mfa_ctx* ctx, const mfa_bounds* key, mfa_decode_tiling* tiling) {
+  if (!ctx || !key || !tiling) return MFA_ERR_INVALID_ARG;
+  for (int i = 0; i < ctx->ntilings; ++i)
+    if (same_key(ctx->tilings[i].key, *key)) {
+      *tiling = ctx->tilings[i].tiling;
+      return MFA_OK;
+    }
+  tiling->ks = 0;
+  tiling->ctas_per_sm = 0;
+  return MFA_ERR_INVALID_ARG;
+}
+
 int64_t mfa_model_bytes(int32_t ncp, int32_t degree) {
   if (ncp < 1 || degree < 0) return -1;
   const int64_t c = ncp;
@@ -129,6 +161,11 @@ int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblock
   prm.ks = 0;
   prm.slabs = 0;
   DecodeTuning tune;
+  mfa_decode_tiling t;
+  if (mfa_ctx_get_decode_tiling(ctx, bounds, &t) == MFA_OK) {
+    tune.ks = t.ks;
+    tune.ctas_per_sm = t.ctas_per_sm;
+  }
   return decode_fp32(ctx, prm, tune, static_cast<cudaStream_t>(stream));
 }
 
@@ -220,6 +257,9 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
     prm.up[a] = (float)up[a];
   }
   prm.brick_n = brick_n;
+  prm.log2n = -1;
+  for (int l = 0; l < 31; ++l)
+    if ((1 << l) == brick_n) prm.log2n = l;
   prm.tf = reinterpret_cast<const float4*>(d_tf);
   prm.tf_n = tf_n;
   prm.image = reinterpret_cast<float4*>(d_image);

@@ -62,48 +62,77 @@ __global__ void __launch_bounds__(kTile * kTile) raycast_kernel(RaycastParams pr
 
   // ---- march ----
   const int n = prm.brick_n;
+  const int sh = prm.log2n;  // >= 0: power-of-two bricks (shift/mask addressing)
   const int Nx = prm.B[0] * n, Ny = prm.B[1] * n, Nz = prm.B[2] * n;
   const float inv_range = 1.0f / (prm.vmax - prm.vmin);
   const float tfs = (float)(prm.tf_n - 1);
+  const int n2 = n * n;
   float cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
   for (int k = 0; k < K; ++k) {
     const float t = fmaf((float)k + 0.5f, prm.dt, t0);
     const float gx = fminf(fmaxf((fmaf(t, d[0], prm.eye[0]) + 1.0f) * prm.half[0], 0.f), (float)(Nx - 1));
     const float gy = fminf(fmaxf((fmaf(t, d[1], prm.eye[1]) + 1.0f) * prm.half[1], 0.f), (float)(Ny - 1));
     const float gz = fminf(fmaxf((fmaf(t, d[2], prm.eye[2]) + 1.0f) * prm.half[2], 0.f), (float)(Nz - 1));
-    const int ix = min((int)floorf(gx), Nx - 2), iy = min((int)floorf(gy), Ny - 2), iz = min((int)floorf(gz), Nz - 2);
+    const int ix = min((int)gx, Nx - 2), iy = min((int)gy, Ny - 2), iz = min((int)gz, Nz - 2);
     const float wx = gx - (float)ix, wy = gy - (float)iy, wz = gz - (float)iz;
+    // brick and local index of the two corner layers on each axis
+    int bx0, by0, bz0, lx0, ly0, lz0;
+    if (sh >= 0) {
+      bx0 = ix >> sh; by0 = iy >> sh; bz0 = iz >> sh;
+      lx0 = ix & (n - 1); ly0 = iy & (n - 1); lz0 = iz & (n - 1);
+    } else {
+      bx0 = ix / n; by0 = iy / n; bz0 = iz / n;
+      lx0 = ix - bx0 * n; ly0 = iy - by0 * n; lz0 = iz - bz0 * n;
+    }
     float4 c[2][2][2];
+    if (lx0 < n - 1 && ly0 < n - 1 && lz0 < n - 1) {
+      // all eight corners in one brick: one table lookup
+      const int slot = __ldg(prm.table + (bz0 * prm.B[1] + by0) * prm.B[0] + bx0);
+      if (slot >= 0 && slot < prm.nslots) {
+        const float4* base = prm.cache + (int64_t)slot * prm.slot_stride + (lz0 * n + ly0) * n + lx0;
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
+        for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
+          for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int X = ix + dx, Y = iy + dy, Z = iz + dz;
-          const int bx = X / n, by = Y / n, bz = Z / n;
-          const int slot = __ldg(prm.table + ((int64_t)bz * prm.B[1] + by) * prm.B[0] + bx);
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (slot >= 0 && slot < prm.nslots)
-            v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + ((Z - bz * n) * n + (Y - by * n)) * n + (X - bx * n));
-          c[dz][dy][dx] = v;
-        }
+            for (int dx = 0; dx < 2; ++dx) c[dz][dy][dx] = __ldg(base + dz * n2 + dy * n + dx);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const bool ox = dx && lx0 == n - 1, oy = dy && ly0 == n - 1, oz = dz && lz0 == n - 1;
+            const int bx = bx0 + ox, by = by0 + oy, bz = bz0 + oz;
+            const int lx = ox ? 0 : lx0 + dx, ly = oy ? 0 : ly0 + dy, lz = oz ? 0 : lz0 + dz;
+            const int slot = __ldg(prm.table + (bz * prm.B[1] + by) * prm.B[0] + bx);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (slot >= 0 && slot < prm.nslots)
+              v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + (lz * n + ly) * n + lx);
+            c[dz][dy][dx] = v;
+          }
+    }
     const float4 s = lerp4(lerp4(lerp4(c[0][0][0], c[0][0][1], wx), lerp4(c[0][1][0], c[0][1][1], wx), wy),
                            lerp4(lerp4(c[1][0][0], c[1][0][1], wx), lerp4(c[1][1][0], c[1][1][1], wx), wy), wz);
     // transfer function
     const float x = fminf(fmaxf((s.x - prm.vmin) * inv_range, 0.f), 1.f) * tfs;
-    const int i0 = min((int)floorf(x), prm.tf_n - 2);
+    const int i0 = min((int)x, prm.tf_n - 2);
     const float4 rgba = lerp4(s_tf[i0], s_tf[i0 + 1], x - (float)i0);
     float a = rgba.w;
-    if (prm.step_voxels != 1.0f) a = 1.0f - powf(1.0f - a, prm.step_voxels);
+    if (prm.step_voxels != 1.0f) a = 1.0f - __powf(1.0f - a, prm.step_voxels);
     // headlight shading from the world-space gradient
     const float g0 = s.y * prm.gscale[0], g1 = s.z * prm.gscale[1], g2 = s.w * prm.gscale[2];
-    const float gl = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+    const float gl2 = g0 * g0 + g1 * g1 + g2 * g2;
     float shade = 1.0f, spec = 0.0f;
-    if (gl >= 1e-8f) {
-      const float nd = fabsf(g0 * d[0] + g1 * d[1] + g2 * d[2]) / gl;
+    if (gl2 >= 1e-16f) {
+      const float nd = fminf(fabsf(g0 * d[0] + g1 * d[1] + g2 * d[2]) * rsqrtf(gl2), 1.0f);
       shade = prm.ka + prm.kd * nd;
-      spec = prm.ks * powf(nd, prm.shininess);
+      spec = nd > 0.f ? prm.ks * __powf(nd, prm.shininess) : 0.f;
     }
     const float w = (1.0f - A) * a;
     cr = fmaf(w, fmaf(rgba.x, shade, spec), cr);

@@ -30,6 +30,10 @@ class Bounds(ctypes.Structure):
     _fields_ = [("max_degree", ctypes.c_int32), ("max_ncp", ctypes.c_int32), ("max_nsamp", ctypes.c_int32)]
 
 
+class DecodeTiling(ctypes.Structure):
+    _fields_ = [("ks", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
 class View(ctypes.Structure):
     _fields_ = [("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
                 ("fov_y_deg", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
@@ -46,7 +50,7 @@ assert ctypes.sizeof(BlockDesc) == DESC_DTYPE.itemsize == 72
 SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
            "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
-           "mfa_raycast"]
+           "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling"]
 
 
 def _load():
@@ -61,6 +65,8 @@ def _load():
         "mfa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mfa_ctx_device_status": (ctypes.c_int, [P, ctypes.POINTER(U32), ctypes.c_int, P]),
         "mfa_ctx_launch_count": (I64, [P]),
+        "mfa_ctx_set_decode_tiling": (ctypes.c_int, [P, ctypes.POINTER(Bounds), ctypes.POINTER(DecodeTiling)]),
+        "mfa_ctx_get_decode_tiling": (ctypes.c_int, [P, ctypes.POINTER(Bounds), ctypes.POINTER(DecodeTiling)]),
         "mfa_model_bytes": (I64, [I32, I32]),
         "mfa_decode_blocks": (ctypes.c_int, [P, P, I32, P, I32, P, P, I64, P, I64, P, I64, I64,
                                              ctypes.POINTER(Bounds), I32, U32, P]),
@@ -150,6 +156,15 @@ class Context:
 
     def launch_count(self):
         return int(lib.mfa_ctx_launch_count(self.handle))
+
+    def set_decode_tiling(self, bounds, ks=0, ctas_per_sm=0):
+        _check(lib.mfa_ctx_set_decode_tiling(self.handle, ctypes.byref(bounds),
+                                             ctypes.byref(DecodeTiling(ks, ctas_per_sm))), "mfa_ctx_set_decode_tiling")
+
+    def get_decode_tiling(self, bounds):
+        t = DecodeTiling()
+        rc = lib.mfa_ctx_get_decode_tiling(self.handle, ctypes.byref(bounds), ctypes.byref(t))
+        return (t.ks, t.ctas_per_sm) if rc == OK else None
 
 
 def pack_descriptors(bs):
