@@ -287,13 +287,15 @@ __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm,
     // kFit
     for (int e = tid; e < ncps; e += blockDim.x) prm.out[cp_off + e] = Y[e];
     if (!prm.rmse) continue;
-    // RMSE: banded value decode of the fitted model against the samples, squares summed in FP64
+    // RMSE: banded value decode of the fitted model against the samples. Each thread sums its
+    // squared errors in FP32 with Kahan compensation; the per-thread sums are reduced in FP64
+    // (FP64 per voxel would run at the low FP64 rate of this GPU).
     {
       const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
       const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
       const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
       const int pxx = s_p[0], pyy = s_p[1], pzz = s_p[2];
-      double sq = 0.0;
+      float ksum = 0.f, kcomp = 0.f;
       for (int k0 = 0; k0 < nz; k0 += ks) {
         const int kc = min(ks, nz - k0);
         for (int e = tid; e < plane * kc; e += blockDim.x) {  // T0 -> Y2
@@ -317,11 +319,15 @@ __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm,
           const TabEntry te = tx[i];
           float f = 0.f;
           for (int d = 0; d <= pxx; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
-          const double diff = (double)f - (double)X[(int64_t)k0 * nx * ny + e];
-          sq += diff * diff;
+          const float diff = f - X[(int64_t)k0 * nx * ny + e];
+          const float y = diff * diff - kcomp;
+          const float t = ksum + y;
+          kcomp = (t - ksum) - y;
+          ksum = t;
         }
         __syncthreads();
       }
+      double sq = (double)ksum - (double)kcomp;
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
       if ((tid & 31) == 0) s_red[tid >> 5] = sq;
       __syncthreads();

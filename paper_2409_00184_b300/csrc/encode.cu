@@ -100,6 +100,90 @@ bool host_knots_ok(const float* t, int p, int C) {
   return t[p] < t[C];
 }
 
+// Host-side analysis of a batch: validation, axis classes of equal (p, C, n, knots), per-block items.
+struct BatchAnalysis {
+  std::vector<EncItem> items;
+  std::vector<EncClass> classes;
+  int pinv_len = 0, tab_len = 0, maxC = 0, maxN = 0, max_slot = -1;
+  int64_t max_vox = 0;
+};
+
+int analyze_batch(const mfa_block_desc* h_desc, int nblocks, const float* h_knots, int64_t knots_len,
+                  int64_t cps_len, BatchAnalysis& out) {
+  out.items.assign(nblocks, EncItem());
+  std::map<std::vector<float>, int> index;  // key: p, C, n, knots...
+  for (int b = 0; b < nblocks; ++b) {
+    const mfa_block_desc& d = h_desc[b];
+    int64_t ncps = 1, vox = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int p = d.degree[a], C = d.ncp[a], n = d.nsamp[a];
+      if (p < 1 || p > MFA_MAX_DEGREE || C < p + 1 || C > MFA_MAX_NCP || n < 2 || n > MFA_MAX_NSAMP || C > n ||
+          d.knot_off[a] < 0 || d.knot_off[a] + C + p + 1 > knots_len)
+        return MFA_ERR_INVALID_ARG;
+      const float* t = h_knots + d.knot_off[a];
+      if (!host_knots_ok(t, p, C)) return MFA_ERR_INVALID_ARG;
+      std::vector<float> key = {(float)p, (float)C, (float)n};
+      key.insert(key.end(), t, t + C + p + 1);
+      auto it = index.find(key);
+      int cls;
+      if (it == index.end()) {
+        EncClass c;
+        std::memset(&c, 0, sizeof(c));
+        c.p = p; c.C = C; c.n = n;
+        c.pinv_off = out.pinv_len;
+        c.tab_off = out.tab_len;
+        std::memcpy(c.t, t, sizeof(float) * (C + p + 1));
+        out.pinv_len += C * n;
+        out.tab_len += n;
+        cls = (int)out.classes.size();
+        out.classes.push_back(c);
+        index.emplace(key, cls);
+      } else {
+        cls = it->second;
+      }
+      out.items[b].cls[a] = cls;
+      ncps *= C;
+      vox *= n;
+      out.maxC = std::max(out.maxC, C);
+      out.maxN = std::max(out.maxN, n);
+    }
+    if (d.cp_off < 0 || d.cp_off + ncps > cps_len || d.slot < 0) return MFA_ERR_INVALID_ARG;
+    out.items[b].slot = d.slot;
+    out.items[b].cp_off = d.cp_off;
+    out.max_slot = std::max(out.max_slot, d.slot);
+    out.max_vox = std::max(out.max_vox, vox);
+  }
+  return MFA_OK;
+}
+
+// Enqueues the FP64 class set-up and the fit for device-resident items/classes/pools.
+int run_fit(mfa_ctx* ctx, int nblocks, int nclasses, int maxC, int maxN, const EncItem* items,
+            const EncClass* classes, float* pinv, TabEntry* tabs, const float* data, int64_t slot_stride,
+            int64_t nslots, float* cps_out, double* rmse, cudaStream_t s) {
+  encode_class_kernel<<<nclasses, kThreads, 0, s>>>(classes, pinv, tabs, ctx->d_status);
+  ctx->launches++;
+  if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
+  ContractParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.mode = kFit;
+  prm.nblocks = nblocks;
+  prm.items = items;
+  prm.classes = classes;
+  prm.pinv = pinv;
+  prm.tabs = tabs;
+  prm.rmse = rmse;
+  prm.x = data;
+  prm.slot_stride = slot_stride;
+  prm.nslots = nslots;
+  prm.out = cps_out;
+  prm.status = ctx->d_status;
+  prm.counter = ctx->d_counters + kEncodeQueue;
+  prm.maxC = maxC;
+  prm.maxN = maxN;
+  prm.pmax = MFA_MAX_DEGREE;
+  return contract3(ctx, prm, s);
+}
+
 }  // namespace
 }  // namespace mfa
 
@@ -123,64 +207,24 @@ int mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out, const mfa_block_
   if (!ctx || !out || nblocks < 1 || !h_desc || !h_knots || knots_len < 1 || cps_len < 1) return MFA_ERR_INVALID_ARG;
   if (nblocks >= (1 << 30)) return MFA_ERR_CAPACITY;
   *out = nullptr;
-  std::vector<EncItem> items(nblocks);
-  std::vector<EncClass> classes;
-  std::map<std::vector<float>, int> index;  // key: p, C, n, knots...
+  BatchAnalysis an;
+  const int rc = analyze_batch(h_desc, nblocks, h_knots, knots_len, cps_len, an);
+  if (rc != MFA_OK) return rc;
   mfa_encode_plan* plan = new (std::nothrow) mfa_encode_plan();
   if (!plan) return MFA_ERR_CUDA;
-  int pinv_len = 0, tab_len = 0;
-  for (int b = 0; b < nblocks; ++b) {
-    const mfa_block_desc& d = h_desc[b];
-    int64_t ncps = 1, vox = 1;
-    for (int a = 0; a < 3; ++a) {
-      const int p = d.degree[a], C = d.ncp[a], n = d.nsamp[a];
-      if (p < 1 || p > MFA_MAX_DEGREE || C < p + 1 || C > MFA_MAX_NCP || n < 2 || n > MFA_MAX_NSAMP || C > n ||
-          d.knot_off[a] < 0 || d.knot_off[a] + C + p + 1 > knots_len) {
-        delete plan;
-        return MFA_ERR_INVALID_ARG;
-      }
-      const float* t = h_knots + d.knot_off[a];
-      if (!host_knots_ok(t, p, C)) { delete plan; return MFA_ERR_INVALID_ARG; }
-      std::vector<float> key = {(float)p, (float)C, (float)n};
-      key.insert(key.end(), t, t + C + p + 1);
-      auto it = index.find(key);
-      int cls;
-      if (it == index.end()) {
-        EncClass c;
-        std::memset(&c, 0, sizeof(c));
-        c.p = p; c.C = C; c.n = n;
-        c.pinv_off = pinv_len;
-        c.tab_off = tab_len;
-        std::memcpy(c.t, t, sizeof(float) * (C + p + 1));
-        pinv_len += C * n;
-        tab_len += n;
-        cls = (int)classes.size();
-        classes.push_back(c);
-        index.emplace(key, cls);
-      } else {
-        cls = it->second;
-      }
-      items[b].cls[a] = cls;
-      ncps *= C;
-      vox *= n;
-      plan->maxC = std::max(plan->maxC, C);
-      plan->maxN = std::max(plan->maxN, n);
-    }
-    if (d.cp_off < 0 || d.cp_off + ncps > cps_len || d.slot < 0) { delete plan; return MFA_ERR_INVALID_ARG; }
-    items[b].slot = d.slot;
-    items[b].cp_off = d.cp_off;
-    plan->max_slot = std::max(plan->max_slot, d.slot);
-    plan->max_vox = std::max(plan->max_vox, vox);
-  }
   plan->ctx = ctx;
   plan->nblocks = nblocks;
-  plan->nclasses = (int)classes.size();
+  plan->nclasses = (int)an.classes.size();
+  plan->maxC = an.maxC;
+  plan->maxN = an.maxN;
+  plan->max_slot = an.max_slot;
+  plan->max_vox = an.max_vox;
   if (cudaMalloc(&plan->d_items, sizeof(EncItem) * nblocks) != cudaSuccess ||
-      cudaMalloc(&plan->d_classes, sizeof(EncClass) * classes.size()) != cudaSuccess ||
-      cudaMalloc(&plan->d_pinv, sizeof(float) * pinv_len) != cudaSuccess ||
-      cudaMalloc(&plan->d_tabs, sizeof(TabEntry) * tab_len) != cudaSuccess ||
-      cudaMemcpy(plan->d_items, items.data(), sizeof(EncItem) * nblocks, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(plan->d_classes, classes.data(), sizeof(EncClass) * classes.size(), cudaMemcpyHostToDevice) !=
+      cudaMalloc(&plan->d_classes, sizeof(EncClass) * an.classes.size()) != cudaSuccess ||
+      cudaMalloc(&plan->d_pinv, sizeof(float) * an.pinv_len) != cudaSuccess ||
+      cudaMalloc(&plan->d_tabs, sizeof(TabEntry) * an.tab_len) != cudaSuccess ||
+      cudaMemcpy(plan->d_items, an.items.data(), sizeof(EncItem) * nblocks, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(plan->d_classes, an.classes.data(), sizeof(EncClass) * an.classes.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess) {
     mfa_encode_plan_destroy(plan);
     return MFA_ERR_CUDA;
@@ -205,29 +249,10 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
   if ((reinterpret_cast<uintptr_t>(d_data) & 3) || (reinterpret_cast<uintptr_t>(d_cps_out) & 3) ||
       (reinterpret_cast<uintptr_t>(d_rmse) & 7))
     return MFA_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  encode_class_kernel<<<plan->nclasses, kThreads, 0, s>>>(plan->d_classes, plan->d_pinv, plan->d_tabs, ctx->d_status);
-  ctx->launches++;
-  if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
-  ContractParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.mode = kFit;
-  prm.nblocks = plan->nblocks;
-  prm.items = plan->d_items;
-  prm.classes = plan->d_classes;
-  prm.pinv = plan->d_pinv;
-  prm.tabs = plan->d_tabs;
-  prm.rmse = d_rmse;
-  prm.x = d_data;
-  prm.slot_stride = slot_stride_voxels;
-  prm.nslots = nslots;
-  prm.out = d_cps_out;
-  prm.status = ctx->d_status;
-  prm.counter = ctx->d_counters + kEncodeQueue;
-  prm.maxC = plan->maxC;
-  prm.maxN = plan->maxN;
-  prm.pmax = MFA_MAX_DEGREE;
-  return contract3(ctx, prm, s);
+  return run_fit(ctx, plan->nblocks, plan->nclasses, plan->maxC, plan->maxN, plan->d_items, plan->d_classes,
+                 plan->d_pinv, plan->d_tabs, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse,
+                 static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"
+
