@@ -190,6 +190,33 @@ int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
                        float* d_cps_out, double* d_rmse /* nullable, one per block */,
                        void* stream);
 
+/* Allocation-free least-squares encode. The paper has no counterpart to this entry point: it
+ * exists for callers that cannot call cudaMalloc - a process whose device memory is reserved
+ * by another runtime's memory pool, so that a fresh allocation fails or has to wait for that
+ * pool, or a per-frame loop that must not stall, which cudaMalloc and cudaFree can do because
+ * they may synchronise the device. It fits the same least-squares control points and RMSE as
+ * mfa_encode_plan_create + mfa_encode_blocks, without a context or a plan and without allocating:
+ * its scratch (status word, queue counter, class table, block items, pseudo-inverses and basis
+ * tables) lives in one fixed 2 MiB device array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   - The batch's scratch need, 256 bytes + 168 per axis class + 24 per block + 4*C*n per axis
+ *     class (pseudo-inverse) + 20*n per axis class (basis table), each part rounded up to 256
+ *     bytes, must fit the 2 MiB; a larger batch returns MFA_ERR_CAPACITY and enqueues nothing.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture on that device.
+ *   - The call copies the host descriptors into the array, enqueues the fit on `stream` and then
+ *     synchronises `stream`; it returns MFA_ERR_DEVICE if a device-side check failed (the status
+ *     word, e.g. MFA_DEV_NOT_SPD), else MFA_OK.
+ *   - Every call uses the same array; it clears the status word and counter itself. Calls whose
+ *     work overlaps on the GPU (other threads, other streams) race on the array: serialise them.
+ * Arguments as for mfa_encode_plan_create (h_desc, nblocks, h_knots, knots_len, cps_len) and
+ * mfa_encode_blocks (d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse); the current CUDA
+ * device is used. */
+int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t nblocks,
+                              const float* h_knots, int64_t knots_len,
+                              const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
+                              float* d_cps_out, int64_t cps_len, double* d_rmse, void* stream);
+
 /* ---- ray casting (Algorithm 4) -------------------------------------------------------- */
 typedef struct {
   float eye[3], target[3], up[3];

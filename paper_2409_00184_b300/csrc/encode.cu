@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -256,3 +257,88 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
 
 }  // extern "C"
 
+// ---- allocation-free encode -----------------------------------------------------------------
+// One fixed device array serves as the encode's scratch (status word, queue counter, class table,
+// block items, pseudo-inverses, basis tables) for callers that cannot allocate device memory.
+// It exists once per device that loads the library and lives until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;
+static __device__ __align__(256) unsigned char g_encode_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_encode_scratch on the current device. In host code the array's name is
+// only a host-side stand-in, so the address comes from cudaGetSymbolAddress, once per device.
+int scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return MFA_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_encode_scratch) != cudaSuccess || !p) return MFA_ERR_CUDA;
+    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return MFA_OK;
+}
+}  // namespace
+
+extern "C" int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t nblocks, const float* h_knots,
+                                         int64_t knots_len, const float* d_data, int64_t slot_stride_voxels,
+                                         int64_t nslots, float* d_cps_out, int64_t cps_len, double* d_rmse,
+                                         void* stream) {
+  if (!h_desc || !h_knots || !d_data || !d_cps_out || nblocks < 1 || knots_len < 1 || cps_len < 1)
+    return MFA_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_data) & 3) || (reinterpret_cast<uintptr_t>(d_cps_out) & 3) ||
+      (reinterpret_cast<uintptr_t>(d_rmse) & 7))
+    return MFA_ERR_INVALID_ARG;
+  if (nblocks >= (1 << 30)) return MFA_ERR_CAPACITY;
+  BatchAnalysis an;
+  int rc = analyze_batch(h_desc, nblocks, h_knots, knots_len, cps_len, an);
+  if (rc != MFA_OK) return rc;
+  if (slot_stride_voxels < an.max_vox || nslots <= an.max_slot) return MFA_ERR_INVALID_ARG;
+
+  // scratch layout: [0, 256) status word and queue counters, then the tables, 256-byte aligned
+  size_t off = 256;
+  auto take = [&off](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_cls = take(sizeof(EncClass) * an.classes.size());
+  const size_t o_items = take(sizeof(EncItem) * an.items.size());
+  const size_t o_pinv = take(sizeof(float) * an.pinv_len);
+  const size_t o_tabs = take(sizeof(TabEntry) * an.tab_len);
+  if (off > kNoAllocScratchBytes) return MFA_ERR_CAPACITY;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MFA_ERR_CUDA;
+  unsigned char* base = nullptr;
+  rc = scratch_address(dev, &base);
+  if (rc != MFA_OK) return rc;
+  mfa_ctx local;  // host-side view for the launchers; its device pointers point into the scratch
+  local.device = dev;
+  if (cudaDeviceGetAttribute(&local.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  local.d_status = reinterpret_cast<uint32_t*>(base);
+  local.d_counters = reinterpret_cast<uint32_t*>(base + 16);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: the status word and counters start at zero
+  if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + o_cls, an.classes.data(), sizeof(EncClass) * an.classes.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + o_items, an.items.data(), sizeof(EncItem) * an.items.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  rc = run_fit(&local, nblocks, (int)an.classes.size(), an.maxC, an.maxN,
+               reinterpret_cast<const EncItem*>(base + o_items), reinterpret_cast<const EncClass*>(base + o_cls),
+               reinterpret_cast<float*>(base + o_pinv), reinterpret_cast<TabEntry*>(base + o_tabs), d_data,
+               slot_stride_voxels, nslots, d_cps_out, d_rmse, s);
+  if (rc != MFA_OK) return rc;
+  uint32_t status = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpy(&status, base, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  return status ? MFA_ERR_DEVICE : MFA_OK;
+}

@@ -50,7 +50,7 @@ assert ctypes.sizeof(BlockDesc) == DESC_DTYPE.itemsize == 72
 SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
            "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
-           "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling"]
+           "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc"]
 
 
 def _load():
@@ -76,6 +76,7 @@ def _load():
         "mfa_encode_plan_create": (ctypes.c_int, [P, ctypes.POINTER(P), P, I32, P, I64, I64]),
         "mfa_encode_plan_destroy": (None, [P]),
         "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
+        "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
         "mfa_raycast": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
                                        ctypes.POINTER(View), P, I32, P, P]),
     }
@@ -266,6 +267,23 @@ def encode_blocks(ctx, plan, data, slot_stride, nslots, cps_out, rmse=None, stre
         _need(rmse, plan.nblocks, "rmse")
     _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
                                  _ptr(rmse), _stream(stream)), "mfa_encode_blocks")
+
+
+def encode_blocks_noalloc(blocks, data, slot_stride, nslots, cps_out, rmse=None, stream=None):
+    """mfa_encode_blocks_noalloc: the least-squares fit with the library's fixed device scratch (no context,
+    no plan, no device allocation); synchronises the stream before returning."""
+    _need(data, nslots * slot_stride, "data")
+    _need(cps_out, blocks.cps_len, "cps_out")
+    if rmse is not None:
+        _need(rmse, blocks.n, "rmse")
+    desc = np.ascontiguousarray(blocks.host_desc)
+    rc = lib.mfa_encode_blocks_noalloc(desc.ctypes.data_as(ctypes.c_void_p), blocks.n,
+                                       blocks.host_knots.ctypes.data_as(ctypes.c_void_p), blocks.host_knots.size,
+                                       _ptr(data), slot_stride, nslots, _ptr(cps_out), blocks.cps_len, _ptr(rmse),
+                                       _stream(stream))
+    if rc == ERR_CAPACITY:
+        raise MfaError(rc, "mfa_encode_blocks_noalloc: the batch's tables exceed the fixed 2 MiB scratch")
+    _check(rc, "mfa_encode_blocks_noalloc")
 
 
 def make_view(v):
