@@ -250,6 +250,7 @@ int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream) {
     c.maxC = prm.bounds.max_ncp;
     c.maxN = prm.bounds.max_nsamp;
     c.pmax = prm.bounds.max_degree;
+    c.rows32 = prm.bounds.max_nsamp == 32;
     const int rc = contract3(ctx, c, stream);
     if (rc != MFA_ERR_CAPACITY) return rc;
   }

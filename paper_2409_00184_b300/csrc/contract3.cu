@@ -2,32 +2,47 @@
 // the adjoint:
 //     Y[c][b][a] = sum_{k,j,i} X[k][j][i] Ax[i][a] Ay[j][b] Az[k][c]
 //   kFit:      A = (N^T N)^{-1} N^T per axis (from the encode plan) -> least-squares control points,
-//              then optionally the FP64 RMSE of the fitted model over the samples (Table 1's metric);
+//              then optionally the RMSE of the fitted model over the samples (Table 1's metric);
 //   kAdjoint:  A = N (collocation matrix, built from the knots in the CTA) -> N^T R;
 //   kGradient: G = (M_x (x) M_y (x) M_z) P - N^T D with M = N^T N, the gradient of
 //              0.5*||decode(P) - D||^2 (= N^T (N P - D)) without a forward decode of the samples.
-// One CTA per block, persistent queue. The grid streams through in z-slabs of ks planes:
+// One CTA per block; the grid streams through in z-slabs of ks planes:
 //   x:  Y1[(k,j)][a] = sum_i X[k][j][i] Ax[i][a]   thread per sample row, all columns in registers,
-//                                                  the row read with 16-byte loads, Ax rows broadcast
+//                                                  Ax rows broadcast from shared memory
 //   y:  Y2[k][b][a]  = sum_j Y1[(k,j)][a] Ay[j][b]  4 columns b per thread
 //   z:  Y[c][b][a]  += sum_k Y2[k][b][a] Az[k][c]   4 columns c per thread
+// Two kernels share these stages. The TMA kernel (rows of 32 samples) loads each slab with one
+// cp.async.bulk.tensor into a 128-byte-swizzled shared buffer, double-buffered on mbarriers, and
+// prefetches the next (block, slab) of its static schedule while it computes the current one; the
+// swizzle makes the thread-per-row 16-byte reads bank-conflict-free. The queue kernel (any row
+// length) reads rows from global memory with 16-byte loads and takes blocks from an atomic queue.
 #include <algorithm>
+#include <cstring>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace mfa {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kTmaRow = 32;  // samples per row on the TMA path (128 bytes)
 
 struct C3Smem {
-  int A[3], M[3], tab[3], knots, Y1, Y2, Y, P, Z, total;  // offsets in 4-byte words
+  int A[3], M[3], tab[3], knots, Y1, Y2, Y, P, Z, X, total;  // offsets in 4-byte words
+};
+
+struct C3Geom {
+  int p[3], C[3], n[3], cls[3];
+  int slot, valid, bad;
+  int64_t cpoff, koff[3];
 };
 
 int round4(int v) { return (v + 3) & ~3; }
 
-C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse) {
+C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xbuf_words) {
   const int CPs = (CP % 8 == 0) ? CP + 4 : CP;
   C3Smem L;
   int o = 0;
@@ -41,320 +56,598 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse) {
   L.Y = o;  o += round4(maxC * maxC * maxC);
   L.P = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
   L.Z = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
+  L.X = o;  if (xbuf_words) o += 256 + 2 * xbuf_words;  // two slab buffers + slack for 1024-byte alignment
   L.total = o;
   return L;
 }
 
+// Geometry of block `item` (one thread): from the plan's items/classes (kFit) or a checked descriptor.
+__device__ void c3_fetch(const ContractParams& prm, int item, C3Geom& g) {
+  g.valid = item < prm.nblocks;
+  g.bad = 0;
+  if (!g.valid) return;
+  if (prm.mode == kFit) {
+    const EncItem it = prm.items[item];
+    for (int a = 0; a < 3; ++a) {
+      const EncClass& c = prm.classes[it.cls[a]];
+      g.p[a] = c.p; g.C[a] = c.C; g.n[a] = c.n; g.cls[a] = it.cls[a];
+    }
+    g.slot = it.slot;
+    g.cpoff = it.cp_off;
+  } else {
+    BlockGeom bg;
+    const uint32_t bad = load_desc(prm.desc + item, prm.bounds, prm.knots_len, prm.cps_len, prm.nslots,
+                                   prm.slot_stride, bg);
+    if (bad) {
+      flag(prm.status, bad);
+      g.bad = 1;
+      return;
+    }
+    for (int a = 0; a < 3; ++a) { g.p[a] = bg.p[a]; g.C[a] = bg.C[a]; g.n[a] = bg.n[a]; g.koff[a] = bg.knot_off[a]; }
+    g.slot = bg.slot;
+    g.cpoff = bg.cp_off;
+  }
+}
+
+// Builds the three n x CP matrices (zero-padded columns), the RMSE tables (kFit), M = N^T N and P
+// (kGradient), zeroes Y. Ends with a barrier; sets *s_bad when a knot vector is invalid.
 template <int CP>
-__global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm, C3Smem L, int ks, int vec_ok) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ int s_item, s_bad, s_slot;
-  __shared__ int s_p[3], s_C[3], s_n[3], s_cls[3];
-  __shared__ int64_t s_cpoff, s_koff[3];
-  __shared__ double s_red[kThreads / 32];
-  constexpr int CPs = (CP % 8 == 0) ? CP + 4 : CP;
-  constexpr int Q4 = CP / 4;
-  const int tid = threadIdx.x;
-  const int mode = prm.mode;
-
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) {
-      s_item = atomicAdd(prm.counter, 1u);
-      s_bad = 0;
-      if (s_item < prm.nblocks) {
-        if (mode == kFit) {
-          const EncItem it = prm.items[s_item];
-          for (int a = 0; a < 3; ++a) {
-            const EncClass& c = prm.classes[it.cls[a]];
-            s_p[a] = c.p; s_C[a] = c.C; s_n[a] = c.n; s_cls[a] = it.cls[a];
-          }
-          s_slot = it.slot;
-          s_cpoff = it.cp_off;
-        } else {
-          BlockGeom g;
-          const uint32_t bad = load_desc(prm.desc + s_item, prm.bounds, prm.knots_len, prm.cps_len, prm.nslots,
-                                         prm.slot_stride, g);
-          if (bad) {
-            flag(prm.status, bad);
-            s_bad = 1;
-          } else {
-            for (int a = 0; a < 3; ++a) { s_p[a] = g.p[a]; s_C[a] = g.C[a]; s_n[a] = g.n[a]; s_koff[a] = g.knot_off[a]; }
-            s_slot = g.slot;
-            s_cpoff = g.cp_off;
-          }
-        }
+__device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int* s_bad) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int ncps = g.C[0] * g.C[1] * g.C[2];
+  if (prm.mode == kFit) {
+    for (int a = 0; a < 3; ++a) {
+      const EncClass& c = prm.classes[g.cls[a]];
+      float* A = sm + L.A[a];
+      for (int e = tid; e < c.n * CP; e += nthr) {
+        const int i = e / CP, col = e - i * CP;
+        A[e] = col < c.C ? prm.pinv[c.pinv_off + i * c.C + col] : 0.f;
       }
+      if (prm.rmse) {
+        TabEntry* tb = reinterpret_cast<TabEntry*>(sm + L.tab[a]);
+        for (int e = tid; e < c.n; e += nthr) tb[e] = prm.tabs[c.tab_off + e];
+      }
+    }
+  } else {
+    float* kn = sm + L.knots;
+    for (int a = 0; a < 3; ++a) {
+      for (int i = tid; i < g.C[a] + g.p[a] + 1; i += nthr) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
+      for (int e = tid; e < g.n[a] * CP; e += nthr) sm[L.A[a] + e] = 0.f;
     }
     __syncthreads();
-    if (s_item >= prm.nblocks) break;
-    if (s_bad) continue;
-    const int Cx = s_C[0], Cy = s_C[1], Cz = s_C[2];
-    const int nx = s_n[0], ny = s_n[1], nz = s_n[2];
-    const int plane = Cx * Cy, ncps = plane * Cz;
-    const int64_t cp_off = s_cpoff;
-    const float* X = prm.x + (int64_t)s_slot * prm.slot_stride;
-    float* Ax = sm + L.A[0];
-    float* Ay = sm + L.A[1];
-    float* Az = sm + L.A[2];
-
-    // ---- set-up: the three n x CP matrices (zero-padded columns) ----
-    if (mode == kFit) {
-      for (int a = 0; a < 3; ++a) {
-        const EncClass& c = prm.classes[s_cls[a]];
-        float* A = sm + L.A[a];
-        for (int e = tid; e < c.n * CP; e += blockDim.x) {
-          const int i = e / CP, col = e - i * CP;
-          A[e] = col < c.C ? prm.pinv[c.pinv_off + i * c.C + col] : 0.f;
-        }
-        if (prm.rmse) {
-          TabEntry* tb = reinterpret_cast<TabEntry*>(sm + L.tab[a]);
-          for (int e = tid; e < c.n; e += blockDim.x) tb[e] = prm.tabs[c.tab_off + e];
-        }
-      }
-    } else {
-      float* kn = sm + L.knots;
-      for (int a = 0; a < 3; ++a) {
-        for (int i = tid; i < s_C[a] + s_p[a] + 1; i += blockDim.x) kn[a * kKnotMax + i] = prm.knots[s_koff[a] + i];
-        for (int e = tid; e < s_n[a] * CP; e += blockDim.x) sm[L.A[a] + e] = 0.f;
-      }
-      __syncthreads();
-      if (tid < 3 && !knots_ok(kn + tid * kKnotMax, s_p[tid], s_C[tid])) {
-        atomicOr(&s_bad, 1);
-        flag(prm.status, MFA_DEV_BAD_KNOTS);
-      }
-      const int a = tid < nx ? 0 : (tid < nx + ny ? 1 : (tid < nx + ny + nz ? 2 : -1));
-      if (a >= 0) {
-        const int i = a == 0 ? tid : (a == 1 ? tid - nx : tid - nx - ny);
-        const float* t = kn + a * kKnotMax;
-        const float u = sample_param(i, s_n[a]);
-        const int s = find_span(t, s_p[a], s_C[a], u);
-        float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
-        basis_funs<MFA_MAX_DEGREE>(t, s_p[a], s, u, N, dN);
-        for (int r = 0; r <= s_p[a]; ++r) sm[L.A[a] + i * CP + s - s_p[a] + r] = N[r];
-      }
+    if (tid < 3 && !knots_ok(kn + tid * kKnotMax, g.p[tid], g.C[tid])) {
+      atomicOr(s_bad, 1);
+      flag(prm.status, MFA_DEV_BAD_KNOTS);
     }
-    __syncthreads();
-    if (s_bad) continue;
-    if (mode == kGradient) {
-      for (int a = 0; a < 3; ++a) {  // M = N^T N
-        const float* A = sm + L.A[a];
-        float* M = sm + L.M[a];
-        const int C = s_C[a], n = s_n[a];
-        for (int e = tid; e < C * C; e += blockDim.x) {
-          const int r = e / C, c = e - r * C;
-          float acc = 0.f;
-          for (int i = 0; i < n; ++i) acc = fmaf(A[i * CP + r], A[i * CP + c], acc);
-          M[e] = acc;
-        }
-      }
-      for (int e = tid; e < ncps; e += blockDim.x) sm[L.P + e] = prm.cps[cp_off + e];
+    const int a = tid < nx ? 0 : (tid < nx + ny ? 1 : (tid < nx + ny + nz ? 2 : -1));
+    if (a >= 0) {
+      const int i = a == 0 ? tid : (a == 1 ? tid - nx : tid - nx - ny);
+      const float* t = kn + a * kKnotMax;
+      const float u = sample_param(i, g.n[a]);
+      const int s = find_span(t, g.p[a], g.C[a], u);
+      float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
+      basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, u, N, dN);
+      for (int r = 0; r <= g.p[a]; ++r) sm[L.A[a] + i * CP + s - g.p[a] + r] = N[r];
     }
-    float* Y = sm + L.Y;
-    for (int e = tid; e < ncps; e += blockDim.x) Y[e] = 0.f;
-
-    const bool vec = vec_ok && (nx % 4 == 0);
-    float* Y1 = sm + L.Y1;
-    float* Y2 = sm + L.Y2;
-    for (int k0 = 0; k0 < nz; k0 += ks) {
-      const int kc = min(ks, nz - k0);
-      const int rows = kc * ny;
-      // x: one sample row per thread, all CP columns in registers
-      for (int r = tid; r < rows; r += blockDim.x) {
-        const float* xr = X + ((int64_t)k0 * ny + r) * nx;
-        float acc[CP];
-#pragma unroll
-        for (int c = 0; c < CP; ++c) acc[c] = 0.f;
-        if (vec) {
-          for (int i = 0; i < nx; i += 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(xr + i));
-            const float xs[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4* ar = reinterpret_cast<const float4*>(Ax + (i + q) * CP);
-#pragma unroll
-              for (int c4 = 0; c4 < Q4; ++c4) {
-                const float4 w = ar[c4];
-                acc[4 * c4 + 0] = fmaf(xs[q], w.x, acc[4 * c4 + 0]);
-                acc[4 * c4 + 1] = fmaf(xs[q], w.y, acc[4 * c4 + 1]);
-                acc[4 * c4 + 2] = fmaf(xs[q], w.z, acc[4 * c4 + 2]);
-                acc[4 * c4 + 3] = fmaf(xs[q], w.w, acc[4 * c4 + 3]);
-              }
-            }
-          }
-        } else {
-          for (int i = 0; i < nx; ++i) {
-            const float xv = __ldg(xr + i);
-            const float4* ar = reinterpret_cast<const float4*>(Ax + i * CP);
-#pragma unroll
-            for (int c4 = 0; c4 < Q4; ++c4) {
-              const float4 w = ar[c4];
-              acc[4 * c4 + 0] = fmaf(xv, w.x, acc[4 * c4 + 0]);
-              acc[4 * c4 + 1] = fmaf(xv, w.y, acc[4 * c4 + 1]);
-              acc[4 * c4 + 2] = fmaf(xv, w.z, acc[4 * c4 + 2]);
-              acc[4 * c4 + 3] = fmaf(xv, w.w, acc[4 * c4 + 3]);
-            }
-          }
-        }
-        float4* yr = reinterpret_cast<float4*>(Y1 + r * CPs);
-#pragma unroll
-        for (int c4 = 0; c4 < Q4; ++c4)
-          yr[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
-      }
-      __syncthreads();
-      // y: Y2[kl][b][a] = sum_j Y1[(kl, j)][a] Ay[j][b], 4 values of b per thread
-      {
-        const int nb4 = (Cy + 3) / 4;
-        for (int e = tid; e < kc * nb4 * Cx; e += blockDim.x) {
-          const int a = e % Cx, t = e / Cx, b4 = t % nb4, kl = t / nb4;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float* y1 = Y1 + kl * ny * CPs + a;
-          for (int j = 0; j < ny; ++j) {
-            const float yv = y1[j * CPs];
-            const float4 w = *reinterpret_cast<const float4*>(Ay + j * CP + 4 * b4);
-            acc.x = fmaf(yv, w.x, acc.x);
-            acc.y = fmaf(yv, w.y, acc.y);
-            acc.z = fmaf(yv, w.z, acc.z);
-            acc.w = fmaf(yv, w.w, acc.w);
-          }
-          const float av[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int bb = 4 * b4 + q;
-            if (bb < Cy) Y2[(kl * Cy + bb) * Cx + a] = av[q];
-          }
-        }
-      }
-      __syncthreads();
-      // z: Y[c][b][a] += sum_kl Y2[kl][b][a] Az[k0 + kl][c], 4 values of c per thread
-      {
-        const int nc4 = (Cz + 3) / 4;
-        for (int e = tid; e < nc4 * plane; e += blockDim.x) {
-          const int ab = e % plane, c4 = e / plane;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int kl = 0; kl < kc; ++kl) {
-            const float yv = Y2[kl * plane + ab];
-            const float4 w = *reinterpret_cast<const float4*>(Az + (k0 + kl) * CP + 4 * c4);
-            acc.x = fmaf(yv, w.x, acc.x);
-            acc.y = fmaf(yv, w.y, acc.y);
-            acc.z = fmaf(yv, w.z, acc.z);
-            acc.w = fmaf(yv, w.w, acc.w);
-          }
-          const float av[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int c = 4 * c4 + q;
-            if (c < Cz) Y[c * plane + ab] += av[q];
-          }
-        }
-      }
-      __syncthreads();
-    }
-
-    // ---- epilogues ----
-    if (mode == kAdjoint) {
-      for (int e = tid; e < ncps; e += blockDim.x) prm.out[cp_off + e] = Y[e];
-      continue;
-    }
-    if (mode == kGradient) {
-      float* P = sm + L.P;
-      float* Z = sm + L.Z;
-      const float* Mx = sm + L.M[0];
-      const float* My = sm + L.M[1];
-      const float* Mz = sm + L.M[2];
-      for (int e = tid; e < ncps; e += blockDim.x) {  // Z = P x_1 M_x
-        const int a = e % Cx, cb = e / Cx;
+  }
+  __syncthreads();
+  if (prm.mode == kGradient) {
+    for (int a = 0; a < 3; ++a) {  // M = N^T N
+      const float* A = sm + L.A[a];
+      float* M = sm + L.M[a];
+      const int C = g.C[a], n = g.n[a];
+      for (int e = tid; e < C * C; e += nthr) {
+        const int r = e / C, c = e - r * C;
         float acc = 0.f;
-        for (int q = 0; q < Cx; ++q) acc = fmaf(P[cb * Cx + q], Mx[q * Cx + a], acc);
-        Z[e] = acc;
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) acc = fmaf(A[i * CP + r], A[i * CP + c], acc);
+        M[e] = acc;
       }
-      __syncthreads();
-      for (int e = tid; e < ncps; e += blockDim.x) {  // P <- Z x_2 M_y
-        const int a = e % Cx, bb = (e / Cx) % Cy, c = e / plane;
-        float acc = 0.f;
-        for (int q = 0; q < Cy; ++q) acc = fmaf(Z[(c * Cy + q) * Cx + a], My[q * Cy + bb], acc);
-        P[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < ncps; e += blockDim.x) {  // G = P x_3 M_z - N^T D
-        const int ab = e % plane, c = e / plane;
-        float acc = 0.f;
-        for (int q = 0; q < Cz; ++q) acc = fmaf(P[q * plane + ab], Mz[q * Cz + c], acc);
-        prm.out[cp_off + e] = acc - Y[e];
-      }
-      continue;
     }
-    // kFit
-    for (int e = tid; e < ncps; e += blockDim.x) prm.out[cp_off + e] = Y[e];
-    if (!prm.rmse) continue;
-    // RMSE: banded value decode of the fitted model against the samples. Each thread sums its
-    // squared errors in FP32 with Kahan compensation; the per-thread sums are reduced in FP64
-    // (FP64 per voxel would run at the low FP64 rate of this GPU).
-    {
-      const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
-      const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
-      const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
-      const int pxx = s_p[0], pyy = s_p[1], pzz = s_p[2];
-      float ksum = 0.f, kcomp = 0.f;
-      for (int k0 = 0; k0 < nz; k0 += ks) {
-        const int kc = min(ks, nz - k0);
-        for (int e = tid; e < plane * kc; e += blockDim.x) {  // T0 -> Y2
-          const int kl = e / plane, ab = e - kl * plane;
-          const TabEntry te = tz[k0 + kl];
-          float acc = 0.f;
-          for (int d = 0; d <= pzz; ++d) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
-          Y2[e] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < Cx * ny * kc; e += blockDim.x) {  // U0 -> Y1
-          const int a = e % Cx, r = e / Cx, j = r % ny, kl = r / ny;
-          const TabEntry te = ty[j];
-          float acc = 0.f;
-          for (int d = 0; d <= pyy; ++d) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
-          Y1[e] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < nx * ny * kc; e += blockDim.x) {
-          const int i = e % nx, r = e / nx;
-          const TabEntry te = tx[i];
-          float f = 0.f;
-          for (int d = 0; d <= pxx; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
-          const float diff = f - X[(int64_t)k0 * nx * ny + e];
-          const float y = diff * diff - kcomp;
-          const float t = ksum + y;
-          kcomp = (t - ksum) - y;
-          ksum = t;
-        }
-        __syncthreads();
-      }
-      double sq = (double)ksum - (double)kcomp;
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if ((tid & 31) == 0) s_red[tid >> 5] = sq;
-      __syncthreads();
-      if (tid == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += s_red[w];
-        prm.rmse[s_item] = sqrt(tot / ((double)nx * ny * nz));
-      }
+    for (int e = tid; e < ncps; e += nthr) sm[L.P + e] = prm.cps[g.cpoff + e];
+  }
+  for (int e = tid; e < ncps; e += nthr) sm[L.Y + e] = 0.f;
+  __syncthreads();
+}
+
+template <int CP>
+__device__ __forceinline__ void fma_row4(float (&acc)[CP], const float* Ax, int i, const float4 v) {
+  const float xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4* ar = reinterpret_cast<const float4*>(Ax + (i + q) * CP);
+#pragma unroll
+    for (int c4 = 0; c4 < CP / 4; ++c4) {
+      const float4 w = ar[c4];
+      acc[4 * c4 + 0] = fmaf(xs[q], w.x, acc[4 * c4 + 0]);
+      acc[4 * c4 + 1] = fmaf(xs[q], w.y, acc[4 * c4 + 1]);
+      acc[4 * c4 + 2] = fmaf(xs[q], w.z, acc[4 * c4 + 2]);
+      acc[4 * c4 + 3] = fmaf(xs[q], w.w, acc[4 * c4 + 3]);
     }
   }
 }
 
 template <int CP>
+__device__ __forceinline__ void store_row(float* Y1, int r, const float (&acc)[CP]) {
+  constexpr int CPs = (CP % 8 == 0) ? CP + 4 : CP;
+  float4* yr = reinterpret_cast<float4*>(Y1 + r * CPs);
+#pragma unroll
+  for (int c4 = 0; c4 < CP / 4; ++c4)
+    yr[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
+}
+
+// Stage x from global memory (any row length; 16-byte loads when rows allow).
+template <int CP>
+__device__ void c3_stage_x_global(const float* X, const float* Ax, float* Y1, int k0, int kc, int nx, int ny,
+                                  bool vec) {
+  const int rows = kc * ny;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const float* xr = X + ((int64_t)k0 * ny + r) * nx;
+    float acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+    if (vec) {
+      for (int i = 0; i < nx; i += 4) fma_row4<CP>(acc, Ax, i, __ldg(reinterpret_cast<const float4*>(xr + i)));
+    } else {
+      for (int i = 0; i < nx; ++i) {
+        const float xv = __ldg(xr + i);
+        const float4* ar = reinterpret_cast<const float4*>(Ax + i * CP);
+#pragma unroll
+        for (int c4 = 0; c4 < CP / 4; ++c4) {
+          const float4 w = ar[c4];
+          acc[4 * c4 + 0] = fmaf(xv, w.x, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(xv, w.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(xv, w.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(xv, w.w, acc[4 * c4 + 3]);
+        }
+      }
+    }
+    store_row<CP>(Y1, r, acc);
+  }
+}
+
+// Stage x from a 128-byte-swizzled shared slab of 32-sample rows: logical 16-byte chunk c of row r
+// sits at chunk c ^ (r & 7).
+template <int CP>
+__device__ void c3_stage_x_smem(const float4* xb, const float* Ax, float* Y1, int rows) {
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    float acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+    const float4* row = xb + r * 8;
+    const int sw = r & 7;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) fma_row4<CP>(acc, Ax, 4 * c, row[c ^ sw]);
+    store_row<CP>(Y1, r, acc);
+  }
+}
+
+template <int CP>
+__device__ void c3_stage_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0, int kc) {
+  constexpr int CPs = (CP % 8 == 0) ? CP + 4 : CP;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Cx = g.C[0], Cy = g.C[1], Cz = g.C[2], ny = g.n[1];
+  const int plane = Cx * Cy;
+  const float* Y1 = sm + L.Y1;
+  float* Y2 = sm + L.Y2;
+  float* Y = sm + L.Y;
+  const float* Ay = sm + L.A[1];
+  const float* Az = sm + L.A[2];
+  // y: Y2[kl][b][a] = sum_j Y1[(kl, j)][a] Ay[j][b], 4 values of b per thread
+  const int nb4 = (Cy + 3) / 4;
+  for (int e = tid; e < kc * nb4 * Cx; e += nthr) {
+    const int a = e % Cx, t = e / Cx, b4 = t % nb4, kl = t / nb4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* y1 = Y1 + kl * ny * CPs + a;
+#pragma unroll 4
+    for (int j = 0; j < ny; ++j) {
+      const float yv = y1[j * CPs];
+      const float4 w = *reinterpret_cast<const float4*>(Ay + j * CP + 4 * b4);
+      acc.x = fmaf(yv, w.x, acc.x);
+      acc.y = fmaf(yv, w.y, acc.y);
+      acc.z = fmaf(yv, w.z, acc.z);
+      acc.w = fmaf(yv, w.w, acc.w);
+    }
+    const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int bb = 4 * b4 + q;
+      if (bb < Cy) Y2[(kl * Cy + bb) * Cx + a] = av[q];
+    }
+  }
+  __syncthreads();
+  // z: Y[c][b][a] += sum_kl Y2[kl][b][a] Az[k0 + kl][c], 4 values of c per thread
+  const int nc4 = (Cz + 3) / 4;
+  for (int e = tid; e < nc4 * plane; e += nthr) {
+    const int ab = e % plane, c4 = e / plane;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+    for (int kl = 0; kl < kc; ++kl) {
+      const float yv = Y2[kl * plane + ab];
+      const float4 w = *reinterpret_cast<const float4*>(Az + (k0 + kl) * CP + 4 * c4);
+      acc.x = fmaf(yv, w.x, acc.x);
+      acc.y = fmaf(yv, w.y, acc.y);
+      acc.z = fmaf(yv, w.z, acc.z);
+      acc.w = fmaf(yv, w.w, acc.w);
+    }
+    const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 4 * c4 + q;
+      if (c < Cz) Y[c * plane + ab] += av[q];
+    }
+  }
+  __syncthreads();
+}
+
+// Writes the block's result: Y (fit, adjoint) or M P - Y (gradient); for the fit also the RMSE of
+// the fitted model (banded value decode vs the samples; per-thread FP32 Kahan sums reduced in FP64).
+template <int CP>
+__device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int item,
+                            const float* X, int ks, double* s_red) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Cx = g.C[0], Cy = g.C[1], Cz = g.C[2];
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int plane = Cx * Cy, ncps = plane * Cz;
+  const float* Y = sm + L.Y;
+  if (prm.mode == kAdjoint) {
+    for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
+    return;
+  }
+  if (prm.mode == kGradient) {
+    // M = N^T N is banded: N_a and N_q overlap only when |a - q| <= p
+    float* P = sm + L.P;
+    float* Z = sm + L.Z;
+    const float* Mx = sm + L.M[0];
+    const float* My = sm + L.M[1];
+    const float* Mz = sm + L.M[2];
+    const int px = g.p[0], py = g.p[1], pz = g.p[2];
+    for (int e = tid; e < ncps; e += nthr) {  // Z = P x_1 M_x
+      const int a = e % Cx, cb = e / Cx;
+      float acc = 0.f;
+      for (int q = max(0, a - px); q <= min(Cx - 1, a + px); ++q) acc = fmaf(P[cb * Cx + q], Mx[q * Cx + a], acc);
+      Z[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ncps; e += nthr) {  // P <- Z x_2 M_y
+      const int a = e % Cx, bb = (e / Cx) % Cy, c = e / plane;
+      float acc = 0.f;
+      for (int q = max(0, bb - py); q <= min(Cy - 1, bb + py); ++q)
+        acc = fmaf(Z[(c * Cy + q) * Cx + a], My[q * Cy + bb], acc);
+      P[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ncps; e += nthr) {  // G = P x_3 M_z - N^T D
+      const int ab = e % plane, c = e / plane;
+      float acc = 0.f;
+      for (int q = max(0, c - pz); q <= min(Cz - 1, c + pz); ++q) acc = fmaf(P[q * plane + ab], Mz[q * Cz + c], acc);
+      prm.out[g.cpoff + e] = acc - Y[e];
+    }
+    return;
+  }
+  for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
+  if (!prm.rmse) return;
+  const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
+  const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
+  const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
+  float* Y1 = sm + L.Y1;
+  float* Y2 = sm + L.Y2;
+  float ksum = 0.f, kcomp = 0.f;
+  for (int k0 = 0; k0 < nz; k0 += ks) {
+    const int kc = min(ks, nz - k0);
+    for (int e = tid; e < plane * kc; e += nthr) {  // T0 -> Y2
+      const int kl = e / plane, ab = e - kl * plane;
+      const TabEntry te = tz[k0 + kl];
+      float acc = 0.f;
+      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
+      Y2[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < Cx * ny * kc; e += nthr) {  // U0 -> Y1
+      const int a = e % Cx, r = e / Cx, j = r % ny, kl = r / ny;
+      const TabEntry te = ty[j];
+      float acc = 0.f;
+      for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
+      Y1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < nx * ny * kc; e += nthr) {
+      const int i = e % nx, r = e / nx;
+      const TabEntry te = tx[i];
+      float f = 0.f;
+      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
+      const float diff = f - __ldg(X + (int64_t)k0 * nx * ny + e);
+      const float y = diff * diff - kcomp;
+      const float t = ksum + y;
+      kcomp = (t - ksum) - y;
+      ksum = t;
+    }
+    __syncthreads();
+  }
+  double sq = (double)ksum - (double)kcomp;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((tid & 31) == 0) s_red[tid >> 5] = sq;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(nthr / 32); ++w) tot += s_red[w];
+    prm.rmse[item] = sqrt(tot / ((double)nx * ny * nz));
+  }
+}
+
+// RMSE contribution of one z-slab on the TMA path: banded value decode of the fitted model Y
+// (stage z -> Y2, stage y -> Y1, stage x) compared with the slab's samples in the swizzled buffer.
+// Squared errors go into a per-thread FP32 Kahan sum.
+__device__ void c3_rmse_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, const float4* xb, int k0, int kc,
+                                  float& ksum, float& kcomp) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Cx = g.C[0], Cy = g.C[1], ny = g.n[1];
+  const int plane = Cx * Cy;
+  const float* Y = sm + L.Y;
+  float* Y1 = sm + L.Y1;
+  float* Y2 = sm + L.Y2;
+  const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
+  const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
+  const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
+  {  // stage z: Y2[kl][ab]
+    int kl = tid / plane, ab = tid - (tid / plane) * plane;
+    for (int e = tid; e < plane * kc; e += nthr) {
+      const TabEntry te = tz[k0 + kl];
+      float acc = 0.f;
+      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
+      Y2[e] = acc;
+      ab += nthr;
+      while (ab >= plane) { ab -= plane; ++kl; }
+    }
+  }
+  __syncthreads();
+  {  // stage y: Y1[(kl, j)][a], thread keeps column a
+    const int step = nthr / Cx, gq = tid / Cx;
+    if (gq < step) {
+      const int a = tid - gq * Cx;
+      int kl = gq / ny, j = gq - (gq / ny) * ny;
+      for (int r = gq; r < kc * ny; r += step) {
+        const TabEntry te = ty[j];
+        float acc = 0.f;
+        for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
+        Y1[r * Cx + a] = acc;
+        j += step;
+        while (j >= ny) { j -= ny; ++kl; }
+      }
+    }
+  }
+  __syncthreads();
+  {  // stage x: thread keeps sample i (32-sample rows), compares with the swizzled samples
+    const int i = tid & 31, r0 = tid >> 5, rstep = nthr >> 5;
+    const TabEntry te = tx[i];
+    for (int r = r0; r < kc * ny; r += rstep) {
+      float f = 0.f;
+      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
+      const float4 c4 = xb[r * 8 + ((i >> 2) ^ (r & 7))];
+      const float dv = (i & 3) == 0 ? c4.x : ((i & 3) == 1 ? c4.y : ((i & 3) == 2 ? c4.z : c4.w));
+      const float diff = f - dv;
+      const float y = diff * diff - kcomp;
+      const float t = ksum + y;
+      kcomp = (t - ksum) - y;
+      ksum = t;
+    }
+  }
+  __syncthreads();
+}
+
+// Queue kernel: blocks from an atomic counter, rows read from global memory.
+template <int CP>
+__global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm, C3Smem L, int ks, int vec_ok) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_item, s_bad;
+  __shared__ C3Geom s_g;
+  __shared__ double s_red[kThreads / 32];
+  const int tid = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s_item = atomicAdd(prm.counter, 1u);
+      s_bad = 0;
+      c3_fetch(prm, s_item, s_g);
+    }
+    __syncthreads();
+    if (!s_g.valid) break;
+    if (s_g.bad) continue;
+    const C3Geom& g = s_g;
+    c3_setup<CP>(prm, L, sm, g, &s_bad);
+    if (s_bad) continue;
+    const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
+    const bool vec = vec_ok && (g.n[0] % 4 == 0);
+    for (int k0 = 0; k0 < g.n[2]; k0 += ks) {
+      const int kc = min(ks, g.n[2] - k0);
+      c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1], vec);
+      __syncthreads();
+      c3_stage_yz<CP>(L, sm, g, k0, kc);
+    }
+    c3_epilogue<CP>(prm, L, sm, g, s_item, X, ks, s_red);
+  }
+}
+
+// TMA kernel: static schedule (blocks blockIdx.x, +gridDim.x, ...), slab loads double-buffered.
+template <int CP>
+__global__ void __launch_bounds__(kThreads)
+contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const __grid_constant__ CUtensorMap xmap) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ C3Geom s_g[2];
+  __shared__ int s_bad;
+  __shared__ double s_red[kThreads / 32];
+  const int tid = threadIdx.x;
+  float4* xbuf = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(sm + L.X) + 1023) & ~uintptr_t(1023));
+  const int buf_f4 = box_rows * (kTmaRow / 4);
+  const uint32_t box_bytes = (uint32_t)box_rows * kTmaRow * 4;
+  const int64_t rows_per_slot = prm.slot_stride / kTmaRow;
+
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+    c3_fetch(prm, blockIdx.x, s_g[0]);
+  }
+  __syncthreads();
+
+  uint32_t q_issue = 0, q_cons = 0;  // slabs issued / consumed by this CTA (same in every thread)
+  int cur = 0;
+  int item = blockIdx.x;
+  auto tma_ok = [&](const C3Geom& g) {
+    return g.valid && !g.bad && g.n[0] == kTmaRow && (int64_t)ks * g.n[1] <= box_rows;
+  };
+  auto issue = [&](const C3Geom& g, int k0) {  // one thread
+    const int b = q_issue & 1;
+    mbar_arrive_expect_tx(&s_bar[b], box_bytes);
+    const int64_t row = (int64_t)g.slot * rows_per_slot + (int64_t)k0 * g.n[1];
+    tma_load_2d(xbuf + b * buf_f4, &xmap, &s_bar[b], 0, (int)row);
+  };
+  if (tma_ok(s_g[0])) {
+    if (tid == 0) issue(s_g[0], 0);
+    ++q_issue;
+  }
+
+  while (s_g[cur].valid) {
+    const int nitem = item + gridDim.x;
+    if (tid == 0) {
+      s_bad = 0;
+      c3_fetch(prm, nitem, s_g[cur ^ 1]);
+    }
+    __syncthreads();
+    const C3Geom& g = s_g[cur];
+    const C3Geom& gn = s_g[cur ^ 1];
+    const bool use_tma = tma_ok(g);
+    if (!g.bad) c3_setup<CP>(prm, L, sm, g, &s_bad);
+    const bool skip = g.bad || s_bad;
+    const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
+    const int nz = g.valid && !g.bad ? g.n[2] : 0;
+    const int nslab = (nz + ks - 1) / ks;
+    // units of this block: the contraction's slabs, then (fit with RMSE, TMA rows) the residual slabs
+    const bool rmse_pass = prm.mode == kFit && prm.rmse && use_tma;
+    const int nunits = nslab * (rmse_pass ? 2 : 1);
+    float ksum = 0.f, kcomp = 0.f;
+    for (int u = 0; u < nunits; ++u) {
+      const int pass = u >= nslab, s = pass ? u - nslab : u;
+      const int k0 = s * ks, kc = min(ks, nz - k0);
+      // prefetch the next unit of the schedule into the other buffer
+      if (u + 1 < nunits) {
+        if (use_tma) {
+          if (tid == 0) issue(g, ((u + 1) % nslab) * ks);
+          ++q_issue;
+        }
+      } else if (tma_ok(gn)) {
+        if (tid == 0) issue(gn, 0);
+        ++q_issue;
+      }
+      if (use_tma) {
+        const int b = q_cons & 1;
+        const bool ok = mbar_wait_bounded(&s_bar[b], (q_cons >> 1) & 1);
+        ++q_cons;
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) {
+            flag(prm.status, MFA_DEV_TIMEOUT);
+            for (uint32_t q = q_cons; q < q_issue; ++q) mbar_wait_bounded(&s_bar[q & 1], (q >> 1) & 1);
+          }
+          __syncthreads();
+          return;
+        }
+        if (!skip) {
+          if (pass == 0) c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
+          else c3_rmse_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, ksum, kcomp);
+        }
+      } else if (!skip) {
+        c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
+                              (g.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) &&
+                                  (prm.slot_stride % 4 == 0));
+      }
+      __syncthreads();
+      if (!skip && pass == 0) c3_stage_yz<CP>(L, sm, g, k0, kc);
+    }
+    if (nslab == 0 && tma_ok(gn)) {  // no slab of this block carried the next block's prefetch
+      if (tid == 0) issue(gn, 0);
+      ++q_issue;
+    }
+    if (!skip && nslab > 0) {
+      if (rmse_pass) {
+        const int ncps = g.C[0] * g.C[1] * g.C[2];
+        for (int e = tid; e < ncps; e += blockDim.x) prm.out[g.cpoff + e] = sm[L.Y + e];
+        double sq = (double)ksum - (double)kcomp;
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+          double tot = 0.0;
+          for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += s_red[w];
+          prm.rmse[item] = sqrt(tot / ((double)g.n[0] * g.n[1] * g.n[2]));
+        }
+      } else {
+        c3_epilogue<CP>(prm, L, sm, g, item, X, ks, s_red);
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+    item = nitem;
+  }
+}
+
+template <int CP>
 cudaError_t launch_c3(mfa_ctx* ctx, const ContractParams& prm, const C3Smem& L, int ks, int vec_ok,
-                      cudaStream_t stream) {
-  auto kern = contract3_kernel<CP>;
+                      const CUtensorMap* xmap, int box_rows, cudaStream_t stream) {
   const size_t smem = (size_t)L.total * 4;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
-  kern<<<grid, kThreads, smem, stream>>>(prm, L, ks, vec_ok);
+  cudaError_t e;
+  if (xmap) {
+    auto kern = contract3_tma_kernel<CP>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
+    kern<<<grid, kThreads, smem, stream>>>(prm, L, ks, box_rows, *xmap);
+  } else {
+    auto kern = contract3_kernel<CP>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
+    kern<<<grid, kThreads, smem, stream>>>(prm, L, ks, vec_ok);
+  }
   ctx->launches++;
   return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map over the sample grids viewed as rows of 32 floats: box = 32 x box_rows, 128-byte swizzle.
+bool make_row_map(CUtensorMap* map, const float* x, int64_t nslots, int64_t slot_stride, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int64_t rows = nslots * slot_stride / kTmaRow;
+  if (rows < 1 || rows >= (int64_t(1) << 31)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kTmaRow, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kTmaRow * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kTmaRow, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -362,25 +655,34 @@ cudaError_t launch_c3(mfa_ctx* ctx, const ContractParams& prm, const C3Smem& L, 
 int contract3(mfa_ctx* ctx, ContractParams prm, cudaStream_t stream) {
   const int CP = round4(prm.maxC);
   const bool rmse = prm.rmse != nullptr;
+  // TMA path: rows of 32 samples (caller's hint), 16-byte aligned grids whose slots hold whole rows
+  const bool tma = prm.rows32 && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) && (prm.slot_stride % kTmaRow == 0);
   int ks = std::min(8, prm.maxN);
-  C3Smem L = c3_layout(prm.mode, CP, prm.maxC, prm.maxN, ks, rmse);
+  if (tma) ks = std::max(1, std::min(ks, 256 / prm.maxN));
+  auto layout = [&](int k) { return c3_layout(prm.mode, CP, prm.maxC, prm.maxN, k, rmse, tma ? k * prm.maxN * kTmaRow : 0); };
+  C3Smem L = layout(ks);
   while ((size_t)L.total * 4 > kMaxDynSmem && ks > 1) {
     ks = std::max(1, ks / 2);
-    L = c3_layout(prm.mode, CP, prm.maxC, prm.maxN, ks, rmse);
+    L = layout(ks);
   }
   if ((size_t)L.total * 4 > kMaxDynSmem) return MFA_ERR_CAPACITY;
+  CUtensorMap map;
+  const int box_rows = ks * prm.maxN;
+  const bool use_map = tma && make_row_map(&map, prm.x, prm.nslots, prm.slot_stride, box_rows);
+  if (!use_map) L = c3_layout(prm.mode, CP, prm.maxC, prm.maxN, ks, rmse, 0);
   const int vec_ok = (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) && (prm.slot_stride % 4 == 0);
-  if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  if (!use_map && cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  const CUtensorMap* mp = use_map ? &map : nullptr;
   cudaError_t e;
   switch (CP) {
-    case 4: e = launch_c3<4>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 8: e = launch_c3<8>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 12: e = launch_c3<12>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 16: e = launch_c3<16>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 20: e = launch_c3<20>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 24: e = launch_c3<24>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 28: e = launch_c3<28>(ctx, prm, L, ks, vec_ok, stream); break;
-    case 32: e = launch_c3<32>(ctx, prm, L, ks, vec_ok, stream); break;
+    case 4: e = launch_c3<4>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 8: e = launch_c3<8>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 12: e = launch_c3<12>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 16: e = launch_c3<16>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 20: e = launch_c3<20>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 24: e = launch_c3<24>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 28: e = launch_c3<28>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
+    case 32: e = launch_c3<32>(ctx, prm, L, ks, vec_ok, mp, box_rows, stream); break;
     default: return MFA_ERR_INVALID_ARG;
   }
   return e == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;

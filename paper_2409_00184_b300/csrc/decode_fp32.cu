@@ -3,12 +3,14 @@
 // Each micro-block's model f(u,v,w) = sum N_a(u) N_b(v) N_c(w) P_abc (Sec. 4.2) is evaluated on
 // its regular sample grid as three banded mode products, so each output costs p+1 FMAs per
 // stage instead of (p+1)^3:
-//   stage z:  T0[k][b][a] = sum_c P[c][b][a] N_c(w_k),     T1 = same with N'_c
-//   stage y:  U0[k][j][a] = sum_b T0[k][b][a] N_b(v_j),    U1 = T0 with N'_b,  U2 = T1 with N_b
+//   stage z:  T[k][b][a] = (sum_c P[c][b][a] N_c(w_k), same with N'_c)              (float2)
+//   stage y:  U[k][j][a] = (T0 N_b(v_j), T0 N'_b(v_j), T1 N_b(v_j)) summed over b      (float4)
 //   stage x:  (f, f_u, f_v, f_w)[k][j][i] = sum_a (U0 N_a, U0 N'_a, U1 N_a, U2 N_a)(u_i)
 // Work unit = (block, slab of `ks` z-planes); a persistent grid pulls units from an atomic
 // counter. Control points, basis tables and the stage outputs of one unit live in shared
 // memory; only the final float4 per voxel goes to HBM (coalesced 512-byte rows per warp).
+// Stage outputs are interleaved so stage x reads one 16-byte word per (row, control index), and
+// the loops advance their (k, j, a) indices incrementally instead of dividing.
 #include <algorithm>
 
 #include "common.cuh"
@@ -17,24 +19,23 @@
 namespace mfa {
 
 struct DecodeSmem {
-  int knots, boff, bN, bdN, P, T0, T1, U0, U1, U2, total;  // offsets in 4-byte words
+  int knots, boff, bN, bdN, T, P, U, total;  // offsets in 4-byte words
 };
 
-static DecodeSmem decode_smem_layout(int pmax, int maxC, int maxN, int ks) {
+static int r4(int v) { return (v + 3) & ~3; }
+
+// [knots | basis tables | T | P/U]: U (stage y output) overwrites P, which stage z has consumed.
+static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks) {
   DecodeSmem L;
   int o = 0;
-  const int q = pmax + 1;
-  L.knots = o; o += 3 * (MFA_MAX_NCP + MFA_MAX_DEGREE + 1);
-  L.boff = o;  o += 3 * maxN;
-  L.bN = o;    o += 3 * maxN * q;
-  L.bdN = o;   o += 3 * maxN * q;
-  o = (o + 3) & ~3;
-  L.P = o;     o += maxC * maxC * maxC;
-  L.T0 = o;    o += maxC * maxC * ks;
-  L.T1 = o;    o += maxC * maxC * ks;
-  L.U0 = o;    o += maxC * maxN * ks;
-  L.U1 = o;    o += maxC * maxN * ks;
-  L.U2 = o;    o += maxC * maxN * ks;
+  L.knots = o; o += r4(3 * kKnotMax);
+  L.boff = o;  o += r4(3 * maxN);
+  L.bN = o;    o += 3 * maxN * 4;   // float4 per sample: N_{s-p..s} (zero padded)
+  L.bdN = o;   o += 3 * maxN * 4;   // float4 per sample: N'
+  L.T = o;     o += r4(maxC * maxC * ks * (value_only ? 1 : 2));
+  L.P = o;
+  L.U = o;
+  o += std::max(r4(maxC * maxC * maxC), r4(maxC * maxN * ks * (value_only ? 1 : 4)));
   L.total = o;
   return L;
 }
@@ -43,21 +44,17 @@ template <int PMAX, bool VALUE_ONLY>
 __global__ void __launch_bounds__(kDecodeThreads)
 decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_unit, s_block, s_bad;
+  __shared__ int s_unit, s_bad;
   __shared__ BlockGeom s_g;
   constexpr int Q = PMAX + 1;
   const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
   const int maxN = prm.bounds.max_nsamp;
   float* s_knots = sm + L.knots;
   int* s_boff = reinterpret_cast<int*>(sm + L.boff);
-  float* s_bN = sm + L.bN;
-  float* s_bdN = sm + L.bdN;
+  float4* s_bN = reinterpret_cast<float4*>(sm + L.bN);
+  float4* s_bdN = reinterpret_cast<float4*>(sm + L.bdN);
   float* s_P = sm + L.P;
-  float* s_T0 = sm + L.T0;
-  float* s_T1 = sm + L.T1;
-  float* s_U0 = sm + L.U0;
-  float* s_U1 = sm + L.U1;
-  float* s_U2 = sm + L.U2;
 
   int count = prm.list ? (prm.count ? *prm.count : prm.list_len) : prm.nblocks;
   if (prm.list && (count < 0 || count > prm.list_len)) {
@@ -72,12 +69,11 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
       s_unit = atomicAdd(prm.counter, 1u);
       s_bad = 0;
       const int64_t unit = s_unit;
-      int b = -1;
       if (unit < total_units) {
         const int item = (int)(unit / prm.slabs);
-        b = prm.list ? prm.list[item] : item;
-        uint32_t bad = 0;
+        const int b = prm.list ? prm.list[item] : item;
         const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
+        uint32_t bad = 0;
         if (b < 0 || b >= prm.nblocks) bad = MFA_DEV_BAD_LIST;
         else bad = load_desc(prm.desc + b, prm.bounds, prm.knots_len, prm.cps_len, prm.nslots,
                              prm.slot_stride, s_g, !list_slots);
@@ -87,33 +83,31 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
         }
         if (bad) { flag(prm.status, bad); s_bad = 1; }
       }
-      s_block = b;
     }
     __syncthreads();
     if ((int64_t)s_unit >= total_units) break;
     if (s_bad) continue;
-    const BlockGeom g = s_g;
     const int slab = (int)((int64_t)s_unit % prm.slabs);
     const int k0 = slab * prm.ks;
-    if (k0 >= g.n[2]) continue;
-    const int kc = min(prm.ks, g.n[2] - k0);
-    const int Cx = g.C[0], Cy = g.C[1], Cz = g.C[2];
-    const int nx = g.n[0], ny = g.n[1];
+    const int nz = s_g.n[2];
+    if (k0 >= nz) continue;
+    const int kc = min(prm.ks, nz - k0);
+    const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
+    const int nx = s_g.n[0], ny = s_g.n[1];
+    const int px = s_g.p[0], py = s_g.p[1], pz = s_g.p[2];
 
-    // knots -> shared
-    for (int a = 0; a < 3; ++a) {
-      const int len = g.C[a] + g.p[a] + 1;
-      for (int i = tid; i < len; i += blockDim.x)
-        s_knots[a * (MFA_MAX_NCP + MFA_MAX_DEGREE + 1) + i] = prm.knots[g.knot_off[a] + i];
+    // knots -> shared; control points -> shared (coalesced)
+    if (tid < 3 * kKnotMax) {
+      const int a = tid / kKnotMax, i = tid - a * kKnotMax;
+      if (i < s_g.C[a] + s_g.p[a] + 1) s_knots[tid] = prm.knots[s_g.knot_off[a] + i];
     }
-    // control points -> shared (coalesced)
     const int ncps = Cx * Cy * Cz;
-    const float* gP = prm.cps + g.cp_off;
-    for (int e = tid; e < ncps; e += blockDim.x) s_P[e] = gP[e];
+    const float* gP = prm.cps + s_g.cp_off;
+    for (int e = tid; e < ncps; e += nthr) s_P[e] = __ldg(gP + e);
     __syncthreads();
-    if (tid < 3) {
-      const float* t = s_knots + tid * (MFA_MAX_NCP + MFA_MAX_DEGREE + 1);
-      if (!knots_ok(t, g.p[tid], g.C[tid])) { atomicOr(&s_bad, 1); flag(prm.status, MFA_DEV_BAD_KNOTS); }
+    if (tid < 3 && !knots_ok(s_knots + tid * kKnotMax, s_g.p[tid], s_g.C[tid])) {
+      atomicOr(&s_bad, 1);
+      flag(prm.status, MFA_DEV_BAD_KNOTS);
     }
     // basis tables: x (nx samples), y (ny samples), z (the slab's kc samples)
     {
@@ -122,116 +116,126 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
       else if (tid < nx + ny) { a = 1; i = tid - nx; smp = i; }
       else if (tid < nx + ny + kc) { a = 2; i = tid - nx - ny; smp = k0 + i; }
       if (a >= 0) {
-        const float* t = s_knots + a * (MFA_MAX_NCP + MFA_MAX_DEGREE + 1);
-        const float u = sample_param(smp, g.n[a]);
-        const int s = find_span(t, g.p[a], g.C[a], u);
-        float N[Q], dN[Q];
-        basis_funs<PMAX>(t, g.p[a], s, u, N, dN);
-        s_boff[a * maxN + i] = s - g.p[a];
+        const float* t = s_knots + a * kKnotMax;
+        const float u = sample_param(smp, s_g.n[a]);
+        const int s = find_span(t, s_g.p[a], s_g.C[a], u);
+        float N[4] = {0.f, 0.f, 0.f, 0.f}, dN[4] = {0.f, 0.f, 0.f, 0.f};
+        float Nq[Q], dNq[Q];
+        basis_funs<PMAX>(t, s_g.p[a], s, u, Nq, dNq);
 #pragma unroll
-        for (int r = 0; r < Q; ++r) {
-          s_bN[(a * maxN + i) * Q + r] = N[r];
-          s_bdN[(a * maxN + i) * Q + r] = dN[r];
-        }
+        for (int r = 0; r < Q; ++r) { N[r] = Nq[r]; dN[r] = dNq[r]; }
+        s_boff[a * maxN + i] = s - s_g.p[a];
+        s_bN[a * maxN + i] = make_float4(N[0], N[1], N[2], N[3]);
+        s_bdN[a * maxN + i] = make_float4(dN[0], dN[1], dN[2], dN[3]);
       }
     }
     __syncthreads();
     if (s_bad) continue;
 
-    // stage z
+    // ---- stage z: T[kl][b][a] over the slab, flat index e = kl*plane + ab ----
     {
-      const int pz = g.p[2];
       const int plane = Cx * Cy;
       const int tot = plane * kc;
-      for (int e = tid; e < tot; e += blockDim.x) {
-        const int kl = e / plane;
-        const int ab = e - kl * plane;
+      int kl = tid / plane, ab = tid - (tid / plane) * plane;
+      for (int e = tid; e < tot; e += nthr) {
         const int oz = s_boff[2 * maxN + kl];
-        const float* Nz = s_bN + (2 * maxN + kl) * Q;
-        const float* dNz = s_bdN + (2 * maxN + kl) * Q;
+        const float4 Nz = s_bN[2 * maxN + kl];
+        const float4 dNz = s_bdN[2 * maxN + kl];
+        const float Nzv[4] = {Nz.x, Nz.y, Nz.z, Nz.w}, dNzv[4] = {dNz.x, dNz.y, dNz.z, dNz.w};
+        const float* Pc = s_P + oz * plane + ab;
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
         for (int d = 0; d < Q; ++d) {
           if (d <= pz) {
-            const float pv = s_P[(oz + d) * plane + ab];
-            t0 = fmaf(pv, Nz[d], t0);
-            if (!VALUE_ONLY) t1 = fmaf(pv, dNz[d], t1);
+            const float pv = Pc[d * plane];
+            t0 = fmaf(pv, Nzv[d], t0);
+            if (!VALUE_ONLY) t1 = fmaf(pv, dNzv[d], t1);
           }
         }
-        s_T0[e] = t0;
-        if (!VALUE_ONLY) s_T1[e] = t1;
+        if (VALUE_ONLY) sm[L.T + e] = t0;
+        else reinterpret_cast<float2*>(sm + L.T)[e] = make_float2(t0, t1);
+        ab += nthr;
+        while (ab >= plane) { ab -= plane; ++kl; }
       }
     }
     __syncthreads();
-    // stage y
+    // ---- stage y: U[kl][j][a]; thread keeps its column a, rows r = (kl, j) advance by step ----
     {
-      const int py = g.p[1];
-      const int tot = Cx * ny * kc;
-      for (int e = tid; e < tot; e += blockDim.x) {
-        const int a = e % Cx;
-        const int r = e / Cx;  // kl * ny + j
-        const int j = r % ny;
-        const int kl = r / ny;
-        const int oy = s_boff[maxN + j];
-        const float* Ny = s_bN + (maxN + j) * Q;
-        const float* dNy = s_bdN + (maxN + j) * Q;
-        const float* T0 = s_T0 + (kl * Cy + oy) * Cx + a;
-        const float* T1 = s_T1 + (kl * Cy + oy) * Cx + a;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+      const int step = nthr / Cx;
+      const int g = tid / Cx;
+      if (g < step) {
+        const int a = tid - g * Cx;
+        const int rows = ny * kc;
+        int kl = g / ny, j = g - (g / ny) * ny;
+        for (int r = g; r < rows; r += step) {
+          const int oy = s_boff[maxN + j];
+          const float4 Ny = s_bN[maxN + j];
+          const float Nyv[4] = {Ny.x, Ny.y, Ny.z, Ny.w};
+          const int tb = (kl * Cy + oy) * Cx + a;
+          if (VALUE_ONLY) {
+            float u0 = 0.f;
 #pragma unroll
-        for (int d = 0; d < Q; ++d) {
-          if (d <= py) {
-            const float tv = T0[d * Cx];
-            u0 = fmaf(tv, Ny[d], u0);
-            if (!VALUE_ONLY) {
-              u1 = fmaf(tv, dNy[d], u1);
-              u2 = fmaf(T1[d * Cx], Ny[d], u2);
+            for (int d = 0; d < Q; ++d)
+              if (d <= py) u0 = fmaf(sm[L.T + tb + d * Cx], Nyv[d], u0);
+            sm[L.U + r * Cx + a] = u0;
+          } else {
+            const float4 dNy = s_bdN[maxN + j];
+            const float dNyv[4] = {dNy.x, dNy.y, dNy.z, dNy.w};
+            const float2* T = reinterpret_cast<const float2*>(sm + L.T);
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < Q; ++d) {
+              if (d <= py) {
+                const float2 tv = T[tb + d * Cx];
+                u0 = fmaf(tv.x, Nyv[d], u0);
+                u1 = fmaf(tv.x, dNyv[d], u1);
+                u2 = fmaf(tv.y, Nyv[d], u2);
+              }
             }
+            reinterpret_cast<float4*>(sm + L.U)[r * Cx + a] = make_float4(u0, u1, u2, 0.f);
           }
+          j += step;
+          while (j >= ny) { j -= ny; ++kl; }
         }
-        s_U0[e] = u0;
-        if (!VALUE_ONLY) { s_U1[e] = u1; s_U2[e] = u2; }
       }
     }
     __syncthreads();
-    // stage x + store: thread owns one x sample, loops over (k, j) rows
+    // ---- stage x + store: thread owns one x sample, loops over (k, j) rows ----
     {
-      const int rows_per_pass = blockDim.x / nx;
+      const int rows_per_pass = nthr / nx;
       const int i = tid % nx;
       const int r0 = tid / nx;
       if (r0 < rows_per_pass) {
-        const int px = g.p[0];
         const int ox = s_boff[i];
-        float Nx[Q], dNx[Q];
-#pragma unroll
-        for (int d = 0; d < Q; ++d) {
-          Nx[d] = s_bN[i * Q + d];
-          dNx[d] = s_bdN[i * Q + d];
-        }
+        const float4 Nx4 = s_bN[i], dNx4 = s_bdN[i];
+        const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
         const int rows = ny * kc;
-        const int64_t base = (int64_t)g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
-        for (int r = r0; r < rows; r += rows_per_pass) {
-          const float* u0 = s_U0 + r * Cx + ox;
-          float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
-          if (VALUE_ONLY) {
+        const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
+        if (VALUE_ONLY) {
+          const float* U = sm + L.U + ox;
+          for (int r = r0; r < rows; r += rows_per_pass) {
+            float f = 0.f;
 #pragma unroll
             for (int d = 0; d < Q; ++d)
-              if (d <= px) f = fmaf(u0[d], Nx[d], f);
+              if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
             __stcs(prm.cache + base + (int64_t)r * nx, f);
-          } else {
-            const float* u1 = s_U1 + r * Cx + ox;
-            const float* u2 = s_U2 + r * Cx + ox;
+          }
+        } else {
+          const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
+          float4* out = reinterpret_cast<float4*>(prm.cache) + base;
+          for (int r = r0; r < rows; r += rows_per_pass) {
+            float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
 #pragma unroll
             for (int d = 0; d < Q; ++d) {
               if (d <= px) {
-                const float a0 = u0[d];
-                f = fmaf(a0, Nx[d], f);
-                fu = fmaf(a0, dNx[d], fu);
-                fv = fmaf(u1[d], Nx[d], fv);
-                fw = fmaf(u2[d], Nx[d], fw);
+                const float4 uv = U[r * Cx + d];
+                f = fmaf(uv.x, Nx[d], f);
+                fu = fmaf(uv.x, dNx[d], fu);
+                fv = fmaf(uv.y, Nx[d], fv);
+                fw = fmaf(uv.z, Nx[d], fw);
               }
             }
-            __stcs(reinterpret_cast<float4*>(prm.cache) + base + (int64_t)r * nx, make_float4(f, fu, fv, fw));
+            __stcs(out + (int64_t)r * nx, make_float4(f, fu, fv, fw));
           }
         }
       }
@@ -259,17 +263,17 @@ static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const Decod
 
 int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaStream_t stream) {
   const int maxN = prm.bounds.max_nsamp, maxC = prm.bounds.max_ncp, pmax = prm.bounds.max_degree;
-  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : 8;
-  DecodeSmem L = decode_smem_layout(pmax, maxC, maxN, ks);
+  const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
+  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : std::min(8, maxN);
+  DecodeSmem L = decode_smem_layout(vo, maxC, maxN, ks);
   while ((size_t)L.total * 4 > kMaxDynSmem && ks > 1) {
     ks = std::max(1, ks / 2);
-    L = decode_smem_layout(pmax, maxC, maxN, ks);
+    L = decode_smem_layout(vo, maxC, maxN, ks);
   }
   if ((size_t)L.total * 4 > kMaxDynSmem) return MFA_ERR_CAPACITY;
   prm.ks = ks;
   prm.slabs = (maxN + ks - 1) / ks;
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
-  const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
   cudaError_t e;
   switch (pmax) {
     case 1: e = vo ? launch_one<1, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<1, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;

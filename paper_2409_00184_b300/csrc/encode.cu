@@ -107,6 +107,7 @@ struct BatchAnalysis {
   std::vector<EncClass> classes;
   int pinv_len = 0, tab_len = 0, maxC = 0, maxN = 0, max_slot = -1;
   int64_t max_vox = 0;
+  bool rows32 = true;  // every block has 32 samples along x
 };
 
 int analyze_batch(const mfa_block_desc* h_desc, int nblocks, const float* h_knots, int64_t knots_len,
@@ -149,6 +150,7 @@ int analyze_batch(const mfa_block_desc* h_desc, int nblocks, const float* h_knot
       out.maxN = std::max(out.maxN, n);
     }
     if (d.cp_off < 0 || d.cp_off + ncps > cps_len || d.slot < 0) return MFA_ERR_INVALID_ARG;
+    out.rows32 = out.rows32 && d.nsamp[0] == 32;
     out.items[b].slot = d.slot;
     out.items[b].cp_off = d.cp_off;
     out.max_slot = std::max(out.max_slot, d.slot);
@@ -160,7 +162,7 @@ int analyze_batch(const mfa_block_desc* h_desc, int nblocks, const float* h_knot
 // Enqueues the FP64 class set-up and the fit for device-resident items/classes/pools.
 int run_fit(mfa_ctx* ctx, int nblocks, int nclasses, int maxC, int maxN, const EncItem* items,
             const EncClass* classes, float* pinv, TabEntry* tabs, const float* data, int64_t slot_stride,
-            int64_t nslots, float* cps_out, double* rmse, cudaStream_t s) {
+            int64_t nslots, float* cps_out, double* rmse, cudaStream_t s, int rows32) {
   encode_class_kernel<<<nclasses, kThreads, 0, s>>>(classes, pinv, tabs, ctx->d_status);
   ctx->launches++;
   if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
@@ -182,6 +184,7 @@ int run_fit(mfa_ctx* ctx, int nblocks, int nclasses, int maxC, int maxN, const E
   prm.maxC = maxC;
   prm.maxN = maxN;
   prm.pmax = MFA_MAX_DEGREE;
+  prm.rows32 = rows32;
   return contract3(ctx, prm, s);
 }
 
@@ -192,7 +195,7 @@ using namespace mfa;
 
 struct mfa_encode_plan {
   mfa_ctx* ctx = nullptr;
-  int nblocks = 0, nclasses = 0, maxC = 0, maxN = 0;
+  int nblocks = 0, nclasses = 0, maxC = 0, maxN = 0, rows32 = 0;
   int max_slot = -1;
   int64_t max_vox = 0;
   EncItem* d_items = nullptr;
@@ -220,6 +223,7 @@ int mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out, const mfa_block_
   plan->maxN = an.maxN;
   plan->max_slot = an.max_slot;
   plan->max_vox = an.max_vox;
+  plan->rows32 = an.rows32;
   if (cudaMalloc(&plan->d_items, sizeof(EncItem) * nblocks) != cudaSuccess ||
       cudaMalloc(&plan->d_classes, sizeof(EncClass) * an.classes.size()) != cudaSuccess ||
       cudaMalloc(&plan->d_pinv, sizeof(float) * an.pinv_len) != cudaSuccess ||
@@ -252,7 +256,7 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
     return MFA_ERR_INVALID_ARG;
   return run_fit(ctx, plan->nblocks, plan->nclasses, plan->maxC, plan->maxN, plan->d_items, plan->d_classes,
                  plan->d_pinv, plan->d_tabs, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse,
-                 static_cast<cudaStream_t>(stream));
+                 static_cast<cudaStream_t>(stream), plan->rows32);
 }
 
 }  // extern "C"
@@ -334,7 +338,7 @@ extern "C" int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t n
   rc = run_fit(&local, nblocks, (int)an.classes.size(), an.maxC, an.maxN,
                reinterpret_cast<const EncItem*>(base + o_items), reinterpret_cast<const EncClass*>(base + o_cls),
                reinterpret_cast<float*>(base + o_pinv), reinterpret_cast<TabEntry*>(base + o_tabs), d_data,
-               slot_stride_voxels, nslots, d_cps_out, d_rmse, s);
+               slot_stride_voxels, nslots, d_cps_out, d_rmse, s, an.rows32);
   if (rc != MFA_OK) return rc;
   uint32_t status = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess ||

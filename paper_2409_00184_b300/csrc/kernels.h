@@ -136,6 +136,7 @@ struct ContractParams {
   uint32_t* status;
   uint32_t* counter;
   int maxC, maxN, pmax;
+  int rows32;            // blocks (mostly) have 32-sample x-rows: use the TMA kernel when aligned
 };
 
 // Returns MFA_ERR_CAPACITY (without launching) when the block shapes do not fit shared memory.

@@ -19,7 +19,7 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
                      fmaf(w, b.w - a.w, a.w));
 }
 
-__global__ void __launch_bounds__(kTile * kTile) raycast_kernel(RaycastParams prm) {
+__global__ void __launch_bounds__(kTile * kTile, 4) raycast_kernel(RaycastParams prm) {
   __shared__ float4 s_tf[kMaxTf];
   const int tid = threadIdx.y * kTile + threadIdx.x;
   for (int e = tid; e < prm.tf_n; e += kTile * kTile) s_tf[e] = prm.tf[e];
