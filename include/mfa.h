@@ -173,6 +173,61 @@ int mfa_adjoint_blocks(mfa_ctx* ctx,
                        const float* d_cps, float* d_grad_cps, int64_t cps_len,
                        const mfa_bounds* bounds, int32_t precision, void* stream);
 
+/* Camera and shading of a ray cast (Algorithm 4), see mfa_raycast. */
+typedef struct {
+  float eye[3], target[3], up[3];
+  float fov_y_deg;
+  int32_t width, height;
+  float step_voxels;   /* sample spacing in voxels of the longest axis (1 = one per voxel) */
+  float opacity_max;   /* early termination once accumulated opacity exceeds this          */
+  float ka, kd, ks, shininess;  /* headlight Blinn-Phong coefficients                     */
+  float vmin, vmax;    /* value range mapped onto the transfer function                   */
+} mfa_view;
+
+/* ---- one frame as a CUDA graph (the per-POV decode + render of Sec. 4.3, Algorithm 4) - */
+#define MFA_FRAME_SORT_BY_COST 0x1u /* order the visible list by decreasing max(C) first     */
+#define MFA_FRAME_RAYCAST      0x2u /* build the brick table and ray-cast after the decode   */
+
+/* Everything a frame reads; pointers and sizes are fixed when the graph is captured. Per frame
+ * the caller writes the visible block ids into d_list[0 .. *d_count) (device memory, count <=
+ * list_capacity) and replays the graph. Decoded block m of the (ordered) list goes to cache slot
+ * m (the cache holds list_capacity slots of slot_stride_voxels float4). With MFA_FRAME_RAYCAST the
+ * blocks are the bricks of a Bx*By*Bz volume (nblocks = Bx*By*Bz, brick id z-major) of brick_n^3
+ * samples each; the graph rewrites d_brick_table (nblocks int32: list position or -1) and renders
+ * into d_image as mfa_raycast does. */
+typedef struct {
+  const mfa_block_desc* d_desc;
+  int32_t nblocks;
+  int32_t* d_list;            /* list_capacity int32, reordered in place by SORT_BY_COST */
+  int32_t list_capacity;
+  const int32_t* d_count;     /* device int32: the frame's number of visible blocks */
+  const float* d_knots;
+  int64_t knots_len;
+  const float* d_cps;
+  int64_t cps_len;
+  float* d_cache;
+  int64_t slot_stride_voxels;
+  mfa_bounds bounds;
+  uint32_t flags;             /* MFA_FRAME_* */
+  /* ray cast (MFA_FRAME_RAYCAST only) */
+  int32_t* d_brick_table;
+  int32_t brick_dims[3];
+  int32_t brick_n;
+  const mfa_view* view;
+  const float* d_tf;
+  int32_t tf_n;
+  float* d_image;
+} mfa_frame_desc;
+
+typedef struct mfa_frame_graph mfa_frame_graph;
+/* Captures the frame's kernels (cost ordering, persistent decode with the device-side count,
+ * brick table, ray cast) into a CUDA graph on a private stream and instantiates it. Allocates a
+ * list_capacity int32 scratch for the ordering. The mfa_view is read at capture time. */
+int  mfa_frame_graph_create(mfa_ctx* ctx, mfa_frame_graph** out, const mfa_frame_desc* frame);
+/* Replays the captured frame on `stream`. */
+int  mfa_frame_graph_launch(mfa_frame_graph* graph, void* stream);
+void mfa_frame_graph_destroy(mfa_frame_graph* graph);
+
 /* ---- least-squares encode (Algorithm 1's model(NCP, degree)) ------------------------- */
 /* A plan validates a batch on the host, copies its descriptors and knots to the device
  * and groups the axes into classes of equal (knots, p, C, n). Executing it computes, per
@@ -218,15 +273,7 @@ int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t nblocks,
                               float* d_cps_out, int64_t cps_len, double* d_rmse, void* stream);
 
 /* ---- ray casting (Algorithm 4) -------------------------------------------------------- */
-typedef struct {
-  float eye[3], target[3], up[3];
-  float fov_y_deg;
-  int32_t width, height;
-  float step_voxels;   /* sample spacing in voxels of the longest axis (1 = one per voxel) */
-  float opacity_max;   /* early termination once accumulated opacity exceeds this          */
-  float ka, kd, ks, shininess;  /* headlight Blinn-Phong coefficients                     */
-  float vmin, vmax;    /* value range mapped onto the transfer function                   */
-} mfa_view;
+
 
 /* Renders width*height premultiplied RGBA floats (row 0 at the top) into d_image from a
  * decoded cache of bricks of brick_n^3 voxels. d_brick_table[(bz*By + by)*Bx + bx] is the

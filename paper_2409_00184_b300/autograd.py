@@ -1,0 +1,96 @@
+"""Differentiable least-squares encode on top of the library's decode and adjoint kernels.
+
+`DecodeValue` is a torch.autograd.Function: forward = value-only decode of every block's control
+points (mfa_decode_blocks, MFA_DECODE_VALUE_ONLY), backward = the transposed contraction of the
+incoming gradient (mfa_adjoint_blocks). The basis is recomputed from the knots inside both kernels;
+nothing but the control points is saved for backward.
+
+`fit_gradient_descent` fits control points to sample grids by (Nesterov-accelerated) gradient
+descent on 0.5*||decode(P) - D||^2 (the least-squares fit of Algorithm 1's model()), using the
+library's fused gradient kernel (N^T N P - N^T D) and a per-block step 1/L, with L the largest
+eigenvalue of that block's Gram operator (found by power iteration through the same kernel).
+The arithmetic of every decode, adjoint and gradient runs in the library; the optimizer's vector
+updates are torch tensor operations.
+"""
+
+import torch
+
+from . import mfa
+
+
+class DecodeValue(torch.autograd.Function):
+    """f = decode_value(P) on each block's sample grid (slot-addressed, slot_stride floats per slot)."""
+
+    @staticmethod
+    def forward(fctx, cps, lib_ctx, blocks, slot_stride, nslots):
+        out = torch.zeros(nslots * slot_stride, device=cps.device, dtype=torch.float32)
+        mfa.decode_blocks(lib_ctx, blocks, out, slot_stride, nslots, flags=mfa.DECODE_VALUE_ONLY,
+                          cps=cps.contiguous())
+        fctx.lib = (lib_ctx, blocks, slot_stride, nslots)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        lib_ctx, blocks, slot_stride, nslots = fctx.lib
+        grad = torch.empty(blocks.cps_len, device=grad_out.device, dtype=torch.float32)
+        mfa.adjoint_blocks(lib_ctx, blocks, grad_out.contiguous(), slot_stride, nslots, grad)
+        return grad, None, None, None, None
+
+
+def decode_value(cps, lib_ctx, blocks, slot_stride, nslots):
+    return DecodeValue.apply(cps, lib_ctx, blocks, slot_stride, nslots)
+
+
+def block_ids(blocks, device="cuda"):
+    """Block index of every control point (for per-block reductions)."""
+    sizes = torch.as_tensor((blocks.host_desc["ncp"].astype("int64")).prod(axis=1), device=device)
+    return torch.repeat_interleave(torch.arange(blocks.n, device=device), sizes)
+
+
+def lipschitz(lib_ctx, blocks, slot_stride, nslots, iters=30, seed=0):
+    """Per-block largest eigenvalue of N^T N (the gradient's Lipschitz constant), by power iteration
+    with the fused gradient kernel at zero data: G(P; D = 0) = N^T N P."""
+    dev = blocks.cps.device
+    ids = block_ids(blocks, dev)
+    zero = torch.zeros(nslots * slot_stride, device=dev)
+    g = torch.Generator(device=dev).manual_seed(seed)
+    v = torch.rand(blocks.cps_len, device=dev, generator=g) + 0.5
+    lam = torch.zeros(blocks.n, device=dev)
+    hv = torch.empty_like(v)
+    for _ in range(iters):
+        nrm = torch.zeros(blocks.n, device=dev).index_add_(0, ids, v * v).sqrt()
+        v = v / nrm[ids]
+        mfa.adjoint_blocks(lib_ctx, blocks, zero, slot_stride, nslots, hv, cps=v)
+        lam = torch.zeros(blocks.n, device=dev).index_add_(0, ids, v * hv)
+        v = hv.clone()
+    return lam
+
+
+def fit_gradient_descent(lib_ctx, blocks, data, slot_stride, nslots, iters=2000, nesterov=True, P0=None,
+                         tol=None, P_ref=None, check_every=25):
+    """Least-squares control points by gradient descent with per-block step 1/L.
+
+    Stops after `iters` steps or, with P_ref given, once max|P - P_ref| / range(P_ref) <= tol (checked
+    every `check_every` steps). Returns (P, history of (step, relative error))."""
+    dev = blocks.cps.device
+    ids = block_ids(blocks, dev)
+    L = lipschitz(lib_ctx, blocks, slot_stride, nslots) * 1.01
+    step = (1.0 / L)[ids]
+    P = torch.zeros(blocks.cps_len, device=dev) if P0 is None else P0.clone()
+    Y, P_prev = P.clone(), P.clone()
+    G = torch.empty_like(P)
+    hist = []
+    rng = None if P_ref is None else float(P_ref.max() - P_ref.min())
+    for k in range(1, iters + 1):
+        mfa.adjoint_blocks(lib_ctx, blocks, data, slot_stride, nslots, G, cps=Y if nesterov else P)
+        P_new = (Y if nesterov else P) - step * G
+        if nesterov:
+            Y = P_new + (k - 1.0) / (k + 2.0) * (P_new - P_prev)
+            P_prev = P_new
+        P = P_new
+        if P_ref is not None and (k % check_every == 0 or k == iters):
+            err = float((P - P_ref).abs().max()) / rng
+            hist.append((k, err))
+            if tol is not None and err <= tol:
+                break
+    return P, hist

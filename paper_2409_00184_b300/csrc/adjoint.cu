@@ -1,6 +1,7 @@
 // Adjoint of the micro-model decode: dP_abc = sum_{k,j,i} R[k][j][i] N_a(u_i) N_b(v_j) N_c(w_k).
 // (Entry point; the common case runs on the dense contraction kernel of contract3.cu. The banded
-// gather kernel below is the general path for shapes beyond that kernel's shared memory.)
+// gather kernel below is the general path for shapes that kernel does not take: shared memory
+// beyond its budget, or the fused gradient on sample rows the TMA path cannot load.)
 //
 // The gradient of 0.5*||decode(P) - D||^2 with respect to the control points, i.e. the transposed
 // contraction that makes the least-squares encode of Algorithm 1's model() a gradient method.
@@ -252,7 +253,7 @@ int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream) {
     c.pmax = prm.bounds.max_degree;
     c.rows32 = prm.bounds.max_nsamp == 32;
     const int rc = contract3(ctx, c, stream);
-    if (rc != MFA_ERR_CAPACITY) return rc;
+    if (rc != MFA_ERR_CAPACITY && rc != MFA_ERR_UNSUPPORTED) return rc;
   }
   const int maxN = prm.bounds.max_nsamp, maxC = prm.bounds.max_ncp, pmax = prm.bounds.max_degree;
   int ks = std::min(8, maxN);

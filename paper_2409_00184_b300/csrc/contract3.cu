@@ -4,8 +4,10 @@
 //   kFit:      A = (N^T N)^{-1} N^T per axis (from the encode plan) -> least-squares control points,
 //              then optionally the RMSE of the fitted model over the samples (Table 1's metric);
 //   kAdjoint:  A = N (collocation matrix, built from the knots in the CTA) -> N^T R;
-//   kGradient: G = (M_x (x) M_y (x) M_z) P - N^T D with M = N^T N, the gradient of
-//              0.5*||decode(P) - D||^2 (= N^T (N P - D)) without a forward decode of the samples.
+//   kGradient: G = N^T (decode(P) - D), the gradient of 0.5*||decode(P) - D||^2: each slab of samples is
+//              replaced in shared memory by its residual (a banded value decode of P minus the samples)
+//              before the contraction, so the cancellation happens per sample, at the data's scale.
+//              TMA kernel only; other shapes use the banded adjoint kernel.
 // One CTA per block; the grid streams through in z-slabs of ks planes:
 //   x:  Y1[(k,j)][a] = sum_i X[k][j][i] Ax[i][a]   thread per sample row, all columns in registers,
 //                                                  Ax rows broadcast from shared memory
@@ -31,7 +33,7 @@ constexpr int kThreads = 256;
 constexpr int kTmaRow = 32;  // samples per row on the TMA path (128 bytes)
 
 struct C3Smem {
-  int A[3], M[3], tab[3], knots, Y1, Y2, Y, P, Z, X, total;  // offsets in 4-byte words
+  int A[3], off[3], tab[3], knots, Y1, Y2, Y, P, X, total;  // offsets in 4-byte words
 };
 
 struct C3Geom {
@@ -47,7 +49,7 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xb
   C3Smem L;
   int o = 0;
   for (int a = 0; a < 3; ++a) { L.A[a] = o; o += maxN * CP; }
-  for (int a = 0; a < 3; ++a) { L.M[a] = o; if (mode == kGradient) o += maxC * maxC; }
+  for (int a = 0; a < 3; ++a) { L.off[a] = o; if (mode == kGradient) o += maxN; }
   for (int a = 0; a < 3; ++a) { L.tab[a] = o; if (mode == kFit && rmse) o += maxN * (int)(sizeof(TabEntry) / 4); }
   L.knots = o; if (mode != kFit) o += 3 * kKnotMax;
   o = round4(o);
@@ -55,7 +57,6 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xb
   L.Y2 = o; o += round4(ks * maxC * maxC);
   L.Y = o;  o += round4(maxC * maxC * maxC);
   L.P = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
-  L.Z = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
   L.X = o;  if (xbuf_words) o += 256 + 2 * xbuf_words;  // two slab buffers + slack for 1024-byte alignment
   L.total = o;
   return L;
@@ -89,8 +90,8 @@ __device__ void c3_fetch(const ContractParams& prm, int item, C3Geom& g) {
   }
 }
 
-// Builds the three n x CP matrices (zero-padded columns), the RMSE tables (kFit), M = N^T N and P
-// (kGradient), zeroes Y. Ends with a barrier; sets *s_bad when a knot vector is invalid.
+// Builds the three n x CP matrices (zero-padded columns), the RMSE tables (kFit), the span offsets
+// and P (kGradient), zeroes Y. Ends with a barrier; sets *s_bad when a knot vector is invalid.
 template <int CP>
 __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int* s_bad) {
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -111,9 +112,11 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
     }
   } else {
     float* kn = sm + L.knots;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a) {  // every maxN row zeroed: padded sample rows must contribute nothing
       for (int i = tid; i < g.C[a] + g.p[a] + 1; i += nthr) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
-      for (int e = tid; e < g.n[a] * CP; e += nthr) sm[L.A[a] + e] = 0.f;
+      for (int e = tid; e < prm.maxN * CP; e += nthr) sm[L.A[a] + e] = 0.f;
+      if (prm.mode == kGradient)
+        for (int i = tid; i < prm.maxN; i += nthr) reinterpret_cast<int*>(sm + L.off[a])[i] = 0;
     }
     __syncthreads();
     if (tid < 3 && !knots_ok(kn + tid * kKnotMax, g.p[tid], g.C[tid])) {
@@ -129,24 +132,12 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
       float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
       basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, u, N, dN);
       for (int r = 0; r <= g.p[a]; ++r) sm[L.A[a] + i * CP + s - g.p[a] + r] = N[r];
+      if (prm.mode == kGradient) reinterpret_cast<int*>(sm + L.off[a])[i] = s - g.p[a];
     }
   }
   __syncthreads();
-  if (prm.mode == kGradient) {
-    for (int a = 0; a < 3; ++a) {  // M = N^T N
-      const float* A = sm + L.A[a];
-      float* M = sm + L.M[a];
-      const int C = g.C[a], n = g.n[a];
-      for (int e = tid; e < C * C; e += nthr) {
-        const int r = e / C, c = e - r * C;
-        float acc = 0.f;
-#pragma unroll 4
-        for (int i = 0; i < n; ++i) acc = fmaf(A[i * CP + r], A[i * CP + c], acc);
-        M[e] = acc;
-      }
-    }
+  if (prm.mode == kGradient)
     for (int e = tid; e < ncps; e += nthr) sm[L.P + e] = prm.cps[g.cpoff + e];
-  }
   for (int e = tid; e < ncps; e += nthr) sm[L.Y + e] = 0.f;
   __syncthreads();
 }
@@ -281,7 +272,7 @@ __device__ void c3_stage_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0,
   __syncthreads();
 }
 
-// Writes the block's result: Y (fit, adjoint) or M P - Y (gradient); for the fit also the RMSE of
+// Writes the block's result Y; for the fit also the RMSE of
 // the fitted model (banded value decode vs the samples; per-thread FP32 Kahan sums reduced in FP64).
 template <int CP>
 __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int item,
@@ -291,39 +282,8 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = Cx * Cy, ncps = plane * Cz;
   const float* Y = sm + L.Y;
-  if (prm.mode == kAdjoint) {
+  if (prm.mode != kFit) {  // adjoint N^T R, or gradient N^T (decode(P) - D)
     for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
-    return;
-  }
-  if (prm.mode == kGradient) {
-    // M = N^T N is banded: N_a and N_q overlap only when |a - q| <= p
-    float* P = sm + L.P;
-    float* Z = sm + L.Z;
-    const float* Mx = sm + L.M[0];
-    const float* My = sm + L.M[1];
-    const float* Mz = sm + L.M[2];
-    const int px = g.p[0], py = g.p[1], pz = g.p[2];
-    for (int e = tid; e < ncps; e += nthr) {  // Z = P x_1 M_x
-      const int a = e % Cx, cb = e / Cx;
-      float acc = 0.f;
-      for (int q = max(0, a - px); q <= min(Cx - 1, a + px); ++q) acc = fmaf(P[cb * Cx + q], Mx[q * Cx + a], acc);
-      Z[e] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < ncps; e += nthr) {  // P <- Z x_2 M_y
-      const int a = e % Cx, bb = (e / Cx) % Cy, c = e / plane;
-      float acc = 0.f;
-      for (int q = max(0, bb - py); q <= min(Cy - 1, bb + py); ++q)
-        acc = fmaf(Z[(c * Cy + q) * Cx + a], My[q * Cy + bb], acc);
-      P[e] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < ncps; e += nthr) {  // G = P x_3 M_z - N^T D
-      const int ab = e % plane, c = e / plane;
-      float acc = 0.f;
-      for (int q = max(0, c - pz); q <= min(Cz - 1, c + pz); ++q) acc = fmaf(P[q * plane + ab], Mz[q * Cz + c], acc);
-      prm.out[g.cpoff + e] = acc - Y[e];
-    }
     return;
   }
   for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
@@ -374,6 +334,66 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
     for (int w = 0; w < (int)(nthr / 32); ++w) tot += s_red[w];
     prm.rmse[item] = sqrt(tot / ((double)nx * ny * nz));
   }
+}
+
+// Gradient mode: replaces the slab's samples D in the swizzled buffer by r = decode_value(P) - D
+// (banded value decode with the dense collocation rows A and the span offsets).
+__device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, float4* xb, int k0, int kc,
+                                      int CP) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Cx = g.C[0], Cy = g.C[1], ny = g.n[1];
+  const int plane = Cx * Cy;
+  const float* P = sm + L.P;
+  float* Y1 = sm + L.Y1;
+  float* Y2 = sm + L.Y2;
+  const int* ox = reinterpret_cast<const int*>(sm + L.off[0]);
+  const int* oy = reinterpret_cast<const int*>(sm + L.off[1]);
+  const int* oz = reinterpret_cast<const int*>(sm + L.off[2]);
+  const float* Ax = sm + L.A[0];
+  const float* Ay = sm + L.A[1];
+  const float* Az = sm + L.A[2];
+  {  // stage z: Y2[kl][ab]
+    int kl = tid / plane, ab = tid - (tid / plane) * plane;
+    for (int e = tid; e < plane * kc; e += nthr) {
+      const int k = k0 + kl, o = oz[k];
+      float acc = 0.f;
+      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(P[(o + d) * plane + ab], Az[k * CP + o + d], acc);
+      Y2[e] = acc;
+      ab += nthr;
+      while (ab >= plane) { ab -= plane; ++kl; }
+    }
+  }
+  __syncthreads();
+  {  // stage y: Y1[(kl, j)][a]
+    const int step = nthr / Cx, gq = tid / Cx;
+    if (gq < step) {
+      const int a = tid - gq * Cx;
+      int kl = gq / ny, j = gq - (gq / ny) * ny;
+      for (int r = gq; r < kc * ny; r += step) {
+        const int o = oy[j];
+        float acc = 0.f;
+        for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + o + d) * Cx + a], Ay[j * CP + o + d], acc);
+        Y1[r * Cx + a] = acc;
+        j += step;
+        while (j >= ny) { j -= ny; ++kl; }
+      }
+    }
+  }
+  __syncthreads();
+  {  // stage x and r = f - D in place (32-sample rows, swizzled)
+    const int i = tid & 31, r0 = tid >> 5, rstep = nthr >> 5;
+    const int o = ox[i];
+    float w[MFA_MAX_DEGREE + 1];
+    for (int d = 0; d <= MFA_MAX_DEGREE; ++d) w[d] = d <= g.p[0] ? Ax[i * CP + o + d] : 0.f;
+    float* xf = reinterpret_cast<float*>(xb);
+    for (int r = r0; r < kc * ny; r += rstep) {
+      float f = 0.f;
+      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + o + d], w[d], f);
+      const int idx = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
+      xf[idx] = f - xf[idx];
+    }
+  }
+  __syncthreads();
 }
 
 // RMSE contribution of one z-slab on the TMA path: banded value decode of the fitted model Y
@@ -498,6 +518,8 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
   auto tma_ok = [&](const C3Geom& g) {
     return g.valid && !g.bad && g.n[0] == kTmaRow && (int64_t)ks * g.n[1] <= box_rows;
   };
+  if (tid == 0 && prm.mode == kGradient && s_g[0].valid && !s_g[0].bad && s_g[0].n[0] > kTmaRow)
+    flag(prm.status, MFA_DEV_BAD_DESC);
   auto issue = [&](const C3Geom& g, int k0) {  // one thread
     const int b = q_issue & 1;
     mbar_arrive_expect_tx(&s_bar[b], box_bytes);
@@ -554,9 +576,26 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
           return;
         }
         if (!skip) {
-          if (pass == 0) c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
-          else c3_rmse_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, ksum, kcomp);
+          if (pass == 0) {
+            if (prm.mode == kGradient) c3_residual_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, CP);
+            c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
+          } else {
+            c3_rmse_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, ksum, kcomp);
+          }
         }
+      } else if (!skip && prm.mode == kGradient) {
+        // rows shorter than 32 samples: fill the buffer no TMA copy is using, zero-padded and swizzled
+        float4* xb = xbuf + (q_issue & 1) * buf_f4;
+        float* xf = reinterpret_cast<float*>(xb);
+        const int nx = g.n[0], rows = kc * g.n[1];
+        for (int e = tid; e < rows * kTmaRow; e += blockDim.x) {
+          const int r = e >> 5, i = e & 31;
+          const float v = i < nx ? X[((int64_t)k0 * g.n[1] + r) * nx + i] : 0.f;
+          xf[r * kTmaRow + (((i >> 2) ^ (r & 7)) << 2) + (i & 3)] = v;
+        }
+        __syncthreads();
+        c3_residual_slab_smem(L, sm, g, xb, k0, kc, CP);
+        c3_stage_x_smem<CP>(xb, sm + L.A[0], sm + L.Y1, rows);
       } else if (!skip) {
         c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
                               (g.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) &&
@@ -666,9 +705,11 @@ int contract3(mfa_ctx* ctx, ContractParams prm, cudaStream_t stream) {
     L = layout(ks);
   }
   if ((size_t)L.total * 4 > kMaxDynSmem) return MFA_ERR_CAPACITY;
+  if (prm.mode == kGradient && !tma) return MFA_ERR_UNSUPPORTED;
   CUtensorMap map;
   const int box_rows = ks * prm.maxN;
   const bool use_map = tma && make_row_map(&map, prm.x, prm.nslots, prm.slot_stride, box_rows);
+  if (!use_map && prm.mode == kGradient) return MFA_ERR_UNSUPPORTED;
   if (!use_map) L = c3_layout(prm.mode, CP, prm.maxC, prm.maxN, ks, rmse, 0);
   const int vec_ok = (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) && (prm.slot_stride % 4 == 0);
   if (!use_map && cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;

@@ -42,6 +42,18 @@ class View(ctypes.Structure):
                 ("vmin", ctypes.c_float), ("vmax", ctypes.c_float)]
 
 
+class FrameDesc(ctypes.Structure):
+    _fields_ = [("d_desc", ctypes.c_void_p), ("nblocks", ctypes.c_int32), ("d_list", ctypes.c_void_p),
+                ("list_capacity", ctypes.c_int32), ("d_count", ctypes.c_void_p), ("d_knots", ctypes.c_void_p),
+                ("knots_len", ctypes.c_int64), ("d_cps", ctypes.c_void_p), ("cps_len", ctypes.c_int64),
+                ("d_cache", ctypes.c_void_p), ("slot_stride_voxels", ctypes.c_int64), ("bounds", Bounds),
+                ("flags", ctypes.c_uint32), ("d_brick_table", ctypes.c_void_p), ("brick_dims", ctypes.c_int32 * 3),
+                ("brick_n", ctypes.c_int32), ("view", ctypes.c_void_p), ("d_tf", ctypes.c_void_p),
+                ("tf_n", ctypes.c_int32), ("d_image", ctypes.c_void_p)]
+
+
+FRAME_SORT_BY_COST, FRAME_RAYCAST = 1, 2
+
 DESC_DTYPE = np.dtype({"names": ["degree", "ncp", "nsamp", "slot", "knot_off", "cp_off"],
                        "formats": [("<i4", 3), ("<i4", 3), ("<i4", 3), "<i4", ("<i8", 3), "<i8"],
                        "offsets": [0, 12, 24, 36, 40, 64], "itemsize": 72})
@@ -50,7 +62,8 @@ assert ctypes.sizeof(BlockDesc) == DESC_DTYPE.itemsize == 72
 SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
            "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
-           "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc"]
+           "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
+           "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy"]
 
 
 def _load():
@@ -77,6 +90,9 @@ def _load():
         "mfa_encode_plan_destroy": (None, [P]),
         "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
         "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
+        "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
+        "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
+        "mfa_frame_graph_destroy": (None, [P]),
         "mfa_raycast": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
                                        ctypes.POINTER(View), P, I32, P, P]),
     }
@@ -302,3 +318,53 @@ def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, st
     vw = make_view(view)
     _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims), brick_n,
                            ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)), "mfa_raycast")
+
+
+class FrameGraph:
+    """mfa_frame_graph: one frame (cost ordering, decode of the visible list, brick table, ray cast)
+    captured as a CUDA graph. Write the visible ids into `list_buf` and their number into `count_buf`
+    (device int32 tensors) before each launch()."""
+
+    def __init__(self, ctx, blocks, list_buf, count_buf, cache, slot_stride, sort=True,
+                 table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None):
+        self.ctx = ctx
+        self._keep = [blocks, list_buf, count_buf, cache, table, tf, image]
+        cap = list_buf.numel()
+        _need(cache, cap * slot_stride * 4, "cache")
+        flags = FRAME_SORT_BY_COST if sort else 0
+        self._view = None
+        fd = FrameDesc()
+        fd.d_desc, fd.nblocks = _ptr(blocks.desc), blocks.n
+        fd.d_list, fd.list_capacity, fd.d_count = _ptr(list_buf), cap, _ptr(count_buf)
+        fd.d_knots, fd.knots_len = _ptr(blocks.knots), blocks.knots.numel()
+        fd.d_cps, fd.cps_len = _ptr(blocks.cps), blocks.cps.numel()
+        fd.d_cache, fd.slot_stride_voxels = _ptr(cache), slot_stride
+        fd.bounds = blocks.bounds
+        if view is not None:
+            flags |= FRAME_RAYCAST
+            _need(table, blocks.n, "table")
+            _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
+            self._view = make_view(view)
+            fd.d_brick_table = _ptr(table)
+            fd.brick_dims = (ctypes.c_int32 * 3)(*brick_dims)
+            fd.brick_n = brick_n
+            fd.view = ctypes.cast(ctypes.pointer(self._view), ctypes.c_void_p)
+            fd.d_tf, fd.tf_n, fd.d_image = _ptr(tf), tf.shape[0], _ptr(image)
+        fd.flags = flags
+        h = ctypes.c_void_p()
+        _check(lib.mfa_frame_graph_create(ctx.handle, ctypes.byref(h), ctypes.byref(fd)), "mfa_frame_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib.mfa_frame_graph_launch(self.handle, _stream(stream)), "mfa_frame_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib.mfa_frame_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

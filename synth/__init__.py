@@ -156,18 +156,63 @@ def gm_noise_field(N, seed, device="cpu", noise_amp=0.1, octaves=4, base_freq=4.
     return out
 
 
-def flame_field(N, seed, device="cpu", octaves=6, base_freq=4.0, front_voxels=2.0, chunk=32):
-    """Turbulence with a thin tanh front around the level set z = 0.4 + 0.15 T(x) (stand-in for Flame)."""
-    out = torch.empty((N, N, N), dtype=torch.float32, device=device)
+def flame_at(X, Y, Z, N, seed, octaves=6, base_freq=4.0, front_voxels=2.0):
+    """Flame stand-in at points (X, Y, Z) in [0, 1]^3 (torch tensors): turbulence T with a tanh front of
+    width front_voxels/(N-1) around the level set z = 0.4 + 0.15 T."""
     norm = sum(0.5 ** o for o in range(octaves))
     w = front_voxels / (N - 1)
+    T = fbm(X, Y, Z, seed, octaves, base_freq, absolute=True) / norm
+    phi = Z - 0.4 - 0.15 * T
+    front = 0.5 * (1.0 - torch.tanh(phi / w))
+    return 0.8 * front + 0.2 * T
+
+
+def flame_field(N, seed, device="cpu", octaves=6, base_freq=4.0, front_voxels=2.0, chunk=32):
+    """Turbulence with a thin tanh front around the level set z = 0.4 + 0.15 T(x) (stand-in for Flame), on N^3 nodes."""
+    out = torch.empty((N, N, N), dtype=torch.float32, device=device)
     for z0 in range(0, N, chunk):
         X, Y, Z = _node_coords(N, z0, min(N, z0 + chunk), device)
-        T = fbm(X, Y, Z, seed, octaves, base_freq, absolute=True) / norm
-        phi = Z - 0.4 - 0.15 * T
-        front = 0.5 * (1.0 - torch.tanh(phi / w))
-        out[z0:z0 + chunk] = 0.8 * front + 0.2 * T
+        out[z0:z0 + chunk] = flame_at(X, Y, Z, N, seed, octaves, base_freq, front_voxels)
     return out
+
+
+def greville_cps(field_at, Bdims, n, ncp, degree, device="cpu", max_points=1 << 24):
+    """Control points = a field evaluated at the Greville abscissae of each brick (clamped uniform knots).
+
+    field_at(X, Y, Z) takes global coordinates in [0, 1]^3 (node-centred on Bdims*n nodes per axis);
+    ncp[b] is the isotropic C of brick b (z-major ids). Returns a list of (C, C, C) float32 arrays."""
+    Bx, By, Bz = Bdims
+    N = (Bx * n, By * n, Bz * n)
+    out = [None] * len(ncp)
+    ids = np.arange(len(ncp))
+    for C in sorted(set(int(c) for c in ncp)):
+        xi = torch.as_tensor(greville(clamped_uniform_knots(C, degree), degree), dtype=torch.float64, device=device)
+        sel = ids[np.asarray(ncp) == C]
+        per = C ** 3
+        step = max(1, max_points // per)
+        for s0 in range(0, len(sel), step):
+            bb = torch.as_tensor(sel[s0:s0 + step], device=device)
+            bz, by, bx = bb // (Bx * By), (bb // Bx) % By, bb % Bx
+            Zl, Yl, Xl = torch.meshgrid(xi, xi, xi, indexing="ij")
+            gx = (bx[:, None, None, None] * n + Xl[None] * (n - 1)) / (N[0] - 1)
+            gy = (by[:, None, None, None] * n + Yl[None] * (n - 1)) / (N[1] - 1)
+            gz = (bz[:, None, None, None] * n + Zl[None] * (n - 1)) / (N[2] - 1)
+            vals = field_at(gx.float(), gy.float(), gz.float()).cpu().numpy().astype(np.float32)
+            for m, b in enumerate(sel[s0:s0 + step]):
+                out[b] = vals[m]
+    return out
+
+
+def fov_for_visible(target, bricks_per_axis, frame=0, lo=5.0, hi=120.0, iters=30, **kw):
+    """Field of view (degrees) for which about `target` bricks are visible in orbit frame `frame`."""
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        nvis = len(visible_bricks(orbit_view(frame, fov_y_deg=mid, **kw), bricks_per_axis))
+        if nvis < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
 
 
 def marschner_lobb(x, y, z, f_m=6.0, alpha=0.05):

@@ -1,0 +1,152 @@
+"""Per-frame decode + ray cast replayed from a CUDA graph (mfa_frame_graph), and the decode autotuner.
+
+Adaptive NCP per block comes from the gradient energy of a flame-like field (classes by energy
+percentile); control points are that field at each block's Greville abscissae (inputs from `synth`).
+Each frame writes its visible list and count into device buffers and replays the same graph.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import TOL_FP32, rel_errors
+from oracle import decode as odec
+from oracle import raycast as ocast
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    from paper_2409_00184_b300 import mfa as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mfa):
+    c = mfa.Context(0)
+    yield c
+    c.close()
+
+
+def flame_blockset(N, n, classes, percentiles, p, seed, device):
+    field = synth.flame_field(N, seed, device=device)
+    blocks = synth.blocks_from_field(field, n)
+    ncp = synth.ncp_by_energy(synth.gradient_energy(blocks), classes, percentiles)
+    del field, blocks
+    B = N // n
+    cps = synth.greville_cps(lambda X, Y, Z: synth.flame_at(X, Y, Z, N, seed), (B, B, B), n, ncp, p, device=device)
+    bs = synth.make_block_set([(c, c, c) for c in ncp], [(p, p, p)] * len(ncp), [(n, n, n)] * len(ncp), cps)
+    return bs, B
+
+
+def _frame_buffers(capacity, nblocks, n, img, device="cuda"):
+    return (torch.zeros(capacity, dtype=torch.int32, device=device), torch.zeros(1, dtype=torch.int32, device=device),
+            torch.full((capacity * n ** 3 * 4,), float("nan"), device=device),
+            torch.zeros(nblocks, dtype=torch.int32, device=device),
+            torch.zeros(img[1], img[0], 4, device=device))
+
+
+def test_frames_reduced_config3(mfa, ctx):
+    """128^3 flame field, 512 bricks of 16^3, C in {4, 6, 8, 12}; two orbit frames through one graph."""
+    N, n, p = 128, 16, 2
+    bs, B = flame_blockset(N, n, (4, 6, 8, 12), (50, 75, 90), p, synth.BASE_SEED + 3, "cpu")
+    blk = mfa.DeviceBlocks(bs)
+    fov = synth.fov_for_visible(110, B)
+    views = [synth.orbit_view(f, fov_y_deg=fov, width=48, height=40) for f in (0, 5)]
+    cap = 160
+    lst, cnt, cache, table, image = _frame_buffers(cap, len(bs), n, (48, 40))
+    tf = torch.from_numpy(synth.transfer_function(synth.BASE_SEED + 3)).cuda()
+    graphs = [mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True, table=table, brick_dims=(B, B, B),
+                             brick_n=n, view=v, tf=tf, image=image) for v in views]
+    for v, g in zip(views, graphs):
+        vis = synth.visible_bricks(v, B)
+        assert 0 < len(vis) <= cap
+        lst[: len(vis)] = torch.from_numpy(vis).cuda()
+        cnt.fill_(len(vis))
+        g.launch()
+        assert ctx.device_status() == 0
+        order = lst[: len(vis)].cpu().numpy()
+        # the graph ordered the list by decreasing C, stably, and kept every visible id once
+        assert sorted(order.tolist()) == sorted(vis.tolist())
+        keys = bs.ncp[order].max(axis=1)
+        assert np.all(np.diff(keys) <= 0)
+        c = cache.view(cap, n ** 3, 4).cpu().numpy()
+        want_cache = np.zeros((cap, n, n, n, 4))
+        for m, b in enumerate(order):
+            want = odec.decode_block(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b])
+            ve, ge = rel_errors(c[m].reshape(n, n, n, 4), want)
+            assert ve <= TOL_FP32 and max(ge) <= TOL_FP32, (m, b, ve, ge)
+            want_cache[m] = want
+        tab = np.full(len(bs), -1, np.int32)
+        tab[order] = np.arange(len(order), dtype=np.int32)
+        assert np.array_equal(table.cpu().numpy(), tab)
+        # ray cast of the frame against the oracle's Algorithm 4 over the same FP32 cache
+        got = image.cpu().numpy()
+        want_img = ocast.raycast(c.reshape(cap, n, n, n, 4), tab.reshape(B, B, B), n, v, tf.cpu().numpy())
+        d = np.abs(got - want_img).max(axis=-1)
+        assert d.max() <= 1e-2 and (d <= 1e-4).mean() >= 0.999
+    for g in graphs:
+        g.close()
+
+
+def test_frames_full_config3_sampled(mfa, ctx):
+    """1024^3 flame field, 32768 bricks of 32^3, C in {4..24} by gradient energy, ~6000 visible per frame."""
+    N, n, p = 1024, 32, 2
+    bs, B = flame_blockset(N, n, synth.FLAME_NCP_CLASSES, synth.FLAME_NCP_PERCENTILES, p, synth.BASE_SEED + 3, "cuda")
+    torch.cuda.empty_cache()
+    blk = mfa.DeviceBlocks(bs)
+    fov = synth.fov_for_visible(6000, B)
+    cap = 6400
+    lst = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cache = torch.empty(cap * n ** 3 * 4, device="cuda")
+    g = mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True)
+    rng = synth.rng(17)
+    for frame in (0, 7):
+        vis = synth.visible_bricks(synth.orbit_view(frame, fov_y_deg=fov), B)
+        assert 5700 <= len(vis) <= cap
+        lst[: len(vis)] = torch.from_numpy(vis).cuda()
+        cnt.fill_(len(vis))
+        g.launch()
+        assert ctx.device_status() == 0
+        order = lst[: len(vis)].cpu().numpy()
+        assert sorted(order.tolist()) == sorted(vis.tolist())
+        assert np.all(np.diff(bs.ncp[order].max(axis=1)) <= 0)
+        c = cache.view(cap, n ** 3, 4)
+        got, want = [], []
+        for m in rng.choice(len(order), 48, replace=False):
+            b = order[m]
+            kji = rng.integers(0, n, size=(300, 3))
+            lin = torch.as_tensor((kji[:, 0] * n + kji[:, 1]) * n + kji[:, 2], device="cuda")
+            got.append(c[m][lin].cpu().numpy())
+            want.append(odec.decode_voxels(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b], kji))
+        ve, ge = rel_errors(np.concatenate(got), np.concatenate(want))
+        assert ve <= TOL_FP32 and max(ge) <= TOL_FP32, (frame, ve, ge)
+    g.close()
+
+
+def test_autotuner_installs_a_tiling_and_keeps_parity(mfa, ctx, tmp_path):
+    from paper_2409_00184_b300 import autotune
+    bs = synth.random_block_set(64, 401, ncp_choices=(6, 8, 12), nsamp_choices=(16, 32), degree_choices=(2,))
+    blk = mfa.DeviceBlocks(bs)
+    cache = torch.zeros(blk.nslots * blk.slot_voxels * 4, device="cuda")
+    res = autotune.tune_decode(ctx, blk, cache, blk.slot_voxels, blk.nslots, ks_candidates=(2, 8),
+                               cta_candidates=(0, 2), iters=2, warmup=1)
+    assert ctx.get_decode_tiling(blk.bounds) == (res["ks"], res["ctas_per_sm"])
+    assert len(res["table"]) == 4
+    path = tmp_path / "tune.json"
+    autotune.save(path, [res])
+    ctx.set_decode_tiling(blk.bounds, 0, 0)
+    autotune.load(path, ctx)
+    assert ctx.get_decode_tiling(blk.bounds) == (res["ks"], res["ctas_per_sm"])
+    cache.fill_(float("nan"))
+    mfa.decode_blocks(ctx, blk, cache, blk.slot_voxels, blk.nslots)
+    assert ctx.device_status() == 0
+    c = cache.view(blk.nslots, blk.slot_voxels, 4).cpu().numpy()
+    for b in range(0, len(bs), 7):
+        nx, ny, nz = bs.nsamp[b]
+        want = odec.decode_block(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b])
+        ve, ge = rel_errors(c[bs.slot[b], : nx * ny * nz].reshape(nz, ny, nx, 4), want)
+        assert ve <= TOL_FP32 and max(ge) <= TOL_FP32
