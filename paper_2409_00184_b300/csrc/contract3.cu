@@ -225,49 +225,50 @@ __device__ void c3_stage_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0,
   float* Y = sm + L.Y;
   const float* Ay = sm + L.A[1];
   const float* Az = sm + L.A[2];
-  // y: Y2[kl][b][a] = sum_j Y1[(kl, j)][a] Ay[j][b], 4 values of b per thread
-  const int nb4 = (Cy + 3) / 4;
-  for (int e = tid; e < kc * nb4 * Cx; e += nthr) {
-    const int a = e % Cx, t = e / Cx, b4 = t % nb4, kl = t / nb4;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  // y: thread per (kl, a), every b in registers: Y2[kl][b][a] = sum_j Y1[(kl, j)][a] Ay[j][b]
+  for (int e = tid; e < kc * Cx; e += nthr) {
+    const int kl = e / Cx, a = e - kl * Cx;
+    float acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
     const float* y1 = Y1 + kl * ny * CPs + a;
-#pragma unroll 4
     for (int j = 0; j < ny; ++j) {
       const float yv = y1[j * CPs];
-      const float4 w = *reinterpret_cast<const float4*>(Ay + j * CP + 4 * b4);
-      acc.x = fmaf(yv, w.x, acc.x);
-      acc.y = fmaf(yv, w.y, acc.y);
-      acc.z = fmaf(yv, w.z, acc.z);
-      acc.w = fmaf(yv, w.w, acc.w);
-    }
-    const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+      const float4* ar = reinterpret_cast<const float4*>(Ay + j * CP);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int bb = 4 * b4 + q;
-      if (bb < Cy) Y2[(kl * Cy + bb) * Cx + a] = av[q];
+      for (int c4 = 0; c4 < CP / 4; ++c4) {
+        const float4 w = ar[c4];
+        acc[4 * c4 + 0] = fmaf(yv, w.x, acc[4 * c4 + 0]);
+        acc[4 * c4 + 1] = fmaf(yv, w.y, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = fmaf(yv, w.z, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = fmaf(yv, w.w, acc[4 * c4 + 3]);
+      }
     }
+#pragma unroll
+    for (int bb = 0; bb < CP; ++bb)
+      if (bb < Cy) Y2[(kl * Cy + bb) * Cx + a] = acc[bb];
   }
   __syncthreads();
-  // z: Y[c][b][a] += sum_kl Y2[kl][b][a] Az[k0 + kl][c], 4 values of c per thread
-  const int nc4 = (Cz + 3) / 4;
-  for (int e = tid; e < nc4 * plane; e += nthr) {
-    const int ab = e % plane, c4 = e / plane;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
+  // z: thread per (b, a), every c in registers: Y[c][b][a] += sum_kl Y2[kl][b][a] Az[k0 + kl][c]
+  for (int ab = tid; ab < plane; ab += nthr) {
+    float acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
     for (int kl = 0; kl < kc; ++kl) {
       const float yv = Y2[kl * plane + ab];
-      const float4 w = *reinterpret_cast<const float4*>(Az + (k0 + kl) * CP + 4 * c4);
-      acc.x = fmaf(yv, w.x, acc.x);
-      acc.y = fmaf(yv, w.y, acc.y);
-      acc.z = fmaf(yv, w.z, acc.z);
-      acc.w = fmaf(yv, w.w, acc.w);
-    }
-    const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+      const float4* ar = reinterpret_cast<const float4*>(Az + (k0 + kl) * CP);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = 4 * c4 + q;
-      if (c < Cz) Y[c * plane + ab] += av[q];
+      for (int c4 = 0; c4 < CP / 4; ++c4) {
+        const float4 w = ar[c4];
+        acc[4 * c4 + 0] = fmaf(yv, w.x, acc[4 * c4 + 0]);
+        acc[4 * c4 + 1] = fmaf(yv, w.y, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = fmaf(yv, w.z, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = fmaf(yv, w.w, acc[4 * c4 + 3]);
+      }
     }
+#pragma unroll
+    for (int c = 0; c < CP; ++c)
+      if (c < Cz) Y[c * plane + ab] += acc[c];
   }
   __syncthreads();
 }
@@ -300,7 +301,7 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
       const int kl = e / plane, ab = e - kl * plane;
       const TabEntry te = tz[k0 + kl];
       float acc = 0.f;
-      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
       Y2[e] = acc;
     }
     __syncthreads();
@@ -308,7 +309,7 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
       const int a = e % Cx, r = e / Cx, j = r % ny, kl = r / ny;
       const TabEntry te = ty[j];
       float acc = 0.f;
-      for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
       Y1[e] = acc;
     }
     __syncthreads();
@@ -316,7 +317,7 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
       const int i = e % nx, r = e / nx;
       const TabEntry te = tx[i];
       float f = 0.f;
-      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
       const float diff = f - __ldg(X + (int64_t)k0 * nx * ny + e);
       const float y = diff * diff - kcomp;
       const float t = ksum + y;
@@ -352,31 +353,22 @@ __device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& 
   const float* Ax = sm + L.A[0];
   const float* Ay = sm + L.A[1];
   const float* Az = sm + L.A[2];
-  {  // stage z: Y2[kl][ab]
-    int kl = tid / plane, ab = tid - (tid / plane) * plane;
-    for (int e = tid; e < plane * kc; e += nthr) {
+  for (int ab = tid; ab < plane; ab += nthr) {  // stage z: thread per (b, a), all kl of the slab
+    for (int kl = 0; kl < kc; ++kl) {
       const int k = k0 + kl, o = oz[k];
       float acc = 0.f;
-      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(P[(o + d) * plane + ab], Az[k * CP + o + d], acc);
-      Y2[e] = acc;
-      ab += nthr;
-      while (ab >= plane) { ab -= plane; ++kl; }
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(P[(o + d) * plane + ab], Az[k * CP + o + d], acc);
+      Y2[kl * plane + ab] = acc;
     }
   }
   __syncthreads();
-  {  // stage y: Y1[(kl, j)][a]
-    const int step = nthr / Cx, gq = tid / Cx;
-    if (gq < step) {
-      const int a = tid - gq * Cx;
-      int kl = gq / ny, j = gq - (gq / ny) * ny;
-      for (int r = gq; r < kc * ny; r += step) {
-        const int o = oy[j];
-        float acc = 0.f;
-        for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + o + d) * Cx + a], Ay[j * CP + o + d], acc);
-        Y1[r * Cx + a] = acc;
-        j += step;
-        while (j >= ny) { j -= ny; ++kl; }
-      }
+  for (int e = tid; e < kc * Cx; e += nthr) {  // stage y: thread per (kl, a), all j
+    const int kl = e / Cx, a = e - kl * Cx;
+    for (int j = 0; j < ny; ++j) {
+      const int o = oy[j];
+      float acc = 0.f;
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) acc = fmaf(Y2[(kl * Cy + o + d) * Cx + a], Ay[j * CP + o + d], acc);
+      Y1[(kl * ny + j) * Cx + a] = acc;
     }
   }
   __syncthreads();
@@ -388,7 +380,7 @@ __device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& 
     float* xf = reinterpret_cast<float*>(xb);
     for (int r = r0; r < kc * ny; r += rstep) {
       float f = 0.f;
-      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + o + d], w[d], f);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(Y1[r * Cx + o + d], w[d], f);
       const int idx = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
       xf[idx] = f - xf[idx];
     }
@@ -410,31 +402,22 @@ __device__ void c3_rmse_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, c
   const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
   const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
   const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
-  {  // stage z: Y2[kl][ab]
-    int kl = tid / plane, ab = tid - (tid / plane) * plane;
-    for (int e = tid; e < plane * kc; e += nthr) {
+  for (int ab = tid; ab < plane; ab += nthr) {  // stage z: thread per (b, a), all kl of the slab
+    for (int kl = 0; kl < kc; ++kl) {
       const TabEntry te = tz[k0 + kl];
       float acc = 0.f;
-      for (int d = 0; d <= g.p[2]; ++d) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
-      Y2[e] = acc;
-      ab += nthr;
-      while (ab >= plane) { ab -= plane; ++kl; }
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
+      Y2[kl * plane + ab] = acc;
     }
   }
   __syncthreads();
-  {  // stage y: Y1[(kl, j)][a], thread keeps column a
-    const int step = nthr / Cx, gq = tid / Cx;
-    if (gq < step) {
-      const int a = tid - gq * Cx;
-      int kl = gq / ny, j = gq - (gq / ny) * ny;
-      for (int r = gq; r < kc * ny; r += step) {
-        const TabEntry te = ty[j];
-        float acc = 0.f;
-        for (int d = 0; d <= g.p[1]; ++d) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
-        Y1[r * Cx + a] = acc;
-        j += step;
-        while (j >= ny) { j -= ny; ++kl; }
-      }
+  for (int e = tid; e < kc * Cx; e += nthr) {  // stage y: thread per (kl, a), all j
+    const int kl = e / Cx, a = e - kl * Cx;
+    for (int j = 0; j < ny; ++j) {
+      const TabEntry te = ty[j];
+      float acc = 0.f;
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
+      Y1[(kl * ny + j) * Cx + a] = acc;
     }
   }
   __syncthreads();
@@ -443,7 +426,7 @@ __device__ void c3_rmse_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, c
     const TabEntry te = tx[i];
     for (int r = r0; r < kc * ny; r += rstep) {
       float f = 0.f;
-      for (int d = 0; d <= g.p[0]; ++d) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
       const float4 c4 = xb[r * 8 + ((i >> 2) ^ (r & 7))];
       const float dv = (i & 3) == 0 ? c4.x : ((i & 3) == 1 ? c4.y : ((i & 3) == 2 ? c4.z : c4.w));
       const float diff = f - dv;
