@@ -113,6 +113,12 @@ int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* strea
 /* Number of kernels this context launched since creation (all entry points). */
 int64_t mfa_ctx_launch_count(const mfa_ctx* ctx);
 
+/* Device statistics kept by the context (64-bit counters, summed over launches). */
+#define MFA_STAT_RAY_SAMPLES 0   /* samples marched by mfa_raycast (after early termination) */
+#define MFA_NUM_STATS        1
+/* Synchronises `stream` and copies the first `nstats` counters to stats[]; resets them if `reset`. */
+int mfa_ctx_read_stats(mfa_ctx* ctx, uint64_t* stats, int nstats, int reset, void* stream);
+
 /* Tile shape of the FP32 decode for one batch class: `ks` z-planes per work unit and at most
  * `ctas_per_sm` resident CTAs of the persistent grid (0 = library default for either field).
  * A context holds up to 64 entries keyed by (max_degree, max_ncp, max_nsamp) of the call's

@@ -16,6 +16,7 @@ struct mfa_ctx {
   int num_sms = 0;
   uint32_t* d_status = nullptr;   // device status word (MFA_DEV_* bits)
   uint32_t* d_counters = nullptr; // work-queue counters, one per concurrent launch kind
+  unsigned long long* d_stats = nullptr;  // device statistics (MFA_STAT_*)
   int64_t launches = 0;           // kernels enqueued through this context
   int ntilings = 0;
   mfa_tiling_entry tilings[64];   // decode tile shapes keyed by batch bounds (autotuner)

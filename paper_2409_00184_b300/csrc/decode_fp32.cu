@@ -264,7 +264,8 @@ static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const Decod
 int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaStream_t stream) {
   const int maxN = prm.bounds.max_nsamp, maxC = prm.bounds.max_ncp, pmax = prm.bounds.max_degree;
   const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
-  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : std::min(8, maxN);
+  // default slab depth from the tiling sweep on 32^3 blocks: 4 planes per unit
+  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : std::min(4, maxN);
   DecodeSmem L = decode_smem_layout(vo, maxC, maxN, ks);
   while ((size_t)L.total * 4 > kMaxDynSmem && ks > 1) {
     ks = std::max(1, ks / 2);

@@ -39,11 +39,14 @@ int mfa_ctx_create(mfa_ctx** out, int device) {
   c->num_sms = prop.multiProcessorCount;
   if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&c->d_counters, kNumCounters * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_stats, MFA_NUM_STATS * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->d_stats, 0, MFA_NUM_STATS * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(c->d_counters, 0, kNumCounters * sizeof(uint32_t)) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(c->d_status);
     cudaFree(c->d_counters);
+    cudaFree(c->d_stats);
     delete c;
     return MFA_ERR_CUDA;
   }
@@ -55,6 +58,7 @@ void mfa_ctx_destroy(mfa_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
+  cudaFree(ctx->d_stats);
   delete ctx;
 }
 
@@ -82,6 +86,17 @@ int mfa_ctx_device_status(mfa_ctx* ctx, uint32_t* status, int clear, void* strea
 }
 
 int64_t mfa_ctx_launch_count(const mfa_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int mfa_ctx_read_stats(mfa_ctx* ctx, uint64_t* stats, int nstats, int reset, void* stream) {
+  if (!ctx || !stats || nstats < 1 || nstats > MFA_NUM_STATS) return MFA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MFA_ERR_CUDA;
+  unsigned long long tmp[MFA_NUM_STATS];
+  if (cudaMemcpy(tmp, ctx->d_stats, sizeof(tmp), cudaMemcpyDeviceToHost) != cudaSuccess) return MFA_ERR_CUDA;
+  for (int i = 0; i < nstats; ++i) stats[i] = tmp[i];
+  if (reset && cudaMemset(ctx->d_stats, 0, sizeof(tmp)) != cudaSuccess) return MFA_ERR_CUDA;
+  return MFA_OK;
+}
 
 static bool same_key(const mfa_bounds& a, const mfa_bounds& b) {
   return a.max_degree == b.max_degree && a.max_ncp == b.max_ncp && a.max_nsamp == b.max_nsamp;
@@ -279,6 +294,7 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
   prm.shininess = view->shininess;
   prm.vmin = view->vmin;
   prm.vmax = view->vmax;
+  prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
   return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
 }
 

@@ -26,8 +26,10 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_kernel(RaycastParams
   __syncthreads();
   const int px = blockIdx.x * kTile + threadIdx.x;
   const int py = blockIdx.y * kTile + threadIdx.y;
-  if (px >= prm.W || py >= prm.H) return;
+  const bool inside = px < prm.W && py < prm.H;
 
+  int marched = 0;
+  if (inside) {
   // ---- FP32 ray set-up, every operation rounded on its own ----
   const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * px + 1), (float)prm.W), 1.0f), prm.tan_w);
   const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn((float)(2 * py + 1), (float)prm.H)), prm.tan_h);
@@ -139,9 +141,15 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_kernel(RaycastParams
     cg = fmaf(w, fmaf(rgba.y, shade, spec), cg);
     cb = fmaf(w, fmaf(rgba.z, shade, spec), cb);
     A += w;
-    if (A > prm.opacity_max) break;
+    if (A > prm.opacity_max) { marched = k + 1; break; }
+    marched = k + 1;
   }
   prm.image[(int64_t)py * prm.W + px] = make_float4(cr, cg, cb, A);
+  }
+  // marched-sample count for the roofline: warp sum, one atomic per warp
+  unsigned long long m = (unsigned long long)marched;
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if ((threadIdx.x & 31) == 0 && prm.samples) atomicAdd(prm.samples, m);
 }
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {

@@ -63,7 +63,8 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
-           "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy"]
+           "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
+           "mfa_ctx_read_stats"]
 
 
 def _load():
@@ -93,6 +94,7 @@ def _load():
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
+        "mfa_ctx_read_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int, P]),
         "mfa_raycast": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
                                        ctypes.POINTER(View), P, I32, P, P]),
     }
@@ -173,6 +175,12 @@ class Context:
 
     def launch_count(self):
         return int(lib.mfa_ctx_launch_count(self.handle))
+
+    def ray_samples(self, reset=True, stream=None):
+        """Samples marched by mfa_raycast since the last reset (synchronises the stream)."""
+        v = (ctypes.c_uint64 * 1)()
+        _check(lib.mfa_ctx_read_stats(self.handle, v, 1, int(reset), _stream(stream)), "mfa_ctx_read_stats")
+        return int(v[0])
 
     def set_decode_tiling(self, bounds, ks=0, ctas_per_sm=0):
         _check(lib.mfa_ctx_set_decode_tiling(self.handle, ctypes.byref(bounds),
