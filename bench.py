@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--workload", choices=["step", "frames", "gd"], default="step",
+    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision"], default="step",
                     help="step: the default 512^3 step; frames: adaptive-NCP frames replayed from a CUDA graph "
-                         "(1024^3, ~6000 visible blocks); gd: gradient-descent fit (256^3, 512 blocks)")
+                         "(1024^3, ~6000 visible blocks); gd: gradient-descent fit (256^3, 512 blocks); "
+                         "precision: degree-3 decode in FP32 / split-BF16 / BF16 / FP16 with errors")
     return ap.parse_args()
 
 
@@ -394,6 +395,86 @@ def run_gd(args):
     return 0
 
 
+def run_precision(args):
+    """Decode precision table: the 512^3 field of the default step at degree 3, 12^3 control points, decoded
+    by the FP32 banded kernel and by the tensor-core kernel in split-BF16, BF16 and FP16. Each variant is
+    timed over K launches (cache 2.15 GB, larger than L2) and checked against the FP64 oracle's decode of
+    the same FP32 control points on sampled voxels."""
+    from oracle import decode as odec
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    seed, p = synth.BASE_SEED + 2, 3
+    B, vox = (N_FIELD // BRICK) ** 3, BRICK ** 3
+    field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+    D = synth.blocks_from_field(field, BRICK).contiguous().view(-1)
+    del field
+    zero = np.zeros((NCP, NCP, NCP))
+    bs = synth.make_block_set([(NCP,) * 3] * B, [(p,) * 3] * B, [(BRICK,) * 3] * B, [zero] * B)
+    blk = mfa.DeviceBlocks(bs)
+    plan = mfa.EncodePlan(ctx, blk)
+    mfa.encode_blocks(ctx, plan, D, vox, B, blk.cps)
+    del D
+    cache = torch.empty(B * vox * 4, device="cuda")
+    stream = torch.cuda.current_stream()
+    g = synth.rng(seed + 7)
+    pick = g.choice(B, 12, replace=False)
+    kji = g.integers(0, BRICK, size=(400, 3))
+    lin = torch.as_tensor((kji[:, 0] * BRICK + kji[:, 1]) * BRICK + kji[:, 2], device="cuda")
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, p)).astype(np.float64) for _ in range(3))
+    cps = blk.cps.view(B, NCP ** 3)
+    want = np.concatenate([odec.decode_voxels(cps[b].double().cpu().numpy().reshape((NCP,) * 3), knots, (p,) * 3,
+                                              (BRICK,) * 3, kji) for b in pick])
+    vr, gm = want[:, 0].max() - want[:, 0].min(), np.abs(want[:, 1:]).max()
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    algo = B * (vox * 16 + NCP ** 3 * 4 + 72)
+    K = args.steps
+    variants = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    n0 = ctx.launch_count()
+    for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16),
+                       ("fp16", mfa.PREC_FP16)):
+        for _ in range(max(3, args.warmup)):
+            mfa.decode_blocks(ctx, blk, cache, vox, B, precision=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            mfa.decode_blocks(ctx, blk, cache, vox, B, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        if ctx.device_status():
+            raise RuntimeError(f"device status after the {name} decode")
+        c4 = cache.view(B, vox, 4)
+        got = np.concatenate([c4[int(b)][lin].double().cpu().numpy() for b in pick])
+        variants[name] = {"ms": ms, "Gvoxel_s": B * vox / (ms * 1e-3) / 1e9, "GB_s": algo / (ms * 1e-3) / 1e9,
+                          "hbm_frac": algo / (ms * 1e-3) / 1e9 / hbm,
+                          "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
+                          "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm)}
+    launches = ctx.launch_count() - n0
+    clk = clocks.stop()
+    sp = variants["split_bf16"]
+    line = {"metric": "Gvoxel/s MFA decode (value+grad) per precision, max err vs FP64 oracle",
+            "value": sp["Gvoxel_s"], "unit": "Gvoxel/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup),
+            "ms_per_step": sp["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3 (split) / f32 accumulate", "data": "synthetic",
+            "config": {"workload": "512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degree 3, 12^3 "
+                                   "control points (library LS fit); value+gradient decode per precision",
+                       "l2": "cache 2.15 GB, larger than L2; no flush",
+                       "error_sample": "12 blocks x 400 voxels; value: max|df|/range(f), grad: max|dg|/max|g|"},
+            "roofline": {"kernel": "decode_tc (split-BF16)", "bound": "hbm", "achieved": sp["GB_s"], "peak": hbm,
+                         "unit": "GB/s", "frac": sp["hbm_frac"], "traffic": None,
+                         "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"},
+            "variants": variants, "split_vs_fp32_speedup": variants["fp32"]["ms"] / sp["ms"],
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -403,6 +484,8 @@ def main():
         return run_frames(args) if rank == 0 else 0
     if args.workload == "gd":
         return run_gd(args) if rank == 0 else 0
+    if args.workload == "precision":
+        return run_precision(args) if rank == 0 else 0
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist

@@ -153,7 +153,6 @@ int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblock
   if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_cps, 4) || !aligned(d_cache, 16) ||
       (d_list && !aligned(d_list, 4)) || (d_count && !aligned(d_count, 4)))
     return MFA_ERR_INVALID_ARG;
-  if (precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
   // work units (item x z-slab) are counted by a 32-bit queue counter
   if ((int64_t)items * MFA_MAX_NSAMP >= (int64_t)1 << 30) return MFA_ERR_CAPACITY;
   DecodeParams prm;
@@ -175,6 +174,7 @@ int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblock
   prm.counter = ctx->d_counters + kDecodeQueue;
   prm.ks = 0;
   prm.slabs = 0;
+  if (precision != MFA_PREC_FP32) return decode_tc(ctx, prm, precision, static_cast<cudaStream_t>(stream));
   DecodeTuning tune;
   mfa_decode_tiling t;
   if (mfa_ctx_get_decode_tiling(ctx, bounds, &t) == MFA_OK) {

@@ -1,0 +1,118 @@
+"""Tensor-core decode (tcgen05) in BF16, FP16 and split-BF16 against the FP64 oracle.
+
+Tolerances (relative to the value range / the largest gradient component, per precision): split-BF16
+1e-4, plain BF16 1e-2, FP16 1e-2. Errors of each variant are printed for the record.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import gm_blocks_fitted, oracle_decode_set, rel_errors
+from oracle import decode as odec
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"split": 1e-4, "bf16": 1e-2, "fp16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    from paper_2409_00184_b300 import mfa as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mfa):
+    c = mfa.Context(0)
+    yield c
+    c.close()
+
+
+def _prec(mfa, name):
+    return {"split": mfa.PREC_SPLIT_BF16, "bf16": mfa.PREC_BF16, "fp16": mfa.PREC_FP16}[name]
+
+
+def _decode(mfa, ctx, bs, precision, **kw):
+    blk = mfa.DeviceBlocks(bs)
+    cache = torch.full((blk.nslots * blk.slot_voxels * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, cache, blk.slot_voxels, blk.nslots, precision=precision, **kw)
+    return cache.view(blk.nslots, blk.slot_voxels, 4).cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
+@pytest.mark.parametrize("degree", [2, 3])
+def test_tensor_core_decode_fitted_blocks(mfa, ctx, name, degree):
+    """64 fitted blocks of 32^3 (Gaussian mixture + noise, C = 12)."""
+    bs, _ = gm_blocks_fitted(128, 32, 12, degree, synth.BASE_SEED + 4)
+    got = _decode(mfa, ctx, bs, _prec(mfa, name))
+    assert ctx.device_status() == 0
+    want = np.stack(oracle_decode_set(bs))
+    ve, ge = rel_errors(got.reshape(len(bs), 32, 32, 32, 4), want)
+    print(f"{name} degree {degree}: value {ve:.2e}, gradient {max(ge):.2e}")
+    assert ve <= TOL[name] and max(ge) <= TOL[name], (ve, ge)
+
+
+@pytest.mark.parametrize("name", ["split", "bf16"])
+def test_tensor_core_decode_mixed_shapes(mfa, ctx, name):
+    """Anisotropic C in 2..16, degrees 1..3, non-uniform knots, all with 32 samples per axis."""
+    bs = synth.random_block_set(20, 601, ncp_choices=(2, 3, 4, 7, 12, 16), degree_choices=(1, 2, 3),
+                                nsamp_choices=(32,), nonuniform=True)
+    got = _decode(mfa, ctx, bs, _prec(mfa, name))
+    assert ctx.device_status() == 0
+    want = oracle_decode_set(bs)
+    for b in range(len(bs)):
+        ve, ge = rel_errors(got[bs.slot[b]].reshape(32, 32, 32, 4), want[b])
+        assert ve <= TOL[name] and max(ge) <= TOL[name], (b, ve, ge)
+
+
+def test_tensor_core_list_slots_and_shape_checks(mfa, ctx):
+    bs = synth.random_block_set(8, 602, ncp_choices=(6, 8), nsamp_choices=(32,), degree_choices=(2,))
+    blk = mfa.DeviceBlocks(bs)
+    order = torch.tensor([6, 1, 3], dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([2], dtype=torch.int32, device="cuda")
+    cache = torch.full((3 * 32 ** 3 * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, cache, 32 ** 3, 3, precision=mfa.PREC_SPLIT_BF16, list_=order, count=cnt,
+                      flags=mfa.DECODE_LIST_SLOTS)
+    assert ctx.device_status() == 0
+    c = cache.view(3, 32 ** 3, 4).cpu().numpy()
+    for m, b in enumerate([6, 1]):
+        ve, ge = rel_errors(c[m].reshape(32, 32, 32, 4), oracle_decode_set(bs, [b])[0])
+        assert ve <= 1e-4 and max(ge) <= 1e-4
+    assert np.all(np.isnan(c[2]))
+    # shapes outside the tensor-core path: host refusal, or a per-block device flag
+    small = synth.random_block_set(2, 603, ncp_choices=(4,), nsamp_choices=(16,), degree_choices=(2,))
+    sblk = mfa.DeviceBlocks(small)
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.decode_blocks(ctx, sblk, torch.zeros(2 * 16 ** 3 * 4, device="cuda"), 16 ** 3, 2,
+                          precision=mfa.PREC_BF16)
+    assert e.value.code == mfa.ERR_UNSUPPORTED
+    mixed = synth.random_block_set(2, 604, ncp_choices=(4,), nsamp_choices=(16,), degree_choices=(2,))
+    mixed.nsamp[1] = 32
+    mblk = mfa.DeviceBlocks(mixed)
+    mfa.decode_blocks(ctx, mblk, torch.zeros(2 * mblk.slot_voxels * 4, device="cuda"), mblk.slot_voxels, 2,
+                      precision=mfa.PREC_BF16)
+    assert ctx.device_status() & mfa.DEV_BAD_DESC
+
+
+def test_config4_full_size_sampled(mfa, ctx):
+    """Config 4: the 512^3 batch (4096 blocks, 12^3 control points) at degree 3, every precision, sampled
+    voxels against the oracle; prints max and RMS error of value and gradient per variant."""
+    bs, _ = gm_blocks_fitted(512, 32, 12, 3, synth.BASE_SEED + 4, device="cuda")
+    blk = mfa.DeviceBlocks(bs)
+    cache = torch.empty(blk.nslots * blk.slot_voxels * 4, device="cuda")
+    g = synth.rng(44)
+    picks = [(b, g.integers(0, 32, size=(300, 3))) for b in g.choice(len(bs), 64, replace=False)]
+    want = np.concatenate([odec.decode_voxels(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b], kji)
+                           for b, kji in picks])
+    for name, prec in [("fp32", mfa.PREC_FP32), ("split", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16),
+                       ("fp16", mfa.PREC_FP16)]:
+        mfa.decode_blocks(ctx, blk, cache, blk.slot_voxels, blk.nslots, precision=prec)
+        assert ctx.device_status() == 0
+        c = cache.view(blk.nslots, blk.slot_voxels, 4)
+        got = np.concatenate([c[b][torch.as_tensor((k[:, 0] * 32 + k[:, 1]) * 32 + k[:, 2], device="cuda")]
+                             .cpu().numpy() for b, k in picks])
+        ve, ge = rel_errors(got, want)
+        print(f"config 4 {name}: value {ve:.2e} gradient {max(ge):.2e}")
+        assert ve <= TOL.get(name, 1e-5) and max(ge) <= TOL.get(name, 1e-5), (name, ve, ge)
