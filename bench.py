@@ -315,6 +315,7 @@ def run_frames(args):
         raise RuntimeError("device status after warm-up")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(frames + 1)]
     n0 = ctx.launch_count()
+    ctx.ray_samples(reset=True)
     clocks = ClockSampler(0)
     clocks.start()
     ev[0].record(stream)
@@ -325,7 +326,22 @@ def run_frames(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = ctx.launch_count() - n0
+    samples = ctx.ray_samples(reset=True) / frames
     ms = [ev[f].elapsed_time(ev[f + 1]) for f in range(frames)]
+    # the same frames without the ray cast (ordering + decode only), for the per-stage split
+    dgraph = mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True)
+    for f in range(3):
+        dgraph.launch()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dms = 0.0
+    for f in range(frames):
+        lst.copy_(all_lists[f]); cnt.copy_(counts[f: f + 1])
+        d0.record(stream)
+        dgraph.launch()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dms += d0.elapsed_time(d1)
+    dms /= frames
     vox = sum(len(v) for v in lists) * n ** 3
     total = sum(ms)
     line = {"metric": METRIC, "value": vox / (total * 1e-3) / 1e9, "unit": "Gvoxel/s", "n_gpus": 1, "steps": frames,
@@ -335,6 +351,10 @@ def run_frames(args):
                                    "gradient energy, ~6000 visible per frame (32-frame orbit), cost-ordered persistent "
                                    "decode + 1024^2 ray cast replayed from a CUDA graph",
                        "visible_mean": float(np.mean([len(v) for v in lists])), "tiling": tune},
+            "stages": {"decode_ms_per_frame": dms, "raycast_ms_per_frame": total / frames - dms,
+                       "ray_samples_per_frame": samples,
+                       "raycast_Gsample_s": samples / ((total / frames - dms) * 1e-3) / 1e9,
+                       "raycast_TFLOP_s": samples * RAY_FLOPS_PER_SAMPLE / ((total / frames - dms) * 1e-3) / 1e12},
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
     return 0

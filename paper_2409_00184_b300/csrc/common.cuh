@@ -24,7 +24,7 @@ struct mfa_ctx {
 
 namespace mfa {
 
-enum Counter { kDecodeQueue = 0, kAdjointQueue = 1, kEncodeQueue = 2, kNumCounters = 4 };
+enum Counter { kDecodeQueue = 0, kAdjointQueue = 1, kEncodeQueue = 2, kRaycastQueue = 3, kNumCounters = 4 };
 
 // Validated per-block geometry, decoded from an mfa_block_desc inside a kernel.
 struct BlockGeom {

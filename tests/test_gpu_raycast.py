@@ -104,3 +104,44 @@ def test_raycast_argument_checks(mfa, ctx, volume):
     view = synth.default_view(width=8, height=8, vmin=1.0, vmax=1.0)
     with pytest.raises(mfa.MfaError):
         _run(mfa, ctx, cache, ident, n, view, tf)
+
+
+def _fitted_volume(N, n, seed):
+    bs, _ = gm_blocks_fitted(N, n, 8, 2, seed)
+    return np.stack(oracle_decode_set(bs)).astype(np.float32)
+
+
+def test_raycast_non_power_of_two_bricks(mfa, ctx):
+    """Bricks of 12^3 (per-pixel tile kernel) against the oracle, with absent bricks."""
+    n, nb = 12, 4
+    cache = _fitted_volume(nb * n, n, synth.BASE_SEED + 13)
+    _, _, holes = _tables(nb)
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=40, height=36, opacity_max=1.0)
+    ctx.ray_samples(reset=True)
+    got = _run(mfa, ctx, cache, holes, n, view, tf)
+    marched = ctx.ray_samples(reset=True)
+    want = ocast.raycast(cache, holes, n, view, tf)
+    _, _, _, K, _ = ocast.ray_setup(view, (nb * n,) * 3)
+    assert marched == int(np.asarray(K).sum())
+    assert np.max(np.abs(got - want)) <= 1e-4
+
+
+@pytest.mark.parametrize("wh", [(61, 37), (8, 4), (1, 1), (130, 3)])
+def test_raycast_queue_ragged_image_and_sample_count(mfa, ctx, wh):
+    """Bricks of 32^3 (persistent queue kernel), image sizes that are not multiples of the 8x4 warp tile.
+    Without early termination every pixel marches exactly the K samples of its FP32 set-up, so the
+    device's marched-sample counter equals the oracle's sum of K, and every pixel is written once."""
+    n = 32
+    cache = _fitted_volume(64, n, synth.BASE_SEED + 14)
+    ident, _, _ = _tables(2)
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=wh[0], height=wh[1], opacity_max=1.0)
+    ctx.ray_samples(reset=True)
+    got = _run(mfa, ctx, cache, ident, n, view, tf)
+    marched = ctx.ray_samples(reset=True)
+    want = ocast.raycast(cache, ident, n, view, tf)
+    _, _, _, K, _ = ocast.ray_setup(view, (2 * n,) * 3)
+    assert not np.isnan(got).any()
+    assert marched == int(np.asarray(K).sum())
+    assert np.max(np.abs(got - want)) <= 1e-4
