@@ -34,6 +34,7 @@ constexpr int kTmaRow = 32;  // samples per row on the TMA path (128 bytes)
 
 struct C3Smem {
   int A[3], off[3], tab[3], knots, Y1, Y2, Y, P, X, total;  // offsets in 4-byte words
+  int us;  // gradient: row stride of the decoded U rows kept in Y1 (odd: per-thread rows, no bank conflicts)
 };
 
 struct C3Geom {
@@ -49,11 +50,15 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xb
   C3Smem L;
   int o = 0;
   for (int a = 0; a < 3; ++a) { L.A[a] = o; o += maxN * CP; }
+  L.us = CP + 1;
   for (int a = 0; a < 3; ++a) { L.off[a] = o; if (mode == kGradient) o += maxN; }
-  for (int a = 0; a < 3; ++a) { L.tab[a] = o; if (mode == kFit && rmse) o += maxN * (int)(sizeof(TabEntry) / 4); }
+  for (int a = 0; a < 3; ++a) {
+    L.tab[a] = o;
+    if ((mode == kFit && rmse) || mode == kGradient) o += maxN * (int)(sizeof(TabEntry) / 4);
+  }
   L.knots = o; if (mode != kFit) o += 3 * kKnotMax;
   o = round4(o);
-  L.Y1 = o; o += ks * maxN * CPs;
+  L.Y1 = o; o += ks * maxN * (mode == kGradient ? std::max(CPs, L.us) : CPs);
   L.Y2 = o; o += round4(ks * maxC * maxC);
   L.Y = o;  o += round4(maxC * maxC * maxC);
   L.P = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
@@ -132,7 +137,13 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
       float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
       basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, u, N, dN);
       for (int r = 0; r <= g.p[a]; ++r) sm[L.A[a] + i * CP + s - g.p[a] + r] = N[r];
-      if (prm.mode == kGradient) reinterpret_cast<int*>(sm + L.off[a])[i] = s - g.p[a];
+      if (prm.mode == kGradient) {
+        reinterpret_cast<int*>(sm + L.off[a])[i] = s - g.p[a];
+        TabEntry te;  // band of sample i (N[r] is zero for r > p)
+        te.off = s - g.p[a];
+        for (int r = 0; r <= MFA_MAX_DEGREE; ++r) te.N[r] = N[r];
+        reinterpret_cast<TabEntry*>(sm + L.tab[a])[i] = te;
+      }
     }
   }
   __syncthreads();
@@ -337,52 +348,58 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
   }
 }
 
-// Gradient mode: replaces the slab's samples D in the swizzled buffer by r = decode_value(P) - D
-// (banded value decode with the dense collocation rows A and the span offsets).
-__device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, float4* xb, int k0, int kc,
-                                      int CP) {
+// Gradient mode: replaces the slab's samples D in the swizzled buffer by r = decode_value(P) - D.
+// Banded value decode: stage z of P for the slab (-> Y2 = T[kl][b][a]), then thread per sample row
+// r = (kl, j): U[a] = sum_d T[kl][o_j + d][a] N_y[j][d] into the row's scratch in Y1, and
+// f_i = sum_d U[o_i + d] N_x[i][d] through a window u_0..u_3 = U[oc .. oc+3] that slides with the band.
+__device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, float4* xb, int k0, int kc) {
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int Cx = g.C[0], Cy = g.C[1], ny = g.n[1];
+  const int Cx = g.C[0], Cy = g.C[1], nx = g.n[0], ny = g.n[1];
   const int plane = Cx * Cy;
   const float* P = sm + L.P;
-  float* Y1 = sm + L.Y1;
   float* Y2 = sm + L.Y2;
-  const int* ox = reinterpret_cast<const int*>(sm + L.off[0]);
-  const int* oy = reinterpret_cast<const int*>(sm + L.off[1]);
-  const int* oz = reinterpret_cast<const int*>(sm + L.off[2]);
-  const float* Ax = sm + L.A[0];
-  const float* Ay = sm + L.A[1];
-  const float* Az = sm + L.A[2];
-  for (int ab = tid; ab < plane; ab += nthr) {  // stage z: thread per (b, a), all kl of the slab
+  const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
+  const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
+  const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
+  for (int ab = tid; ab < plane; ab += nthr)  // stage z: thread per (b, a), all kl of the slab
     for (int kl = 0; kl < kc; ++kl) {
-      const int k = k0 + kl, o = oz[k];
+      const TabEntry te = tz[k0 + kl];
       float acc = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(P[(o + d) * plane + ab], Az[k * CP + o + d], acc);
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(P[(te.off + d) * plane + ab], te.N[d], acc);
       Y2[kl * plane + ab] = acc;
     }
-  }
   __syncthreads();
-  for (int e = tid; e < kc * Cx; e += nthr) {  // stage y: thread per (kl, a), all j
-    const int kl = e / Cx, a = e - kl * Cx;
-    for (int j = 0; j < ny; ++j) {
-      const int o = oy[j];
-      float acc = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) acc = fmaf(Y2[(kl * Cy + o + d) * Cx + a], Ay[j * CP + o + d], acc);
-      Y1[(kl * ny + j) * Cx + a] = acc;
+  for (int r = tid; r < kc * ny; r += nthr) {  // stages y and x, thread per row
+    const int kl = r / ny, j = r - kl * ny;
+    float* ur = sm + L.Y1 + r * L.us;
+    {
+      const TabEntry te = ty[j];
+      const float* tp = Y2 + (kl * Cy + te.off) * Cx;
+      for (int a = 0; a < Cx; ++a) {
+        float u = 0.f;
+        _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) u = fmaf(tp[d * Cx + a], te.N[d], u);
+        ur[a] = u;
+      }
     }
-  }
-  __syncthreads();
-  {  // stage x and r = f - D in place (32-sample rows, swizzled)
-    const int i = tid & 31, r0 = tid >> 5, rstep = nthr >> 5;
-    const int o = ox[i];
-    float w[MFA_MAX_DEGREE + 1];
-    for (int d = 0; d <= MFA_MAX_DEGREE; ++d) w[d] = d <= g.p[0] ? Ax[i * CP + o + d] : 0.f;
-    float* xf = reinterpret_cast<float*>(xb);
-    for (int r = r0; r < kc * ny; r += rstep) {
-      float f = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(Y1[r * Cx + o + d], w[d], f);
-      const int idx = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
-      xf[idx] = f - xf[idx];
+    float u0 = ur[0], u1 = Cx > 1 ? ur[1] : 0.f, u2 = Cx > 2 ? ur[2] : 0.f, u3 = Cx > 3 ? ur[3] : 0.f;
+    int oc = 0;
+    const int sw = r & 7;
+    for (int i4 = 0; i4 < nx; i4 += 4) {
+      float4* cp = xb + r * 8 + ((i4 >> 2) ^ sw);
+      float dd[4] = {cp->x, cp->y, cp->z, cp->w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (i4 + q < nx) {
+          const TabEntry te = tx[i4 + q];
+          while (oc < te.off) {
+            u0 = u1; u1 = u2; u2 = u3;
+            u3 = oc + 4 < Cx ? ur[oc + 4] : 0.f;
+            ++oc;
+          }
+          dd[q] = fmaf(te.N[0], u0, fmaf(te.N[1], u1, fmaf(te.N[2], u2, te.N[3] * u3))) - dd[q];
+        }
+      }
+      *cp = make_float4(dd[0], dd[1], dd[2], dd[3]);
     }
   }
   __syncthreads();
@@ -560,7 +577,7 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
         }
         if (!skip) {
           if (pass == 0) {
-            if (prm.mode == kGradient) c3_residual_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, CP);
+            if (prm.mode == kGradient) c3_residual_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc);
             c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
           } else {
             c3_rmse_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, ksum, kcomp);
@@ -577,7 +594,7 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
           xf[r * kTmaRow + (((i >> 2) ^ (r & 7)) << 2) + (i & 3)] = v;
         }
         __syncthreads();
-        c3_residual_slab_smem(L, sm, g, xb, k0, kc, CP);
+        c3_residual_slab_smem(L, sm, g, xb, k0, kc);
         c3_stage_x_smem<CP>(xb, sm + L.A[0], sm + L.Y1, rows);
       } else if (!skip) {
         c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
