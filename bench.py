@@ -40,12 +40,16 @@ WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degr
             "LS encode + value/gradient decode + 1024^2 ray cast (1 sample/voxel, 256-entry TF) + adjoint")
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by the
 # sha256 of the kernel source it was taken on; reported as null once the source changes.
-TRAFFIC = {}
+TRAFFIC = {"raycast": {"bytes": 395.87e6 + 17.94e6, "src_sha": "faeafe4f69898824"}}
 # FP32 operations per ray-cast sample in the algorithm (FMA = 2): sample position 14, trilinear
 # interpolation of 4 channels 87, transfer function 18, headlight shading 20, compositing 15.
 RAY_FLOPS_PER_SAMPLE = 154
 # FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# Bytes each ray-cast sample moves through L1: eight float4 corners and two float4 transfer-function
+# entries; the L1 data path moves at most 128 B per clock per SM.
+RAY_L1_BYTES_PER_SAMPLE = 160
+L1_PEAK_GBS = 148 * 128 * 2.032e9 / 1e9
 
 
 def parse():
@@ -57,10 +61,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision"], default="step",
+    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp"], default="step",
                     help="step: the default 512^3 step; frames: adaptive-NCP frames replayed from a CUDA graph "
                          "(1024^3, ~6000 visible blocks); gd: gradient-descent fit (256^3, 512 blocks); "
-                         "precision: degree-3 decode in FP32 / split-BF16 / BF16 / FP16 with errors")
+                         "precision: degree-3 decode in FP32 / split-BF16 / BF16 / FP16 with errors; "
+                         "ncp: Eq. 4 NCP search over every NCP in [3, 32] (512^3, 4096 blocks)")
     return ap.parse_args()
 
 
@@ -495,6 +500,52 @@ def run_precision(args):
     return 0
 
 
+def run_ncp(args):
+    """In-level adaptive encoding (Eq. 4) of the 512^3 field of the default step: every NCP in [3, 32] fitted
+    to the 4096 blocks of 32^3 (degree 2) with its RMSE, then the smallest NCP below the bound per block."""
+    from paper_2409_00184_b300 import adaptive, mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    seed, p, bound = synth.BASE_SEED + 2, DEGREE, 1e-5
+    B, vox = (N_FIELD // BRICK) ** 3, BRICK ** 3
+    field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+    D = synth.blocks_from_field(field, BRICK).contiguous().view(-1)
+    del field
+    cands = adaptive.candidate_ncps(p, BRICK)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        ncp, err = adaptive.search_ncp(ctx, D, BRICK, p, bound)
+    torch.cuda.synchronize()
+    K = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = ctx.launch_count()
+    e0.record(stream)
+    for _ in range(K):
+        ncp, err = adaptive.search_ncp(ctx, D, BRICK, p, bound)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    if ctx.device_status():
+        raise RuntimeError("device status after the NCP search")
+    launches = (ctx.launch_count() - n0) // K
+    got = ncp.cpu().numpy()
+    hist = {int(c): int((got == c).sum()) for c in np.unique(got)}
+    chosen = np.where(got > 0, got, cands[-1])
+    model = sum(int(mfa.model_bytes(int(c), p)) for c in chosen)
+    line = {"metric": "Eq. 4 NCP search: Gvoxel/s of candidate fits (voxels x candidates / time)",
+            "value": B * vox * len(cands) / (ms * 1e-3) / 1e9, "unit": "Gvoxel/s", "n_gpus": 1, "steps": K,
+            "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 set-up and RMSE)", "data": "synthetic",
+            "config": {"workload": "512^3 Gaussian-mixture+noise field, 4096 blocks of 32^3, degree 2, every NCP in "
+                                   "[3, 32] fitted with its RMSE, Eq. 4 selection at RMSE < 1e-5",
+                       "candidates": len(cands), "bound": bound},
+            "ncp_histogram": hist, "no_candidate": int((got < 0).sum()),
+            "compression_ratio": B * vox * 4 / model, "gpu_launches_per_search": launches}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -506,6 +557,8 @@ def main():
         return run_gd(args) if rank == 0 else 0
     if args.workload == "precision":
         return run_precision(args) if rank == 0 else 0
+    if args.workload == "ncp":
+        return run_ncp(args) if rank == 0 else 0
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -567,6 +620,8 @@ def main():
     kernels["raycast"]["Gsample_s"] = samples_per_step / (per["raycast"] * 1e-3) / 1e9
     kernels["raycast"]["samples_per_frame"] = samples_per_step
     kernels["raycast"]["TFLOP_s"] = samples_per_step * RAY_FLOPS_PER_SAMPLE / (per["raycast"] * 1e-3) / 1e12
+    kernels["raycast"]["l1_GB_s"] = samples_per_step * RAY_L1_BYTES_PER_SAMPLE / (per["raycast"] * 1e-3) / 1e9
+    kernels["raycast"]["l1_frac"] = kernels["raycast"]["l1_GB_s"] / L1_PEAK_GBS
     dom = max(names, key=lambda n: per[n])
     src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "raycast": "raycast.cu", "adjoint": "contract3.cu"}[dom]
     tr = TRAFFIC.get(dom)

@@ -254,6 +254,20 @@ int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
                        float* d_cps_out, double* d_rmse /* nullable, one per block */,
                        void* stream);
 
+/* In-level adaptive encoding, Eq. 4 (Sec. 4.2.2): NCP* = the smallest NCP whose error is below the
+ * bound e. d_errors holds, candidate-major, one error per (candidate, block):
+ * d_errors[c*nblocks + b] = Error(h_ncp[c]) of block b, e.g. the RMSE that mfa_encode_blocks
+ * wrote for a batch fitted with h_ncp[c] control points per axis. For every block,
+ * d_ncp_out[b] = min { h_ncp[c] : d_errors[c*nblocks + b] < bound } over all candidates (the
+ * exhaustive search of Eq. 4, whatever the order of the candidates), or -1 when no candidate
+ * meets the bound; a NaN error never meets it. h_ncp (host, ncand entries) must be positive.
+ * Device buffers: d_errors (FP64, ncand*nblocks, 8-byte aligned), d_ncp_out (int32, nblocks).
+ * Returns MFA_ERR_INVALID_ARG for a null ctx or h_ncp, ncand < 1 or > 64, nblocks < 0, a
+ * non-positive candidate or a NaN bound, and (when nblocks > 0) null or misaligned device
+ * buffers; nblocks = 0 enqueues nothing and accepts null device buffers. */
+int mfa_select_ncp(mfa_ctx* ctx, const double* d_errors, int32_t ncand, const int32_t* h_ncp,
+                   int64_t nblocks, double bound, int32_t* d_ncp_out, void* stream);
+
 /* Allocation-free least-squares encode. The paper has no counterpart to this entry point: it
  * exists for callers that cannot call cudaMalloc - a process whose device memory is reserved
  * by another runtime's memory pool, so that a fresh allocation fails or has to wait for that

@@ -64,7 +64,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
-           "mfa_ctx_read_stats"]
+           "mfa_ctx_read_stats", "mfa_select_ncp"]
 
 
 def _load():
@@ -91,6 +91,7 @@ def _load():
         "mfa_encode_plan_destroy": (None, [P]),
         "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
         "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
+        "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
@@ -308,6 +309,23 @@ def encode_blocks_noalloc(blocks, data, slot_stride, nslots, cps_out, rmse=None,
     if rc == ERR_CAPACITY:
         raise MfaError(rc, "mfa_encode_blocks_noalloc: the batch's tables exceed the fixed 2 MiB scratch")
     _check(rc, "mfa_encode_blocks_noalloc")
+
+
+def select_ncp(ctx, errors, ncps, bound, out=None, stream=None):
+    """mfa_select_ncp (Eq. 4): errors is a float64 CUDA tensor (len(ncps), nblocks), candidate-major; returns
+    (or fills) an int32 CUDA tensor with, per block, the smallest candidate NCP whose error is below `bound`,
+    or -1."""
+    ncand = len(ncps)
+    if errors.dtype != torch.float64 or errors.dim() != 2 or errors.shape[0] != ncand:
+        raise ValueError("errors: float64 tensor of shape (len(ncps), nblocks)")
+    nb = errors.shape[1]
+    if out is None:
+        out = torch.empty(nb, dtype=torch.int32, device=errors.device)
+    _need(out, nb, "out")
+    h = (ctypes.c_int32 * ncand)(*[int(c) for c in ncps])
+    _check(lib.mfa_select_ncp(ctx.handle, _ptr(errors), ncand, h, nb, float(bound), _ptr(out), _stream(stream)),
+           "mfa_select_ncp")
+    return out
 
 
 def make_view(v):
