@@ -2,9 +2,11 @@
 // (Sec. 4.2 model, Algorithm 4 value and gradient queries) as dense 16-bit MMAs with FP32 accumulation
 // in tensor memory, for BF16, FP16 and split-BF16 operands.
 //
-// Work unit = (block, slab of 8 z-planes) of a block with 32 samples and at most 16 control points per
-// axis (K = 16 per MMA); every index is padded to 16 and basis rows are written densely (zero outside
-// each band). Derivatives use the B-spline derivative identity: d/du sum_a N_{a,p}(u) c_a =
+// Work unit = one block with 32 samples and at most 16 control points per axis (K = 16 per MMA), taken
+// from an atomic queue and decoded in four slabs of 8 z-planes; every index is padded to 16 and basis
+// rows are written densely (zero outside each band). The stage-z operands (P and its differences) do
+// not depend on the slab and are built once per block. One kernel per precision; BF16 and FP16 keep no
+// "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns). Derivatives use the B-spline derivative identity: d/du sum_a N_{a,p}(u) c_a =
 // sum_a N_{a,p-1}(u) q_a with q_a = p (c_{a+1} - c_a) / (t_{a+p+1} - t_{a+1}) on the knots
 // t_1 .. t_{C+p-1}. The four outputs are four independent chains of mode products on the control points
 // P and their FP32 differences DxP, DyP, DzP, taken before any rounding: every 16-bit operand is then a
@@ -36,60 +38,71 @@ namespace {
 constexpr int kThreadsTC = 256;
 constexpr int kN = 32;       // samples per axis on this path
 constexpr int kK = 16;       // padded control points per axis (one MMA K step)
-constexpr int kKS = 8;       // z-planes per unit
+constexpr int kKS = 8;       // z-planes per slab
+constexpr int kSlabs = kN / kKS;
 constexpr int kRowBytes = 32;                  // one K-major operand row: 16 x 16-bit
 constexpr uint32_t kLBO = 128, kSBO = 256;     // core-matrix strides for K = 16
 constexpr int kTmemCols = 256;
 
 enum Prec { kBF16 = 0, kFP16 = 1, kSplit = 2 };
 
-// shared-memory layout (bytes); operands are stored hi then lo (lo used by split-BF16 only)
 constexpr int kOp256 = 256 * kRowBytes, kOp128 = 128 * kRowBytes, kOp64 = 64 * kRowBytes, kOp16 = 16 * kRowBytes;
 constexpr int kZRows = 224;                   // stage-y basis buffer: 96 zero rows, 32 basis rows, 96 zero rows
 constexpr int kOpZ = kZRows * kRowBytes;
-constexpr int kAz = 0;                        // stage z A: chains 0..3 (hi), then (lo): 8 x 8 KB
-constexpr int kAx = 0;                        //   alias after stage y: stage x A, same shape
-constexpr int kStage = 0;                     //   alias during the final readout: 8 warps x 4 KB
-constexpr int kBz = 8 * kOp256;               // B_z0 = [N_z | 0], B_z1 = [0 | N_z^(p-1)], B_z2 = [0 | N_z]
-constexpr int kTy = kBz + 6 * kOp16;          // stage y B: chains 0..3, rows (k,a), K = b (hi, then lo)
-constexpr int kZy = kTy + 8 * kOp128;         // stage y A: N_y and N_y^(p-1), zero-padded (hi, then lo)
-constexpr int kBx = kZy + 4 * kOpZ;           // stage x B: rows [N_x ; N_x^(p-1)] (hi, lo)
-constexpr int kP = kBx + 2 * kOp64;           // control points, FP32 (16^3)
-constexpr int kBasis = kP + kK * kK * kK * 4;  // per axis and sample: TcBasis (48 B)
-constexpr int kKnots = kBasis + 3 * kN * 48;
-constexpr int kDsc = kKnots + 3 * kKnotMax * 4;  // per axis: p / (t_{c+p+1} - t_{c+1})
-constexpr int kSmemTC = kDsc + 3 * kN * 4 + 1024;  // + slack for 1024-byte alignment
-static_assert(kStage + 8 * 32 * 128 <= kBz, "staging area overlaps the stage z B operands");
-static_assert(kSmemTC <= 227 * 1024, "shared memory budget");
+constexpr int kStageBytes = 8 * 32 * 128;     // readout staging: 8 warps x 32 rows x 8 float4
+constexpr int kPBytes = kK * kK * kK * 4;     // control points, FP32
 
-__device__ __forceinline__ uint16_t to16(float x, int prec) {
-  if (prec == kFP16) return __half_as_ushort(__float2half_rn(x));
+// Shared-memory layout (bytes) for one precision; every operand is stored hi, then (split-BF16 only) lo.
+template <int PREC>
+struct TcLayout {
+  static constexpr int NL = PREC == kSplit ? 2 : 1;
+  static constexpr int Az = 0;                             // stage z A: chains 0..3, per block
+  static constexpr int R1 = Az + 4 * kOp256 * NL;          // stage x A; aliases P (block set-up) and staging
+  static constexpr int R1Bytes = std::max(4 * kOp256 * NL, std::max(kPBytes, kStageBytes));
+  static constexpr int Bz = R1 + R1Bytes;                  // B_z0 = [N_z | 0], B_z1 = [0 | N_z^(p-1)], B_z2 = [0 | N_z]
+  static constexpr int Ty = Bz + 3 * kOp16 * NL;           // stage y B: chains 0..3, rows (k,a), K = b
+  static constexpr int Zy = Ty + 4 * kOp128 * NL;          // stage y A: N_y and N_y^(p-1), zero-padded
+  static constexpr int Bx = Zy + 2 * kOpZ * NL;            // stage x B: rows [N_x ; N_x^(p-1)]
+  static constexpr int Basis = Bx + kOp64 * NL;            // per axis and sample: TcBasis (48 B)
+  static constexpr int Knots = Basis + 3 * kN * 48;
+  static constexpr int Dsc = Knots + 3 * kKnotMax * 4;     // per axis: p / (t_{c+p+1} - t_{c+1})
+  static constexpr int Total = Dsc + 3 * kN * 4 + 1024;    // + slack for 1024-byte alignment
+  // lo-part distances (0 when unused)
+  static constexpr int dAz = 4 * kOp256, dAx = 4 * kOp256, dBz = 3 * kOp16, dTy = 4 * kOp128, dZy = 2 * kOpZ, dBx = kOp64;
+  static_assert(Total <= 227 * 1024, "shared memory budget");
+};
+
+template <int PREC>
+__device__ __forceinline__ uint16_t to16(float x) {
+  if (PREC == kFP16) return __half_as_ushort(__float2half_rn(x));
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
-__device__ __forceinline__ float from16(uint16_t v, int prec) {
-  if (prec == kFP16) return __half2float(__ushort_as_half(v));
+template <int PREC>
+__device__ __forceinline__ float from16(uint16_t v) {
+  if (PREC == kFP16) return __half2float(__ushort_as_half(v));
   return __bfloat162float(__ushort_as_bfloat16(v));
 }
 // Writes x (and, for split-BF16, its remainder x - hi at lo_delta further) at byte offset `off`.
-__device__ __forceinline__ void put(unsigned char* base, uint32_t off, uint32_t lo_delta, float x, int prec) {
-  const uint16_t h = to16(x, prec);
+template <int PREC>
+__device__ __forceinline__ void put(unsigned char* base, uint32_t off, uint32_t lo_delta, float x) {
+  const uint16_t h = to16<PREC>(x);
   *reinterpret_cast<uint16_t*>(base + off) = h;
-  if (prec == kSplit) *reinterpret_cast<uint16_t*>(base + lo_delta + off) = to16(x - from16(h, prec), prec);
+  if (PREC == kSplit) *reinterpret_cast<uint16_t*>(base + lo_delta + off) = to16<PREC>(x - from16<PREC>(h));
 }
 // Writes 8 consecutive K entries of one operand row (16 bytes) and, for split-BF16, their remainders.
-__device__ __forceinline__ void put8(unsigned char* base, uint32_t off, uint32_t lo_delta, const uint32_t* x,
-                                     int prec) {
+template <int PREC>
+__device__ __forceinline__ void put8(unsigned char* base, uint32_t off, uint32_t lo_delta, const uint32_t* x) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float x0 = __uint_as_float(x[2 * i]), x1 = __uint_as_float(x[2 * i + 1]);
-    const uint16_t h0 = to16(x0, prec), h1 = to16(x1, prec);
+    const uint16_t h0 = to16<PREC>(x0), h1 = to16<PREC>(x1);
     h[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-    if (prec == kSplit)
-      l[i] = (uint32_t)to16(x0 - from16(h0, prec), prec) | ((uint32_t)to16(x1 - from16(h1, prec), prec) << 16);
+    if (PREC == kSplit)
+      l[i] = (uint32_t)to16<PREC>(x0 - from16<PREC>(h0)) | ((uint32_t)to16<PREC>(x1 - from16<PREC>(h1)) << 16);
   }
   *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
-  if (prec == kSplit) *reinterpret_cast<uint4*>(base + lo_delta + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  if (PREC == kSplit) *reinterpret_cast<uint4*>(base + lo_delta + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 struct TcBasis {  // one sample: first nonzero index (both degrees) and the band values of degree p, p-1
@@ -98,22 +111,23 @@ struct TcBasis {  // one sample: first nonzero index (both degrees) and the band
   float N[4], Nm[4];
 };
 
-__global__ void __launch_bounds__(kThreadsTC, 1)
-decode_tc_kernel(DecodeParams prm, int prec) {
+template <int PREC>
+__global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_kernel(DecodeParams prm) {
+  using L = TcLayout<PREC>;
+  constexpr bool split = PREC == kSplit;
+  constexpr bool bf = PREC != kFP16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ int s_unit, s_bad;
+  __shared__ int s_item, s_bad;
   __shared__ BlockGeom s_g;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, group = warp >> 2;
-  float* P = reinterpret_cast<float*>(sm + kP);
-  TcBasis* bas = reinterpret_cast<TcBasis*>(sm + kBasis);  // [axis][sample]
-  float* kn = reinterpret_cast<float*>(sm + kKnots);
-  float* dsc = reinterpret_cast<float*>(sm + kDsc);          // [axis][control index]
-  const bool split = prec == kSplit;
-  const bool bf = prec != kFP16;
+  float* P = reinterpret_cast<float*>(sm + L::R1);
+  TcBasis* bas = reinterpret_cast<TcBasis*>(sm + L::Basis);  // [axis][sample]
+  float* kn = reinterpret_cast<float*>(sm + L::Knots);
+  float* dsc = reinterpret_cast<float*>(sm + L::Dsc);          // [axis][control index]
 
   if (warp == 0) {
     tmem_alloc(&s_tmem, kTmemCols);
@@ -124,8 +138,8 @@ decode_tc_kernel(DecodeParams prm, int prec) {
     fence_mbar_init();
   }
   // the zero rows of the stage-y basis buffers are written once; the basis rows per block
-  for (int e = tid * 16; e < 4 * kOpZ; e += kThreadsTC * 16)
-    *reinterpret_cast<uint4*>(sm + kZy + e) = make_uint4(0, 0, 0, 0);
+  for (int e = tid * 16; e < 2 * kOpZ * L::NL; e += kThreadsTC * 16)
+    *reinterpret_cast<uint4*>(sm + L::Zy + e) = make_uint4(0, 0, 0, 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -139,7 +153,6 @@ decode_tc_kernel(DecodeParams prm, int prec) {
     if (blockIdx.x == 0 && tid == 0) flag(prm.status, MFA_DEV_BAD_LIST);
     count = max(0, min(count, prm.list_len));
   }
-  const int64_t total_units = (int64_t)count * prm.slabs;
 
   // D (+)= A * B^T for operands at byte offsets a, b (lo parts at a_lo, b_lo); acc0 = accumulate into D
   auto mma = [&](uint32_t d, uint32_t a, uint32_t a_lo, uint32_t b, uint32_t b_lo, int N, uint32_t acc0) {
@@ -167,15 +180,13 @@ decode_tc_kernel(DecodeParams prm, int prec) {
     tc_fence_after();
   };
 
-  int last_block = -1;
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      s_unit = atomicAdd(prm.counter, 1u);
+      s_item = (int)atomicAdd(prm.counter, 1u);
       s_bad = 0;
-      const int64_t unit = s_unit;
-      if (unit < total_units) {
-        const int item = (int)(unit / prm.slabs);
+      const int item = s_item;
+      if (item < count) {
         const int b = prm.list ? prm.list[item] : item;
         const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
         uint32_t bad = 0;
@@ -194,71 +205,63 @@ decode_tc_kernel(DecodeParams prm, int prec) {
       }
     }
     __syncthreads();
-    if ((int64_t)s_unit >= total_units || timed_out) break;
+    if (s_item >= count || timed_out) break;
     if (s_bad) continue;
-    const int slab = (int)((int64_t)s_unit % prm.slabs);
-    const int k0 = slab * kKS;
-    const int kc = min(kKS, kN - k0);
     const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
-    const int block_id = (int)((int64_t)s_unit / prm.slabs);
 
-    // ---- per block: knots, basis bands of degree p and p-1, difference scales, P, stage-y A, stage-x B ----
-    if (block_id != last_block) {
-      if (tid < 3 * kKnotMax) {
-        const int a = tid / kKnotMax, i = tid - a * kKnotMax;
-        if (i < s_g.C[a] + s_g.p[a] + 1) kn[tid] = prm.knots[s_g.knot_off[a] + i];
-      }
-      const int ncps = Cx * Cy * Cz;
-      for (int e = tid; e < ncps; e += kThreadsTC) P[e] = __ldg(prm.cps + s_g.cp_off + e);
-      __syncthreads();
-      if (tid < 3 && !knots_ok(kn + tid * kKnotMax, s_g.p[tid], s_g.C[tid])) {
-        atomicOr(&s_bad, 1);
-        flag(prm.status, MFA_DEV_BAD_KNOTS);
-      }
-      if (tid < 3 * kN) {
-        const int a = tid / kN, i = tid - a * kN;
-        const int p = s_g.p[a];
-        const float* t = kn + a * kKnotMax;
-        const float u = sample_param(i, kN);
-        const int s = find_span(t, p, s_g.C[a], u);
-        float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1], Nm[MFA_MAX_DEGREE + 1], dNm[MFA_MAX_DEGREE + 1];
-        basis_funs<MFA_MAX_DEGREE>(t, p, s, u, N, dN);
-        // degree p-1 on the knots t_1 .. t_{C+p-1}: span s-1, nonzero functions s-p .. s-1
-        basis_funs<MFA_MAX_DEGREE>(t + 1, p - 1, s - 1, u, Nm, dNm);
-        TcBasis tb;
-        tb.off = s - p;
-        tb.pad[0] = tb.pad[1] = tb.pad[2] = 0;
-        for (int r = 0; r < 4; ++r) { tb.N[r] = N[r]; tb.Nm[r] = Nm[r]; }
-        bas[a * kN + i] = tb;
-        // difference scale of control index i (i < C-1)
-        float sc = 0.f;
-        if (i < s_g.C[a] - 1) {
-          const float den = t[i + p + 1] - t[i + 1];
-          if (den > 0.f) sc = (float)p / den;
-        }
-        dsc[a * kN + i] = sc;
-      }
-      __syncthreads();
-      if (s_bad) { last_block = -1; continue; }
-      // stage-y A: rows 96..127 of the two zero-padded buffers = N_y(u_j) and N_y^(p-1)(u_j), K = b;
-      // stage-x B: rows n < 32 = N_x(u_n), rows 32..63 = N_x^(p-1)(u_{n-32}), K = a
-      for (int e = tid; e < 2 * 64 * kK; e += kThreadsTC) {
-        const int which = e / (64 * kK), rem = e - which * (64 * kK), n = rem / kK, c = rem - (rem / kK) * kK;
-        const int axis = which == 0 ? 1 : 0;
-        const TcBasis tb = bas[axis * kN + (n & 31)];
-        const int d = c - tb.off;
-        float v = 0.f;
-        if (n < 32) { if (d >= 0 && d <= 3 && c < s_g.C[axis]) v = tb.N[d]; }
-        else if (d >= 0 && d <= 3 && c < s_g.C[axis] - 1) v = tb.Nm[d];
-        if (which == 0)
-          put(sm + kZy + (n < 32 ? 0 : kOpZ), kmajor_off(96 + (n & 31), c, kLBO, kSBO), 2 * kOpZ, v, prec);
-        else
-          put(sm + kBx, kmajor_off(n, c, kLBO, kSBO), kOp64, v, prec);
-      }
-      last_block = block_id;
+    // ---- per block: knots, basis bands of degree p and p-1, difference scales, P ----
+    if (tid < 3 * kKnotMax) {
+      const int a = tid / kKnotMax, i = tid - a * kKnotMax;
+      if (i < s_g.C[a] + s_g.p[a] + 1) kn[tid] = prm.knots[s_g.knot_off[a] + i];
     }
-
-    // ---- stage z operands: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index) ----
+    const int ncps = Cx * Cy * Cz;
+    for (int e = tid; e < ncps; e += kThreadsTC) P[e] = __ldg(prm.cps + s_g.cp_off + e);
+    __syncthreads();
+    if (tid < 3 && !knots_ok(kn + tid * kKnotMax, s_g.p[tid], s_g.C[tid])) {
+      atomicOr(&s_bad, 1);
+      flag(prm.status, MFA_DEV_BAD_KNOTS);
+    }
+    if (tid < 3 * kN) {
+      const int a = tid / kN, i = tid - a * kN;
+      const int p = s_g.p[a];
+      const float* t = kn + a * kKnotMax;
+      const float u = sample_param(i, kN);
+      const int s = find_span(t, p, s_g.C[a], u);
+      float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1], Nm[MFA_MAX_DEGREE + 1], dNm[MFA_MAX_DEGREE + 1];
+      basis_funs<MFA_MAX_DEGREE>(t, p, s, u, N, dN);
+      // degree p-1 on the knots t_1 .. t_{C+p-1}: span s-1, nonzero functions s-p .. s-1
+      basis_funs<MFA_MAX_DEGREE>(t + 1, p - 1, s - 1, u, Nm, dNm);
+      TcBasis tb;
+      tb.off = s - p;
+      tb.pad[0] = tb.pad[1] = tb.pad[2] = 0;
+      for (int r = 0; r < 4; ++r) { tb.N[r] = N[r]; tb.Nm[r] = Nm[r]; }
+      bas[a * kN + i] = tb;
+      // difference scale of control index i (i < C-1)
+      float sc = 0.f;
+      if (i < s_g.C[a] - 1) {
+        const float den = t[i + p + 1] - t[i + 1];
+        if (den > 0.f) sc = (float)p / den;
+      }
+      dsc[a * kN + i] = sc;
+    }
+    __syncthreads();
+    if (s_bad) continue;
+    // stage-y A: rows 96..127 of the two zero-padded buffers = N_y(u_j) and N_y^(p-1)(u_j), K = b;
+    // stage-x B: rows n < 32 = N_x(u_n), rows 32..63 = N_x^(p-1)(u_{n-32}), K = a
+    for (int e = tid; e < 2 * 64 * kK; e += kThreadsTC) {
+      const int which = e / (64 * kK), rem = e - which * (64 * kK), n = rem / kK, c = rem - (rem / kK) * kK;
+      const int axis = which == 0 ? 1 : 0;
+      const TcBasis tb = bas[axis * kN + (n & 31)];
+      const int d = c - tb.off;
+      float v = 0.f;
+      if (n < 32) { if (d >= 0 && d <= 3 && c < s_g.C[axis]) v = tb.N[d]; }
+      else if (d >= 0 && d <= 3 && c < s_g.C[axis] - 1) v = tb.Nm[d];
+      if (which == 0)
+        put<PREC>(sm + L::Zy + (n < 32 ? 0 : kOpZ), kmajor_off(96 + (n & 31), c, kLBO, kSBO), L::dZy, v);
+      else
+        put<PREC>(sm + L::Bx, kmajor_off(n, c, kLBO, kSBO), L::dBx, v);
+    }
+    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index)
     for (int e = tid; e < 256 * kK; e += kThreadsTC) {
       const int R = e >> 4, c = e & 15, b = R >> 4, a = R & 15;
       float v0 = 0.f, vu = 0.f, vv = 0.f, vw = 0.f;
@@ -271,126 +274,136 @@ decode_tc_kernel(DecodeParams prm, int prec) {
         if (c < Cz - 1) vw = dsc[2 * kN + c] * (P[idx + Cy * Cx] - p0);
       }
       const uint32_t off = kmajor_off(R, c, kLBO, kSBO);
-      put(sm + kAz, off, 4 * kOp256, v0, prec);
-      put(sm + kAz + kOp256, off, 4 * kOp256, vu, prec);
-      put(sm + kAz + 2 * kOp256, off, 4 * kOp256, vv, prec);
-      put(sm + kAz + 3 * kOp256, off, 4 * kOp256, vw, prec);
+      put<PREC>(sm + L::Az, off, L::dAz, v0);
+      put<PREC>(sm + L::Az + kOp256, off, L::dAz, vu);
+      put<PREC>(sm + L::Az + 2 * kOp256, off, L::dAz, vv);
+      put<PREC>(sm + L::Az + 3 * kOp256, off, L::dAz, vw);
     }
-    for (int e = tid; e < 3 * 16 * kK; e += kThreadsTC) {  // B_z0, B_z1, B_z2: 16 x 16 each
-      const int which = e >> 8, n = (e >> 4) & 15, c = e & 15;
-      const int kl = n & 7;
-      float v = 0.f;
-      if (kl < kc && (n < 8) == (which == 0)) {
-        const TcBasis tb = bas[2 * kN + k0 + kl];
-        const int d = c - tb.off;
-        if (d >= 0 && d <= 3) {
-          if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
-          else if (c < Cz) v = tb.N[d];
+    // (P in R1 is dead from here on: R1 becomes the stage-x operand and the readout staging)
+
+    for (int slab = 0; slab < kSlabs && !timed_out; ++slab) {
+      const int k0 = slab * kKS;
+      for (int e = tid; e < 3 * 16 * kK; e += kThreadsTC) {  // B_z0, B_z1, B_z2: 16 x 16 each
+        const int which = e >> 8, n = (e >> 4) & 15, c = e & 15;
+        const int kl = n & 7;
+        float v = 0.f;
+        if ((n < 8) == (which == 0)) {
+          const TcBasis tb = bas[2 * kN + k0 + kl];
+          const int d = c - tb.off;
+          if (d >= 0 && d <= 3) {
+            if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
+            else if (c < Cz) v = tb.N[d];
+          }
         }
+        put<PREC>(sm + L::Bz + which * kOp16, kmajor_off(n, c, kLBO, kSBO), L::dBz, v);
       }
-      put(sm + kBz + which * kOp16, kmajor_off(n, c, kLBO, kSBO), 3 * kOp16, v, prec);
-    }
-    operands_ready();
-    // ---- stage z, per 128-row tile t: columns 16t: [chain 0 | chain 3], 32 + 16t: [chain 2 | chain 1] ----
-    if (tid == 0) {
-      for (int t = 0; t < 2; ++t) {
-        const uint32_t ro = t * 16 * kSBO;
-        mma(tmem + 16 * t, kAz + ro, kAz + 4 * kOp256 + ro, kBz, kBz + 3 * kOp16, 16, 0);
-        mma(tmem + 16 * t, kAz + 3 * kOp256 + ro, kAz + 7 * kOp256 + ro, kBz + kOp16, kBz + 4 * kOp16, 16, 1);
-        mma(tmem + 32 + 16 * t, kAz + 2 * kOp256 + ro, kAz + 6 * kOp256 + ro, kBz, kBz + 3 * kOp16, 16, 0);
-        mma(tmem + 32 + 16 * t, kAz + kOp256 + ro, kAz + 5 * kOp256 + ro, kBz + 2 * kOp16, kBz + 5 * kOp16, 16, 1);
-      }
-      mma_commit(&s_bar);
-    }
-    wait_mma();
-    if (timed_out) break;
-    // readout z -> stage-y B of chain c: element (row 16k + a, K = b); every entry of all 128 rows is written
-    {
-      const int R = 128 * group + 32 * quarter + lane, b = R >> 4, a = R & 15;
-      uint32_t r0[16], r1[16];
-      const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 16 * group;
-      tmem_ld16(ta, r0);
-      tmem_ld16(ta + 32, r1);
-      tmem_ld_wait();
-#pragma unroll
-      for (int kl = 0; kl < kKS; ++kl) {
-        const uint32_t off = kmajor_off(kl * 16 + a, b, kLBO, kSBO);
-        put(sm + kTy, off, 4 * kOp128, __uint_as_float(r0[kl]), prec);
-        put(sm + kTy + kOp128, off, 4 * kOp128, __uint_as_float(r1[8 + kl]), prec);
-        put(sm + kTy + 2 * kOp128, off, 4 * kOp128, __uint_as_float(r1[kl]), prec);
-        put(sm + kTy + 3 * kOp128, off, 4 * kOp128, __uint_as_float(r0[8 + kl]), prec);
-      }
-    }
-    operands_ready();
-    // ---- stage y: D[32c + j][(k,a)] = sum_b basis_c(u_j)_b T_c[(k,a)][b], chains accumulated ----
-    if (tid == 0) {
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t za = kZy + (c == 2 ? kOpZ : 0) + (uint32_t)((96 - 32 * c) / 8) * kSBO;
-        mma(tmem, za, za + 2 * kOpZ, kTy + c * kOp128, kTy + (4 + c) * kOp128, 128, c > 0);
-      }
-      mma_commit(&s_bar);
-    }
-    wait_mma();
-    if (timed_out) break;
-    // readout y: warp (quarter c, group g) holds chain c, sample j = lane, planes k = 4g .. 4g+3;
-    // stage-x A of chain c: element (row 32k + j, K = a), 16 consecutive K entries = two 16-byte stores
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const int kl = 4 * group + kk;
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * kl, r);
-      tmem_ld_wait();
-      const uint32_t off = kmajor_off(kl * 32 + lane, 0, kLBO, kSBO);
-      unsigned char* base = sm + kAx + quarter * kOp256;
-      put8(base, off, 4 * kOp256, r, prec);
-      put8(base, off + kLBO, 4 * kOp256, r + 8, prec);
-    }
-    operands_ready();
-    // ---- stage x per 128-row tile: f | f_u | f_v | f_w in columns 0..127 of the tile ----
-    const int tiles_x = (kc * kN + 127) / 128;
-    if (tid == 0) {
-      for (int t = 0; t < tiles_x; ++t) {
-        const uint32_t d = tmem + 128 * t, ro = t * 16 * kSBO;
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t bo = c == 1 ? 4 * kSBO : 0;
-          mma(d + 32 * c, kAx + c * kOp256 + ro, kAx + (4 + c) * kOp256 + ro, kBx + bo, kBx + kOp64 + bo, 32, 0);
+      operands_ready();
+      // ---- stage z, per 128-row tile t: columns 16t: [chain 0 | chain 3], 32 + 16t: [chain 2 | chain 1] ----
+      if (tid == 0) {
+        for (int t = 0; t < 2; ++t) {
+          const uint32_t ro = t * 16 * kSBO;
+          mma(tmem + 16 * t, L::Az + ro, L::Az + L::dAz + ro, L::Bz, L::Bz + L::dBz, 16, 0);
+          mma(tmem + 16 * t, L::Az + 3 * kOp256 + ro, L::Az + 3 * kOp256 + L::dAz + ro, L::Bz + kOp16,
+              L::Bz + kOp16 + L::dBz, 16, 1);
+          mma(tmem + 32 + 16 * t, L::Az + 2 * kOp256 + ro, L::Az + 2 * kOp256 + L::dAz + ro, L::Bz, L::Bz + L::dBz,
+              16, 0);
+          mma(tmem + 32 + 16 * t, L::Az + kOp256 + ro, L::Az + kOp256 + L::dAz + ro, L::Bz + 2 * kOp16,
+              L::Bz + 2 * kOp16 + L::dBz, 16, 1);
         }
+        mma_commit(&s_bar);
       }
-      mma_commit(&s_bar);
-    }
-    wait_mma();
-    if (timed_out) break;
-    // readout x: warp group g takes tile g; each warp stages its 32 rows, 8 voxels at a time
-    if (group < tiles_x) {
-      float4* stg = reinterpret_cast<float4*>(sm + kStage + warp * 32 * 128);
-      float4* out = reinterpret_cast<float4*>(prm.cache) + (int64_t)s_g.slot * prm.slot_stride +
-                    (int64_t)k0 * kN * kN;
-      for (int h = 0; h < 2; ++h) {
-        uint32_t f[16], fu[16], fv[16], fw[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 128 * group + 16 * h;
-        tmem_ld16(ta, f);
-        tmem_ld16(ta + 32, fu);
-        tmem_ld16(ta + 64, fv);
-        tmem_ld16(ta + 96, fw);
+      wait_mma();
+      if (timed_out) break;
+      // readout z -> stage-y B of chain c: element (row 16k + a, K = b); every entry of all 128 rows is written
+      {
+        const int R = 128 * group + 32 * quarter + lane, b = R >> 4, a = R & 15;
+        uint32_t r0[16], r1[16];
+        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 16 * group;
+        tmem_ld16(ta, r0);
+        tmem_ld16(ta + 32, r1);
         tmem_ld_wait();
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const int q = 8 * half + v;
-            stg[lane * 8 + (v ^ (lane & 7))] = make_float4(__uint_as_float(f[q]), __uint_as_float(fu[q]),
-                                                           __uint_as_float(fv[q]), __uint_as_float(fw[q]));
-          }
-          __syncwarp();
-#pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int rr = 4 * it + (lane >> 3), v = lane & 7;
-            const int Rg = 128 * group + 32 * quarter + rr;
-            if (Rg < kc * kN) __stcs(out + (int64_t)Rg * kN + 16 * h + 8 * half + v, stg[rr * 8 + (v ^ (rr & 7))]);
-          }
-          __syncwarp();
+        for (int kl = 0; kl < kKS; ++kl) {
+          const uint32_t off = kmajor_off(kl * 16 + a, b, kLBO, kSBO);
+          put<PREC>(sm + L::Ty, off, L::dTy, __uint_as_float(r0[kl]));
+          put<PREC>(sm + L::Ty + kOp128, off, L::dTy, __uint_as_float(r1[8 + kl]));
+          put<PREC>(sm + L::Ty + 2 * kOp128, off, L::dTy, __uint_as_float(r1[kl]));
+          put<PREC>(sm + L::Ty + 3 * kOp128, off, L::dTy, __uint_as_float(r0[8 + kl]));
         }
       }
+      operands_ready();
+      // ---- stage y: D[32c + j][(k,a)] = sum_b basis_c(u_j)_b T_c[(k,a)][b], chains accumulated ----
+      if (tid == 0) {
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t za = L::Zy + (c == 2 ? kOpZ : 0) + (uint32_t)((96 - 32 * c) / 8) * kSBO;
+          mma(tmem, za, za + L::dZy, L::Ty + c * kOp128, L::Ty + c * kOp128 + L::dTy, 128, c > 0);
+        }
+        mma_commit(&s_bar);
+      }
+      wait_mma();
+      if (timed_out) break;
+      // readout y: warp (quarter c, group g) holds chain c, sample j = lane, planes k = 4g .. 4g+3;
+      // stage-x A of chain c: element (row 32k + j, K = a), 16 consecutive K entries = two 16-byte stores
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int kl = 4 * group + kk;
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * kl, r);
+        tmem_ld_wait();
+        const uint32_t off = kmajor_off(kl * 32 + lane, 0, kLBO, kSBO);
+        unsigned char* base = sm + L::R1 + quarter * kOp256;
+        put8<PREC>(base, off, L::dAx, r);
+        put8<PREC>(base, off + kLBO, L::dAx, r + 8);
+      }
+      operands_ready();
+      // ---- stage x per 128-row tile: f | f_u | f_v | f_w in columns 0..127 of the tile ----
+      if (tid == 0) {
+        for (int t = 0; t < 2; ++t) {
+          const uint32_t d = tmem + 128 * t, ro = t * 16 * kSBO;
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t bo = c == 1 ? 4 * kSBO : 0;
+            mma(d + 32 * c, L::R1 + c * kOp256 + ro, L::R1 + c * kOp256 + L::dAx + ro, L::Bx + bo,
+                L::Bx + L::dBx + bo, 32, 0);
+          }
+        }
+        mma_commit(&s_bar);
+      }
+      wait_mma();
+      if (timed_out) break;
+      // readout x: warp group g takes tile g; each warp stages its 32 rows, 8 voxels at a time
+      {
+        float4* stg = reinterpret_cast<float4*>(sm + L::R1 + warp * 32 * 128);
+        float4* out = reinterpret_cast<float4*>(prm.cache) + (int64_t)s_g.slot * prm.slot_stride +
+                      (int64_t)k0 * kN * kN;
+        for (int h = 0; h < 2; ++h) {
+          uint32_t f[16], fu[16], fv[16], fw[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 128 * group + 16 * h;
+          tmem_ld16(ta, f);
+          tmem_ld16(ta + 32, fu);
+          tmem_ld16(ta + 64, fv);
+          tmem_ld16(ta + 96, fw);
+          tmem_ld_wait();
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const int q = 8 * half + v;
+              stg[lane * 8 + (v ^ (lane & 7))] = make_float4(__uint_as_float(f[q]), __uint_as_float(fu[q]),
+                                                             __uint_as_float(fv[q]), __uint_as_float(fw[q]));
+            }
+            __syncwarp();
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+              const int rr = 4 * it + (lane >> 3), v = lane & 7;
+              const int Rg = 128 * group + 32 * quarter + rr;
+              __stcs(out + (int64_t)Rg * kN + 16 * h + 8 * half + v, stg[rr * 8 + (v ^ (rr & 7))]);
+            }
+            __syncwarp();
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // staging (R1) and the tensor memory are reused by the next slab
     }
   }
   tc_fence_before();
@@ -398,21 +411,34 @@ decode_tc_kernel(DecodeParams prm, int prec) {
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+template <int PREC>
+int launch_tc(mfa_ctx* ctx, DecodeParams prm, cudaStream_t stream) {
+  using L = TcLayout<PREC>;
+  const size_t smem = L::Total;
+  if (cudaFuncSetAttribute(decode_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return MFA_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_tc_kernel<PREC>, kThreadsTC, smem) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  // every resident CTA holds 256 of the SM's 512 tensor-memory columns
+  per_sm = std::max(1, std::min(per_sm, 512 / kTmemCols));
+  if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  decode_tc_kernel<PREC><<<ctx->num_sms * per_sm, kThreadsTC, smem, stream>>>(prm);
+  ctx->launches++;
+  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+}
+
 }  // namespace
 
 int decode_tc(mfa_ctx* ctx, DecodeParams prm, int precision, cudaStream_t stream) {
   if (prm.bounds.max_nsamp != kN || prm.bounds.max_ncp > kK) return MFA_ERR_UNSUPPORTED;
   if (prm.flags & MFA_DECODE_VALUE_ONLY) return MFA_ERR_UNSUPPORTED;
-  const int prec = precision == MFA_PREC_BF16 ? kBF16 : (precision == MFA_PREC_FP16 ? kFP16 : kSplit);
   prm.ks = kKS;
-  prm.slabs = kN / kKS;
-  const size_t smem = kSmemTC;
-  if (cudaFuncSetAttribute(decode_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MFA_ERR_CUDA;
-  if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
-  decode_tc_kernel<<<ctx->num_sms, kThreadsTC, smem, stream>>>(prm, prec);
-  ctx->launches++;
-  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+  prm.slabs = kSlabs;
+  if (precision == MFA_PREC_BF16) return launch_tc<kBF16>(ctx, prm, stream);
+  if (precision == MFA_PREC_FP16) return launch_tc<kFP16>(ctx, prm, stream);
+  return launch_tc<kSplit>(ctx, prm, stream);
 }
 
 }  // namespace mfa
