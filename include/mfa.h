@@ -295,6 +295,16 @@ int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t nblocks,
                               const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
                               float* d_cps_out, int64_t cps_len, double* d_rmse, void* stream);
 
+/* ---- failure-detection self-test --------------------------------------------------- */
+/* Test hook; the paper has no counterpart. Launches one CTA whose thread 0 initialises an
+ * mbarrier that nothing ever arrives on and waits for it with the library's bounded wait,
+ * limited to `polls` polls (1 .. 2^20; each poll is a try_wait plus a short sleep). The wait
+ * must give up: the kernel then ORs MFA_DEV_TIMEOUT into the context's status word and
+ * returns, exactly as the TMA and tensor-core kernels do when a copy or MMA never completes.
+ * No copy or MMA is in flight, so nothing is left running. Returns MFA_ERR_INVALID_ARG for
+ * a null ctx or `polls` out of range. */
+int mfa_selftest_wait_timeout(mfa_ctx* ctx, int32_t polls, void* stream);
+
 /* ---- ray casting (Algorithm 4) -------------------------------------------------------- */
 
 

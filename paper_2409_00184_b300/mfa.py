@@ -64,7 +64,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
-           "mfa_ctx_read_stats", "mfa_select_ncp"]
+           "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout"]
 
 
 def _load():
@@ -92,6 +92,7 @@ def _load():
         "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
         "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
         "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
+        "mfa_selftest_wait_timeout": (ctypes.c_int, [P, I32, P]),
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
@@ -176,6 +177,10 @@ class Context:
 
     def launch_count(self):
         return int(lib.mfa_ctx_launch_count(self.handle))
+
+    def selftest_wait_timeout(self, polls=1000, stream=None):
+        """mfa_selftest_wait_timeout: a bounded wait on a barrier nothing arrives on (sets MFA_DEV_TIMEOUT)."""
+        _check(lib.mfa_selftest_wait_timeout(self.handle, int(polls), _stream(stream)), "mfa_selftest_wait_timeout")
 
     def ray_samples(self, reset=True, stream=None):
         """Samples marched by mfa_raycast since the last reset (synchronises the stream)."""

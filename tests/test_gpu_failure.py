@@ -1,0 +1,50 @@
+"""Failure detection on the GPU without a fault: the bounded mbarrier wait gives up on a barrier that nothing
+arrives on, reports MFA_DEV_TIMEOUT in the context's status word, and leaves the context usable."""
+
+import pytest
+import torch
+
+import synth
+from gpu_util import TOL_FP32, oracle_decode_set, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    from paper_2409_00184_b300 import mfa as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mfa):
+    c = mfa.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("polls", [1, 1000])
+def test_bounded_wait_times_out_and_context_stays_usable(mfa, ctx, polls):
+    assert ctx.device_status() == 0
+    ctx.selftest_wait_timeout(polls)
+    assert ctx.device_status() == mfa.DEV_TIMEOUT  # the read synchronises and clears the word
+    assert ctx.device_status() == 0
+    # the same context (and its tensor-core and TMA kernels) still produce correct results
+    bs = synth.random_block_set(6, 801, ncp_choices=(4, 8, 12), nsamp_choices=(32,), degree_choices=(2, 3))
+    blk = mfa.DeviceBlocks(bs)
+    for prec, tol in ((mfa.PREC_FP32, TOL_FP32), (mfa.PREC_SPLIT_BF16, 1e-4)):
+        cache = torch.full((blk.nslots * blk.slot_voxels * 4,), float("nan"), device="cuda")
+        mfa.decode_blocks(ctx, blk, cache, blk.slot_voxels, blk.nslots, precision=prec)
+        assert ctx.device_status() == 0
+        got = cache.view(blk.nslots, 32, 32, 32, 4).cpu().numpy()
+        want = oracle_decode_set(bs)
+        for b in range(len(bs)):
+            ve, ge = rel_errors(got[bs.slot[b]], want[b])
+            assert ve <= tol and max(ge) <= tol, (prec, b, ve, ge)
+
+
+def test_selftest_argument_checks(mfa, ctx):
+    for polls in (0, -1, (1 << 20) + 1):
+        with pytest.raises(mfa.MfaError):
+            ctx.selftest_wait_timeout(polls)
+    assert ctx.device_status() == 0
