@@ -6,9 +6,11 @@
 //   stage z:  T[k][b][a] = (sum_c P[c][b][a] N_c(w_k), same with N'_c)              (float2)
 //   stage y:  U[k][j][a] = (T0 N_b(v_j), T0 N'_b(v_j), T1 N_b(v_j)) summed over b      (float4)
 //   stage x:  (f, f_u, f_v, f_w)[k][j][i] = sum_a (U0 N_a, U0 N'_a, U1 N_a, U2 N_a)(u_i)
-// Work unit = (block, slab of `ks` z-planes); a persistent grid pulls units from an atomic
-// counter. Control points, basis tables and the stage outputs of one unit live in shared
-// memory; only the final float4 per voxel goes to HBM (coalesced 512-byte rows per warp).
+// Work unit = (block, group of slabs of `ks` z-planes each); a persistent grid pulls units from an
+// atomic counter. A unit loads the block's knots and control points and builds its basis tables
+// once, then runs the three stages slab by slab. Control points, basis tables and the stage outputs
+// live in shared memory; only the final float4 per voxel goes to HBM (coalesced 512-byte rows per
+// warp).
 // Stage outputs are interleaved so stage x reads one 16-byte word per (row, control index), and
 // the loops advance their (k, j, a) indices incrementally instead of dividing.
 #include <algorithm>
@@ -24,8 +26,11 @@ struct DecodeSmem {
 
 static int r4(int v) { return (v + 3) & ~3; }
 
-// [knots | basis tables | T | P/U]: U (stage y output) overwrites P, which stage z has consumed.
-static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks) {
+constexpr int kUnitPlanes = 32;  // z-planes per work unit (the set-up is shared by its slabs)
+
+// [knots | basis tables | T | P | U]. With one slab per unit (`alias`), U (stage y output) overwrites
+// P, which stage z has consumed; units of several slabs keep P for all of them.
+static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks, bool alias) {
   DecodeSmem L;
   int o = 0;
   L.knots = o; o += r4(3 * kKnotMax);
@@ -33,9 +38,15 @@ static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks
   L.bN = o;    o += 3 * maxN * 4;   // float4 per sample: N_{s-p..s} (zero padded)
   L.bdN = o;   o += 3 * maxN * 4;   // float4 per sample: N'
   L.T = o;     o += r4(maxC * maxC * ks * (value_only ? 1 : 2));
+  const int pw = r4(maxC * maxC * maxC), uw = r4(maxC * maxN * ks * (value_only ? 1 : 4));
   L.P = o;
-  L.U = o;
-  o += std::max(r4(maxC * maxC * maxC), r4(maxC * maxN * ks * (value_only ? 1 : 4)));
+  if (alias) {
+    L.U = o;
+    o += std::max(pw, uw);
+  } else {
+    L.U = o + pw;
+    o += pw + uw;
+  }
   L.total = o;
   return L;
 }
@@ -87,11 +98,11 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
     __syncthreads();
     if ((int64_t)s_unit >= total_units) break;
     if (s_bad) continue;
-    const int slab = (int)((int64_t)s_unit % prm.slabs);
-    const int k0 = slab * prm.ks;
+    const int part = (int)((int64_t)s_unit % prm.slabs);
+    const int kz0 = part * prm.ks * prm.group;  // first z-plane of this unit
     const int nz = s_g.n[2];
-    if (k0 >= nz) continue;
-    const int kc = min(prm.ks, nz - k0);
+    if (kz0 >= nz) continue;
+    const int kzn = min(prm.ks * prm.group, nz - kz0);  // z-planes of this unit
     const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
     const int nx = s_g.n[0], ny = s_g.n[1];
     const int px = s_g.p[0], py = s_g.p[1], pz = s_g.p[2];
@@ -109,13 +120,13 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
       atomicOr(&s_bad, 1);
       flag(prm.status, MFA_DEV_BAD_KNOTS);
     }
-    // basis tables: x (nx samples), y (ny samples), z (the slab's kc samples)
-    {
-      int a = -1, i = 0, smp = 0;
-      if (tid < nx) { a = 0; i = tid; smp = tid; }
-      else if (tid < nx + ny) { a = 1; i = tid - nx; smp = i; }
-      else if (tid < nx + ny + kc) { a = 2; i = tid - nx - ny; smp = k0 + i; }
-      if (a >= 0) {
+    // basis tables: x (nx samples), y (ny samples), z (the unit's kzn samples)
+    for (int e = tid; e < nx + ny + kzn; e += nthr) {
+      int a, i, smp;
+      if (e < nx) { a = 0; i = e; smp = e; }
+      else if (e < nx + ny) { a = 1; i = e - nx; smp = i; }
+      else { a = 2; i = e - nx - ny; smp = kz0 + i; }
+      {
         const float* t = s_knots + a * kKnotMax;
         const float u = sample_param(smp, s_g.n[a]);
         const int s = find_span(t, s_g.p[a], s_g.C[a], u);
@@ -132,110 +143,115 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
     __syncthreads();
     if (s_bad) continue;
 
-    // ---- stage z: T[kl][b][a] over the slab, flat index e = kl*plane + ab ----
-    {
-      const int plane = Cx * Cy;
-      const int tot = plane * kc;
-      int kl = tid / plane, ab = tid - (tid / plane) * plane;
-      for (int e = tid; e < tot; e += nthr) {
-        const int oz = s_boff[2 * maxN + kl];
-        const float4 Nz = s_bN[2 * maxN + kl];
-        const float4 dNz = s_bdN[2 * maxN + kl];
-        const float Nzv[4] = {Nz.x, Nz.y, Nz.z, Nz.w}, dNzv[4] = {dNz.x, dNz.y, dNz.z, dNz.w};
-        const float* Pc = s_P + oz * plane + ab;
-        float t0 = 0.f, t1 = 0.f;
-#pragma unroll
-        for (int d = 0; d < Q; ++d) {
-          if (d <= pz) {
-            const float pv = Pc[d * plane];
-            t0 = fmaf(pv, Nzv[d], t0);
-            if (!VALUE_ONLY) t1 = fmaf(pv, dNzv[d], t1);
+    for (int k0 = kz0; k0 < kz0 + kzn; k0 += prm.ks) {  // slabs of the unit
+      const int kc = min(prm.ks, kz0 + kzn - k0);
+      const int zt = 2 * maxN + (k0 - kz0);  // z-table row of the slab's first plane
+
+      // ---- stage z: T[kl][b][a] over the slab, flat index e = kl*plane + ab ----
+      {
+        const int plane = Cx * Cy;
+        const int tot = plane * kc;
+        int kl = tid / plane, ab = tid - (tid / plane) * plane;
+        for (int e = tid; e < tot; e += nthr) {
+          const int oz = s_boff[zt + kl];
+          const float4 Nz = s_bN[zt + kl];
+          const float4 dNz = s_bdN[zt + kl];
+          const float Nzv[4] = {Nz.x, Nz.y, Nz.z, Nz.w}, dNzv[4] = {dNz.x, dNz.y, dNz.z, dNz.w};
+          const float* Pc = s_P + oz * plane + ab;
+          float t0 = 0.f, t1 = 0.f;
+  #pragma unroll
+          for (int d = 0; d < Q; ++d) {
+            if (d <= pz) {
+              const float pv = Pc[d * plane];
+              t0 = fmaf(pv, Nzv[d], t0);
+              if (!VALUE_ONLY) t1 = fmaf(pv, dNzv[d], t1);
+            }
+          }
+          if (VALUE_ONLY) sm[L.T + e] = t0;
+          else reinterpret_cast<float2*>(sm + L.T)[e] = make_float2(t0, t1);
+          ab += nthr;
+          while (ab >= plane) { ab -= plane; ++kl; }
+        }
+      }
+      __syncthreads();
+      // ---- stage y: U[kl][j][a]; thread keeps its column a, rows r = (kl, j) advance by step ----
+      {
+        const int step = nthr / Cx;
+        const int g = tid / Cx;
+        if (g < step) {
+          const int a = tid - g * Cx;
+          const int rows = ny * kc;
+          int kl = g / ny, j = g - (g / ny) * ny;
+          for (int r = g; r < rows; r += step) {
+            const int oy = s_boff[maxN + j];
+            const float4 Ny = s_bN[maxN + j];
+            const float Nyv[4] = {Ny.x, Ny.y, Ny.z, Ny.w};
+            const int tb = (kl * Cy + oy) * Cx + a;
+            if (VALUE_ONLY) {
+              float u0 = 0.f;
+  #pragma unroll
+              for (int d = 0; d < Q; ++d)
+                if (d <= py) u0 = fmaf(sm[L.T + tb + d * Cx], Nyv[d], u0);
+              sm[L.U + r * Cx + a] = u0;
+            } else {
+              const float4 dNy = s_bdN[maxN + j];
+              const float dNyv[4] = {dNy.x, dNy.y, dNy.z, dNy.w};
+              const float2* T = reinterpret_cast<const float2*>(sm + L.T);
+              float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+  #pragma unroll
+              for (int d = 0; d < Q; ++d) {
+                if (d <= py) {
+                  const float2 tv = T[tb + d * Cx];
+                  u0 = fmaf(tv.x, Nyv[d], u0);
+                  u1 = fmaf(tv.x, dNyv[d], u1);
+                  u2 = fmaf(tv.y, Nyv[d], u2);
+                }
+              }
+              reinterpret_cast<float4*>(sm + L.U)[r * Cx + a] = make_float4(u0, u1, u2, 0.f);
+            }
+            j += step;
+            while (j >= ny) { j -= ny; ++kl; }
           }
         }
-        if (VALUE_ONLY) sm[L.T + e] = t0;
-        else reinterpret_cast<float2*>(sm + L.T)[e] = make_float2(t0, t1);
-        ab += nthr;
-        while (ab >= plane) { ab -= plane; ++kl; }
       }
-    }
-    __syncthreads();
-    // ---- stage y: U[kl][j][a]; thread keeps its column a, rows r = (kl, j) advance by step ----
-    {
-      const int step = nthr / Cx;
-      const int g = tid / Cx;
-      if (g < step) {
-        const int a = tid - g * Cx;
-        const int rows = ny * kc;
-        int kl = g / ny, j = g - (g / ny) * ny;
-        for (int r = g; r < rows; r += step) {
-          const int oy = s_boff[maxN + j];
-          const float4 Ny = s_bN[maxN + j];
-          const float Nyv[4] = {Ny.x, Ny.y, Ny.z, Ny.w};
-          const int tb = (kl * Cy + oy) * Cx + a;
+      __syncthreads();
+      // ---- stage x + store: thread owns one x sample, loops over (k, j) rows ----
+      {
+        const int rows_per_pass = nthr / nx;
+        const int i = tid % nx;
+        const int r0 = tid / nx;
+        if (r0 < rows_per_pass) {
+          const int ox = s_boff[i];
+          const float4 Nx4 = s_bN[i], dNx4 = s_bdN[i];
+          const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
+          const int rows = ny * kc;
+          const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
           if (VALUE_ONLY) {
-            float u0 = 0.f;
-#pragma unroll
-            for (int d = 0; d < Q; ++d)
-              if (d <= py) u0 = fmaf(sm[L.T + tb + d * Cx], Nyv[d], u0);
-            sm[L.U + r * Cx + a] = u0;
+            const float* U = sm + L.U + ox;
+            for (int r = r0; r < rows; r += rows_per_pass) {
+              float f = 0.f;
+  #pragma unroll
+              for (int d = 0; d < Q; ++d)
+                if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
+              __stcs(prm.cache + base + (int64_t)r * nx, f);
+            }
           } else {
-            const float4 dNy = s_bdN[maxN + j];
-            const float dNyv[4] = {dNy.x, dNy.y, dNy.z, dNy.w};
-            const float2* T = reinterpret_cast<const float2*>(sm + L.T);
-            float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < Q; ++d) {
-              if (d <= py) {
-                const float2 tv = T[tb + d * Cx];
-                u0 = fmaf(tv.x, Nyv[d], u0);
-                u1 = fmaf(tv.x, dNyv[d], u1);
-                u2 = fmaf(tv.y, Nyv[d], u2);
+            const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
+            float4* out = reinterpret_cast<float4*>(prm.cache) + base;
+            for (int r = r0; r < rows; r += rows_per_pass) {
+              float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
+  #pragma unroll
+              for (int d = 0; d < Q; ++d) {
+                if (d <= px) {
+                  const float4 uv = U[r * Cx + d];
+                  f = fmaf(uv.x, Nx[d], f);
+                  fu = fmaf(uv.x, dNx[d], fu);
+                  fv = fmaf(uv.y, Nx[d], fv);
+                  fw = fmaf(uv.z, Nx[d], fw);
+                }
               }
+              __stcs(out + (int64_t)r * nx, make_float4(f, fu, fv, fw));
             }
-            reinterpret_cast<float4*>(sm + L.U)[r * Cx + a] = make_float4(u0, u1, u2, 0.f);
-          }
-          j += step;
-          while (j >= ny) { j -= ny; ++kl; }
-        }
-      }
-    }
-    __syncthreads();
-    // ---- stage x + store: thread owns one x sample, loops over (k, j) rows ----
-    {
-      const int rows_per_pass = nthr / nx;
-      const int i = tid % nx;
-      const int r0 = tid / nx;
-      if (r0 < rows_per_pass) {
-        const int ox = s_boff[i];
-        const float4 Nx4 = s_bN[i], dNx4 = s_bdN[i];
-        const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
-        const int rows = ny * kc;
-        const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
-        if (VALUE_ONLY) {
-          const float* U = sm + L.U + ox;
-          for (int r = r0; r < rows; r += rows_per_pass) {
-            float f = 0.f;
-#pragma unroll
-            for (int d = 0; d < Q; ++d)
-              if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
-            __stcs(prm.cache + base + (int64_t)r * nx, f);
-          }
-        } else {
-          const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
-          float4* out = reinterpret_cast<float4*>(prm.cache) + base;
-          for (int r = r0; r < rows; r += rows_per_pass) {
-            float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
-#pragma unroll
-            for (int d = 0; d < Q; ++d) {
-              if (d <= px) {
-                const float4 uv = U[r * Cx + d];
-                f = fmaf(uv.x, Nx[d], f);
-                fu = fmaf(uv.x, dNx[d], fu);
-                fv = fmaf(uv.y, Nx[d], fv);
-                fw = fmaf(uv.z, Nx[d], fw);
-              }
-            }
-            __stcs(out + (int64_t)r * nx, make_float4(f, fu, fv, fw));
           }
         }
       }
@@ -264,16 +280,24 @@ static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const Decod
 int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaStream_t stream) {
   const int maxN = prm.bounds.max_nsamp, maxC = prm.bounds.max_ncp, pmax = prm.bounds.max_degree;
   const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
-  // default slab depth from the tiling sweep on 32^3 blocks: 4 planes per unit
-  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : std::min(4, maxN);
-  DecodeSmem L = decode_smem_layout(vo, maxC, maxN, ks);
+  // default slab depth from the tiling sweep on 32^3 blocks: 4 planes, 2 when C > 16 (larger T and U)
+  int ks = tune.ks > 0 ? std::min(tune.ks, maxN) : std::min(maxC > 16 ? 2 : 4, maxN);
+  // units of kUnitPlanes z-planes (several slabs) share one set-up of knots, control points and basis
+  // tables; when P and U do not both fit, one slab per unit with U over P
+  int group = std::max(1, std::min(kUnitPlanes, maxN) / ks);
+  DecodeSmem L = decode_smem_layout(vo, maxC, maxN, ks, group == 1);
+  if ((size_t)L.total * 4 > kMaxDynSmem && group > 1) {
+    group = 1;
+    L = decode_smem_layout(vo, maxC, maxN, ks, true);
+  }
   while ((size_t)L.total * 4 > kMaxDynSmem && ks > 1) {
     ks = std::max(1, ks / 2);
-    L = decode_smem_layout(vo, maxC, maxN, ks);
+    L = decode_smem_layout(vo, maxC, maxN, ks, true);
   }
   if ((size_t)L.total * 4 > kMaxDynSmem) return MFA_ERR_CAPACITY;
   prm.ks = ks;
-  prm.slabs = (maxN + ks - 1) / ks;
+  prm.group = group;
+  prm.slabs = (maxN + ks * group - 1) / (ks * group);
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
   cudaError_t e;
   switch (pmax) {

@@ -30,8 +30,9 @@ struct DecodeParams {
   uint32_t flags;
   uint32_t* status;
   uint32_t* counter;
-  int ks;     // z-planes per work unit
-  int slabs;  // work units per block = ceil(max_nsamp / ks)
+  int ks;     // z-planes per slab
+  int group;  // slabs per work unit
+  int slabs;  // work units per block = ceil(max_nsamp / (ks * group))
 };
 
 struct DecodeTuning {
