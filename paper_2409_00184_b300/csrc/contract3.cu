@@ -58,7 +58,7 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xb
   }
   L.knots = o; if (mode != kFit) o += 3 * kKnotMax;
   o = round4(o);
-  L.Y1 = o; o += ks * maxN * (mode == kGradient ? std::max(CPs, L.us) : CPs);
+  L.Y1 = o; o += ks * maxN * std::max(CPs, L.us);
   L.Y2 = o; o += round4(ks * maxC * maxC);
   L.Y = o;  o += round4(maxC * maxC * maxC);
   L.P = o;  if (mode == kGradient) o += round4(maxC * maxC * maxC);
@@ -97,12 +97,12 @@ __device__ void c3_fetch(const ContractParams& prm, int item, C3Geom& g) {
 
 // Builds the three n x CP matrices (zero-padded columns), the RMSE tables (kFit), the span offsets
 // and P (kGradient), zeroes Y. Ends with a barrier; sets *s_bad when a knot vector is invalid.
-template <int CP>
+template <int CP, int MODE>
 __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int* s_bad) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int ncps = g.C[0] * g.C[1] * g.C[2];
-  if (prm.mode == kFit) {
+  if (MODE == kFit) {
     for (int a = 0; a < 3; ++a) {
       const EncClass& c = prm.classes[g.cls[a]];
       float* A = sm + L.A[a];
@@ -120,8 +120,10 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
     for (int a = 0; a < 3; ++a) {  // every maxN row zeroed: padded sample rows must contribute nothing
       for (int i = tid; i < g.C[a] + g.p[a] + 1; i += nthr) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
       for (int e = tid; e < prm.maxN * CP; e += nthr) sm[L.A[a] + e] = 0.f;
-      if (prm.mode == kGradient)
+      if (MODE == kGradient) {  // entries past n[a] stay zero: offset 0, zero band
         for (int i = tid; i < prm.maxN; i += nthr) reinterpret_cast<int*>(sm + L.off[a])[i] = 0;
+        for (int e = tid; e < prm.maxN * (int)(sizeof(TabEntry) / 4); e += nthr) sm[L.tab[a] + e] = 0.f;
+      }
     }
     __syncthreads();
     if (tid < 3 && !knots_ok(kn + tid * kKnotMax, g.p[tid], g.C[tid])) {
@@ -137,7 +139,7 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
       float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
       basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, u, N, dN);
       for (int r = 0; r <= g.p[a]; ++r) sm[L.A[a] + i * CP + s - g.p[a] + r] = N[r];
-      if (prm.mode == kGradient) {
+      if (MODE == kGradient) {
         reinterpret_cast<int*>(sm + L.off[a])[i] = s - g.p[a];
         TabEntry te;  // band of sample i (N[r] is zero for r > p)
         te.off = s - g.p[a];
@@ -147,7 +149,7 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
     }
   }
   __syncthreads();
-  if (prm.mode == kGradient)
+  if (MODE == kGradient)
     for (int e = tid; e < ncps; e += nthr) sm[L.P + e] = prm.cps[g.cpoff + e];
   for (int e = tid; e < ncps; e += nthr) sm[L.Y + e] = 0.f;
   __syncthreads();
@@ -286,7 +288,7 @@ __device__ void c3_stage_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0,
 
 // Writes the block's result Y; for the fit also the RMSE of
 // the fitted model (banded value decode vs the samples; per-thread FP32 Kahan sums reduced in FP64).
-template <int CP>
+template <int CP, int MODE>
 __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* sm, const C3Geom& g, int item,
                             const float* X, int ks, double* s_red) {
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -294,7 +296,7 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = Cx * Cy, ncps = plane * Cz;
   const float* Y = sm + L.Y;
-  if (prm.mode != kFit) {  // adjoint N^T R, or gradient N^T (decode(P) - D)
+  if (MODE != kFit) {  // adjoint N^T R, or gradient N^T (decode(P) - D)
     for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
     return;
   }
@@ -348,116 +350,84 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
   }
 }
 
-// Gradient mode: replaces the slab's samples D in the swizzled buffer by r = decode_value(P) - D.
-// Banded value decode: stage z of P for the slab (-> Y2 = T[kl][b][a]), then thread per sample row
-// r = (kl, j): U[a] = sum_d T[kl][o_j + d][a] N_y[j][d] into the row's scratch in Y1, and
-// f_i = sum_d U[o_i + d] N_x[i][d] through a window u_0..u_3 = U[oc .. oc+3] that slides with the band.
-__device__ void c3_residual_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, float4* xb, int k0, int kc) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int Cx = g.C[0], Cy = g.C[1], nx = g.n[0], ny = g.n[1];
-  const int plane = Cx * Cy;
-  const float* P = sm + L.P;
-  float* Y2 = sm + L.Y2;
-  const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
-  const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
-  const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
-  for (int ab = tid; ab < plane; ab += nthr)  // stage z: thread per (b, a), all kl of the slab
-    for (int kl = 0; kl < kc; ++kl) {
-      const TabEntry te = tz[k0 + kl];
-      float acc = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(P[(te.off + d) * plane + ab], te.N[d], acc);
-      Y2[kl * plane + ab] = acc;
-    }
-  __syncthreads();
-  for (int r = tid; r < kc * ny; r += nthr) {  // stages y and x, thread per row
-    const int kl = r / ny, j = r - kl * ny;
-    float* ur = sm + L.Y1 + r * L.us;
-    {
-      const TabEntry te = ty[j];
-      const float* tp = Y2 + (kl * Cy + te.off) * Cx;
-      for (int a = 0; a < Cx; ++a) {
-        float u = 0.f;
-        _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) u = fmaf(tp[d * Cx + a], te.N[d], u);
-        ur[a] = u;
-      }
-    }
-    float u0 = ur[0], u1 = Cx > 1 ? ur[1] : 0.f, u2 = Cx > 2 ? ur[2] : 0.f, u3 = Cx > 3 ? ur[3] : 0.f;
-    int oc = 0;
-    const int sw = r & 7;
-    for (int i4 = 0; i4 < nx; i4 += 4) {
-      float4* cp = xb + r * 8 + ((i4 >> 2) ^ sw);
-      float dd[4] = {cp->x, cp->y, cp->z, cp->w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (i4 + q < nx) {
-          const TabEntry te = tx[i4 + q];
-          while (oc < te.off) {
-            u0 = u1; u1 = u2; u2 = u3;
-            u3 = oc + 4 < Cx ? ur[oc + 4] : 0.f;
-            ++oc;
-          }
-          dd[q] = fmaf(te.N[0], u0, fmaf(te.N[1], u1, fmaf(te.N[2], u2, te.N[3] * u3))) - dd[q];
-        }
-      }
-      *cp = make_float4(dd[0], dd[1], dd[2], dd[3]);
-    }
-  }
-  __syncthreads();
-}
+// Banded value decode of one z-slab inside the contraction kernel, on rows of 32 samples in the
+// 128-byte-swizzled slab buffer (logical 16-byte chunk c of row r at chunk c ^ (r & 7)):
+//   stage z  T[kl][b][a]  = sum_d Q[o_k + d][b][a] N_z[k][d]      (-> Y2; flat over (kl, b, a))
+//   stage y  U[(kl,j)][a] = sum_d T[kl][o_j + d][a] N_y[j][d]      (-> rows of Y1, stride ys; a thread
+//                                                                 keeps one column a and steps over rows)
+//   stage x  f[(kl,j)][i] = sum_d U[(kl,j)][o_i + d] N_x[i][d]     (a thread owns sample i)
+// kResidual (gradient): Q = P, and the buffer's samples D become r = f - D in place.
+// kRmse (fit): Q = the fitted control points, (f - D)^2 goes into the thread's Kahan sum.
+enum SlabDecode { kResidual = 0, kRmse = 1 };
 
-// RMSE contribution of one z-slab on the TMA path: banded value decode of the fitted model Y
-// (stage z -> Y2, stage y -> Y1, stage x) compared with the slab's samples in the swizzled buffer.
-// Squared errors go into a per-thread FP32 Kahan sum.
-__device__ void c3_rmse_slab_smem(const C3Smem& L, float* sm, const C3Geom& g, const float4* xb, int k0, int kc,
-                                  float& ksum, float& kcomp) {
+template <int MODE, bool SHORT_ROWS>
+__device__ void c3_value_decode_slab(const C3Smem& L, float* sm, const C3Geom& g, const float* Q, float4* xb,
+                                     int k0, int kc, int ys, float& ksum, float& kcomp) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int Cx = g.C[0], Cy = g.C[1], ny = g.n[1];
   const int plane = Cx * Cy;
-  const float* Y = sm + L.Y;
   float* Y1 = sm + L.Y1;
   float* Y2 = sm + L.Y2;
   const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
   const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
   const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
-  for (int ab = tid; ab < plane; ab += nthr) {  // stage z: thread per (b, a), all kl of the slab
-    for (int kl = 0; kl < kc; ++kl) {
+  {  // stage z, flat index e = kl*plane + ab with incremental (kl, ab)
+    int kl = tid / plane, ab = tid - (tid / plane) * plane;
+    for (int e = tid; e < kc * plane; e += nthr) {
       const TabEntry te = tz[k0 + kl];
       float acc = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(Y[(te.off + d) * plane + ab], te.N[d], acc);
-      Y2[kl * plane + ab] = acc;
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[2]) acc = fmaf(Q[(te.off + d) * plane + ab], te.N[d], acc);
+      Y2[e] = acc;
+      ab += nthr;
+      while (ab >= plane) { ab -= plane; ++kl; }
     }
   }
   __syncthreads();
-  for (int e = tid; e < kc * Cx; e += nthr) {  // stage y: thread per (kl, a), all j
-    const int kl = e / Cx, a = e - kl * Cx;
-    for (int j = 0; j < ny; ++j) {
-      const TabEntry te = ty[j];
-      float acc = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) acc = fmaf(Y2[(kl * Cy + te.off + d) * Cx + a], te.N[d], acc);
-      Y1[(kl * ny + j) * Cx + a] = acc;
+  {  // stage y: thread keeps column a; rows r = (kl, j) advance by `step`
+    const int step = nthr / Cx, grp = tid / Cx;
+    if (grp < step) {
+      const int a = tid - grp * Cx;
+      int kl = grp / ny, j = grp - (grp / ny) * ny;
+      for (int r = grp; r < kc * ny; r += step) {
+        const TabEntry te = ty[j];
+        const float* tp = Y2 + (kl * Cy + te.off) * Cx + a;
+        float u = 0.f;
+        _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[1]) u = fmaf(tp[d * Cx], te.N[d], u);
+        Y1[r * ys + a] = u;
+        j += step;
+        while (j >= ny) { j -= ny; ++kl; }
+      }
     }
   }
   __syncthreads();
-  {  // stage x: thread keeps sample i (32-sample rows), compares with the swizzled samples
-    const int i = tid & 31, r0 = tid >> 5, rstep = nthr >> 5;
+  // stage x: thread owns sample i of 32-sample rows; rows r0, r0 + nthr/32, ...; with SHORT_ROWS the
+  // samples i >= nx (zero padding of shorter rows) are left as they are
+  const int i = tid & 31;
+  if (!SHORT_ROWS || i < g.n[0]) {
+    const int rstep = nthr >> 5;
     const TabEntry te = tx[i];
-    for (int r = r0; r < kc * ny; r += rstep) {
+    float* xf = reinterpret_cast<float*>(xb);
+    for (int r = tid >> 5; r < kc * ny; r += rstep) {
+      const float* ur = Y1 + r * ys + te.off;
       float f = 0.f;
-      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(Y1[r * Cx + te.off + d], te.N[d], f);
-      const float4 c4 = xb[r * 8 + ((i >> 2) ^ (r & 7))];
-      const float dv = (i & 3) == 0 ? c4.x : ((i & 3) == 1 ? c4.y : ((i & 3) == 2 ? c4.z : c4.w));
-      const float diff = f - dv;
-      const float y = diff * diff - kcomp;
-      const float t = ksum + y;
-      kcomp = (t - ksum) - y;
-      ksum = t;
+      _Pragma("unroll") for (int d = 0; d <= MFA_MAX_DEGREE; ++d) if (d <= g.p[0]) f = fmaf(ur[d], te.N[d], f);
+      const int idx = r * 32 + (((i >> 2) ^ (r & 7)) << 2) + (i & 3);
+      if (MODE == kResidual) {
+        xf[idx] = f - xf[idx];
+      } else {
+        const float diff = f - xf[idx];
+        const float y = diff * diff - kcomp;
+        const float t = ksum + y;
+        kcomp = (t - ksum) - y;
+        ksum = t;
+      }
     }
   }
   __syncthreads();
 }
 
 // Queue kernel: blocks from an atomic counter, rows read from global memory.
-template <int CP>
+template <int CP, int MODE>
 __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm, C3Smem L, int ks, int vec_ok) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item, s_bad;
@@ -475,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm,
     if (!s_g.valid) break;
     if (s_g.bad) continue;
     const C3Geom& g = s_g;
-    c3_setup<CP>(prm, L, sm, g, &s_bad);
+    c3_setup<CP, MODE>(prm, L, sm, g, &s_bad);
     if (s_bad) continue;
     const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
     const bool vec = vec_ok && (g.n[0] % 4 == 0);
@@ -485,12 +455,12 @@ __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm,
       __syncthreads();
       c3_stage_yz<CP>(L, sm, g, k0, kc);
     }
-    c3_epilogue<CP>(prm, L, sm, g, s_item, X, ks, s_red);
+    c3_epilogue<CP, MODE>(prm, L, sm, g, s_item, X, ks, s_red);
   }
 }
 
 // TMA kernel: static schedule (blocks blockIdx.x, +gridDim.x, ...), slab loads double-buffered.
-template <int CP>
+template <int CP, int MODE>
 __global__ void __launch_bounds__(kThreads)
 contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const __grid_constant__ CUtensorMap xmap) {
   extern __shared__ __align__(16) float sm[];
@@ -518,7 +488,7 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
   auto tma_ok = [&](const C3Geom& g) {
     return g.valid && !g.bad && g.n[0] == kTmaRow && (int64_t)ks * g.n[1] <= box_rows;
   };
-  if (tid == 0 && prm.mode == kGradient && s_g[0].valid && !s_g[0].bad && s_g[0].n[0] > kTmaRow)
+  if (tid == 0 && MODE == kGradient && s_g[0].valid && !s_g[0].bad && s_g[0].n[0] > kTmaRow)
     flag(prm.status, MFA_DEV_BAD_DESC);
   auto issue = [&](const C3Geom& g, int k0) {  // one thread
     const int b = q_issue & 1;
@@ -541,13 +511,13 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
     const C3Geom& g = s_g[cur];
     const C3Geom& gn = s_g[cur ^ 1];
     const bool use_tma = tma_ok(g);
-    if (!g.bad) c3_setup<CP>(prm, L, sm, g, &s_bad);
+    if (!g.bad) c3_setup<CP, MODE>(prm, L, sm, g, &s_bad);
     const bool skip = g.bad || s_bad;
     const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
     const int nz = g.valid && !g.bad ? g.n[2] : 0;
     const int nslab = (nz + ks - 1) / ks;
     // units of this block: the contraction's slabs, then (fit with RMSE, TMA rows) the residual slabs
-    const bool rmse_pass = prm.mode == kFit && prm.rmse && use_tma;
+    const bool rmse_pass = MODE == kFit && prm.rmse && use_tma;
     const int nunits = nslab * (rmse_pass ? 2 : 1);
     float ksum = 0.f, kcomp = 0.f;
     for (int u = 0; u < nunits; ++u) {
@@ -577,13 +547,15 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
         }
         if (!skip) {
           if (pass == 0) {
-            if (prm.mode == kGradient) c3_residual_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc);
+            if (MODE == kGradient)
+              c3_value_decode_slab<kResidual, false>(L, sm, g, sm + L.P, xbuf + b * buf_f4, k0, kc, L.us, ksum,
+                                                     kcomp);
             c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
           } else {
-            c3_rmse_slab_smem(L, sm, g, xbuf + b * buf_f4, k0, kc, ksum, kcomp);
+            c3_value_decode_slab<kRmse, false>(L, sm, g, sm + L.Y, xbuf + b * buf_f4, k0, kc, L.us, ksum, kcomp);
           }
         }
-      } else if (!skip && prm.mode == kGradient) {
+      } else if (!skip && MODE == kGradient) {
         // rows shorter than 32 samples: fill the buffer no TMA copy is using, zero-padded and swizzled
         float4* xb = xbuf + (q_issue & 1) * buf_f4;
         float* xf = reinterpret_cast<float*>(xb);
@@ -594,7 +566,7 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
           xf[r * kTmaRow + (((i >> 2) ^ (r & 7)) << 2) + (i & 3)] = v;
         }
         __syncthreads();
-        c3_residual_slab_smem(L, sm, g, xb, k0, kc);
+        c3_value_decode_slab<kResidual, true>(L, sm, g, sm + L.P, xb, k0, kc, L.us, ksum, kcomp);
         c3_stage_x_smem<CP>(xb, sm + L.A[0], sm + L.Y1, rows);
       } else if (!skip) {
         c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
@@ -622,7 +594,7 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
           prm.rmse[item] = sqrt(tot / ((double)g.n[0] * g.n[1] * g.n[2]));
         }
       } else {
-        c3_epilogue<CP>(prm, L, sm, g, item, X, ks, s_red);
+        c3_epilogue<CP, MODE>(prm, L, sm, g, item, X, ks, s_red);
       }
     }
     __syncthreads();
@@ -638,7 +610,8 @@ cudaError_t launch_c3(mfa_ctx* ctx, const ContractParams& prm, const C3Smem& L, 
   int occ = 0;
   cudaError_t e;
   if (xmap) {
-    auto kern = contract3_tma_kernel<CP>;
+    auto kern = prm.mode == kFit ? contract3_tma_kernel<CP, kFit>
+                                 : (prm.mode == kAdjoint ? contract3_tma_kernel<CP, kAdjoint> : contract3_tma_kernel<CP, kGradient>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
@@ -647,7 +620,8 @@ cudaError_t launch_c3(mfa_ctx* ctx, const ContractParams& prm, const C3Smem& L, 
     const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
     kern<<<grid, kThreads, smem, stream>>>(prm, L, ks, box_rows, *xmap);
   } else {
-    auto kern = contract3_kernel<CP>;
+    if (prm.mode == kGradient) return cudaErrorInvalidValue;  // the gradient needs the TMA path
+    auto kern = prm.mode == kFit ? contract3_kernel<CP, kFit> : contract3_kernel<CP, kAdjoint>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
