@@ -268,6 +268,20 @@ int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
 int mfa_select_ncp(mfa_ctx* ctx, const double* d_errors, int32_t ncand, const int32_t* h_ncp,
                    int64_t nblocks, double bound, int32_t* d_ncp_out, void* stream);
 
+/* Multi-resolution partition (Sec. 4.2 and Algorithm 1): the micro-blocks of one level of detail.
+ * d_field holds dims[0] x dims[1] x dims[2] FP32 samples, [z][y][x] (x fastest). Level `stride`
+ * (1, 2, 4, ...) cuts the field into blocks of n*stride samples per axis (dims[a] must be a
+ * multiple of n*stride) and keeps every stride-th sample of each, so every micro-block has n^3
+ * samples. Block (bx, by, bz) has id (bz*By + by)*Bx + bx with B_a = dims[a]/(n*stride); its
+ * sample (i, j, k) is field[(bz*n + k)*stride][(by*n + j)*stride][(bx*n + i)*stride].
+ * d_ids (nullable) lists the nblocks block ids to gather, else ids 0..nblocks-1 are gathered;
+ * entry e goes to slot e of d_out (slot_stride >= n^3 floats per slot). Device buffers 4-byte
+ * aligned. Returns MFA_ERR_INVALID_ARG for null pointers, n < 2 or > MFA_MAX_NSAMP, stride < 1,
+ * dims not multiples of n*stride, nblocks < 0 or, without d_ids, more than the level's blocks;
+ * a listed id outside the level sets MFA_DEV_BAD_LIST and its slot is left untouched. */
+int mfa_lod_gather(mfa_ctx* ctx, const float* d_field, const int32_t dims[3], int32_t n, int32_t stride,
+                   const int32_t* d_ids, int32_t nblocks, float* d_out, int64_t slot_stride, void* stream);
+
 /* Allocation-free least-squares encode. The paper has no counterpart to this entry point: it
  * exists for callers that cannot call cudaMalloc - a process whose device memory is reserved
  * by another runtime's memory pool, so that a fresh allocation fails or has to wait for that

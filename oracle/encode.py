@@ -15,7 +15,9 @@ A = N_z (x) N_y (x) N_x of the per-axis collocation matrices N_a[i, c] = N_c(u_i
   for full-column-rank factors: P = D x_1 N_x^+ x_2 N_y^+ x_3 N_z^+, with each
   N_a^+ = (N_a^T N_a)^{-1} N_a^T from a library solve.
 
-Eq. 2 (model size) and Eq. 4 (NCP* selection) are written out as well.
+Eq. 2 (model size) and Eq. 4 (NCP* selection) are written out as well, and the cross-level
+adaptive encoding of Algorithm 1 (Sec. 4.2.3) over levels of detail built by strided
+decimation of the field.
 """
 
 import numpy as np
@@ -91,3 +93,66 @@ def fit_separable_batch(Dblocks, knots, degrees):
     Py = pseudo_inverse(collocation(knots[1], degrees[1], ny))
     Pz = pseudo_inverse(collocation(knots[2], degrees[2], nz))
     return np.einsum("ck,bj,ai,nkji->ncba", Pz, Py, Px, D, optimize=True)
+
+
+def lod_blocks(field, n, stride):
+    """Micro-blocks of one level of detail: blocks of n*stride samples per axis of a field (Nz, Ny, Nx),
+    keeping every stride-th sample. Returns (blocks (B, n, n, n) as [k][j][i], blocks_per_axis (Bx, By, Bz));
+    block id = (bz*By + by)*Bx + bx."""
+    F = np.asarray(field)
+    Nz, Ny, Nx = F.shape
+    span = n * stride
+    Bx, By, Bz = Nx // span, Ny // span, Nz // span
+    out = []
+    for bz in range(Bz):
+        for by in range(By):
+            for bx in range(Bx):
+                blk = F[bz * span:(bz + 1) * span:stride, by * span:(by + 1) * span:stride,
+                        bx * span:(bx + 1) * span:stride]
+                out.append(blk)
+    return np.array(out), (Bx, By, Bz)
+
+
+def cross_level_select(field, n, degree, bound, levels, knots_of=None):
+    """Algorithm 1 (cross-level adaptive encoding), coarsest level first.
+
+    The coarsest level searches every micro-block; a finer level searches only the micro-blocks whose
+    parent (the coarser block containing them) was complex. A search fits every NCP in [degree + 2, n]
+    and takes NCP* by Eq. 4 on the fit's RMSE; the block is simple when NCP* = degree + 2, else complex
+    (no NCP below the bound: complex, encoded with NCP = n). Blocks not searched take NCP = degree + 1.
+    knots_of(C) gives the knot vector used for C control points (default: clamped uniform).
+    Returns a list of dicts (level, ncp, searched, complex, errors {block: {C: RMSE}})."""
+    if knots_of is None:
+        def knots_of(C):
+            inner = [j / (C - degree) for j in range(1, C - degree)]
+            return np.array([0.0] * (degree + 1) + inner + [1.0] * (degree + 1))
+    cands = list(range(degree + 2, n + 1))
+    result, parent_complex, parent_B = [], None, None
+    for lvl in range(levels - 1, -1, -1):
+        blocks, B = lod_blocks(field, n, 2 ** lvl)
+        nb = len(blocks)
+        ncp = np.full(nb, degree + 1, dtype=np.int64)
+        searched = np.zeros(nb, dtype=bool)
+        cplx = np.zeros(nb, dtype=bool)
+        errors = {}
+        for b in range(nb):
+            bx, by, bz = b % B[0], (b // B[0]) % B[1], b // (B[0] * B[1])
+            if parent_complex is not None:
+                parent = ((bz // 2) * parent_B[1] + by // 2) * parent_B[0] + bx // 2
+                if not parent_complex[parent]:
+                    continue
+            searched[b] = True
+            D = blocks[b].astype(np.float64)
+            errs = {}
+            for C in cands:
+                kn = (knots_of(C),) * 3
+                P = fit_separable(D, kn, (degree,) * 3)
+                errs[C] = rmse(P, D, kn, (degree,) * 3)
+            errors[b] = errs
+            star = select_ncp(errs, bound)
+            ncp[b] = n if star is None else star
+            cplx[b] = star != degree + 2
+        result.append({"level": lvl, "ncp": ncp, "searched": searched, "complex": cplx, "errors": errors,
+                       "blocks_per_axis": B})
+        parent_complex, parent_B = cplx, B
+    return result

@@ -66,3 +66,78 @@ def search_ncp(ctx, data, nsamp, degree, bound, candidates=None, keep_errors=Tru
         plan.close()
     ncp = mfa.select_ncp(ctx, errors, candidates, bound, stream=stream)
     return ncp, (errors if keep_errors else None)
+
+
+def mixed_blocks(ncps, degree, nsamp, device="cuda"):
+    """DeviceBlocks of isotropic models with per-block NCP (ncps: int array), clamped uniform knots
+    (one vector per distinct NCP), nsamp^3 samples; block b reads sample slot b."""
+    ncps = np.asarray(ncps, dtype=np.int64)
+    nb = len(ncps)
+    vectors, offs, o = [], {}, 0
+    for C in sorted(set(ncps.tolist())):
+        t = clamped_uniform_knots(C, degree)
+        offs[C] = o
+        vectors.append(t)
+        o += len(t)
+    knots = np.concatenate(vectors) if vectors else np.zeros(0, np.float32)
+    koff = np.array([offs[C] for C in ncps.tolist()], np.int64).reshape(-1, 1).repeat(3, axis=1)
+    cp_off = np.concatenate([[0], np.cumsum(ncps ** 3)[:-1]]).astype(np.int64) if nb else np.zeros(0, np.int64)
+    batch = _Batch(
+        degree=np.full((nb, 3), degree, np.int32), ncp=np.repeat(ncps.reshape(-1, 1), 3, axis=1).astype(np.int32),
+        nsamp=np.full((nb, 3), nsamp, np.int32), slot=np.arange(nb, dtype=np.int64), knot_off=koff,
+        cp_off=cp_off, knots=knots)
+    cps = torch.zeros(int((ncps ** 3).sum()), dtype=torch.float32, device=device)
+    return mfa.DeviceBlocks(batch, device=device, cps=cps)
+
+
+def cross_level_encode(ctx, field, n, degree, bound, levels, encode=True, search_all=False, stream=None):
+    """Cross-level adaptive encoding (Sec. 4.2.3, Algorithm 1) of a float32 CUDA field (Nz, Ny, Nx).
+
+    Level l (0 = finest) has micro-blocks of n^3 samples taken every 2^l samples. From the coarsest level
+    to the finest: the blocks of the coarsest level, and at every finer level the blocks whose parent
+    block is complex, are searched over NCP in [degree + 2, n] (Eq. 4 on the RMSE of each fit); a searched
+    block is simple when its NCP* is degree + 2, complex otherwise (no candidate below the bound counts
+    as complex and is encoded with NCP = n). Blocks that are not searched take NCP = degree + 1.
+    With `encode`, every level is then fitted with its per-block NCP in one batched call. With
+    `search_all`, every block of every level is searched (in-level adaptive encoding alone, the baseline
+    that Algorithm 1 speeds up).
+
+    Returns a list, coarsest level first, of dicts: level, stride, blocks_per_axis, ncp (int32 numpy),
+    searched, complex (bool numpy), fits (candidate fits run), and with `encode` blocks (DeviceBlocks
+    holding the control points) and rmse (float64 CUDA tensor)."""
+    Nz, Ny, Nx = field.shape
+    cands = list(range(degree + 2, min(n, mfa.MAX_NCP) + 1))
+    out, parent_complex, parent_B = [], None, None
+    for lvl in range(levels - 1, -1, -1):
+        s = 2 ** lvl
+        B = (Nx // (n * s), Ny // (n * s), Nz // (n * s))
+        nb = B[0] * B[1] * B[2]
+        if parent_complex is None or search_all:
+            search = np.arange(nb)
+        else:
+            bz, by, bx = np.unravel_index(np.arange(nb), (B[2], B[1], B[0]))
+            parent = ((bz // 2) * parent_B[1] + by // 2) * parent_B[0] + bx // 2
+            search = np.nonzero(parent_complex[parent])[0]
+        ncp = np.full(nb, degree + 1, np.int32)
+        cplx = np.zeros(nb, bool)
+        if len(search):
+            ids = torch.as_tensor(search.astype(np.int32), device=field.device)
+            D = mfa.lod_gather(ctx, field, n, s, ids=ids, stream=stream)
+            sel, _ = search_ncp(ctx, D.view(-1), n, degree, bound, candidates=cands, keep_errors=False,
+                                stream=stream)
+            sel = sel.cpu().numpy()
+            ncp[search] = np.where(sel > 0, sel, n)
+            cplx[search] = sel != degree + 2
+        rec = {"level": lvl, "stride": s, "blocks_per_axis": B, "ncp": ncp, "complex": cplx,
+               "searched": np.isin(np.arange(nb), search), "fits": len(search) * len(cands)}
+        if encode:
+            D = mfa.lod_gather(ctx, field, n, s, stream=stream)
+            blk = mixed_blocks(ncp, degree, n, device=field.device)
+            plan = mfa.EncodePlan(ctx, blk)
+            rmse = torch.empty(nb, dtype=torch.float64, device=field.device)
+            mfa.encode_blocks(ctx, plan, D.view(-1), n ** 3, nb, blk.cps, rmse, stream=stream)
+            plan.close()
+            rec["blocks"], rec["rmse"] = blk, rmse
+        out.append(rec)
+        parent_complex, parent_B = cplx, B
+    return out

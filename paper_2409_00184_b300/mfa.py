@@ -64,7 +64,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
-           "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout"]
+           "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather"]
 
 
 def _load():
@@ -93,6 +93,7 @@ def _load():
         "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
         "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
         "mfa_selftest_wait_timeout": (ctypes.c_int, [P, I32, P]),
+        "mfa_lod_gather": (ctypes.c_int, [P, P, ctypes.POINTER(I32), I32, I32, P, I32, P, I64, P]),
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
@@ -330,6 +331,27 @@ def select_ncp(ctx, errors, ncps, bound, out=None, stream=None):
     h = (ctypes.c_int32 * ncand)(*[int(c) for c in ncps])
     _check(lib.mfa_select_ncp(ctx.handle, _ptr(errors), ncand, h, nb, float(bound), _ptr(out), _stream(stream)),
            "mfa_select_ncp")
+    return out
+
+
+def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=None):
+    """mfa_lod_gather: the n^3 micro-blocks of one level of detail (every stride-th sample of blocks of
+    n*stride samples per axis) of a float32 CUDA field of shape (Nz, Ny, Nx). ids: int32 CUDA tensor of
+    block ids (None = the first nblocks, default all). Returns a float32 tensor (len, n^3)."""
+    if field.dim() != 3:
+        raise ValueError("field: (Nz, Ny, Nx) tensor")
+    Nz, Ny, Nx = field.shape
+    span = n * stride
+    total = (Nx // span) * (Ny // span) * (Nz // span)
+    count = ids.numel() if ids is not None else (total if nblocks is None else nblocks)
+    if out is None:
+        out = torch.empty((count, n ** 3), dtype=torch.float32, device=field.device)
+    _need(out, count * n ** 3, "out")
+    dims = (ctypes.c_int32 * 3)(Nx, Ny, Nz)
+    if count == 0:
+        return out
+    _check(lib.mfa_lod_gather(ctx.handle, _ptr(field), dims, n, stride, _ptr(ids), count, _ptr(out), n ** 3,
+                              _stream(stream)), "mfa_lod_gather")
     return out
 
 

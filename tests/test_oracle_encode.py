@@ -101,3 +101,64 @@ def test_marschner_lobb_gradient_matches_finite_differences():
         a = synth.marschner_lobb(*(p + e).T)[0]
         b = synth.marschner_lobb(*(p - e).T)[0]
         assert np.max(np.abs((a - b) / (2 * h) - an)) < 1e-6
+
+
+def test_lod_blocks_closed_form():
+    """Level of detail with stride s: sample (i, j, k) of block (bx, by, bz) is the field at
+    ((bx n + i) s, (by n + j) s, (bz n + k) s); with f = x + 10 y + 100 z that is a closed form."""
+    N, n, s = 24, 3, 4
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    F = x + 10.0 * y + 100.0 * z
+    blocks, B = encode.lod_blocks(F, n, s)
+    assert B == (2, 2, 2) and blocks.shape == (8, n, n, n)
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    for b in range(8):
+        bx, by, bz = b % 2, (b // 2) % 2, b // 4
+        want = (bx * n + i) * s + 10.0 * (by * n + j) * s + 100.0 * (bz * n + k) * s
+        assert np.array_equal(blocks[b], want)
+
+
+def test_cross_level_constant_half_is_never_refined():
+    """Algorithm 1 on a field that is constant for z < N/2 and random for z >= N/2 (n = 4, degree 1,
+    NCP in [3, 4]): constant blocks are fitted exactly by any NCP, so they are simple (NCP* = 3) at the
+    coarsest level and their descendants are never searched (NCP = degree + 1 = 2); random blocks need
+    the interpolating NCP = n = 4 (zero error), so they are complex and every level refines them."""
+    N, n, p = 32, 4, 1
+    F = np.full((N, N, N), 0.5)
+    F[N // 2:] = synth.rng(44).uniform(0, 1, (N // 2, N, N))
+    res = encode.cross_level_select(F, n, p, 1e-3, levels=3)
+    assert [r["level"] for r in res] == [2, 1, 0]
+    for r in res:
+        Bx, By, Bz = r["blocks_per_axis"]
+        bz = np.arange(Bx * By * Bz) // (Bx * By)
+        upper = bz >= Bz // 2
+        if r["level"] == 2:
+            assert r["searched"].all()
+        else:
+            assert np.array_equal(r["searched"], upper)
+        assert np.array_equal(r["complex"], upper)
+        assert np.all(r["ncp"][upper] == n)
+        lower_searched = ~upper & r["searched"]
+        assert np.all(r["ncp"][lower_searched] == p + 2)
+        assert np.all(r["ncp"][~r["searched"]] == p + 1)
+        for b, errs in r["errors"].items():
+            if not upper[b]:
+                assert max(errs.values()) < 1e-12
+            else:
+                assert errs[n] < 1e-12 and errs[p + 2] > 1e-3
+
+
+def test_cross_level_searches_exactly_the_children_of_complex_blocks():
+    g = synth.rng(45)
+    N, n, p = 48, 6, 2
+    F = g.uniform(0, 1, (N, N, N))
+    F[:, : N // 2] = np.linspace(0, 1, N)[None, None, :]  # linear in x: exactly fitted, simple
+    res = encode.cross_level_select(F, n, p, 1e-2, levels=3)
+    for coarse, fine in zip(res[:-1], res[1:]):
+        Bx, By, Bz = fine["blocks_per_axis"]
+        ids = np.arange(Bx * By * Bz)
+        bx, by, bz = ids % Bx, (ids // Bx) % By, ids // (Bx * By)
+        cB = coarse["blocks_per_axis"]
+        parent = ((bz // 2) * cB[1] + by // 2) * cB[0] + bx // 2
+        assert np.array_equal(fine["searched"], coarse["complex"][parent])
+    assert any(r["complex"].any() for r in res) and any((~r["complex"] & r["searched"]).any() for r in res)
