@@ -77,6 +77,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest of every rank's x (a float); x itself for one rank. Uses the initialised process
+    group (NCCL with CUDA tensors on the GPUs; gloo with CPU tensors in the tests)."""
+    if ws <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws, units_per_rank, ms):
+    """Whole-job throughput in G-units/s: every rank's units over the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank / (ms * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -651,16 +667,12 @@ def main():
     ms = start.elapsed_time(end) / K
     names = ["encode", "decode", "raycast", "adjoint"]
     per = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)) for i, n in enumerate(names)}
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
     st = ctx.device_status()
     if st:
         raise RuntimeError(f"device status {st:#x} after the timed steps")
     voxels = w.B * w.vox
-    value = ws * voxels / (ms * 1e-3) / 1e9
+    value = job_throughput(ws, voxels, ms)
 
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -723,8 +735,8 @@ def main():
             hostImg.copy_(w.image, non_blocking=True)
         e2.record(stream)
         barrier()
-        ms_e2e = s2.elapsed_time(e2) / Ke
-        e2e = {"value": ws * voxels / (ms_e2e * 1e-3) / 1e9, "unit": "Gvoxel/s",
+        ms_e2e = max_over_ranks(s2.elapsed_time(e2) / Ke, ws, "cuda")
+        e2e = {"value": job_throughput(ws, voxels, ms_e2e), "unit": "Gvoxel/s",
                "h2d_bytes_per_step": hostD.numel() * 4, "d2h_bytes_per_step": hostImg.numel() * 4,
                "ms_per_step": ms_e2e,
                "pipelining": "pinned host samples copied each step on a second stream into one of two device "
