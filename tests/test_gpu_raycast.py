@@ -145,3 +145,16 @@ def test_raycast_queue_ragged_image_and_sample_count(mfa, ctx, wh):
     assert not np.isnan(got).any()
     assert marched == int(np.asarray(K).sum())
     assert np.max(np.abs(got - want)) <= 1e-4
+
+
+def test_raycast_half_voxel_steps_and_value_window(mfa, ctx, volume):
+    """step_voxels = 1/2 (opacity correction 1 - (1 - a)^(1/2) per sample) and a value window narrower than
+    the field's range (values outside it clamp to the end entries)."""
+    cache, n = volume
+    ident, _, holes = _tables(4)
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=48, height=40, opacity_max=1.0, step_voxels=0.5, vmin=0.2, vmax=0.8)
+    for table in (ident, holes):
+        got = _run(mfa, ctx, cache, table, n, view, tf)
+        want = ocast.raycast(cache, table, n, view, tf)
+        assert np.max(np.abs(got - want)) <= 1e-4

@@ -93,3 +93,50 @@ def test_center_pixel_ray_is_view_direction():
     d, _, _, _, _ = raycast.ray_setup(view, (64, 64, 64))
     fwd = -np.array(view["eye"]) / np.linalg.norm(view["eye"])
     assert np.max(np.abs(d[2, 3] - fwd)) < 1e-6
+
+
+def test_opacity_correction_closed_form():
+    """Half-voxel steps (step_voxels = 1/2): alpha' = 1 - (1 - alpha)^(1/2) per sample, so a constant field
+    gives A = 1 - (1 - alpha)^(K/2) over the K samples of the chord."""
+    B, n = 2, 8
+    N = B * n
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, 0.5), 0 * x, 0 * x, 0 * x], -1))
+    alpha = float(np.float32(0.05))
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=1.0, step_voxels=0.5)
+    img = raycast.raycast(cache, table, n, view, _const_tf([1.0, 1.0, 1.0, alpha]))
+    _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
+    assert K[2, 2] == 2 * (N - 1)
+    assert abs(img[2, 2, 3] - (1 - (1 - alpha) ** (K[2, 2] / 2))) < 1e-12
+
+
+def test_transfer_function_interpolation_and_clamp():
+    """A two-entry transfer function over [vmin, vmax] interpolates linearly in the value and clamps
+    outside: constant fields at 0.25 and at 2.0 give alpha(0.25) = a0 + 0.25 (a1 - a0) and alpha(1) = a1."""
+    B, n = 2, 8
+    N = B * n
+    a0, a1 = float(np.float32(0.02)), float(np.float32(0.1))
+    tf = np.array([[1.0, 0.0, 0.0, a0], [0.0, 0.0, 1.0, a1]], dtype=np.float32)
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=1.0, vmin=0.0, vmax=1.0)
+    _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
+    for value, a, rgb in [(0.25, a0 + 0.25 * (a1 - a0), (0.75, 0.0, 0.25)), (2.0, a1, (0.0, 0.0, 1.0))]:
+        cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, value), 0 * x, 0 * x, 0 * x], -1))
+        img = raycast.raycast(cache, table, n, view, tf)
+        A = 1 - (1 - a) ** K[2, 2]
+        assert abs(img[2, 2, 3] - A) < 1e-12
+        assert np.max(np.abs(img[2, 2, :3] - np.array(rgb) * A)) < 1e-12
+
+
+def test_trilinear_interpolation_across_bricks_is_exact_for_linear_fields():
+    """A field linear in x, f = 0.1 + 0.05 x (node units), seen by the centre ray along z (world x = 0, i.e.
+    node x = (N - 1)/2 = 7.5, halfway between the last node of brick 0 and the first of brick 1): every sample
+    reads f = 0.1 + 0.05 * 7.5 = 0.475 exactly, and a transfer function linear in the value gives its alpha."""
+    B, n = 2, 8
+    N = B * n
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([0.1 + 0.05 * x, 0 * x, 0 * x, 0 * x], -1))
+    a0, a1 = float(np.float32(0.0)), float(np.float32(0.08))
+    tf = np.array([[1.0, 1.0, 1.0, a0], [1.0, 1.0, 1.0, a1]], dtype=np.float32)
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=1.0, vmin=0.0, vmax=1.0)
+    img = raycast.raycast(cache, table, n, view, tf)
+    _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
+    a = a0 + 0.475 * (a1 - a0)
+    assert abs(img[2, 2, 3] - (1 - (1 - a) ** K[2, 2])) < 1e-12
