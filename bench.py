@@ -61,12 +61,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod"], default="step",
+    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct"],
+                    default="step",
                     help="step: the default 512^3 step; frames: adaptive-NCP frames replayed from a CUDA graph "
                          "(1024^3, ~6000 visible blocks); gd: gradient-descent fit (256^3, 512 blocks); "
                          "precision: degree-3 decode in FP32 / split-BF16 / BF16 / FP16 with errors; "
                          "ncp: Eq. 4 NCP search over every NCP in [3, 32] (512^3, 4096 blocks); "
-                         "lod: Algorithm 1 cross-level encode of a 512^3 flame over 4 levels of detail")
+                         "lod: Algorithm 1 cross-level encode of a 512^3 flame over 4 levels of detail; "
+                         "direct: ray cast with per-sample micro-model queries vs the decoded cache")
     return ap.parse_args()
 
 
@@ -610,6 +612,54 @@ def run_lod(args):
     return 0
 
 
+def run_direct(args):
+    """The default step's field, models and view rendered two ways: Algorithm 4 with per-sample queries of
+    the 4096 fitted micro-models (mfa_raycast_direct, no cache), and decode-to-cache + trilinear ray cast."""
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    w = Workload(mfa, ctx, synth.BASE_SEED + 2)
+    w.step()  # fit the control points and decode the cache
+    table = w.table
+    stream = torch.cuda.current_stream()
+    img_direct = torch.empty_like(w.image)
+    tf = w.tf
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ctx.ray_samples(reset=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, ctx.ray_samples(reset=True) / reps
+
+    K = max(1, min(args.steps, 5))
+    ms_direct, s_direct = timed(lambda: mfa.raycast_direct(ctx, w.blk, table, BRICK, w.view, tf, img_direct), K)
+    ms_cache, s_cache = timed(lambda: mfa.raycast(ctx, w.cache, w.vox, w.B, table, BRICK, w.view, tf, w.image), K)
+    ms_dec, _ = timed(lambda: mfa.decode_blocks(ctx, w.blk, w.cache, w.vox, w.B), K)
+    if ctx.device_status():
+        raise RuntimeError("device status after the ray casts")
+    diff = (img_direct - w.image).abs()
+    line = {"metric": "Algorithm 4 with per-sample micro-model queries: Gsample/s (no decoded cache)",
+            "value": s_direct / (ms_direct * 1e-3) / 1e9, "unit": "Gsample/s", "n_gpus": 1, "steps": K, "warmup": 2,
+            "ms_per_step": ms_direct, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512^3 Gaussian-mixture+noise field, 4096 fitted micro-models (12^3, degree 2), "
+                                   "1024^2 view, O_max 0.99: direct queries vs decode + trilinear cache ray cast"},
+            "samples_direct": s_direct, "samples_cache": s_cache,
+            "cache_path": {"decode_ms": ms_dec, "raycast_ms": ms_cache, "total_ms": ms_dec + ms_cache,
+                           "Gsample_s": s_cache / (ms_cache * 1e-3) / 1e9},
+            "image_diff": {"max": float(diff.max()), "mean": float(diff.mean())}}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -625,6 +675,8 @@ def main():
         return run_ncp(args) if rank == 0 else 0
     if args.workload == "lod":
         return run_lod(args) if rank == 0 else 0
+    if args.workload == "direct":
+        return run_direct(args) if rank == 0 else 0
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist

@@ -333,6 +333,23 @@ int mfa_raycast(mfa_ctx* ctx,
                 const mfa_view* view, const float* d_tf, int32_t tf_n,
                 float* d_image, void* stream);
 
+/* Algorithm 4 with per-sample queries of the micro-models instead of a decoded cache: the same rays,
+ * transfer function, shading and compositing as mfa_raycast, but every sample evaluates the value
+ * and parametric gradient of the B-spline model of its brick (the paper's valueMicroModel and
+ * gradientMicroModel). d_brick_table[(bz*By + by)*Bx + bx] is the block index (into d_desc) of
+ * brick (bx, by, bz), or -1 if absent (reads as zero). Every block must have brick_n samples per
+ * axis: its model covers nodes b*brick_n .. b*brick_n + brick_n - 1 of the brick grid (parameter
+ * u = (g - b*brick_n)/(brick_n - 1)); in the one-node gap before the next brick the sample is the
+ * linear blend, along that axis, of the two models at their common boundary (multilinear where
+ * gaps of several axes meet), as trilinear interpolation of a decoded cache would be there.
+ * Descriptors, knots and control points as for mfa_decode_blocks (bounds: the batch's maxima,
+ * max_nsamp >= brick_n); a block that fails its checks reads as absent and sets its status bit.
+ * Samples marched add to MFA_STAT_RAY_SAMPLES. */
+int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,
+                       int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
+                       const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                       const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

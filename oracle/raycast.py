@@ -23,11 +23,20 @@ uses these readings:
 The integers that floating point decides before marching (hit or miss, and the
 number of samples) are computed in FP32 with the operation order an FP32 kernel
 uses, so that both sides take the same decision; everything after that is FP64.
+
+:func:`raycast_direct` marches the same rays but queries the micro-models themselves at every
+sample (value and parametric gradient of the B-spline, as Algorithm 4's value and gradient
+queries do), with this reading for non-overlapping bricks: the model of brick b covers nodes
+b n .. b n + n - 1 (parameter u = (g - b n)/(n - 1)); in the one-node gap before brick b + 1 the
+value is the linear blend, along that axis, of the two models at their boundary (u = 1 of brick b,
+u = 0 of brick b + 1), multilinear where the gaps of several axes meet.
 """
 
 import math
 
 import numpy as np
+
+from . import decode as _decode
 
 f32 = np.float32
 
@@ -121,9 +130,51 @@ def transfer(tf, f, vmin, vmax):
 def raycast(cache, table, brick_n, view, tf):
     """Render an (H, W, 4) premultiplied RGBA image; cache: (slots, n, n, n, 4) as (f, f_u, f_v, f_w)."""
     cache = np.asarray(cache, dtype=np.float64)
-    tf = np.asarray(tf, dtype=np.float64)
     table = np.asarray(table)
+    return _march(table.shape, brick_n, view, tf, lambda g: fetch(cache, table, brick_n, g))
+
+
+def fetch_direct(blocks, table, brick_n, g):
+    """(f, f_u, f_v, f_w) of the micro-models at voxel coordinates g (M, 3), FP64 (reading in the module
+    docstring). blocks(b) -> (P (C_z, C_y, C_x), knots (t_x, t_y, t_z), degrees); table[bz, by, bx] is
+    the block of a brick or -1 (absent: zero)."""
     Bz, By, Bx = table.shape
+    B = np.array([Bx, By, Bz])
+    n = brick_n
+    g = np.clip(g, 0.0, (B * n - 1).astype(np.float64))
+    b = np.minimum(np.floor(g / n).astype(np.int64), B - 1)
+    local = g - b * n
+    gap = local > n - 1
+    u_in = np.minimum(local, n - 1) / (n - 1)
+    w = np.where(gap, local - (n - 1), 0.0)
+    out = np.zeros((len(g), 4))
+    for combo in range(8):
+        side = np.array([(combo >> a) & 1 for a in range(3)])
+        use = np.all(gap | (side == 0), axis=1)  # side 1 exists only on gap axes
+        if not use.any():
+            continue
+        bb = b + side[None, :]
+        uu = np.where(gap, np.where(side[None, :] == 1, 0.0, 1.0), u_in)
+        wt = np.prod(np.where(gap, np.where(side[None, :] == 1, w, 1.0 - w), 1.0), axis=1)
+        blk = np.full(len(g), -1, dtype=np.int64)
+        blk[use] = table[bb[use, 2], bb[use, 1], bb[use, 0]]
+        for k in np.unique(blk[use & (blk >= 0)]):
+            sel = use & (blk == k)
+            P, knots, degrees = blocks(int(k))
+            out[sel] += wt[sel, None] * _decode.evaluate_points(P, knots, degrees, uu[sel])
+    return out
+
+
+def raycast_direct(blocks, table, brick_n, view, tf):
+    """Render with a per-sample query of the micro-models (see fetch_direct) instead of a decoded cache."""
+    table = np.asarray(table)
+    return _march(table.shape, brick_n, view, tf, lambda g: fetch_direct(blocks, table, brick_n, g))
+
+
+def _march(table_shape, brick_n, view, tf, sample):
+    """Front-to-back marching of every pixel's ray; sample(g) gives (f, f_u, f_v, f_w) at voxel coords g."""
+    tf = np.asarray(tf, dtype=np.float64)
+    Bz, By, Bx = table_shape
     nodes = (Bx * brick_n, By * brick_n, Bz * brick_n)
     H, W = int(view["height"]), int(view["width"])
     d, t0, dt, K, eye = ray_setup(view, nodes)
@@ -149,7 +200,7 @@ def raycast(cache, table, brick_n, view, tf):
         t = t0[idx] + (k + 0.5) * dt
         pos = eye[None, :] + t[:, None] * d[idx]
         g = (pos + 1.0) * half[None, :]
-        s = fetch(cache, table, brick_n, g)
+        s = sample(g)
         rgba = transfer(tf, s[:, 0], vmin, vmax)
         a = rgba[:, 3] if step == 1.0 else 1.0 - (1.0 - rgba[:, 3]) ** step
         grad = s[:, 1:4] * gscale[None, :]

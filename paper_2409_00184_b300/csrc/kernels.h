@@ -73,6 +73,20 @@ struct RaycastParams {
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream);
 
+// Micro-models queried per sample by the direct ray caster (prm.table holds block indices).
+struct DirectModels {
+  const mfa_block_desc* desc;
+  int nblocks;
+  const float* knots;
+  int64_t knots_len;
+  const float* cps;
+  int64_t cps_len;
+  mfa_bounds bounds;
+  uint32_t* status;
+};
+
+int raycast_direct(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, cudaStream_t stream);
+
 struct AdjointParams {
   const mfa_block_desc* desc;
   int nblocks;

@@ -224,16 +224,11 @@ int mfa_adjoint_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nbloc
   return adjoint(ctx, prm, static_cast<cudaStream_t>(stream));
 }
 
-int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
-                const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
-                const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
-  if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
-  if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
-    return MFA_ERR_INVALID_ARG;
-  if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
-    return MFA_ERR_INVALID_ARG;
-  for (int a = 0; a < 3; ++a)
-    if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+// Host checks of the view and the brick grid, and the FP32 camera/march parameters of a ray cast.
+int view_params(mfa::RaycastParams& prm, const int32_t brick_dims[3], int32_t brick_n, const mfa_view* view) {
   if (view->width < 1 || view->height < 1 || view->width > 16384 || view->height > 16384) return MFA_ERR_INVALID_ARG;
   if (!(view->fov_y_deg > 0.f && view->fov_y_deg < 180.f) || !(view->step_voxels > 0.f) ||
       !(view->vmax > view->vmin))
@@ -254,11 +249,6 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
   const double tan_h = std::tan((double)view->fov_y_deg * M_PI / 360.0);
   const double tan_w = tan_h * view->width / view->height;
 
-  RaycastParams prm;
-  prm.cache = reinterpret_cast<const float4*>(d_cache);
-  prm.slot_stride = slot_stride_voxels;
-  prm.nslots = nslots;
-  prm.table = d_brick_table;
   int nmax = 0;
   for (int a = 0; a < 3; ++a) {
     prm.B[a] = brick_dims[a];
@@ -275,9 +265,6 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
   prm.log2n = -1;
   for (int l = 0; l < 31; ++l)
     if ((1 << l) == brick_n) prm.log2n = l;
-  prm.tf = reinterpret_cast<const float4*>(d_tf);
-  prm.tf_n = tf_n;
-  prm.image = reinterpret_cast<float4*>(d_image);
   prm.W = view->width;
   prm.H = view->height;
   prm.tan_w = (float)tan_w;
@@ -294,8 +281,74 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
   prm.shininess = view->shininess;
   prm.vmin = view->vmin;
   prm.vmax = view->vmax;
+  return MFA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
+  if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
+    return MFA_ERR_INVALID_ARG;
+  if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
+    return MFA_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
+  RaycastParams prm;
+  const int vs = view_params(prm, brick_dims, brick_n, view);
+  if (vs != MFA_OK) return vs;
+  prm.cache = reinterpret_cast<const float4*>(d_cache);
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.table = d_brick_table;
+  prm.tf = reinterpret_cast<const float4*>(d_tf);
+  prm.tf_n = tf_n;
+  prm.image = reinterpret_cast<float4*>(d_image);
   prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
   return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
+}
+
+int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,
+                       int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
+                       const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                       const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
+  if (!ctx || !d_desc || !d_knots || !d_cps || !bounds || !d_brick_table || !brick_dims || !view || !d_tf ||
+      !d_image)
+    return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_cps, 4) || !aligned(d_tf, 16) ||
+      !aligned(d_image, 16) || !aligned(d_brick_table, 4))
+    return MFA_ERR_INVALID_ARG;
+  if (nblocks < 0 || knots_len < 0 || cps_len < 0 || brick_n < 2 || brick_n > MFA_MAX_NSAMP || tf_n < 2)
+    return MFA_ERR_INVALID_ARG;
+  if (bounds->max_degree < 1 || bounds->max_degree > MFA_MAX_DEGREE || bounds->max_ncp < 2 ||
+      bounds->max_ncp > MFA_MAX_NCP || bounds->max_nsamp < brick_n || bounds->max_nsamp > MFA_MAX_NSAMP)
+    return MFA_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
+  RaycastParams prm;
+  const int vs = view_params(prm, brick_dims, brick_n, view);
+  if (vs != MFA_OK) return vs;
+  prm.cache = nullptr;
+  prm.slot_stride = 0;
+  prm.nslots = 0;
+  prm.table = d_brick_table;
+  prm.tf = reinterpret_cast<const float4*>(d_tf);
+  prm.tf_n = tf_n;
+  prm.image = reinterpret_cast<float4*>(d_image);
+  prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
+  DirectModels m;
+  m.desc = d_desc;
+  m.nblocks = nblocks;
+  m.knots = d_knots;
+  m.knots_len = knots_len;
+  m.cps = d_cps;
+  m.cps_len = cps_len;
+  m.bounds = *bounds;
+  m.status = ctx->d_status;
+  return raycast_direct(ctx, prm, m, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

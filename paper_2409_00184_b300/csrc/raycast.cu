@@ -15,6 +15,13 @@
 //    brick slot of the next sample is fetched one sample ahead, so the table lookup is off the path
 //    of the corner loads, whose offsets are compile-time constants.
 //  * raycast_tile_kernel (any brick size): one thread per pixel, 16x16-pixel tiles per CTA.
+//  * raycast_direct_kernel: the same rays and compositing, but every sample queries the micro-models
+//    themselves (value and parametric gradient of the B-spline, Algorithm 4's value and gradient
+//    queries) instead of a decoded cache. Brick b's model covers nodes b n .. b n + n - 1 (parameter
+//    u = (g - b n)/(n - 1)); in the one-node gap before brick b + 1 the sample is the linear blend,
+//    along that axis, of the two models at their boundary, multilinear where gaps of several axes meet.
+#include <cstdint>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -258,6 +265,184 @@ int launch_queue(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {
   if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
   raycast_queue_kernel<L><<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, counter);
   return MFA_OK;
+}
+
+// ---- direct query of the micro-models ----
+
+struct ModelGeom {
+  int block;  // -1: none loaded
+  bool ok;
+  int p[3], C[3];
+  int64_t koff[3], cpoff;
+};
+
+// Loads and checks block `block`'s descriptor and knots (once per change of block along a ray).
+__device__ __forceinline__ void load_model(const DirectModels& m, int brick_n, int block, ModelGeom& g) {
+  g.block = block;
+  g.ok = false;
+  if (block < 0 || block >= m.nblocks) return;
+  BlockGeom bg;
+  const uint32_t bad = load_desc(m.desc + block, m.bounds, m.knots_len, m.cps_len, 1, INT64_MAX, bg, false);
+  if (bad) { flag(m.status, bad); return; }
+  for (int a = 0; a < 3; ++a) {
+    if (bg.n[a] != brick_n) { flag(m.status, MFA_DEV_BAD_DESC); return; }
+    if (!knots_ok(m.knots + bg.knot_off[a], bg.p[a], bg.C[a])) { flag(m.status, MFA_DEV_BAD_KNOTS); return; }
+    g.p[a] = bg.p[a];
+    g.C[a] = bg.C[a];
+    g.koff[a] = bg.knot_off[a];
+  }
+  g.cpoff = bg.cp_off;
+  g.ok = true;
+}
+
+// (f, f_u, f_v, f_w) of one model at parameters (u, v, w): basis of degree p and its derivative per axis,
+// then the (p+1)^3 control points of the span.
+__device__ __forceinline__ float4 eval_model(const DirectModels& m, const ModelGeom& g, float u, float v, float w) {
+  const float prm3[3] = {u, v, w};
+  float N[3][MFA_MAX_DEGREE + 1], dN[3][MFA_MAX_DEGREE + 1];
+  int off[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float* t = m.knots + g.koff[a];
+    const int s = find_span(t, g.p[a], g.C[a], prm3[a]);
+    basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, prm3[a], N[a], dN[a]);
+    off[a] = s - g.p[a];
+  }
+  const int Cx = g.C[0], Cy = g.C[1];
+  float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
+#pragma unroll
+  for (int c = 0; c <= MFA_MAX_DEGREE; ++c) {
+    if (c > g.p[2]) break;
+#pragma unroll
+    for (int b = 0; b <= MFA_MAX_DEGREE; ++b) {
+      if (b > g.p[1]) break;
+      const float* row = m.cps + g.cpoff + ((int64_t)(off[2] + c) * Cy + off[1] + b) * Cx + off[0];
+      float sa = 0.f, sda = 0.f;
+#pragma unroll
+      for (int a = 0; a <= MFA_MAX_DEGREE; ++a) {
+        if (a > g.p[0]) break;
+        const float P = __ldg(row + a);
+        sa = fmaf(N[0][a], P, sa);
+        sda = fmaf(dN[0][a], P, sda);
+      }
+      const float nbc = N[1][b] * N[2][c];
+      f = fmaf(nbc, sa, f);
+      fu = fmaf(nbc, sda, fu);
+      fv = fmaf(dN[1][b] * N[2][c], sa, fv);
+      fw = fmaf(N[1][b] * dN[2][c], sa, fw);
+    }
+  }
+  return make_float4(f, fu, fv, fw);
+}
+
+__device__ __forceinline__ float4 sample_direct(const RaycastParams& prm, const DirectModels& m, const float (&gv)[3],
+                                                ModelGeom& cur) {
+  const int n = prm.brick_n;
+  const float inv = 1.0f / (float)(n - 1);
+  int b[3];
+  float u[3], w[3];
+  bool gap[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b[a] = min((int)(gv[a] / (float)n), prm.B[a] - 1);
+    const float local = gv[a] - (float)(b[a] * n);
+    gap[a] = local > (float)(n - 1);
+    u[a] = gap[a] ? 1.0f : local * inv;
+    w[a] = gap[a] ? local - (float)(n - 1) : 0.f;
+  }
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int combo = 0; combo < 8; ++combo) {
+    bool use = true;
+    float wt = 1.f;
+    int bb[3];
+    float uu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int side = (combo >> a) & 1;
+      if (side && !gap[a]) use = false;
+      bb[a] = b[a] + side;
+      uu[a] = gap[a] ? (side ? 0.f : 1.f) : u[a];
+      wt *= gap[a] ? (side ? w[a] : 1.f - w[a]) : 1.f;
+    }
+    if (!use) continue;
+    const int block = __ldg(prm.table + ((int64_t)bb[2] * prm.B[1] + bb[1]) * prm.B[0] + bb[0]);
+    if (block < 0) continue;
+    if (block != cur.block) load_model(m, n, block, cur);
+    if (!cur.ok) continue;
+    const float4 v = eval_model(m, cur, uu[0], uu[1], uu[2]);
+    acc.x = fmaf(wt, v.x, acc.x);
+    acc.y = fmaf(wt, v.y, acc.y);
+    acc.z = fmaf(wt, v.z, acc.z);
+    acc.w = fmaf(wt, v.w, acc.w);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kQueueThreads) raycast_direct_kernel(RaycastParams prm, DirectModels models,
+                                                                       uint32_t* counter) {
+  extern __shared__ float4 s_tf[];  // tf_n entries
+  for (int e = threadIdx.x; e < prm.tf_n; e += kQueueThreads) s_tf[e] = prm.tf[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int tiles_x = (prm.W + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * ((prm.H + kTileH - 1) / kTileH);
+  const int n = prm.brick_n;
+  const float Nmax[3] = {(float)(prm.B[0] * n - 1), (float)(prm.B[1] * n - 1), (float)(prm.B[2] * n - 1)};
+  const float inv_range = 1.0f / (prm.vmax - prm.vmin);
+  const float tfs = (float)(prm.tf_n - 1);
+  unsigned long long marched = 0;
+  ModelGeom cur;
+  cur.block = -1;
+  cur.ok = false;
+
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = (int)atomicAdd(counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= ntiles) break;
+    const int px = (tile % tiles_x) * kTileW + (lane % kTileW);
+    const int py = (tile / tiles_x) * kTileH + (lane / kTileW);
+    if (px < prm.W && py < prm.H) {
+      float d[3], t0;
+      const int K = ray_setup(prm, px, py, d, t0);
+      float gb[3], dg[3];
+      const float ts = fmaf(0.5f, prm.dt, t0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gb[a] = (fmaf(ts, d[a], prm.eye[a]) + 1.0f) * prm.half[a];
+        dg[a] = prm.dt * d[a] * prm.half[a];
+      }
+      float cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+      int k = 0;
+      while (k < K) {
+        const float kf = (float)k;
+        float gv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gv[a] = fminf(fmaxf(fmaf(kf, dg[a], gb[a]), 0.f), Nmax[a]);
+        const float4 s = sample_direct(prm, models, gv, cur);
+        ++k;
+        if (composite(prm, s_tf, s, d, inv_range, tfs, cr, cg, cb, A)) break;
+      }
+      prm.image[(int64_t)py * prm.W + px] = make_float4(cr, cg, cb, A);
+      marched += (unsigned long long)k;
+    }
+  }
+  count_marched(prm, marched, lane);
+}
+
+int raycast_direct(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, cudaStream_t stream) {
+  if (prm.tf_n > kMaxTf) return MFA_ERR_CAPACITY;
+  const size_t smem = (size_t)prm.tf_n * sizeof(float4);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_direct_kernel, kQueueThreads, smem) !=
+      cudaSuccess)
+    return MFA_ERR_CUDA;
+  uint32_t* counter = ctx->d_counters + kRaycastQueue;
+  if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  raycast_direct_kernel<<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, models,
+                                                                                                    counter);
+  ctx->launches++;
+  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
 }
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {

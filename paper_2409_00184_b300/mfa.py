@@ -64,7 +64,8 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
-           "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather"]
+           "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
+           "mfa_raycast_direct"]
 
 
 def _load():
@@ -94,6 +95,8 @@ def _load():
         "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
         "mfa_selftest_wait_timeout": (ctypes.c_int, [P, I32, P]),
         "mfa_lod_gather": (ctypes.c_int, [P, P, ctypes.POINTER(I32), I32, I32, P, I32, P, I64, P]),
+        "mfa_raycast_direct": (ctypes.c_int, [P, P, I32, P, I64, P, I64, ctypes.POINTER(Bounds), P,
+                                              ctypes.POINTER(I32), I32, P, P, I32, P, P]),
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
@@ -360,6 +363,20 @@ def make_view(v):
                 (ctypes.c_float * 3)(*v["up"]), v["fov_y_deg"], int(v["width"]), int(v["height"]),
                 v.get("step_voxels", 1.0), v["opacity_max"], v["ka"], v["kd"], v["ks"], v["shininess"],
                 v["vmin"], v["vmax"])
+
+
+def raycast_direct(ctx, blocks, table, brick_n, view, tf, image, cps=None, stream=None):
+    """mfa_raycast_direct: per-sample queries of the micro-models of a DeviceBlocks batch; table is an int32
+    (Bz, By, Bx) CUDA tensor of block indices (-1 = absent), image a float32 (H, W, 4) CUDA tensor."""
+    cps = blocks.cps if cps is None else cps
+    Bz, By, Bx = table.shape
+    _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
+    v = make_view(view)
+    dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
+    _check(lib.mfa_raycast_direct(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
+                                  _ptr(cps), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table), dims, brick_n,
+                                  ctypes.byref(v), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+           "mfa_raycast_direct")
 
 
 def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None):

@@ -158,3 +158,32 @@ def test_raycast_half_voxel_steps_and_value_window(mfa, ctx, volume):
         got = _run(mfa, ctx, cache, table, n, view, tf)
         want = ocast.raycast(cache, table, n, view, tf)
         assert np.max(np.abs(got - want)) <= 1e-4
+
+
+@pytest.mark.parametrize("N,n,holes", [(64, 16, False), (64, 16, True), (64, 32, False)])
+def test_raycast_direct_model_queries_match_oracle(mfa, ctx, N, n, holes):
+    """mfa_raycast_direct (per-sample queries of the fitted micro-models) against the oracle's direct renderer,
+    early termination off; every pixel marches its K samples. Also reports how far the cache renderer's
+    trilinear interpolation of the decoded nodes is from the direct queries (the cache discretisation)."""
+    bs, _ = gm_blocks_fitted(N, n, 8, 2, synth.BASE_SEED + 18)
+    B = N // n
+    table = np.arange(B ** 3, dtype=np.int32).reshape(B, B, B)
+    if holes:
+        table[synth.rng(19).random(table.shape) < 0.3] = -1
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=40, height=32, opacity_max=1.0)
+    blk = mfa.DeviceBlocks(bs)
+    img = torch.full((view["height"], view["width"], 4), float("nan"), device="cuda")
+    ctx.ray_samples(reset=True)
+    mfa.raycast_direct(ctx, blk, torch.from_numpy(table).cuda(), n, view, torch.from_numpy(tf).cuda(), img)
+    marched = ctx.ray_samples(reset=True)
+    assert ctx.device_status() == 0
+    got = img.cpu().numpy()
+    want = ocast.raycast_direct(lambda k: (bs.block_cps(k), bs.block_knots(k), tuple(bs.degree[k])), table, n,
+                                view, tf)
+    _, _, _, K, _ = ocast.ray_setup(view, (N, N, N))
+    assert marched == int(np.asarray(K).sum())
+    assert np.max(np.abs(got - want)) <= 1e-4
+    cache = np.stack(oracle_decode_set(bs)).astype(np.float32)
+    via_cache = ocast.raycast(cache, table, n, view, tf)
+    print(f"N={N} n={n} holes={holes}: max |direct - cache| = {np.max(np.abs(want - via_cache)):.2e}")

@@ -140,3 +140,68 @@ def test_trilinear_interpolation_across_bricks_is_exact_for_linear_fields():
     _, _, _, K, _ = raycast.ray_setup(view, (N, N, N))
     a = a0 + 0.475 * (a1 - a0)
     assert abs(img[2, 2, 3] - (1 - (1 - a) ** K[2, 2])) < 1e-12
+
+
+def _poly_bricks(B, n, p, C, c0, cx2, cz):
+    """Per-brick control points (Marsden's identity) of F(gx, gy, gz) = c0 + cx2 gx^2 + cz gz in global node
+    units: on brick (bx, by, bz), g = b n + u (n - 1) per axis, so F is a polynomial of degree <= 2 in u, w."""
+    from test_oracle_decode import poly_cps
+    t = np.array([0.0] * (p + 1) + [j / (C - p) for j in range(1, C - p)] + [1.0] * (p + 1))
+    knots = (t, t, t)
+    blocks, table = [], np.full((B, B, B), -1, dtype=np.int32)
+    for bz in range(B):
+        for by in range(B):
+            for bx in range(B):
+                coef = np.zeros((p + 1, p + 1, p + 1))
+                coef[0, 0, 0] = c0 + cx2 * (bx * n) ** 2 + cz * bz * n
+                coef[0, 0, 1] = 2 * cx2 * bx * n * (n - 1)
+                coef[0, 0, 2] = cx2 * (n - 1) ** 2
+                coef[1, 0, 0] = cz * (n - 1)
+                table[bz, by, bx] = len(blocks)
+                blocks.append(poly_cps(coef, knots, (p, p, p), (C, C, C)))
+    return (lambda k: (blocks[k], knots, (p, p, p))), table
+
+
+def test_direct_query_reproduces_polynomial_fields_and_blends_gaps():
+    """fetch_direct at random points: inside a brick the exact F and its parametric gradient (F' (n - 1));
+    in the one-node gap between bricks along x the linear blend of F at the two boundary nodes."""
+    B, n, p, C = 3, 6, 2, 5
+    c0, cx2, cz = 0.1, 0.003, 0.02
+    blocks, table = _poly_bricks(B, n, p, C, c0, cx2, cz)
+    g = synth.rng(61).uniform(0, B * n - 1, (400, 3))
+    got = raycast.fetch_direct(blocks, table, n, g)
+    F = lambda gx, gz: c0 + cx2 * gx ** 2 + cz * gz
+    bx = np.minimum(np.floor(g[:, 0] / n), B - 1)
+    lx = g[:, 0] - bx * n
+    gap = lx > n - 1
+    inside = ~gap & ~(g[:, 2] - np.minimum(np.floor(g[:, 2] / n), B - 1) * n > n - 1)
+    assert inside.sum() > 100 and (gap & ~(g[:, 2] % n > n - 1)).sum() > 10
+    assert np.max(np.abs(got[inside, 0] - F(g[inside, 0], g[inside, 2]))) < 1e-12
+    assert np.max(np.abs(got[inside, 1] - 2 * cx2 * g[inside, 0] * (n - 1))) < 1e-11
+    assert np.max(np.abs(got[inside, 2])) < 1e-12
+    assert np.max(np.abs(got[inside, 3] - cz * (n - 1))) < 1e-12
+    xg = gap & ~(g[:, 2] % n > n - 1)  # gap along x only (z inside a brick; y does not matter)
+    w = lx[xg] - (n - 1)
+    lo, hi = bx[xg] * n + n - 1, (bx[xg] + 1) * n
+    want = (1 - w) * F(lo, g[xg, 2]) + w * F(hi, g[xg, 2])
+    assert np.max(np.abs(got[xg, 0] - want)) < 1e-12
+
+
+def test_direct_and_cache_renders_agree_on_linear_fields():
+    """A field linear in every axis is reproduced exactly by the models, by the blends in the gaps and by
+    trilinear interpolation of its nodes, so the two renderers give the same image."""
+    B, n, p, C = 2, 8, 2, 4
+    blocks, table = _poly_bricks(B, n, p, C, 0.2, 0.0, 0.03)
+    cache = np.zeros((B ** 3, n, n, n, 4))
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    for bz in range(B):
+        for by in range(B):
+            for bx in range(B):
+                gz = bz * n + k
+                cache[table[bz, by, bx]] = np.stack([0.2 + 0.03 * gz, 0 * gz, 0 * gz, 0 * gz + 0.03 * (n - 1)], -1)
+    tf = np.array([[0.9, 0.5, 0.1, 0.0], [0.1, 0.5, 0.9, 0.1]], dtype=np.float32)
+    view = synth.default_view(width=12, height=10, opacity_max=1.0)
+    a = raycast.raycast(cache, table, n, view, tf)
+    b = raycast.raycast_direct(blocks, table, n, view, tf)
+    assert np.max(np.abs(a - b)) < 1e-12
+    assert a[..., 3].max() > 0.1
