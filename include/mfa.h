@@ -54,6 +54,7 @@ extern "C" {
 #define MFA_ERR_TIMEOUT     -4   /* a bounded device wait gave up (see MFA_DEV_TIMEOUT)   */
 #define MFA_ERR_CAPACITY    -5   /* request exceeds a fixed library limit                */
 #define MFA_ERR_DEVICE      -6   /* the device status word holds error bits              */
+#define MFA_ERR_IO          -7   /* a model store could not be written or read           */
 
 /* ---- device status word bits (mfa_ctx_device_status) -------------------------------- */
 #define MFA_DEV_BAD_DESC   0x1u  /* degree/ncp/nsamp outside the launch bounds or limits */
@@ -349,6 +350,51 @@ int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nbloc
                        int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
                        const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
                        const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream);
+
+/* ---- out-of-core model storage and caching (Sec. 4.3: Algorithms 2 and 3) ------------- */
+/* Storage: micro-models in the byte layout whose size is Eq. 2, 1 + ((NCP + degree)*3 + NCP^3)*4:
+ * one byte holding the degree, then for each axis x, y, z the first NCP + degree knots as float32
+ * (the last knot of a clamped vector repeats the one before it and is implied), then the NCP^3
+ * control points as float32, x fastest. Only isotropic models (equal NCP and degree on the three
+ * axes) have this layout. A store file holds a header ("MFAPACK1", uint32 count, uint32 0), an index
+ * of count entries (uint64 byte offset, uint32 NCP, uint32 degree) and the models back to back.
+ * mfa_store_write writes blocks 0..nblocks-1 of a host batch (descriptors, knots, control points as
+ * for mfa_decode_blocks) to `path`; MFA_ERR_INVALID_ARG for an anisotropic or inconsistent block,
+ * MFA_ERR_IO when the file cannot be written. */
+int mfa_store_write(const char* path, const mfa_block_desc* h_desc, int32_t nblocks, const float* h_knots,
+                    int64_t knots_len, const float* h_cps, int64_t cps_len);
+
+/* An LRU cache of up to `capacity` micro-models of a store, in host memory (page-locked when
+ * `pinned` is non-zero, which needs a CUDA device; pageable otherwise). It reads models from the
+ * store file on demand (one positioned read per model). Not thread-safe except for the prefetch
+ * thread it owns. */
+typedef struct mfa_model_cache mfa_model_cache;
+int  mfa_cache_create(mfa_model_cache** out, const char* path, int32_t capacity, int32_t pinned);
+void mfa_cache_destroy(mfa_model_cache* cache);
+/* Number of models in the store and the largest model's NCP and degree (any pointer may be null). */
+int  mfa_cache_info(const mfa_model_cache* cache, int32_t* count, int32_t* max_ncp, int32_t* max_degree);
+/* Algorithm 2, caching for one point of view: for every listed model, in order, a hit marks it most
+ * recently used; a miss loads it from storage into a free entry or into the least recently used
+ * one. All n models must fit (n <= capacity; repeated ids count once). h_stats (nullable, 4 int64):
+ * hits, misses, bytes read from storage, elapsed nanoseconds. MFA_ERR_INVALID_ARG for an id
+ * outside the store or n > capacity, MFA_ERR_IO when a read fails. */
+int  mfa_cache_lookup(mfa_model_cache* cache, const int32_t* h_ids, int32_t n, int64_t* h_stats);
+/* Copies the listed models (already in the cache: call mfa_cache_lookup first) to the device as one
+ * batch: d_desc[i] describes model h_ids[i] with slot i and `nsamp` samples per axis, its knots (all
+ * NCP + degree + 1 per axis) and control points packed into d_knots / d_cps (capacities in floats).
+ * h_lens (2 int64): the knot and control-point counts written; h_bounds: the batch's bounds. The
+ * packing goes through the cache's host staging buffers and three cudaMemcpyAsync on `stream`; the
+ * next upload waits for these copies before it reuses the staging. MFA_ERR_CAPACITY when the
+ * device buffers are too small, MFA_ERR_INVALID_ARG for a model that is not cached. */
+int  mfa_cache_upload(mfa_model_cache* cache, const int32_t* h_ids, int32_t n, int32_t nsamp,
+                      mfa_block_desc* d_desc, float* d_knots, int64_t knots_cap, float* d_cps, int64_t cps_cap,
+                      int64_t* h_lens, mfa_bounds* h_bounds, void* stream);
+/* Algorithm 3, prefetching for the next point of view: a background thread loads the listed models
+ * that are not cached (LRU replacement as above) until the list ends or mfa_cache_prefetch_stop is
+ * called (rendering done). The cache must not be used by other calls in between. stop joins the
+ * thread; h_stats (nullable, 2 int64): models loaded, bytes read. */
+int  mfa_cache_prefetch_start(mfa_model_cache* cache, const int32_t* h_ids, int32_t n);
+int  mfa_cache_prefetch_stop(mfa_model_cache* cache, int64_t* h_stats);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,7 @@ const char* mfa_status_string(int status) {
     case MFA_ERR_TIMEOUT: return "bounded device wait timed out";
     case MFA_ERR_CAPACITY: return "request exceeds a library limit";
     case MFA_ERR_DEVICE: return "device status word holds error bits";
+    case MFA_ERR_IO: return "model store read or write failed";
     default: return "unknown status";
   }
 }

@@ -14,7 +14,7 @@ import torch
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmfa.so")
 
 OK = 0
-ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVICE = -1, -2, -3, -4, -5, -6
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVICE, ERR_IO = -1, -2, -3, -4, -5, -6, -7
 DEV_BAD_DESC, DEV_BAD_KNOTS, DEV_BAD_RANGE, DEV_BAD_LIST, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4, 8, 16, 32
 PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
 DECODE_VALUE_ONLY, DECODE_LIST_SLOTS = 1, 2
@@ -65,7 +65,8 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
-           "mfa_raycast_direct"]
+           "mfa_raycast_direct", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
+           "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop"]
 
 
 def _load():
@@ -97,6 +98,14 @@ def _load():
         "mfa_lod_gather": (ctypes.c_int, [P, P, ctypes.POINTER(I32), I32, I32, P, I32, P, I64, P]),
         "mfa_raycast_direct": (ctypes.c_int, [P, P, I32, P, I64, P, I64, ctypes.POINTER(Bounds), P,
                                               ctypes.POINTER(I32), I32, P, P, I32, P, P]),
+        "mfa_store_write": (ctypes.c_int, [ctypes.c_char_p, P, I32, P, I64, P, I64]),
+        "mfa_cache_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_char_p, I32, I32]),
+        "mfa_cache_destroy": (None, [P]),
+        "mfa_cache_info": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "mfa_cache_lookup": (ctypes.c_int, [P, P, I32, P]),
+        "mfa_cache_upload": (ctypes.c_int, [P, P, I32, I32, P, P, I64, P, I64, P, ctypes.POINTER(Bounds), P]),
+        "mfa_cache_prefetch_start": (ctypes.c_int, [P, P, I32]),
+        "mfa_cache_prefetch_stop": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_create": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(FrameDesc)]),
         "mfa_frame_graph_launch": (ctypes.c_int, [P, P]),
         "mfa_frame_graph_destroy": (None, [P]),
@@ -356,6 +365,83 @@ def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=N
     _check(lib.mfa_lod_gather(ctx.handle, _ptr(field), dims, n, stride, _ptr(ids), count, _ptr(out), n ** 3,
                               _stream(stream)), "mfa_lod_gather")
     return out
+
+
+def store_write(path, bs):
+    """mfa_store_write: every block of a host batch (synth.BlockSet-like arrays) into a store file."""
+    desc = pack_descriptors(bs)
+    knots = np.ascontiguousarray(bs.knots, dtype=np.float32)
+    cps = np.ascontiguousarray(bs.cps, dtype=np.float32)
+    _check(lib.mfa_store_write(str(path).encode(), desc.ctypes.data_as(ctypes.c_void_p), len(desc),
+                               knots.ctypes.data_as(ctypes.c_void_p), knots.size,
+                               cps.ctypes.data_as(ctypes.c_void_p), cps.size), "mfa_store_write")
+
+
+def _host_ids(ids):
+    a = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class DeviceBatch:
+    """Device buffers for up to `capacity` uploaded models of at most max_ncp^3 control points (the
+    attributes decode_blocks and raycast_direct read: desc, knots, cps, n, bounds)."""
+
+    def __init__(self, capacity, max_ncp, max_degree, device="cuda"):
+        self.desc = torch.zeros(capacity * 72, dtype=torch.uint8, device=device)
+        self.knots = torch.zeros(capacity * 3 * (max_ncp + max_degree + 1), dtype=torch.float32, device=device)
+        self.cps = torch.zeros(capacity * max_ncp ** 3, dtype=torch.float32, device=device)
+        self.n, self.bounds, self.cps_len = 0, Bounds(1, 2, 2), 0
+
+
+class ModelCache:
+    """mfa_model_cache: LRU cache of a store's micro-models in host memory (Algorithms 2 and 3)."""
+
+    def __init__(self, path, capacity, pinned=True):
+        h = ctypes.c_void_p()
+        _check(lib.mfa_cache_create(ctypes.byref(h), str(path).encode(), int(capacity), int(bool(pinned))),
+               "mfa_cache_create")
+        self.handle, self.capacity = h, capacity
+
+    def info(self):
+        c, mc, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.mfa_cache_info(self.handle, ctypes.byref(c), ctypes.byref(mc), ctypes.byref(md)), "mfa_cache_info")
+        return c.value, mc.value, md.value
+
+    def lookup(self, ids):
+        a, p = _host_ids(ids)
+        st = (ctypes.c_int64 * 4)()
+        _check(lib.mfa_cache_lookup(self.handle, p, a.size, st), "mfa_cache_lookup")
+        return {"hits": st[0], "misses": st[1], "bytes": st[2], "ns": st[3]}
+
+    def upload(self, ids, nsamp, batch, stream=None):
+        a, p = _host_ids(ids)
+        lens = (ctypes.c_int64 * 2)()
+        _check(lib.mfa_cache_upload(self.handle, p, a.size, nsamp, _ptr(batch.desc), _ptr(batch.knots),
+                                    batch.knots.numel(), _ptr(batch.cps), batch.cps.numel(), lens,
+                                    ctypes.byref(batch.bounds), _stream(stream)), "mfa_cache_upload")
+        batch.n, batch.cps_len = a.size, lens[1]
+        return batch
+
+    def prefetch_start(self, ids):
+        a, p = _host_ids(ids)
+        self._pf = a  # the thread copies the list; kept only for clarity
+        _check(lib.mfa_cache_prefetch_start(self.handle, p, a.size), "mfa_cache_prefetch_start")
+
+    def prefetch_stop(self):
+        st = (ctypes.c_int64 * 2)()
+        _check(lib.mfa_cache_prefetch_stop(self.handle, st), "mfa_cache_prefetch_stop")
+        return {"loaded": st[0], "bytes": st[1]}
+
+    def close(self):
+        if self.handle:
+            lib.mfa_cache_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def make_view(v):
