@@ -2,9 +2,10 @@
 """Benchmark of the micro-model hot path on the 512^3 / 4096-block workload.
 
 One step = one pass of every stage of the path over the batch, all in the library's kernels:
-  least-squares encode of the 4096 sample blocks (FP64 class set-up + FP32 fit + FP64 RMSE),
-  decode of every block to the value+gradient cache, a 1024x1024 ray cast of the cache, and the
-  adjoint of the fit residual (gradient of 0.5*||decode(P) - D||^2 at the fitted P).
+  least-squares encode of the 4096 sample blocks (FP64 class set-up + FP32 fit), decode of every
+  block to the value+gradient cache fused with the comparison to the samples (the fit residual
+  r = decode(P) - D and the FP64 RMSE per block), a 1024x1024 ray cast of the cache, and the adjoint
+  of the residual (gradient of 0.5*||decode(P) - D||^2 at the fitted P).
 The headline is decoded voxels per second of whole step (Gvoxel/s). Inputs are resident in HBM
 and larger than L2 (512 MB of samples, 2.15 GB of cache), so no flush is needed between steps.
 
@@ -37,7 +38,8 @@ N_FIELD, BRICK, NCP, DEGREE = 512, 32, 12, 2
 IMG = 1024
 METRIC = "Gvoxel/s MFA decode (value+grad), % roofline, max err vs FP64 oracle"
 WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degree 2, 12^3 control points: "
-            "LS encode + value/gradient decode + 1024^2 ray cast (1 sample/voxel, 256-entry TF) + adjoint")
+            "LS encode + value/gradient decode fused with residual and RMSE + 1024^2 ray cast (1 sample/voxel, "
+            "256-entry TF) + adjoint of the residual")
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by the
 # sha256 of the kernel source it was taken on; reported as null once the source changes.
 TRAFFIC = {"raycast": {"bytes": 395.87e6 + 17.94e6, "src_sha": "faeafe4f69898824"}}
@@ -176,22 +178,23 @@ class Workload:
         self.image = torch.empty(IMG, IMG, 4, device="cuda")
         self.grad = torch.empty(self.blk.cps_len, device="cuda")
         self.rmse = torch.empty(B, dtype=torch.float64, device="cuda")
+        self.R = torch.empty_like(self.D)  # fit residual decode(P) - D
 
     def step(self, ev=None, D=None):
         m, c, blk, v = self.mfa, self.ctx, self.blk, self.vox
         D = self.D if D is None else D
         if ev:
             ev[0].record()
-        m.encode_blocks(c, self.plan, D, v, self.B, blk.cps, self.rmse)
+        m.encode_blocks(c, self.plan, D, v, self.B, blk.cps)
         if ev:
             ev[1].record()
-        m.decode_blocks(c, blk, self.cache, v, self.B)
+        m.decode_compare_blocks(c, blk, self.cache, v, self.B, D, v, residual=self.R, rmse=self.rmse)
         if ev:
             ev[2].record()
         m.raycast(c, self.cache, v, self.B, self.table, BRICK, self.view, self.tf, self.image)
         if ev:
             ev[3].record()
-        m.adjoint_blocks(c, blk, D, v, self.B, self.grad, cps=blk.cps)
+        m.adjoint_blocks(c, blk, self.R, v, self.B, self.grad)
         if ev:
             ev[4].record()
 
@@ -200,10 +203,11 @@ def algorithmic_bytes(B):
     """Bytes each kernel must move at minimum per launch on this workload."""
     vox, cp = BRICK ** 3, NCP ** 3
     return {
-        "encode": B * (vox * 4 + cp * 4 + 8),          # read samples, write control points + RMSE
-        "decode": B * (vox * 16 + cp * 4 + 72),        # write float4 per voxel, read control points + descriptor
+        "encode": B * (vox * 4 + cp * 4),              # read samples, write control points
+        "decode": B * (vox * (16 + 4 + 4) + cp * 4 + 72 + 8),  # cache float4, read samples, write residual; CPs,
+                                                               # descriptor, RMSE
         "raycast": IMG * IMG * 16,                      # image write; cache reads are counted as traffic, not here
-        "adjoint": B * (vox * 4 + 2 * cp * 4 + 72),    # read samples and control points, write gradient
+        "adjoint": B * (vox * 4 + cp * 4 + 72),        # read the residual, write the gradient
     }
 
 

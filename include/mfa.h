@@ -160,6 +160,25 @@ int mfa_decode_blocks(mfa_ctx* ctx,
                       const mfa_bounds* bounds, int32_t precision, uint32_t flags,
                       void* stream);
 
+/* The FP32 decode fused with the comparison to the samples the models were fitted to (the
+ * residual of the least-squares fit of Algorithm 1's model() and Table 1's RMSE), in one pass:
+ * selection, destination, flags and cache output as mfa_decode_blocks with MFA_PREC_FP32; and for every
+ * decoded voxel r = f - D, with D at d_data + slot*data_slot_stride + voxel (FP32, [z][y][x] per slot,
+ * slot = the block's destination slot; a block with more voxels than data_slot_stride sets
+ * MFA_DEV_BAD_RANGE and is skipped).
+ *   d_residual (nullable): r written with the same addressing as d_data.
+ *   d_rmse (nullable, FP64, one per selected item: list position, or block index without a list):
+ *     sqrt(mean r^2) over the block's voxels; squares are summed per thread in FP32 (Kahan) and
+ *     across threads in FP64. NaN for an item whose block failed its checks. The call zeroes d_rmse
+ *     before the decode and finishes it with one more kernel (d_rmse needs max(list_len, nblocks)
+ *     entries). */
+int mfa_decode_compare_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
+                              const int32_t* d_list, int32_t list_len, const int32_t* d_count,
+                              const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
+                              float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                              const mfa_bounds* bounds, uint32_t flags, const float* d_data,
+                              int64_t data_slot_stride, float* d_residual, double* d_rmse, void* stream);
+
 /* Fills per-axis basis tables for one block, for testing the span search and the
  * Cox-de Boor recurrence on their own: for each axis a and sample i, span[a*MAXN + i]
  * (int32) and N, N' at the p+1 nonzero functions, basis[((a*MAXN + i)*2 + {0,1})*4 + r]

@@ -26,7 +26,11 @@ struct DecodeSmem {
 
 static int r4(int v) { return (v + 3) & ~3; }
 
-constexpr int kUnitPlanes = 32;  // z-planes per work unit (the set-up is shared by its slabs)
+constexpr int kUnitPlanes = 32;
+
+__device__ __forceinline__ void compare_sample(const DecodeParams& prm, int64_t idx, float r, float& ksum,
+                                               float& kcomp);
+constexpr int kPrefetch = 8;  // rows per thread whose samples are loaded together (decode with comparison)  // z-planes per work unit (the set-up is shared by its slabs)
 
 // [knots | basis tables | T | P | U]. With one slab per unit (`alias`), U (stage y output) overwrites
 // P, which stage z has consumed; units of several slabs keep P for all of them.
@@ -51,11 +55,12 @@ static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks
   return L;
 }
 
-template <int PMAX, bool VALUE_ONLY>
+template <int PMAX, bool VALUE_ONLY, bool COMPARE>
 __global__ void __launch_bounds__(kDecodeThreads)
 decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int s_unit, s_bad;
+  __shared__ int s_unit, s_bad, s_item;
+  __shared__ double s_red[kDecodeThreads / 32];
   __shared__ BlockGeom s_g;
   constexpr int Q = PMAX + 1;
   const int tid = threadIdx.x;
@@ -82,6 +87,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
       const int64_t unit = s_unit;
       if (unit < total_units) {
         const int item = (int)(unit / prm.slabs);
+        s_item = item;
         const int b = prm.list ? prm.list[item] : item;
         const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
         uint32_t bad = 0;
@@ -92,6 +98,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           if (item >= prm.nslots) bad = MFA_DEV_BAD_RANGE;
           s_g.slot = item;
         }
+        if (!bad && COMPARE && (int64_t)s_g.n[0] * s_g.n[1] * s_g.n[2] > prm.data_stride) bad = MFA_DEV_BAD_RANGE;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
       }
     }
@@ -143,6 +150,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
     __syncthreads();
     if (s_bad) continue;
 
+    float ksum = 0.f, kcomp = 0.f;  // squared differences to the samples (COMPARE), Kahan-summed per thread
     for (int k0 = kz0; k0 < kz0 + kzn; k0 += prm.ks) {  // slabs of the unit
       const int kc = min(prm.ks, kz0 + kzn - k0);
       const int zt = 2 * maxN + (k0 - kz0);  // z-table row of the slab's first plane
@@ -159,7 +167,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           const float Nzv[4] = {Nz.x, Nz.y, Nz.z, Nz.w}, dNzv[4] = {dNz.x, dNz.y, dNz.z, dNz.w};
           const float* Pc = s_P + oz * plane + ab;
           float t0 = 0.f, t1 = 0.f;
-  #pragma unroll
+#pragma unroll
           for (int d = 0; d < Q; ++d) {
             if (d <= pz) {
               const float pv = Pc[d * plane];
@@ -189,7 +197,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
             const int tb = (kl * Cy + oy) * Cx + a;
             if (VALUE_ONLY) {
               float u0 = 0.f;
-  #pragma unroll
+#pragma unroll
               for (int d = 0; d < Q; ++d)
                 if (d <= py) u0 = fmaf(sm[L.T + tb + d * Cx], Nyv[d], u0);
               sm[L.U + r * Cx + a] = u0;
@@ -198,7 +206,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
               const float dNyv[4] = {dNy.x, dNy.y, dNy.z, dNy.w};
               const float2* T = reinterpret_cast<const float2*>(sm + L.T);
               float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-  #pragma unroll
+#pragma unroll
               for (int d = 0; d < Q; ++d) {
                 if (d <= py) {
                   const float2 tv = T[tb + d * Cx];
@@ -226,11 +234,52 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
           const int rows = ny * kc;
           const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
-          if (VALUE_ONLY) {
+          const int64_t dbase = COMPARE ? (int64_t)s_g.slot * prm.data_stride + (int64_t)k0 * ny * nx + i : 0;
+          // rows in chunks of kPrefetch per thread: with COMPARE the chunk's samples D are loaded before its
+          // arithmetic, so the loads overlap instead of each row waiting for its own
+          if (COMPARE) {
+            for (int rc = r0; rc < rows; rc += kPrefetch * rows_per_pass) {
+              float dpre[kPrefetch];
+#pragma unroll
+              for (int q = 0; q < kPrefetch; ++q) {
+                const int r = rc + q * rows_per_pass;
+                dpre[q] = r < rows ? __ldg(prm.data + dbase + (int64_t)r * nx) : 0.f;
+              }
+#pragma unroll
+              for (int q = 0; q < kPrefetch; ++q) {
+                const int r = rc + q * rows_per_pass;
+                if (r >= rows) break;
+                float f = 0.f;
+                if (VALUE_ONLY) {
+                  const float* U = sm + L.U + ox;
+#pragma unroll
+                  for (int d = 0; d < Q; ++d)
+                    if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
+                  __stcs(prm.cache + base + (int64_t)r * nx, f);
+                } else {
+                  const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
+                  float fu = 0.f, fv = 0.f, fw = 0.f;
+#pragma unroll
+                  for (int d = 0; d < Q; ++d) {
+                    if (d <= px) {
+                      const float4 uv = U[r * Cx + d];
+                      f = fmaf(uv.x, Nx[d], f);
+                      fu = fmaf(uv.x, dNx[d], fu);
+                      fv = fmaf(uv.y, Nx[d], fv);
+                      fw = fmaf(uv.z, Nx[d], fw);
+                    }
+                  }
+                  __stcs(reinterpret_cast<float4*>(prm.cache) + base + (int64_t)r * nx,
+                         make_float4(f, fu, fv, fw));
+                }
+                compare_sample(prm, dbase + (int64_t)r * nx, f - dpre[q], ksum, kcomp);
+              }
+            }
+          } else if (VALUE_ONLY) {
             const float* U = sm + L.U + ox;
             for (int r = r0; r < rows; r += rows_per_pass) {
               float f = 0.f;
-  #pragma unroll
+#pragma unroll
               for (int d = 0; d < Q; ++d)
                 if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
               __stcs(prm.cache + base + (int64_t)r * nx, f);
@@ -240,7 +289,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
             float4* out = reinterpret_cast<float4*>(prm.cache) + base;
             for (int r = r0; r < rows; r += rows_per_pass) {
               float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
-  #pragma unroll
+#pragma unroll
               for (int d = 0; d < Q; ++d) {
                 if (d <= px) {
                   const float4 uv = U[r * Cx + d];
@@ -256,13 +305,53 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
         }
       }
     }
+    if (COMPARE && prm.sq) {  // the unit's sum of squared differences, added to its item in FP64
+      double v = (double)ksum - (double)kcomp;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) s_red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nthr / 32; ++w) tot += s_red[w];
+        atomicAdd(prm.sq + s_item, tot);
+      }
+    }
   }
+}
+
+// The difference r = f - D of one decoded voxel: written when asked, r^2 into the thread's Kahan sum.
+__device__ __forceinline__ void compare_sample(const DecodeParams& prm, int64_t idx, float r, float& ksum,
+                                               float& kcomp) {
+  if (prm.residual) __stcs(prm.residual + idx, r);
+  const float y = r * r - kcomp;
+  const float t = ksum + y;
+  kcomp = (t - ksum) - y;
+  ksum = t;
+}
+
+// RMSE of every selected item from its sum of squared differences: sqrt(sum / voxels), NaN for an
+// item whose block failed its checks (it was not decoded).
+__global__ void rmse_finish_kernel(DecodeParams prm, int max_items) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  int count = prm.list ? (prm.count ? *prm.count : prm.list_len) : prm.nblocks;
+  count = max(0, min(count, max_items));
+  if (item >= count) return;
+  const int b = prm.list ? prm.list[item] : item;
+  BlockGeom g;
+  const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
+  if (b < 0 || b >= prm.nblocks ||
+      load_desc(prm.desc + b, prm.bounds, prm.knots_len, prm.cps_len, prm.nslots, prm.slot_stride, g, !list_slots)) {
+    prm.sq[item] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  const double vox = (double)g.n[0] * g.n[1] * g.n[2];
+  prm.sq[item] = sqrt(prm.sq[item] / vox);
 }
 
 template <int PMAX, bool VO>
 static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const DecodeSmem& L, int ctas_per_sm,
                               cudaStream_t stream) {
-  auto kern = decode_fp32_kernel<PMAX, VO>;
+  auto kern = prm.data ? decode_fp32_kernel<PMAX, VO, true> : decode_fp32_kernel<PMAX, VO, false>;
   const size_t smem = (size_t)L.total * 4;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -299,6 +388,9 @@ int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaSt
   prm.group = group;
   prm.slabs = (maxN + ks * group - 1) / (ks * group);
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  const int max_items = prm.list ? prm.list_len : prm.nblocks;
+  if (prm.data && prm.sq && cudaMemsetAsync(prm.sq, 0, sizeof(double) * (size_t)max_items, stream) != cudaSuccess)
+    return MFA_ERR_CUDA;
   cudaError_t e;
   switch (pmax) {
     case 1: e = vo ? launch_one<1, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<1, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;
@@ -306,7 +398,13 @@ int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaSt
     case 3: e = vo ? launch_one<3, true>(ctx, prm, L, tune.ctas_per_sm, stream) : launch_one<3, false>(ctx, prm, L, tune.ctas_per_sm, stream); break;
     default: return MFA_ERR_INVALID_ARG;
   }
-  return e == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+  if (e != cudaSuccess) return MFA_ERR_CUDA;
+  if (prm.data && prm.sq && max_items > 0) {
+    rmse_finish_kernel<<<(max_items + 255) / 256, 256, 0, stream>>>(prm, max_items);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
+  }
+  return MFA_OK;
 }
 
 }  // namespace mfa

@@ -32,6 +32,11 @@ struct DecodeParams {
   uint32_t* counter;
   int ks;     // z-planes per slab
   int group;  // slabs per work unit
+  // decode fused with the comparison to the fitted samples (FP32 path; data == nullptr: plain decode)
+  const float* data = nullptr;  // sample grids, slot-addressed (data_stride floats per slot)
+  int64_t data_stride = 0;
+  float* residual = nullptr;    // nullable: f - D per voxel, same addressing as data
+  double* sq = nullptr;         // nullable: per item, sum of squared differences, then (finished) the RMSE
   int slabs;  // work units per block = ceil(max_nsamp / (ks * group))
 };
 

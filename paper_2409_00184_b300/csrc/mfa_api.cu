@@ -137,11 +137,15 @@ int64_t mfa_model_bytes(int32_t ncp, int32_t degree) {
   return 1 + ((c + degree) * 3 + c * c * c) * 4;
 }
 
-int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
-                      const int32_t* d_list, int32_t list_len, const int32_t* d_count,
-                      const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
-                      float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
-                      const mfa_bounds* bounds, int32_t precision, uint32_t flags, void* stream) {
+}  // extern "C"
+
+namespace {
+// mfa_decode_blocks, optionally fused with the comparison to the fitted samples (data != nullptr).
+int decode_entry(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const int32_t* d_list, int32_t list_len,
+                 const int32_t* d_count, const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
+                 float* d_cache, int64_t slot_stride_voxels, int64_t nslots, const mfa_bounds* bounds,
+                 int32_t precision, uint32_t flags, const float* d_data, int64_t data_stride, float* d_residual,
+                 double* d_rmse, void* stream) {
   if (!ctx || !bounds_ok(bounds)) return MFA_ERR_INVALID_ARG;
   if (nblocks < 0 || list_len < 0 || knots_len < 0 || cps_len < 0 || slot_stride_voxels < 1 || nslots < 0)
     return MFA_ERR_INVALID_ARG;
@@ -175,6 +179,10 @@ int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblock
   prm.counter = ctx->d_counters + kDecodeQueue;
   prm.ks = 0;
   prm.slabs = 0;
+  prm.data = d_data;
+  prm.data_stride = data_stride;
+  prm.residual = d_residual;
+  prm.sq = d_rmse;
   if (precision != MFA_PREC_FP32) return decode_tc(ctx, prm, precision, static_cast<cudaStream_t>(stream));
   DecodeTuning tune;
   mfa_decode_tiling t;
@@ -183,6 +191,32 @@ int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblock
     tune.ctas_per_sm = t.ctas_per_sm;
   }
   return decode_fp32(ctx, prm, tune, static_cast<cudaStream_t>(stream));
+}
+}  // namespace
+
+extern "C" {
+
+int mfa_decode_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
+                      const int32_t* d_list, int32_t list_len, const int32_t* d_count,
+                      const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
+                      float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                      const mfa_bounds* bounds, int32_t precision, uint32_t flags, void* stream) {
+  return decode_entry(ctx, d_desc, nblocks, d_list, list_len, d_count, d_knots, knots_len, d_cps, cps_len, d_cache,
+                      slot_stride_voxels, nslots, bounds, precision, flags, nullptr, 0, nullptr, nullptr, stream);
+}
+
+int mfa_decode_compare_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks,
+                              const int32_t* d_list, int32_t list_len, const int32_t* d_count,
+                              const float* d_knots, int64_t knots_len, const float* d_cps, int64_t cps_len,
+                              float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                              const mfa_bounds* bounds, uint32_t flags, const float* d_data,
+                              int64_t data_slot_stride, float* d_residual, double* d_rmse, void* stream) {
+  if (!d_data || data_slot_stride < 1 || !aligned(d_data, 4) || (d_residual && !aligned(d_residual, 4)) ||
+      (d_rmse && !aligned(d_rmse, 8)))
+    return MFA_ERR_INVALID_ARG;
+  return decode_entry(ctx, d_desc, nblocks, d_list, list_len, d_count, d_knots, knots_len, d_cps, cps_len, d_cache,
+                      slot_stride_voxels, nslots, bounds, MFA_PREC_FP32, flags, d_data, data_slot_stride, d_residual,
+                      d_rmse, stream);
 }
 
 int mfa_basis_tables(mfa_ctx* ctx, const mfa_block_desc* d_desc, const float* d_knots, int64_t knots_len,

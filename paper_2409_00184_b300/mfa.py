@@ -65,7 +65,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
-           "mfa_raycast_direct", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
+           "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
            "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop"]
 
 
@@ -99,6 +99,8 @@ def _load():
         "mfa_raycast_direct": (ctypes.c_int, [P, P, I32, P, I64, P, I64, ctypes.POINTER(Bounds), P,
                                               ctypes.POINTER(I32), I32, P, P, I32, P, P]),
         "mfa_store_write": (ctypes.c_int, [ctypes.c_char_p, P, I32, P, I64, P, I64]),
+        "mfa_decode_compare_blocks": (ctypes.c_int, [P, P, I32, P, I32, P, P, I64, P, I64, P, I64, I64,
+                                                     ctypes.POINTER(Bounds), U32, P, I64, P, P, P]),
         "mfa_cache_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_char_p, I32, I32]),
         "mfa_cache_destroy": (None, [P]),
         "mfa_cache_info": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
@@ -253,6 +255,31 @@ def decode_blocks(ctx, blocks, cache, slot_stride, nslots, precision=PREC_FP32, 
                                  _ptr(blocks.knots), blocks.knots.numel(), _ptr(cps), cps.numel(),
                                  _ptr(cache), slot_stride, nslots, ctypes.byref(bounds or blocks.bounds),
                                  precision, flags, _stream(stream)), "mfa_decode_blocks")
+
+
+def decode_compare_blocks(ctx, blocks, cache, slot_stride, nslots, data, data_stride, residual=None, rmse=None,
+                          flags=0, cps=None, list_=None, count=None, bounds=None, stream=None):
+    """mfa_decode_compare_blocks: the FP32 decode of decode_blocks and, in the same pass, r = f - D against the
+    sample grids `data` (slot-addressed, data_stride floats per slot): residual (optional, same addressing)
+    and the RMSE per selected item (optional float64 tensor)."""
+    cps = blocks.cps if cps is None else cps
+    if list_ is not None and list_.numel() == 0:
+        return
+    width = 1 if flags & DECODE_VALUE_ONLY else 4
+    _need(cache, nslots * slot_stride * width, "cache")
+    _need(cps, blocks.cps_len, "cps")
+    _need(data, nslots * data_stride, "data")
+    if residual is not None:
+        _need(residual, nslots * data_stride, "residual")
+    if rmse is not None:
+        if rmse.dtype != torch.float64:
+            raise ValueError("rmse: float64 tensor")
+        _need(rmse, list_.numel() if list_ is not None else blocks.n, "rmse")
+    _check(lib.mfa_decode_compare_blocks(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(list_),
+                                         0 if list_ is None else list_.numel(), _ptr(count), _ptr(blocks.knots),
+                                         blocks.knots.numel(), _ptr(cps), cps.numel(), _ptr(cache), slot_stride,
+                                         nslots, ctypes.byref(bounds or blocks.bounds), flags, _ptr(data), data_stride,
+                                         _ptr(residual), _ptr(rmse), _stream(stream)), "mfa_decode_compare_blocks")
 
 
 def basis_tables(ctx, desc_one, knots, stream=None):

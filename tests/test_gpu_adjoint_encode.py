@@ -119,3 +119,56 @@ def test_encode_plan_rejects_bad_batches(mfa, ctx):
     with pytest.raises(mfa.MfaError) as e:
         mfa.EncodePlan(ctx, blk)
     assert e.value.code == mfa.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("flags_name", ["", "VALUE_ONLY"])
+def test_decode_compare_fuses_residual_and_rmse(mfa, ctx, flags_name):
+    """mfa_decode_compare_blocks: the cache equals mfa_decode_blocks', the residual equals decode(P) - D, and
+    the RMSE equals both the fit's RMSE (same fitted P) and the oracle's, on fitted Gaussian-mixture blocks
+    and on a ragged random batch through a device-counted list with list slots."""
+    flags = getattr(mfa, "DECODE_" + flags_name) if flags_name else 0
+    width = 1 if flags_name else 4
+    # fitted blocks: the fit's RMSE is the reference
+    bs, blocks = gm_blocks_fitted(64, 16, 8, 2, synth.BASE_SEED + 20)
+    blk = mfa.DeviceBlocks(bs)
+    nb, vox = len(bs), 16 ** 3
+    D = torch.from_numpy(blocks.reshape(-1)).cuda()
+    plan = mfa.EncodePlan(ctx, blk)
+    fit_rmse = torch.empty(nb, dtype=torch.float64, device="cuda")
+    mfa.encode_blocks(ctx, plan, D, vox, nb, blk.cps, fit_rmse)
+    plan.close()
+    cache_a = torch.zeros(nb * vox * width, device="cuda")
+    cache_b = torch.zeros(nb * vox * width, device="cuda")
+    res = torch.full((nb * vox,), float("nan"), device="cuda")
+    rm = torch.full((nb,), float("nan"), dtype=torch.float64, device="cuda")
+    mfa.decode_blocks(ctx, blk, cache_a, vox, nb, flags=flags)
+    mfa.decode_compare_blocks(ctx, blk, cache_b, vox, nb, D, vox, residual=res, rmse=rm, flags=flags)
+    assert ctx.device_status() == 0
+    assert torch.equal(cache_a, cache_b)
+    f = cache_b.view(nb, vox, width)[:, :, 0]
+    assert torch.equal(res.view(nb, vox), f - D.view(nb, vox))
+    drange = float(blocks.max() - blocks.min())
+    assert float((rm - fit_rmse).abs().max()) <= 1e-6 * drange
+    for b in range(0, nb, 9):
+        P = bs.block_cps(b)
+        want = encode.rmse(P, blocks[b].astype(np.float64), bs.block_knots(b), tuple(bs.degree[b]))
+        assert abs(float(rm[b]) - want) <= 1e-5 * drange
+    # ragged batch, list with a device count and list slots
+    rb = synth.random_block_set(14, 321, nsamp_choices=(5, 13, 32), ncp_choices=(4, 6))
+    rblk = mfa.DeviceBlocks(rb)
+    Dr, stride = _grids(rb, 321)
+    lst = torch.tensor([3, 11, 0, 7, 5], dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([4], dtype=torch.int32, device="cuda")
+    Dl = torch.from_numpy(np.ascontiguousarray(Dr[rb.slot[lst.cpu().numpy()]]).ravel()).cuda()  # slot m: item m
+    cache = torch.zeros(5 * stride * width, device="cuda")
+    rml = torch.full((5,), -1.0, dtype=torch.float64, device="cuda")
+    mfa.decode_compare_blocks(ctx, rblk, cache, stride, 5, Dl, stride, rmse=rml, flags=flags | mfa.DECODE_LIST_SLOTS,
+                              list_=lst, count=cnt)
+    assert ctx.device_status() == 0
+    got = rml.cpu().numpy()
+    for m, b in enumerate(lst.cpu().numpy()[:4]):
+        nx, ny, nz = rb.nsamp[b]
+        g = Dl[m * stride: m * stride + nx * ny * nz].double().cpu().numpy().reshape(nz, ny, nx)
+        want = encode.rmse(rb.block_cps(b), g, rb.block_knots(b), tuple(rb.degree[b]))
+        assert abs(got[m] - want) <= 1e-5 * max(1.0, float(np.abs(g).max())), (m, b)
+    assert got[4] == 0.0  # beyond the device count: zeroed, not decoded
