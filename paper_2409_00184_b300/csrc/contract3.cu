@@ -3,16 +3,19 @@
 //     Y[c][b][a] = sum_{k,j,i} X[k][j][i] Ax[i][a] Ay[j][b] Az[k][c]
 //   kFit:      A = (N^T N)^{-1} N^T per axis (from the encode plan) -> least-squares control points,
 //              then optionally the RMSE of the fitted model over the samples (Table 1's metric);
-//   kAdjoint:  A = N (collocation matrix, built from the knots in the CTA) -> N^T R;
+//   kAdjoint:  A = N (collocation matrix, its band built from the knots in the CTA) -> N^T R;
 //   kGradient: G = N^T (decode(P) - D), the gradient of 0.5*||decode(P) - D||^2: each slab of samples is
 //              replaced in shared memory by its residual (a banded value decode of P minus the samples)
 //              before the contraction, so the cancellation happens per sample, at the data's scale.
 //              TMA kernel only; other shapes use the banded adjoint kernel.
 // One CTA per block; the grid streams through in z-slabs of ks planes:
-//   x:  Y1[(k,j)][a] = sum_i X[k][j][i] Ax[i][a]   thread per sample row, all columns in registers,
-//                                                  Ax rows broadcast from shared memory
-//   y:  Y2[k][b][a]  = sum_j Y1[(k,j)][a] Ay[j][b]  4 columns b per thread
-//   z:  Y[c][b][a]  += sum_k Y2[k][b][a] Az[k][c]   4 columns c per thread
+//   x:  Y1[(k,j)][a] = sum_i X[k][j][i] Ax[i][a]   thread per sample row
+//   y:  Y2[k][b][a]  = sum_j Y1[(k,j)][a] Ay[j][b]  thread per (k, a)
+//   z:  Y[c][b][a]  += sum_k Y2[k][b][a] Az[k][c]   thread per (b, a)
+// The fit's A (the pseudo-inverse) is dense: a thread keeps all columns of its output in registers
+// and reads the rows of A as shared-memory broadcasts. The adjoint's and the gradient's A = N has
+// q = p + 1 nonzeros per sample: those modes keep only the q partial sums of the sample's band and
+// write each column once the band has passed it (a quarter of the dense products at C = 12).
 // Two kernels share these stages. The TMA kernel (rows of 32 samples) loads each slab with one
 // cp.async.bulk.tensor into a 128-byte-swizzled shared buffer, double-buffered on mbarriers, and
 // prefetches the next (block, slab) of its static schedule while it computes the current one; the
@@ -33,7 +36,7 @@ constexpr int kThreads = 256;
 constexpr int kTmaRow = 32;  // samples per row on the TMA path (128 bytes)
 
 struct C3Smem {
-  int A[3], off[3], tab[3], knots, Y1, Y2, Y, P, X, total;  // offsets in 4-byte words
+  int A[3], bandN[3], bandO[3], adv, off[3], tab[3], knots, Y1, Y2, Y, P, X, total;  // offsets in 4-byte words
   int us;  // gradient: row stride of the decoded U rows kept in Y1 (odd: per-thread rows, no bank conflicts)
 };
 
@@ -49,7 +52,14 @@ C3Smem c3_layout(int mode, int CP, int maxC, int maxN, int ks, bool rmse, int xb
   const int CPs = (CP % 8 == 0) ? CP + 4 : CP;
   C3Smem L;
   int o = 0;
-  for (int a = 0; a < 3; ++a) { L.A[a] = o; o += maxN * CP; }
+  for (int a = 0; a < 3; ++a) { L.A[a] = o; if (mode == kFit) o += maxN * CP; }
+  // adjoint and gradient: banded basis per axis and sample (q values as a float4, band offset s - p)
+  for (int a = 0; a < 3; ++a) { L.bandN[a] = o; if (mode != kFit) o += 4 * maxN; }
+  for (int a = 0; a < 3; ++a) { L.bandO[a] = o; if (mode != kFit) o += maxN; }
+  o = round4(o);
+  // per axis: 64-bit mask of the samples where the band moves on by one column, then a flag word
+  // (1: the band starts at column 0 and never moves by more than one column per sample)
+  L.adv = o; if (mode != kFit) o += 12;
   L.us = CP + 1;
   for (int a = 0; a < 3; ++a) { L.off[a] = o; if (mode == kGradient) o += maxN; }
   for (int a = 0; a < 3; ++a) {
@@ -117,9 +127,14 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
     }
   } else {
     float* kn = sm + L.knots;
-    for (int a = 0; a < 3; ++a) {  // every maxN row zeroed: padded sample rows must contribute nothing
+    for (int a = 0; a < 3; ++a) {
       for (int i = tid; i < g.C[a] + g.p[a] + 1; i += nthr) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
-      for (int e = tid; e < prm.maxN * CP; e += nthr) sm[L.A[a] + e] = 0.f;
+      // band entries past n[a] (zero padding of shorter rows): zero weights, offset C - 1 (the band
+      // only moves forward, so those entries close every remaining column and add nothing)
+      for (int i = g.n[a] + tid; i < prm.maxN; i += nthr) {
+        reinterpret_cast<float4*>(sm + L.bandN[a])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<int*>(sm + L.bandO[a])[i] = g.C[a] - 1;
+      }
       if (MODE == kGradient) {  // entries past n[a] stay zero: offset 0, zero band
         for (int i = tid; i < prm.maxN; i += nthr) reinterpret_cast<int*>(sm + L.off[a])[i] = 0;
         for (int e = tid; e < prm.maxN * (int)(sizeof(TabEntry) / 4); e += nthr) sm[L.tab[a] + e] = 0.f;
@@ -138,7 +153,8 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
       const int s = find_span(t, g.p[a], g.C[a], u);
       float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
       basis_funs<MFA_MAX_DEGREE>(t, g.p[a], s, u, N, dN);
-      for (int r = 0; r <= g.p[a]; ++r) sm[L.A[a] + i * CP + s - g.p[a] + r] = N[r];
+      reinterpret_cast<float4*>(sm + L.bandN[a])[i] = make_float4(N[0], N[1], N[2], N[3]);
+      reinterpret_cast<int*>(sm + L.bandO[a])[i] = s - g.p[a];
       if (MODE == kGradient) {
         reinterpret_cast<int*>(sm + L.off[a])[i] = s - g.p[a];
         TabEntry te;  // band of sample i (N[r] is zero for r > p)
@@ -149,6 +165,18 @@ __device__ void c3_setup(const ContractParams& prm, const C3Smem& L, float* sm, 
     }
   }
   __syncthreads();
+  if (MODE != kFit && tid < 3) {
+    const int* bO = reinterpret_cast<const int*>(sm + L.bandO[tid]);
+    unsigned long long m = 0ull;
+    int simple = bO[0] == 0;
+    for (int i = 1; i < g.n[tid]; ++i) {
+      const int step = bO[i] - bO[i - 1];
+      if (step == 1) m |= 1ull << i;
+      else if (step != 0) simple = 0;
+    }
+    reinterpret_cast<unsigned long long*>(sm + L.adv)[tid] = m;
+    reinterpret_cast<int*>(sm + L.adv)[6 + tid] = simple;
+  }
   if (MODE == kGradient)
     for (int e = tid; e < ncps; e += nthr) sm[L.P + e] = prm.cps[g.cpoff + e];
   for (int e = tid; e < ncps; e += nthr) sm[L.Y + e] = 0.f;
@@ -286,6 +314,204 @@ __device__ void c3_stage_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0,
   __syncthreads();
 }
 
+// ---- banded transposed stages (adjoint and gradient: A = N, q = p + 1 nonzeros per sample) ----
+// A sample's band covers the columns o_i .. o_i + q - 1, and o_i never decreases with i. A thread
+// walks its samples in order with the q partial sums of the current band in registers; when the band
+// moves on, the column it leaves is complete and is written out (ACC: added to the output). Every
+// thread of a stage walks the same sample sequence, so the band moves are uniform across a warp.
+// The usual case (band from column 0, at most one column per sample) reads the moves from a bit mask
+// held in a register, so no branch waits on a shared-memory load; other knot vectors take the
+// general walk over the stored offsets.
+template <int Q, bool ACC>
+__device__ __forceinline__ void band_emit(float (&w)[Q], int& o, float* __restrict__ out, int stride) {
+  if (ACC) out[o * stride] += w[0]; else out[o * stride] = w[0];
+#pragma unroll
+  for (int d = 0; d + 1 < Q; ++d) w[d] = w[d + 1];
+  w[Q - 1] = 0.f;
+  ++o;
+}
+
+template <int Q, bool ACC>
+__device__ __forceinline__ void band_advance(float (&w)[Q], int& o, int to, float* __restrict__ out, int stride) {
+  while (o < to) band_emit<Q, ACC>(w, o, out, stride);
+}
+
+template <int Q>
+__device__ __forceinline__ void band_fma(float (&w)[Q], const float4 nw, float x) {
+  w[0] = fmaf(nw.x, x, w[0]);
+  w[1] = fmaf(nw.y, x, w[1]);
+  w[2] = fmaf(nw.z, x, w[2]);
+  if (Q > 3) w[Q > 3 ? 3 : 0] = fmaf(nw.w, x, w[Q > 3 ? 3 : 0]);
+}
+
+struct Band {
+  const float4* __restrict__ N;  // q basis values per sample (zero past q)
+  const int* __restrict__ off;   // first column of the sample's band
+  unsigned long long adv;        // SIMPLE walk: bit i set when the band moves on at sample i
+};
+
+__device__ __forceinline__ Band c3_band(const C3Smem& L, const float* sm, int a) {
+  Band b;
+  b.N = reinterpret_cast<const float4*>(sm + L.bandN[a]);
+  b.off = reinterpret_cast<const int*>(sm + L.bandO[a]);
+  b.adv = reinterpret_cast<const unsigned long long*>(sm + L.adv)[a];
+  return b;
+}
+
+__device__ __forceinline__ bool c3_band_simple(const C3Smem& L, const float* sm, int a) {
+  return reinterpret_cast<const int*>(sm + L.adv)[6 + a] != 0;
+}
+
+// moves the band to sample i's columns
+template <int Q, bool SIMPLE, bool ACC>
+__device__ __forceinline__ void band_to(const Band& bd, int i, float (&w)[Q], int& o, float* __restrict__ out,
+                                        int stride) {
+  if (SIMPLE) {
+    if ((bd.adv >> i) & 1ull) band_emit<Q, ACC>(w, o, out, stride);
+  } else {
+    band_advance<Q, ACC>(w, o, bd.off[i], out, stride);
+  }
+}
+
+// x^T: V[r][a] = sum_i N_a(u_i) X[r][i], thread per row of 32 samples of the swizzled slab buffer.
+template <int Q, bool SIMPLE>
+__device__ void c3_stage_xT_smem(const float4* __restrict__ xb, const Band bd, int C, float* __restrict__ Y1, int ys,
+                                 int rows) {
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    float w[Q];
+#pragma unroll
+    for (int d = 0; d < Q; ++d) w[d] = 0.f;
+    int o = 0;
+    float* yr = Y1 + r * ys;
+    const float4* row = xb + r * 8;
+    const int sw = r & 7;
+#pragma unroll 2
+    for (int c = 0; c < 8; ++c) {
+      const float4 v = row[c ^ sw];
+      const float xs[4] = {v.x, v.y, v.z, v.w};
+      float4 nw[4];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) nw[q4] = bd.N[4 * c + q4];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        band_to<Q, SIMPLE, false>(bd, 4 * c + q4, w, o, yr, 1);
+        band_fma<Q>(w, nw[q4], xs[q4]);
+      }
+    }
+    band_advance<Q, false>(w, o, C, yr, 1);
+  }
+}
+
+// x^T from global memory (rows of any length nx).
+template <int Q>
+__device__ void c3_stage_xT_global(const float* X, const Band bd, int C, float* __restrict__ Y1, int ys, int k0,
+                                   int kc, int nx, int ny) {
+  for (int r = threadIdx.x; r < kc * ny; r += blockDim.x) {
+    const float* xr = X + ((int64_t)k0 * ny + r) * nx;
+    float w[Q];
+#pragma unroll
+    for (int d = 0; d < Q; ++d) w[d] = 0.f;
+    int o = 0;
+    float* yr = Y1 + r * ys;
+    for (int i = 0; i < nx; ++i) {
+      band_advance<Q, false>(w, o, bd.off[i], yr, 1);
+      band_fma<Q>(w, bd.N[i], __ldg(xr + i));
+    }
+    band_advance<Q, false>(w, o, C, yr, 1);
+  }
+}
+
+//   W[kl][b][a]  = sum_j N_b(v_j) V[(kl, j)][a]        thread per (kl, a)
+template <int Q, bool SIMPLE>
+__device__ void c3_stage_yT(const float* __restrict__ Y1, int ys, const Band bd, float* __restrict__ Y2, int kc,
+                            int Cx, int Cy, int ny) {
+  const int plane = Cx * Cy;
+  for (int e = threadIdx.x; e < kc * Cx; e += blockDim.x) {
+    const int kl = e / Cx, a = e - kl * Cx;
+    const float* y1 = Y1 + kl * ny * ys + a;
+    float* y2 = Y2 + kl * plane + a;
+    float w[Q];
+#pragma unroll
+    for (int d = 0; d < Q; ++d) w[d] = 0.f;
+    int o = 0;
+#pragma unroll 4
+    for (int j = 0; j < ny; ++j) {
+      const float v = y1[j * ys];
+      const float4 nw = bd.N[j];
+      band_to<Q, SIMPLE, false>(bd, j, w, o, y2, Cx);
+      band_fma<Q>(w, nw, v);
+    }
+    band_advance<Q, false>(w, o, Cy, y2, Cx);
+  }
+}
+
+//   Y[c][b][a]  += sum_kl N_c(w_{k0+kl}) W[kl][b][a]    thread per (b, a); the band of the slab's first
+//                                                       plane opens the window, columns are added to Y
+template <int Q, bool SIMPLE>
+__device__ void c3_stage_zT(const float* __restrict__ Y2, const Band bd, float* __restrict__ Y, int k0, int kc,
+                            int plane, int Cz) {
+  for (int ab = threadIdx.x; ab < plane; ab += blockDim.x) {
+    float w[Q];
+#pragma unroll
+    for (int d = 0; d < Q; ++d) w[d] = 0.f;
+    int o = bd.off[k0];
+    for (int kl = 0; kl < kc; ++kl) {
+      const float v = Y2[kl * plane + ab];
+      const float4 nw = bd.N[k0 + kl];
+      if (kl > 0) band_to<Q, SIMPLE, true>(bd, k0 + kl, w, o, Y + ab, plane);
+      band_fma<Q>(w, nw, v);
+    }
+#pragma unroll
+    for (int d = 0; d < Q; ++d)
+      if (o + d < Cz) Y[(o + d) * plane + ab] += w[d];
+  }
+}
+
+// Dispatch on the band width (q = 3 covers degrees 1 and 2) and on the walk.
+template <int Q>
+__device__ __forceinline__ void c3_banded_x_smem_q(const C3Smem& L, float* sm, const C3Geom& g, const float4* xb,
+                                                   int rows) {
+  const Band bd = c3_band(L, sm, 0);
+  if (c3_band_simple(L, sm, 0)) c3_stage_xT_smem<Q, true>(xb, bd, g.C[0], sm + L.Y1, L.us, rows);
+  else c3_stage_xT_smem<Q, false>(xb, bd, g.C[0], sm + L.Y1, L.us, rows);
+}
+
+__device__ __forceinline__ void c3_banded_x_smem(const C3Smem& L, float* sm, const C3Geom& g, const float4* xb,
+                                                 int rows) {
+  if (g.p[0] <= 2) c3_banded_x_smem_q<3>(L, sm, g, xb, rows);
+  else c3_banded_x_smem_q<4>(L, sm, g, xb, rows);
+}
+
+__device__ __forceinline__ void c3_banded_x_global(const C3Smem& L, float* sm, const C3Geom& g, const float* X,
+                                                   int k0, int kc) {
+  const Band bd = c3_band(L, sm, 0);
+  if (g.p[0] <= 2) c3_stage_xT_global<3>(X, bd, g.C[0], sm + L.Y1, L.us, k0, kc, g.n[0], g.n[1]);
+  else c3_stage_xT_global<4>(X, bd, g.C[0], sm + L.Y1, L.us, k0, kc, g.n[0], g.n[1]);
+}
+
+template <int Q>
+__device__ __forceinline__ void c3_banded_y_q(const C3Smem& L, float* sm, const C3Geom& g, int kc) {
+  const Band bd = c3_band(L, sm, 1);
+  if (c3_band_simple(L, sm, 1)) c3_stage_yT<Q, true>(sm + L.Y1, L.us, bd, sm + L.Y2, kc, g.C[0], g.C[1], g.n[1]);
+  else c3_stage_yT<Q, false>(sm + L.Y1, L.us, bd, sm + L.Y2, kc, g.C[0], g.C[1], g.n[1]);
+}
+
+template <int Q>
+__device__ __forceinline__ void c3_banded_z_q(const C3Smem& L, float* sm, const C3Geom& g, int k0, int kc) {
+  const Band bd = c3_band(L, sm, 2);
+  const int plane = g.C[0] * g.C[1];
+  if (c3_band_simple(L, sm, 2)) c3_stage_zT<Q, true>(sm + L.Y2, bd, sm + L.Y, k0, kc, plane, g.C[2]);
+  else c3_stage_zT<Q, false>(sm + L.Y2, bd, sm + L.Y, k0, kc, plane, g.C[2]);
+}
+
+// y^T then z^T of one slab
+__device__ __forceinline__ void c3_banded_yz(const C3Smem& L, float* sm, const C3Geom& g, int k0, int kc) {
+  if (g.p[1] <= 2) c3_banded_y_q<3>(L, sm, g, kc); else c3_banded_y_q<4>(L, sm, g, kc);
+  __syncthreads();
+  if (g.p[2] <= 2) c3_banded_z_q<3>(L, sm, g, k0, kc); else c3_banded_z_q<4>(L, sm, g, k0, kc);
+  __syncthreads();
+}
+
 // Writes the block's result Y; for the fit also the RMSE of
 // the fitted model (banded value decode vs the samples; per-thread FP32 Kahan sums reduced in FP64).
 template <int CP, int MODE>
@@ -296,12 +522,9 @@ __device__ void c3_epilogue(const ContractParams& prm, const C3Smem& L, float* s
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = Cx * Cy, ncps = plane * Cz;
   const float* Y = sm + L.Y;
-  if (MODE != kFit) {  // adjoint N^T R, or gradient N^T (decode(P) - D)
-    for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
-    return;
-  }
   for (int e = tid; e < ncps; e += nthr) prm.out[g.cpoff + e] = Y[e];
-  if (!prm.rmse) return;
+  // the adjoint N^T R and the gradient N^T (decode(P) - D) end here; the fit may add its RMSE
+  if (MODE != kFit || !prm.rmse) return;
   const TabEntry* tx = reinterpret_cast<const TabEntry*>(sm + L.tab[0]);
   const TabEntry* ty = reinterpret_cast<const TabEntry*>(sm + L.tab[1]);
   const TabEntry* tz = reinterpret_cast<const TabEntry*>(sm + L.tab[2]);
@@ -451,9 +674,11 @@ __global__ void __launch_bounds__(kThreads) contract3_kernel(ContractParams prm,
     const bool vec = vec_ok && (g.n[0] % 4 == 0);
     for (int k0 = 0; k0 < g.n[2]; k0 += ks) {
       const int kc = min(ks, g.n[2] - k0);
-      c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1], vec);
+      if (MODE == kFit) c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1], vec);
+      else c3_banded_x_global(L, sm, g, X, k0, kc);
       __syncthreads();
-      c3_stage_yz<CP>(L, sm, g, k0, kc);
+      if (MODE == kFit) c3_stage_yz<CP>(L, sm, g, k0, kc);
+      else c3_banded_yz(L, sm, g, k0, kc);
     }
     c3_epilogue<CP, MODE>(prm, L, sm, g, s_item, X, ks, s_red);
   }
@@ -550,7 +775,8 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
             if (MODE == kGradient)
               c3_value_decode_slab<kResidual, false>(L, sm, g, sm + L.P, xbuf + b * buf_f4, k0, kc, L.us, ksum,
                                                      kcomp);
-            c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
+            if (MODE == kFit) c3_stage_x_smem<CP>(xbuf + b * buf_f4, sm + L.A[0], sm + L.Y1, kc * g.n[1]);
+            else c3_banded_x_smem(L, sm, g, xbuf + b * buf_f4, kc * g.n[1]);
           } else {
             c3_value_decode_slab<kRmse, false>(L, sm, g, sm + L.Y, xbuf + b * buf_f4, k0, kc, L.us, ksum, kcomp);
           }
@@ -567,14 +793,20 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
         }
         __syncthreads();
         c3_value_decode_slab<kResidual, true>(L, sm, g, sm + L.P, xb, k0, kc, L.us, ksum, kcomp);
-        c3_stage_x_smem<CP>(xb, sm + L.A[0], sm + L.Y1, rows);
+        c3_banded_x_smem(L, sm, g, xb, rows);
       } else if (!skip) {
-        c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
-                              (g.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) &&
-                                  (prm.slot_stride % 4 == 0));
+        if (MODE == kFit)
+          c3_stage_x_global<CP>(X, sm + L.A[0], sm + L.Y1, k0, kc, g.n[0], g.n[1],
+                                (g.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) &&
+                                    (prm.slot_stride % 4 == 0));
+        else
+          c3_banded_x_global(L, sm, g, X, k0, kc);
       }
       __syncthreads();
-      if (!skip && pass == 0) c3_stage_yz<CP>(L, sm, g, k0, kc);
+      if (!skip && pass == 0) {
+        if (MODE == kFit) c3_stage_yz<CP>(L, sm, g, k0, kc);
+        else c3_banded_yz(L, sm, g, k0, kc);
+      }
     }
     if (nslab == 0 && tma_ok(gn)) {  // no slab of this block carried the next block's prefetch
       if (tid == 0) issue(gn, 0);
@@ -600,6 +832,382 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
     __syncthreads();
     cur ^= 1;
     item = nitem;
+  }
+}
+
+// ---- z-first streaming kernel (fit without its RMSE pass, adjoint; n <= 32 per axis, C <= 16) ----
+// The sample planes stream through a ring of TMA slabs and are contracted over z on arrival:
+//   z:  T[c][j][i] = sum_k Az[k][c] X[k][j][i]     thread per 4 neighbouring (j, i) columns, all C rows
+//                                                   of its columns in registers; the plane's Az row is
+//                                                   one broadcast for every thread, so the stage is
+//                                                   almost only FMAs
+//   y:  U[c][b][i] = sum_j Ay[j][b] T[c][j][i]     thread per (c, i), all b in registers
+//   x:  Y[c][b][a] = sum_i Ax[i][a] U[c][b][i]     thread per (c, b), all a in registers
+// One CTA per SM, two warp groups working on consecutive blocks of the CTA's static schedule:
+//  * the z group (warps 0-7) streams block after block through the z stage; its thread 0 keeps the
+//    TMA ring up to R slabs ahead, into the next block once that block's set-up is published (the
+//    producer reads the geometry from the set-up, so it never waits on a descriptor load);
+//  * the y/x group (warps 8-15) finishes the previous block (y and x stages, output) and sets up the
+//    block three ahead of it: its geometry is fetched before the wait for T, its A matrices are built
+//    after the x stage, and only when the block's class (fit) or degree, C, n and knot vectors
+//    (adjoint) differ from those of the block the buffer held before.
+// Geometry and A rotate through four buffers (block n in buffer n % 4), so the geometry of the next
+// block is published well before the producer needs it; T is handed from the z group
+// (which keeps its sums in registers until a block's last plane) to the y/x group and back on
+// mbarriers (T full, T free, set-up ready), so neither group waits for the other's stages and the
+// samples keep streaming while a block is finished. Slabs are 8 planes (32 KB) where shared memory
+// allows: the streaming rate grows with the bytes per copy. Every wait is bounded (MFA_DEV_TIMEOUT).
+// Blocks whose x-rows or y-columns are shorter than 32 are copied into their T buffer (not yet in
+// use), zero-padded, instead of loaded by TMA; the zero rows of A make the padding contribute nothing.
+constexpr int kZfPlane = 1024;   // samples of a 32 x 32 plane
+constexpr int kZfMaxRing = 16;
+constexpr int kZfGroup = 256;    // threads per warp group
+constexpr int kZfThreads = 2 * kZfGroup;
+constexpr int kBarZ = 1, kBarYX = 2;  // named barriers of the two groups
+
+constexpr int kZfSets = 4;  // set-up buffers (geometry, A, knots)
+
+struct ZfSmem {
+  int A[kZfSets][3], knots[kZfSets], T, U, ring, ks, R, total;  // offsets in 4-byte words; ks planes per slab
+};
+
+ZfSmem zf_layout(int mode, int CP, int ks, int R) {
+  ZfSmem L;
+  int o = 0;
+  for (int p = 0; p < kZfSets; ++p)
+    for (int a = 0; a < 3; ++a) { L.A[p][a] = o; o += 32 * CP; }
+  for (int p = 0; p < kZfSets; ++p) { L.knots[p] = o; if (mode != kFit) o += 3 * kKnotMax; }
+  o = round4(o);
+  L.T = o; o += CP * kZfPlane;
+  L.U = L.T;  // U overwrites T once the y stage has read all of it
+  L.ring = o; o += 252 + R * ks * kZfPlane;  // slack for 1024-byte alignment
+  L.ks = ks;
+  L.R = R;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kZfGroup) : "memory");
+}
+
+// true in every thread of the group if `pred` holds in any of them
+__device__ __forceinline__ bool group_any(int id, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, o;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred o, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, o;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(kZfGroup)
+      : "memory");
+  return r != 0;
+}
+
+// Zero-padded A matrices of a block (32 rows x CP columns per axis) into A[.][a]: the fit's
+// pseudo-inverses from the plan, or the adjoint's collocation matrices from the knots. Run by the y/x
+// group (t = thread of the group); ends with the group's barrier.
+template <int CP, int MODE>
+__device__ void zf_setup(const ContractParams& prm, const int* A, float* kn, float* sm, const C3Geom& g, int t,
+                         int* s_bad) {
+  for (int e = t; e < 3 * 32 * CP; e += kZfGroup) sm[A[0] + e] = 0.f;
+  if (MODE != kFit)
+    for (int a = 0; a < 3; ++a)
+      for (int i = t; i < g.C[a] + g.p[a] + 1; i += kZfGroup) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
+  group_sync(kBarYX);
+  if (MODE == kFit) {
+    for (int a = 0; a < 3; ++a) {
+      const EncClass& c = prm.classes[g.cls[a]];
+      for (int e = t; e < c.n * c.C; e += kZfGroup) {
+        const int i = e / c.C, col = e - i * c.C;
+        sm[A[a] + i * CP + col] = prm.pinv[c.pinv_off + e];
+      }
+    }
+  } else {
+    if (t < 3 && !knots_ok(kn + t * kKnotMax, g.p[t], g.C[t])) {
+      atomicOr(s_bad, 1);
+      flag(prm.status, MFA_DEV_BAD_KNOTS);
+    }
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int a = t < nx ? 0 : (t < nx + ny ? 1 : (t < nx + ny + nz ? 2 : -1));
+    if (a >= 0) {
+      const int i = a == 0 ? t : (a == 1 ? t - nx : t - nx - ny);
+      const float* kt = kn + a * kKnotMax;
+      const float u = sample_param(i, g.n[a]);
+      const int s = find_span(kt, g.p[a], g.C[a], u);
+      float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1];
+      basis_funs<MFA_MAX_DEGREE>(kt, g.p[a], s, u, N, dN);
+      for (int r = 0; r <= g.p[a]; ++r) sm[A[a] + i * CP + s - g.p[a] + r] = N[r];
+    }
+  }
+  group_sync(kBarYX);
+}
+
+// z stage over the kc planes of one slab (rows of 32 in the 128-byte-swizzled layout): thread t of
+// the z group owns samples i = 4(t & 7) .. +3 of row j = t >> 3 in every plane.
+template <int CP>
+__device__ __forceinline__ void zf_stage_z(const float4* buf, const float* Az, int k0, int kc, float (&acc)[CP][4]) {
+  const int j = threadIdx.x >> 3, ch = threadIdx.x & 7;
+#pragma unroll 2
+  for (int kl = 0; kl < kc; ++kl) {
+    const float4 v = buf[(kl * 32 + j) * 8 + (ch ^ (j & 7))];
+    const float4* w4 = reinterpret_cast<const float4*>(Az + (k0 + kl) * CP);
+#pragma unroll
+    for (int c4 = 0; c4 < CP / 4; ++c4) {
+      const float4 w = w4[c4];
+      const float ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float* a = acc[4 * c4 + q];
+        a[0] = fmaf(ws[q], v.x, a[0]);
+        a[1] = fmaf(ws[q], v.y, a[1]);
+        a[2] = fmaf(ws[q], v.z, a[2]);
+        a[3] = fmaf(ws[q], v.w, a[3]);
+      }
+    }
+  }
+}
+
+// y stage: columns e = t and t + 256 of T (c = e >> 5, i = e & 31) in one pass over j; the results
+// stay in registers until the group has read all of T, then overwrite it as U.
+template <int CP>
+__device__ __forceinline__ void zf_y_fma(float (&acc)[CP], const float* Ay, int j, float v) {
+  const float4* w4 = reinterpret_cast<const float4*>(Ay + j * CP);
+#pragma unroll
+  for (int b4 = 0; b4 < CP / 4; ++b4) {
+    const float4 w = w4[b4];
+    acc[4 * b4 + 0] = fmaf(w.x, v, acc[4 * b4 + 0]);
+    acc[4 * b4 + 1] = fmaf(w.y, v, acc[4 * b4 + 1]);
+    acc[4 * b4 + 2] = fmaf(w.z, v, acc[4 * b4 + 2]);
+    acc[4 * b4 + 3] = fmaf(w.w, v, acc[4 * b4 + 3]);
+  }
+}
+
+template <int CP>
+__device__ void zf_stage_y(const float* T, const float* Ay, float* U, int Cy, int Cz, int ny, int t) {
+  const int e0 = t, e1 = t + kZfGroup;
+  const bool h0 = e0 < Cz * 32, h1 = e1 < Cz * 32;  // uniform across a warp (Cz * 32 is a multiple of 32)
+  float a0[CP], a1[CP];
+#pragma unroll
+  for (int b = 0; b < CP; ++b) a0[b] = a1[b] = 0.f;
+  const float* t0 = T + (e0 >> 5) * kZfPlane + (e0 & 31);
+  const float* t1 = T + (e1 >> 5) * kZfPlane + (e1 & 31);
+  if (h1) {
+#pragma unroll 2
+    for (int j = 0; j < ny; ++j) {
+      const float v0 = t0[j * 32], v1 = t1[j * 32];
+      zf_y_fma<CP>(a0, Ay, j, v0);
+      zf_y_fma<CP>(a1, Ay, j, v1);
+    }
+  } else if (h0) {
+#pragma unroll 4
+    for (int j = 0; j < ny; ++j) zf_y_fma<CP>(a0, Ay, j, t0[j * 32]);
+  }
+  group_sync(kBarYX);  // all of T has been read
+#pragma unroll
+  for (int b = 0; b < CP; ++b)
+    if (b < Cy) {
+      if (h0) U[((e0 >> 5) * Cy + b) * 33 + (e0 & 31)] = a0[b];
+      if (h1) U[((e1 >> 5) * Cy + b) * 33 + (e1 & 31)] = a1[b];
+    }
+}
+
+template <int CP>
+__device__ void zf_stage_x(const float* U, const float* Ax, float* out, int Cx, int Cy, int Cz, int nx, int t) {
+  for (int q = t; q < Cz * Cy; q += kZfGroup) {
+    float acc[CP];
+#pragma unroll
+    for (int a = 0; a < CP; ++a) acc[a] = 0.f;
+    const float* ur = U + q * 33;
+#pragma unroll 4
+    for (int i = 0; i < nx; ++i) {
+      const float v = ur[i];
+      const float4* w4 = reinterpret_cast<const float4*>(Ax + i * CP);
+#pragma unroll
+      for (int a4 = 0; a4 < CP / 4; ++a4) {
+        const float4 w = w4[a4];
+        acc[4 * a4 + 0] = fmaf(w.x, v, acc[4 * a4 + 0]);
+        acc[4 * a4 + 1] = fmaf(w.y, v, acc[4 * a4 + 1]);
+        acc[4 * a4 + 2] = fmaf(w.z, v, acc[4 * a4 + 2]);
+        acc[4 * a4 + 3] = fmaf(w.w, v, acc[4 * a4 + 3]);
+      }
+    }
+    float* o = out + (int64_t)q * Cx;
+#pragma unroll
+    for (int a = 0; a < CP; ++a)
+      if (a < Cx) o[a] = acc[a];
+  }
+}
+
+template <int CP, int MODE>
+__global__ void __launch_bounds__(kZfThreads, 1)
+contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtensorMap xmap) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ __align__(8) uint64_t s_full[kZfMaxRing];
+  __shared__ __align__(8) uint64_t s_tfull, s_tfree, s_ready[kZfSets];
+  __shared__ C3Geom s_g[kZfSets], s_built[kZfSets];  // geometry of the buffer's block / of its A matrices
+  __shared__ int s_bad[kZfSets], s_rebuild[kZfSets], s_has[kZfSets];
+  const int tid = threadIdx.x;
+  const int R = L.R, ks = L.ks;
+  float4* ring = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(sm + L.ring) + 1023) & ~uintptr_t(1023));
+  const int slab_f4 = ks * kZfPlane / 4;
+  const uint32_t slab_bytes = (uint32_t)ks * kZfPlane * 4;
+  auto tma_block = [](const C3Geom& g) { return g.valid && !g.bad && g.n[0] == 32 && g.n[1] == 32; };
+
+  if (tid == 0) {
+    for (int r = 0; r < R; ++r) mbar_init(&s_full[r], 1);
+    mbar_init(&s_tfull, kZfGroup);
+    mbar_init(&s_tfree, 1);
+    for (int p = 0; p < kZfSets; ++p) {
+      mbar_init(&s_ready[p], 1);
+      s_has[p] = 0;
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();  // the last CTA-wide barrier: from here on each group synchronises on its own
+
+  if (tid < kZfGroup) {
+    // ------------------------------ z group ------------------------------
+    const int64_t rows_per_slot = prm.slot_stride / 32;
+    // producer (thread 0): the next slab to issue is slab p_slab of the CTA's block number p_n
+    int p_n = 0, p_slab = 0;
+    uint32_t issued = 0, consumed = 0;  // `consumed` is the same in every thread of the group
+    // Fill the ring up to R slabs ahead, into block n + 1 at most (its set-up, published on s_ready,
+    // gives the geometry; it cannot be overwritten before the group has finished block n + 1).
+    auto produce = [&](int n) {
+      while (issued < consumed + (uint32_t)R && p_n <= n + 1) {
+        const int pp = p_n % kZfSets;
+        if (!mbar_test_wait(&s_ready[pp], (p_n / kZfSets) & 1)) break;
+        const C3Geom& pg = s_g[pp];
+        if (!pg.valid) break;
+        if (tma_block(pg) && p_slab * ks < pg.n[2]) {
+          const uint32_t slot = issued % R;
+          mbar_arrive_expect_tx(&s_full[slot], slab_bytes);
+          const int64_t row = (int64_t)pg.slot * rows_per_slot + (int64_t)p_slab * ks * 32;
+          tma_load_2d(ring + slot * slab_f4, &xmap, &s_full[slot], 0, (int)row);
+          ++issued;
+          if (++p_slab * ks < pg.n[2]) continue;
+        }
+        ++p_n;
+        p_slab = 0;
+      }
+    };
+    auto fail = [&]() {  // a wait gave up: report, let this group's copies land, leave
+      if (tid == 0) {
+        flag(prm.status, MFA_DEV_TIMEOUT);
+        for (uint32_t q = consumed; q < issued; ++q) mbar_wait_bounded(&s_full[q % R], (q / R) & 1);
+      }
+    };
+    for (int n = 0;; ++n) {
+      const int p = n % kZfSets;
+      // set-up of block n (geometry, A)
+      if (group_any(kBarZ, !mbar_wait_bounded(&s_ready[p], (n / kZfSets) & 1))) { fail(); return; }
+      if (tid == 0) produce(n);
+      const C3Geom g = s_g[p];
+      if (!g.valid) break;
+      const bool skip = g.bad || s_bad[p];
+      const bool tmab = tma_block(g);
+      const int nz = g.bad ? 0 : g.n[2];
+      const float* Az = sm + L.A[p][2];
+      float* T = sm + L.T;
+      // T is this block's once the y/x group is done with block n - 1 (hand-filled blocks stage their
+      // planes in it, so they take it first)
+      bool own_t = n == 0;
+      auto take_t = [&]() {
+        if (own_t) return true;
+        own_t = true;
+        return !group_any(kBarZ, !mbar_wait_bounded(&s_tfree, (n - 1) & 1));
+      };
+      if (!tmab && nz > 0 && !take_t()) { fail(); return; }
+      float acc[CP][4];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+      const int step = tmab ? ks : min(ks, CP);  // a hand-filled slab must fit T (CP planes)
+      for (int k0 = 0; k0 < nz; k0 += step) {
+        const int kc = min(step, nz - k0);
+        const float4* buf;
+        if (tmab) {
+          if (tid == 0) produce(n);
+          const uint32_t slot = consumed % R;
+          const bool got = mbar_wait_bounded(&s_full[slot], (consumed / R) & 1);
+          ++consumed;
+          if (group_any(kBarZ, !got)) { fail(); return; }
+          buf = ring + slot * slab_f4;
+        } else {
+          const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
+          const int nx = g.n[0], ny = g.n[1];
+          for (int e = tid; e < kc * kZfPlane; e += kZfGroup) {
+            const int row = e >> 5, i = e & 31, kl = row >> 5, j = row & 31;
+            const float v = (i < nx && j < ny) ? X[((int64_t)(k0 + kl) * ny + j) * nx + i] : 0.f;
+            T[row * 32 + (((i >> 2) ^ (row & 7)) << 2) + (i & 3)] = v;
+          }
+          group_sync(kBarZ);
+          buf = reinterpret_cast<const float4*>(T);
+        }
+        if (!skip) zf_stage_z<CP>(buf, Az, k0, kc, acc);
+        group_sync(kBarZ);  // the slab's buffer may be refilled from here on
+      }
+      if (!take_t()) { fail(); return; }
+      if (!skip && nz > 0) {
+        const int j = tid >> 3, i0 = (tid & 7) * 4;
+#pragma unroll
+        for (int c = 0; c < CP; ++c)
+          if (c < g.C[2])
+            *reinterpret_cast<float4*>(T + c * kZfPlane + j * 32 + i0) = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+      }
+      mbar_arrive(&s_tfull);  // every thread of the group: T holds block n's z stage
+    }
+  } else {
+    // ------------------------------ y/x group ------------------------------
+    const int t = tid - kZfGroup;
+    // thread 0 of the group: geometry of block m into buffer m % 4, and whether its A must be built
+    auto fetch = [&](int m) {
+      const int b = m % kZfSets;
+      c3_fetch(prm, blockIdx.x + m * (int)gridDim.x, s_g[b]);
+      const C3Geom& g = s_g[b];
+      const C3Geom& h = s_built[b];
+      bool same = s_has[b] != 0;
+      for (int a = 0; a < 3 && same; ++a)
+        same = MODE == kFit ? g.cls[a] == h.cls[a]
+                            : (g.p[a] == h.p[a] && g.C[a] == h.C[a] && g.n[a] == h.n[a] && g.koff[a] == h.koff[a]);
+      s_rebuild[b] = g.valid && !g.bad && !same;
+      if (s_rebuild[b]) s_bad[b] = 0;
+    };
+    auto build = [&](int m) {  // the group: A of block m when needed, then publish the set-up
+      const int b = m % kZfSets;
+      group_sync(kBarYX);
+      if (s_rebuild[b]) {
+        zf_setup<CP, MODE>(prm, L.A[b], sm + L.knots[b], sm, s_g[b], t, &s_bad[b]);
+        if (t == 0) {
+          s_built[b] = s_g[b];
+          s_has[b] = 1;
+        }
+      }
+      if (t == 0) mbar_arrive(&s_ready[b]);
+    };
+    for (int m = 0; m < kZfSets - 1; ++m) {
+      if (t == 0) fetch(m);
+      build(m);
+    }
+    for (int n = 0;; ++n) {
+      const int b = n % kZfSets;
+      if (t == 0) fetch(n + kZfSets - 1);  // buffer of block n - 1, which both groups are done with
+      const C3Geom g = s_g[b];
+      if (!g.valid) break;
+      const bool ok = mbar_wait_bounded(&s_tfull, n & 1);
+      if (group_any(kBarYX, !ok)) {
+        if (t == 0) flag(prm.status, MFA_DEV_TIMEOUT);
+        return;
+      }
+      const bool work = !g.bad && !s_bad[b] && g.n[2] > 0;
+      if (work) zf_stage_y<CP>(sm + L.T, sm + L.A[b][1], sm + L.U, g.C[1], g.C[2], g.n[1], t);
+      group_sync(kBarYX);
+      if (work) zf_stage_x<CP>(sm + L.U, sm + L.A[b][0], prm.out + g.cpoff, g.C[0], g.C[1], g.C[2], g.n[0], t);
+      group_sync(kBarYX);
+      if (t == 0) mbar_arrive(&s_tfree);  // T (and U in it) may take block n + 1
+      build(n + kZfSets - 1);
+    }
   }
 }
 
@@ -630,6 +1238,23 @@ cudaError_t launch_c3(mfa_ctx* ctx, const ContractParams& prm, const C3Smem& L, 
     const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
     kern<<<grid, kThreads, smem, stream>>>(prm, L, ks, vec_ok);
   }
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+template <int CP>
+cudaError_t launch_zf(mfa_ctx* ctx, const ContractParams& prm, const ZfSmem& L, const CUtensorMap& xmap,
+                      cudaStream_t stream) {
+  const size_t smem = (size_t)L.total * 4;
+  auto kern = prm.mode == kFit ? contract3_zf_kernel<CP, kFit> : contract3_zf_kernel<CP, kAdjoint>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kZfThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::max(1, std::min(ctx->num_sms * occ, prm.nblocks));
+  kern<<<grid, kZfThreads, smem, stream>>>(prm, L, xmap);
   ctx->launches++;
   return cudaGetLastError();
 }
@@ -665,7 +1290,47 @@ bool make_row_map(CUtensorMap* map, const float* x, int64_t nslots, int64_t slot
 
 }  // namespace
 
+// The z-first kernel: the fit without its RMSE pass and the adjoint, for grids of at most 32 samples per
+// axis and at most 16 control points per axis, on 16-byte-aligned sample grids whose slots hold whole
+// rows of 32; one CTA per SM with the deepest ring that fits. Returns MFA_ERR_UNSUPPORTED when the call
+// does not qualify.
+static int contract3_zfirst(mfa_ctx* ctx, const ContractParams& prm, cudaStream_t stream) {
+  const int CP = round4(prm.maxC);
+  const bool qualifies = (prm.mode == kAdjoint || (prm.mode == kFit && prm.rmse == nullptr)) && CP <= 16 &&
+                         prm.maxN <= 32 && (reinterpret_cast<uintptr_t>(prm.x) % 16 == 0) &&
+                         (prm.slot_stride % 32 == 0);
+  if (!qualifies) return MFA_ERR_UNSUPPORTED;
+  // slab planes and ring depth: the largest slab with at least three in the ring, else with two
+  auto depth = [&](int ks) {
+    int R = 0;
+    for (int r = kZfMaxRing; r >= 2 && !R; --r)
+      if ((size_t)zf_layout(prm.mode, CP, ks, r).total * 4 + 1024 <= kMaxDynSmem) R = r;  // room for static smem
+    return R;
+  };
+  int ks = 0, R = 0;
+  for (int need = 3; need >= 2 && !ks; --need)
+    for (int k : {8, 4, 2})
+      if (!ks && depth(k) >= need) { ks = k; R = depth(k); }
+  if (!ks) return MFA_ERR_UNSUPPORTED;
+  const ZfSmem L = zf_layout(prm.mode, CP, ks, R);
+  CUtensorMap map;
+  if (!make_row_map(&map, prm.x, prm.nslots, prm.slot_stride, ks * 32)) return MFA_ERR_UNSUPPORTED;
+  cudaError_t e;
+  switch (CP) {
+    case 4: e = launch_zf<4>(ctx, prm, L, map, stream); break;
+    case 8: e = launch_zf<8>(ctx, prm, L, map, stream); break;
+    case 12: e = launch_zf<12>(ctx, prm, L, map, stream); break;
+    case 16: e = launch_zf<16>(ctx, prm, L, map, stream); break;
+    default: return MFA_ERR_UNSUPPORTED;
+  }
+  return e == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+}
+
 int contract3(mfa_ctx* ctx, ContractParams prm, cudaStream_t stream) {
+  {
+    const int rc = contract3_zfirst(ctx, prm, stream);
+    if (rc != MFA_ERR_UNSUPPORTED) return rc;
+  }
   const int CP = round4(prm.maxC);
   const bool rmse = prm.rmse != nullptr;
   // TMA path: rows of 32 samples (caller's hint), 16-byte aligned grids whose slots hold whole rows
