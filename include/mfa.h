@@ -259,11 +259,13 @@ void mfa_frame_graph_destroy(mfa_frame_graph* graph);
 
 /* ---- least-squares encode (Algorithm 1's model(NCP, degree)) ------------------------- */
 /* A plan validates a batch on the host, copies its descriptors and knots to the device
- * and groups the axes into classes of equal (knots, p, C, n). Executing it computes, per
- * class, M = N^T N and its Cholesky factor in FP64 and the pseudo-inverse (N^T N)^-1 N^T,
- * then fits every block: P = D x_1 N_x^+ x_2 N_y^+ x_3 N_z^+ (the exact least-squares
- * solution of the Kronecker system), and optionally its RMSE over the samples in FP64
- * (Table 1's error metric). Requires p+1 <= C <= n per axis. */
+ * and groups the axes into classes of equal (knots, p, C, n). Creating it also computes, per
+ * class, M = N^T N and its Cholesky factor in FP64 and the pseudo-inverse (N^T N)^-1 N^T
+ * (on the legacy default stream, synchronised before the call returns; a class whose M fails
+ * the pivot check sets MFA_DEV_NOT_SPD in the context status). Executing the plan fits every
+ * block: P = D x_1 N_x^+ x_2 N_y^+ x_3 N_z^+ (the exact least-squares solution of the
+ * Kronecker system), and optionally its RMSE over the samples in FP64 (Table 1's error
+ * metric). Requires p+1 <= C <= n per axis. */
 typedef struct mfa_encode_plan mfa_encode_plan;
 int  mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out,
                             const mfa_block_desc* h_desc, int32_t nblocks,

@@ -8,6 +8,8 @@
 //     FP32, plus the FP32 span/basis table the RMSE pass decodes with.
 //   fit: the shared three-axis contraction kernel (contract3.cu, mode kFit) applies the three
 //     pseudo-inverses to every block and sums the squared fitting error in FP64.
+// A plan sets its classes up once, when it is created; the allocation-free entry point, which has
+// no plan, sets them up on every call.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -159,13 +161,17 @@ int analyze_batch(const mfa_block_desc* h_desc, int nblocks, const float* h_knot
   return MFA_OK;
 }
 
-// Enqueues the FP64 class set-up and the fit for device-resident items/classes/pools.
-int run_fit(mfa_ctx* ctx, int nblocks, int nclasses, int maxC, int maxN, const EncItem* items,
-            const EncClass* classes, float* pinv, TabEntry* tabs, const float* data, int64_t slot_stride,
-            int64_t nslots, float* cps_out, double* rmse, cudaStream_t s, int rows32) {
+// Enqueues the FP64 class set-up (pseudo-inverses and basis tables of every class).
+int run_classes(mfa_ctx* ctx, int nclasses, const EncClass* classes, float* pinv, TabEntry* tabs, cudaStream_t s) {
   encode_class_kernel<<<nclasses, kThreads, 0, s>>>(classes, pinv, tabs, ctx->d_status);
   ctx->launches++;
-  if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+}
+
+// Enqueues the fit for device-resident items/classes/pools (the classes already set up).
+int run_fit(mfa_ctx* ctx, int nblocks, int maxC, int maxN, const EncItem* items, const EncClass* classes,
+            float* pinv, TabEntry* tabs, const float* data, int64_t slot_stride, int64_t nslots, float* cps_out,
+            double* rmse, cudaStream_t s, int rows32) {
   ContractParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.mode = kFit;
@@ -234,6 +240,12 @@ int mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out, const mfa_block_
     mfa_encode_plan_destroy(plan);
     return MFA_ERR_CUDA;
   }
+  // the classes depend only on the plan: set them up once, here
+  if (run_classes(ctx, plan->nclasses, plan->d_classes, plan->d_pinv, plan->d_tabs, 0) != MFA_OK ||
+      cudaStreamSynchronize(0) != cudaSuccess) {
+    mfa_encode_plan_destroy(plan);
+    return MFA_ERR_CUDA;
+  }
   *out = plan;
   return MFA_OK;
 }
@@ -254,8 +266,8 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
   if ((reinterpret_cast<uintptr_t>(d_data) & 3) || (reinterpret_cast<uintptr_t>(d_cps_out) & 3) ||
       (reinterpret_cast<uintptr_t>(d_rmse) & 7))
     return MFA_ERR_INVALID_ARG;
-  return run_fit(ctx, plan->nblocks, plan->nclasses, plan->maxC, plan->maxN, plan->d_items, plan->d_classes,
-                 plan->d_pinv, plan->d_tabs, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse,
+  return run_fit(ctx, plan->nblocks, plan->maxC, plan->maxN, plan->d_items, plan->d_classes, plan->d_pinv,
+                 plan->d_tabs, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse,
                  static_cast<cudaStream_t>(stream), plan->rows32);
 }
 
@@ -335,10 +347,13 @@ extern "C" int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t n
       cudaMemcpyAsync(base + o_items, an.items.data(), sizeof(EncItem) * an.items.size(), cudaMemcpyHostToDevice,
                       s) != cudaSuccess)
     return MFA_ERR_CUDA;
-  rc = run_fit(&local, nblocks, (int)an.classes.size(), an.maxC, an.maxN,
-               reinterpret_cast<const EncItem*>(base + o_items), reinterpret_cast<const EncClass*>(base + o_cls),
-               reinterpret_cast<float*>(base + o_pinv), reinterpret_cast<TabEntry*>(base + o_tabs), d_data,
-               slot_stride_voxels, nslots, d_cps_out, d_rmse, s, an.rows32);
+  rc = run_classes(&local, (int)an.classes.size(), reinterpret_cast<const EncClass*>(base + o_cls),
+                   reinterpret_cast<float*>(base + o_pinv), reinterpret_cast<TabEntry*>(base + o_tabs), s);
+  if (rc != MFA_OK) return rc;
+  rc = run_fit(&local, nblocks, an.maxC, an.maxN, reinterpret_cast<const EncItem*>(base + o_items),
+               reinterpret_cast<const EncClass*>(base + o_cls), reinterpret_cast<float*>(base + o_pinv),
+               reinterpret_cast<TabEntry*>(base + o_tabs), d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse, s,
+               an.rows32);
   if (rc != MFA_OK) return rc;
   uint32_t status = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess ||
