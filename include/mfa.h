@@ -36,6 +36,10 @@
  *     base + slot*slot_stride_voxels.
  *   - decoded cache voxel: 4 floats (f, df/du, df/dv, df/dw); gradients are with respect
  *     to the block parameters u, v, w in [0, 1] (divide by n-1 for per-voxel units).
+ *     Voxels of a slot are [z][y][x] (x fastest), or with MFA_DECODE_CUBES (blocks with even
+ *     n per axis) in 2x2x2-voxel cubes: voxel (x, y, z) at 8*(((z/2)*(n_y/2) + y/2)*(n_x/2) + x/2)
+ *     + 4*(z%2) + 2*(y%2) + x%2, so the 8 voxels of a cube (128 bytes of float4) share a cache
+ *     line; a block with an odd n sets MFA_DEV_BAD_DESC and is skipped.
  */
 #ifndef MFA_H
 #define MFA_H
@@ -73,6 +77,7 @@ extern "C" {
 /* ---- decode flags ------------------------------------------------------------------- */
 #define MFA_DECODE_VALUE_ONLY  0x1u /* write f only: 1 float per voxel instead of 4       */
 #define MFA_DECODE_LIST_SLOTS  0x2u /* with a list: item m goes to slot m (not desc.slot) */
+#define MFA_DECODE_CUBES       0x4u /* cache voxels in the cube layout (see Layouts); FP32 only */
 
 /* ---- fixed limits -------------------------------------------------------------------- */
 #define MFA_MAX_DEGREE 3
@@ -216,6 +221,7 @@ typedef struct {
 /* ---- one frame as a CUDA graph (the per-POV decode + render of Sec. 4.3, Algorithm 4) - */
 #define MFA_FRAME_SORT_BY_COST 0x1u /* order the visible list by decreasing max(C) first     */
 #define MFA_FRAME_RAYCAST      0x2u /* build the brick table and ray-cast after the decode   */
+#define MFA_FRAME_CUBES        0x4u /* decode into (and ray-cast from) the cube layout        */
 
 /* Everything a frame reads; pointers and sizes are fixed when the graph is captured. Per frame
  * the caller writes the visible block ids into d_list[0 .. *d_count) (device memory, count <=
@@ -354,6 +360,17 @@ int mfa_raycast(mfa_ctx* ctx,
                 const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
                 const mfa_view* view, const float* d_tf, int32_t tf_n,
                 float* d_image, void* stream);
+
+/* mfa_raycast with flags. MFA_RAYCAST_CUBES: the cache bricks are in the cube layout that
+ * MFA_DECODE_CUBES writes (brick_n must be even; MFA_ERR_INVALID_ARG otherwise). The image is
+ * the same, bit for bit, as mfa_raycast's over the same voxels in the [z][y][x] layout: only
+ * the addresses of the eight corner loads change. Unknown flags: MFA_ERR_INVALID_ARG. */
+#define MFA_RAYCAST_CUBES 0x1u
+int mfa_raycast_ex(mfa_ctx* ctx,
+                   const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                   const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                   const mfa_view* view, const float* d_tf, int32_t tf_n,
+                   float* d_image, uint32_t flags, void* stream);
 
 /* Algorithm 4 with per-sample queries of the micro-models instead of a decoded cache: the same rays,
  * transfer function, shading and compositing as mfa_raycast, but every sample evaluates the value

@@ -70,6 +70,13 @@ __device__ __forceinline__ bool knots_ok(const float* t, int p, int C) {
   return t[p] < t[C];
 }
 
+// Index of voxel (x, y, z) of an nx x ny x nz cache brick in the cube layout (MFA_DECODE_CUBES; even
+// n per axis): 2x2x2-voxel cubes in [z/2][y/2][x/2] order, the 8 voxels of a cube in [z&1][y&1][x&1]
+// order, so one cube of float4 voxels fills one 128-byte line.
+__device__ __forceinline__ int cube_index(int x, int y, int z, int nx, int ny) {
+  return ((((z >> 1) * (ny >> 1) + (y >> 1)) * (nx >> 1) + (x >> 1)) << 3) | ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
+}
+
 // Sample parameter u_i = i/(n-1), rounded once (IEEE division).
 __device__ __forceinline__ float sample_param(int i, int n) {
   return __fdiv_rn((float)i, (float)(n - 1));

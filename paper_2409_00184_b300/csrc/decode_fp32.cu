@@ -55,7 +55,7 @@ static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks
   return L;
 }
 
-template <int PMAX, bool VALUE_ONLY, bool COMPARE>
+template <int PMAX, bool VALUE_ONLY, bool COMPARE, bool CUBES>
 __global__ void __launch_bounds__(kDecodeThreads)
 decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
   extern __shared__ __align__(16) float sm[];
@@ -99,6 +99,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           s_g.slot = item;
         }
         if (!bad && COMPARE && (int64_t)s_g.n[0] * s_g.n[1] * s_g.n[2] > prm.data_stride) bad = MFA_DEV_BAD_RANGE;
+        if (!bad && (prm.flags & MFA_DECODE_CUBES) && ((s_g.n[0] | s_g.n[1] | s_g.n[2]) & 1)) bad = MFA_DEV_BAD_DESC;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
       }
     }
@@ -234,6 +235,13 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
           const int rows = ny * kc;
           const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
+          // cache index of row r's voxel: [z][y][x], or the cube layout
+          const int64_t sbase = (int64_t)s_g.slot * prm.slot_stride;
+          auto cidx = [&](int r) -> int64_t {
+            if (!CUBES) return base + (int64_t)r * nx;
+            const int kl = r / ny, j = r - kl * ny;
+            return sbase + cube_index(i, j, k0 + kl, nx, ny);
+          };
           const int64_t dbase = COMPARE ? (int64_t)s_g.slot * prm.data_stride + (int64_t)k0 * ny * nx + i : 0;
           // rows in chunks of kPrefetch per thread: with COMPARE the chunk's samples D are loaded before its
           // arithmetic, so the loads overlap instead of each row waiting for its own
@@ -255,7 +263,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
 #pragma unroll
                   for (int d = 0; d < Q; ++d)
                     if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
-                  __stcs(prm.cache + base + (int64_t)r * nx, f);
+                  __stcs(prm.cache + cidx(r), f);
                 } else {
                   const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
                   float fu = 0.f, fv = 0.f, fw = 0.f;
@@ -269,7 +277,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
                       fw = fmaf(uv.z, Nx[d], fw);
                     }
                   }
-                  __stcs(reinterpret_cast<float4*>(prm.cache) + base + (int64_t)r * nx,
+                  __stcs(reinterpret_cast<float4*>(prm.cache) + cidx(r),
                          make_float4(f, fu, fv, fw));
                 }
                 compare_sample(prm, dbase + (int64_t)r * nx, f - dpre[q], ksum, kcomp);
@@ -282,11 +290,11 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
 #pragma unroll
               for (int d = 0; d < Q; ++d)
                 if (d <= px) f = fmaf(U[r * Cx + d], Nx[d], f);
-              __stcs(prm.cache + base + (int64_t)r * nx, f);
+              __stcs(prm.cache + cidx(r), f);
             }
           } else {
             const float4* U = reinterpret_cast<const float4*>(sm + L.U) + ox;
-            float4* out = reinterpret_cast<float4*>(prm.cache) + base;
+            float4* out = reinterpret_cast<float4*>(prm.cache);
             for (int r = r0; r < rows; r += rows_per_pass) {
               float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
 #pragma unroll
@@ -299,7 +307,7 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
                   fw = fmaf(uv.z, Nx[d], fw);
                 }
               }
-              __stcs(out + (int64_t)r * nx, make_float4(f, fu, fv, fw));
+              __stcs(out + cidx(r), make_float4(f, fu, fv, fw));
             }
           }
         }
@@ -351,7 +359,9 @@ __global__ void rmse_finish_kernel(DecodeParams prm, int max_items) {
 template <int PMAX, bool VO>
 static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const DecodeSmem& L, int ctas_per_sm,
                               cudaStream_t stream) {
-  auto kern = prm.data ? decode_fp32_kernel<PMAX, VO, true> : decode_fp32_kernel<PMAX, VO, false>;
+  const bool cubes = (prm.flags & MFA_DECODE_CUBES) != 0;
+  auto kern = prm.data ? (cubes ? decode_fp32_kernel<PMAX, VO, true, true> : decode_fp32_kernel<PMAX, VO, true, false>)
+                       : (cubes ? decode_fp32_kernel<PMAX, VO, false, true> : decode_fp32_kernel<PMAX, VO, false, false>);
   const size_t smem = (size_t)L.total * 4;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

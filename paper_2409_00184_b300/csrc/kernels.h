@@ -74,6 +74,7 @@ struct RaycastParams {
   float gscale[3];     // (N_a - 1)/(2 (brick_n - 1)): parametric -> world gradient scale
   float step_voxels, opacity_max, ka, kd, ks, shininess, vmin, vmax;
   unsigned long long* samples;  // marched samples are added here (one atomic per warp)
+  bool cubes = false;           // cache bricks in the cube layout (MFA_RAYCAST_CUBES)
 };
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream);

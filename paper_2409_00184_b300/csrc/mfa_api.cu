@@ -149,9 +149,10 @@ int decode_entry(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, co
   if (!ctx || !bounds_ok(bounds)) return MFA_ERR_INVALID_ARG;
   if (nblocks < 0 || list_len < 0 || knots_len < 0 || cps_len < 0 || slot_stride_voxels < 1 || nslots < 0)
     return MFA_ERR_INVALID_ARG;
-  if (flags & ~(MFA_DECODE_VALUE_ONLY | MFA_DECODE_LIST_SLOTS)) return MFA_ERR_INVALID_ARG;
+  if (flags & ~(MFA_DECODE_VALUE_ONLY | MFA_DECODE_LIST_SLOTS | MFA_DECODE_CUBES)) return MFA_ERR_INVALID_ARG;
   if ((flags & MFA_DECODE_LIST_SLOTS) && !d_list) return MFA_ERR_INVALID_ARG;
   if (precision < MFA_PREC_FP32 || precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_DECODE_CUBES) && precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
   const int items = d_list ? list_len : nblocks;
   if (items == 0 && !d_count) return MFA_OK;
   if (!d_desc || !d_knots || !d_cps || !d_cache || nblocks == 0) return MFA_ERR_INVALID_ARG;
@@ -325,7 +326,16 @@ extern "C" {
 int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
                 const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
                 const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
+  return mfa_raycast_ex(ctx, d_cache, slot_stride_voxels, nslots, d_brick_table, brick_dims, brick_n, view, d_tf,
+                        tf_n, d_image, 0u, stream);
+}
+
+int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                   const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
+                   const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, uint32_t flags,
+                   void* stream) {
   if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
+  if ((flags & ~MFA_RAYCAST_CUBES) || ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1))) return MFA_ERR_INVALID_ARG;
   if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
     return MFA_ERR_INVALID_ARG;
   if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
@@ -343,6 +353,7 @@ int mfa_raycast(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxels, 
   prm.tf_n = tf_n;
   prm.image = reinterpret_cast<float4*>(d_image);
   prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
+  prm.cubes = (flags & MFA_RAYCAST_CUBES) != 0;
   return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
 }
 

@@ -101,10 +101,17 @@ __device__ __forceinline__ float4 trilinear(const float4 (&c)[2][2][2], float wx
                lerp4(lerp4(c[1][0][0], c[1][0][1], wx), lerp4(c[1][1][0], c[1][1][1], wx), wy), wz);
 }
 
+// Index of brick-local voxel (x, y, z) in its slot: [z][y][x], or the cube layout.
+__device__ __forceinline__ int brick_voxel(bool cubes, int n, int x, int y, int z) {
+  return cubes ? cube_index(x, y, z, n, n) : (z * n + y) * n + x;
+}
+
 // The eight corners of the cell at voxel (ix, iy, iz) when it spans two bricks on some axis (or the
 // brick size is not a power of two): one table lookup per corner.
+template <int LAYOUT>  // 0: [z][y][x], 1: cubes, -1: as prm.cubes says
 __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n, int ix, int iy, int iz,
                                                 float4 (&c)[2][2][2]) {
+  const bool cubes = LAYOUT < 0 ? prm.cubes : LAYOUT == 1;
   const int bx0 = ix / n, by0 = iy / n, bz0 = iz / n;
   const int lx0 = ix - bx0 * n, ly0 = iy - by0 * n, lz0 = iz - bz0 * n;
 #pragma unroll
@@ -118,7 +125,8 @@ __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n,
         const int lx = ox ? 0 : lx0 + dx, ly = oy ? 0 : ly0 + dy, lz = oz ? 0 : lz0 + dz;
         const int slot = __ldg(prm.table + (bz * prm.B[1] + by) * prm.B[0] + bx);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (slot >= 0 && slot < prm.nslots) v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + (lz * n + ly) * n + lx);
+        if (slot >= 0 && slot < prm.nslots)
+          v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + brick_voxel(cubes, n, lx, ly, lz));
         c[dz][dy][dx] = v;
       }
 }
@@ -157,15 +165,17 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
       if (lx0 < n - 1 && ly0 < n - 1 && lz0 < n - 1) {
         const int slot = __ldg(prm.table + (bz0 * prm.B[1] + by0) * prm.B[0] + bx0);
         if (slot >= 0 && slot < prm.nslots) {
-          const float4* base = prm.cache + (int64_t)slot * prm.slot_stride + (lz0 * n + ly0) * n + lx0;
+          const float4* sb = prm.cache + (int64_t)slot * prm.slot_stride;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(base + (e >> 2) * n2 + ((e >> 1) & 1) * n + (e & 1));
+          for (int e = 0; e < 8; ++e)
+            c[e >> 2][(e >> 1) & 1][e & 1] =
+                __ldg(sb + brick_voxel(prm.cubes, n, lx0 + (e & 1), ly0 + ((e >> 1) & 1), lz0 + (e >> 2)));
         } else {
 #pragma unroll
           for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       } else {
-        corners_general(prm, n, ix, iy, iz, c);
+        corners_general<-1>(prm, n, ix, iy, iz, c);
       }
       const float4 s = trilinear(c, gx - (float)ix, gy - (float)iy, gz - (float)iz);
       marched = k + 1;
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
   count_marched(prm, (unsigned long long)marched, tid & 31);
 }
 
-template <int L>
+template <int L, bool CUBES>
 __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(RaycastParams prm, uint32_t* counter) {
   constexpr int n = 1 << L, n2 = n * n;
   extern __shared__ float4 s_tf[];  // tf_n entries
@@ -232,7 +242,18 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
       while (k < K) {
         float4 c[2][2][2];
         if (slot == -2) {
-          corners_general(prm, n, ix, iy, iz, c);
+          corners_general<CUBES ? 1 : 0>(prm, n, ix, iy, iz, c);
+        } else if (slot >= 0 && slot < prm.nslots && CUBES) {
+          // cube layout: the two x, y and z corner planes of the cell
+          const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
+          const int ox[2] = {((lx >> 1) << 3) + (lx & 1), (((lx + 1) >> 1) << 3) + ((lx + 1) & 1)};
+          const int oy[2] = {((ly >> 1) << (L + 2)) + ((ly & 1) << 1), (((ly + 1) >> 1) << (L + 2)) + (((ly + 1) & 1) << 1)};
+          const int oz[2] = {((lz >> 1) << (2 * L + 1)) + ((lz & 1) << 2),
+                             (((lz + 1) >> 1) << (2 * L + 1)) + (((lz + 1) & 1) << 2)};
+          const float4* sb = prm.cache + (int64_t)slot * prm.slot_stride;
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(sb + oz[e >> 2] + oy[(e >> 1) & 1] + ox[e & 1]);
         } else if (slot >= 0 && slot < prm.nslots) {
           const float4* base = prm.cache + (int64_t)slot * prm.slot_stride +
                                ((((iz & (n - 1)) << L) + (iy & (n - 1))) << L) + (ix & (n - 1));
@@ -258,12 +279,13 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
 template <int L>
 int launch_queue(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {
   const size_t smem = (size_t)prm.tf_n * sizeof(float4);
+  auto kern = prm.cubes ? raycast_queue_kernel<L, true> : raycast_queue_kernel<L, false>;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_queue_kernel<L>, kQueueThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQueueThreads, smem) != cudaSuccess)
     return MFA_ERR_CUDA;
   uint32_t* counter = ctx->d_counters + kRaycastQueue;
   if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
-  raycast_queue_kernel<L><<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, counter);
+  kern<<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, counter);
   return MFA_OK;
 }
 

@@ -17,7 +17,8 @@ OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVICE, ERR_IO = -1, -2, -3, -4, -5, -6, -7
 DEV_BAD_DESC, DEV_BAD_KNOTS, DEV_BAD_RANGE, DEV_BAD_LIST, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4, 8, 16, 32
 PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
-DECODE_VALUE_ONLY, DECODE_LIST_SLOTS = 1, 2
+DECODE_VALUE_ONLY, DECODE_LIST_SLOTS, DECODE_CUBES = 1, 2, 4
+RAYCAST_CUBES = 1
 MAX_DEGREE, MAX_NCP, MAX_NSAMP = 3, 32, 64
 
 
@@ -52,7 +53,7 @@ class FrameDesc(ctypes.Structure):
                 ("tf_n", ctypes.c_int32), ("d_image", ctypes.c_void_p)]
 
 
-FRAME_SORT_BY_COST, FRAME_RAYCAST = 1, 2
+FRAME_SORT_BY_COST, FRAME_RAYCAST, FRAME_CUBES = 1, 2, 4
 
 DESC_DTYPE = np.dtype({"names": ["degree", "ncp", "nsamp", "slot", "knot_off", "cp_off"],
                        "formats": [("<i4", 3), ("<i4", 3), ("<i4", 3), "<i4", ("<i8", 3), "<i8"],
@@ -66,7 +67,8 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_frame_graph_create", "mfa_frame_graph_launch", "mfa_frame_graph_destroy",
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
            "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
-           "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop"]
+           "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop",
+           "mfa_raycast_ex"]
 
 
 def _load():
@@ -114,6 +116,8 @@ def _load():
         "mfa_ctx_read_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int, P]),
         "mfa_raycast": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
                                        ctypes.POINTER(View), P, I32, P, P]),
+        "mfa_raycast_ex": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
+                                          ctypes.POINTER(View), P, I32, P, ctypes.c_uint32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -492,15 +496,22 @@ def raycast_direct(ctx, blocks, table, brick_n, view, tf, image, cps=None, strea
            "mfa_raycast_direct")
 
 
-def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None):
-    """mfa_raycast: table is an int32 (Bz, By, Bx) CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
+def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None, cubes=False):
+    """mfa_raycast (mfa_raycast_ex with MFA_RAYCAST_CUBES when `cubes`): table is an int32 (Bz, By, Bx)
+    CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
     Bz, By, Bx = table.shape
     _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
     _need(cache, nslots * slot_stride * 4, "cache")
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
     vw = make_view(view)
-    _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims), brick_n,
-                           ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)), "mfa_raycast")
+    if cubes:
+        _check(lib.mfa_raycast_ex(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
+                                  brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), RAYCAST_CUBES,
+                                  _stream(stream)), "mfa_raycast_ex")
+    else:
+        _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
+                               brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+               "mfa_raycast")
 
 
 class FrameGraph:
@@ -509,12 +520,12 @@ class FrameGraph:
     (device int32 tensors) before each launch()."""
 
     def __init__(self, ctx, blocks, list_buf, count_buf, cache, slot_stride, sort=True,
-                 table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None):
+                 table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None, cubes=False):
         self.ctx = ctx
         self._keep = [blocks, list_buf, count_buf, cache, table, tf, image]
         cap = list_buf.numel()
         _need(cache, cap * slot_stride * 4, "cache")
-        flags = FRAME_SORT_BY_COST if sort else 0
+        flags = (FRAME_SORT_BY_COST if sort else 0) | (FRAME_CUBES if cubes else 0)
         self._view = None
         fd = FrameDesc()
         fd.d_desc, fd.nblocks = _ptr(blocks.desc), blocks.n
