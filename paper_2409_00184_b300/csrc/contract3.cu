@@ -945,13 +945,15 @@ __device__ void zf_setup(const ContractParams& prm, const int* A, float* kn, flo
 }
 
 // z stage over the kc planes of one slab (rows of 32 in the 128-byte-swizzled layout): thread t of
-// the z group owns samples i = 4(t & 7) .. +3 of row j = t >> 3 in every plane.
+// the z group owns samples i = 4(t & 7) .. +3 of row j = t >> 3 in every plane. The FMAs run as packed
+// float2 pairs (two round-to-nearest FMAs per instruction; the same results as scalar fmaf).
 template <int CP>
-__device__ __forceinline__ void zf_stage_z(const float4* buf, const float* Az, int k0, int kc, float (&acc)[CP][4]) {
+__device__ __forceinline__ void zf_stage_z(const float4* buf, const float* Az, int k0, int kc, float2 (&acc)[CP][2]) {
   const int j = threadIdx.x >> 3, ch = threadIdx.x & 7;
 #pragma unroll 2
   for (int kl = 0; kl < kc; ++kl) {
     const float4 v = buf[(kl * 32 + j) * 8 + (ch ^ (j & 7))];
+    const float2 vlo = make_float2(v.x, v.y), vhi = make_float2(v.z, v.w);
     const float4* w4 = reinterpret_cast<const float4*>(Az + (k0 + kl) * CP);
 #pragma unroll
     for (int c4 = 0; c4 < CP / 4; ++c4) {
@@ -959,11 +961,9 @@ __device__ __forceinline__ void zf_stage_z(const float4* buf, const float* Az, i
       const float ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float* a = acc[4 * c4 + q];
-        a[0] = fmaf(ws[q], v.x, a[0]);
-        a[1] = fmaf(ws[q], v.y, a[1]);
-        a[2] = fmaf(ws[q], v.z, a[2]);
-        a[3] = fmaf(ws[q], v.w, a[3]);
+        const float2 ww = make_float2(ws[q], ws[q]);
+        acc[4 * c4 + q][0] = __ffma2_rn(ww, vlo, acc[4 * c4 + q][0]);
+        acc[4 * c4 + q][1] = __ffma2_rn(ww, vhi, acc[4 * c4 + q][1]);
       }
     }
   }
@@ -972,15 +972,14 @@ __device__ __forceinline__ void zf_stage_z(const float4* buf, const float* Az, i
 // y stage: columns e = t and t + 256 of T (c = e >> 5, i = e & 31) in one pass over j; the results
 // stay in registers until the group has read all of T, then overwrite it as U.
 template <int CP>
-__device__ __forceinline__ void zf_y_fma(float (&acc)[CP], const float* Ay, int j, float v) {
+__device__ __forceinline__ void zf_y_fma(float2 (&acc)[CP / 2], const float* Ay, int j, float v) {
   const float4* w4 = reinterpret_cast<const float4*>(Ay + j * CP);
+  const float2 vv = make_float2(v, v);
 #pragma unroll
   for (int b4 = 0; b4 < CP / 4; ++b4) {
     const float4 w = w4[b4];
-    acc[4 * b4 + 0] = fmaf(w.x, v, acc[4 * b4 + 0]);
-    acc[4 * b4 + 1] = fmaf(w.y, v, acc[4 * b4 + 1]);
-    acc[4 * b4 + 2] = fmaf(w.z, v, acc[4 * b4 + 2]);
-    acc[4 * b4 + 3] = fmaf(w.w, v, acc[4 * b4 + 3]);
+    acc[2 * b4 + 0] = __ffma2_rn(make_float2(w.x, w.y), vv, acc[2 * b4 + 0]);
+    acc[2 * b4 + 1] = __ffma2_rn(make_float2(w.z, w.w), vv, acc[2 * b4 + 1]);
   }
 }
 
@@ -988,9 +987,9 @@ template <int CP>
 __device__ void zf_stage_y(const float* T, const float* Ay, float* U, int Cy, int Cz, int ny, int t) {
   const int e0 = t, e1 = t + kZfGroup;
   const bool h0 = e0 < Cz * 32, h1 = e1 < Cz * 32;  // uniform across a warp (Cz * 32 is a multiple of 32)
-  float a0[CP], a1[CP];
+  float2 a0[CP / 2], a1[CP / 2];
 #pragma unroll
-  for (int b = 0; b < CP; ++b) a0[b] = a1[b] = 0.f;
+  for (int b = 0; b < CP / 2; ++b) a0[b] = a1[b] = make_float2(0.f, 0.f);
   const float* t0 = T + (e0 >> 5) * kZfPlane + (e0 & 31);
   const float* t1 = T + (e1 >> 5) * kZfPlane + (e1 & 31);
   if (h1) {
@@ -1008,35 +1007,24 @@ __device__ void zf_stage_y(const float* T, const float* Ay, float* U, int Cy, in
 #pragma unroll
   for (int b = 0; b < CP; ++b)
     if (b < Cy) {
-      if (h0) U[((e0 >> 5) * Cy + b) * 33 + (e0 & 31)] = a0[b];
-      if (h1) U[((e1 >> 5) * Cy + b) * 33 + (e1 & 31)] = a1[b];
+      if (h0) U[((e0 >> 5) * Cy + b) * 33 + (e0 & 31)] = (b & 1) ? a0[b >> 1].y : a0[b >> 1].x;
+      if (h1) U[((e1 >> 5) * Cy + b) * 33 + (e1 & 31)] = (b & 1) ? a1[b >> 1].y : a1[b >> 1].x;
     }
 }
 
 template <int CP>
 __device__ void zf_stage_x(const float* U, const float* Ax, float* out, int Cx, int Cy, int Cz, int nx, int t) {
   for (int q = t; q < Cz * Cy; q += kZfGroup) {
-    float acc[CP];
+    float2 acc[CP / 2];
 #pragma unroll
-    for (int a = 0; a < CP; ++a) acc[a] = 0.f;
+    for (int a = 0; a < CP / 2; ++a) acc[a] = make_float2(0.f, 0.f);
     const float* ur = U + q * 33;
 #pragma unroll 4
-    for (int i = 0; i < nx; ++i) {
-      const float v = ur[i];
-      const float4* w4 = reinterpret_cast<const float4*>(Ax + i * CP);
-#pragma unroll
-      for (int a4 = 0; a4 < CP / 4; ++a4) {
-        const float4 w = w4[a4];
-        acc[4 * a4 + 0] = fmaf(w.x, v, acc[4 * a4 + 0]);
-        acc[4 * a4 + 1] = fmaf(w.y, v, acc[4 * a4 + 1]);
-        acc[4 * a4 + 2] = fmaf(w.z, v, acc[4 * a4 + 2]);
-        acc[4 * a4 + 3] = fmaf(w.w, v, acc[4 * a4 + 3]);
-      }
-    }
+    for (int i = 0; i < nx; ++i) zf_y_fma<CP>(acc, Ax, i, ur[i]);
     float* o = out + (int64_t)q * Cx;
 #pragma unroll
     for (int a = 0; a < CP; ++a)
-      if (a < Cx) o[a] = acc[a];
+      if (a < Cx) o[a] = (a & 1) ? acc[a >> 1].y : acc[a >> 1].x;
   }
 }
 
@@ -1120,9 +1108,9 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
         return !group_any(kBarZ, !mbar_wait_bounded(&s_tfree, (n - 1) & 1));
       };
       if (!tmab && nz > 0 && !take_t()) { fail(); return; }
-      float acc[CP][4];
+      float2 acc[CP][2];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+      for (int c = 0; c < CP; ++c) acc[c][0] = acc[c][1] = make_float2(0.f, 0.f);
       const int step = tmab ? ks : min(ks, CP);  // a hand-filled slab must fit T (CP planes)
       for (int k0 = 0; k0 < nz; k0 += step) {
         const int kc = min(step, nz - k0);
@@ -1154,7 +1142,8 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
 #pragma unroll
         for (int c = 0; c < CP; ++c)
           if (c < g.C[2])
-            *reinterpret_cast<float4*>(T + c * kZfPlane + j * 32 + i0) = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+            *reinterpret_cast<float4*>(T + c * kZfPlane + j * 32 + i0) =
+                make_float4(acc[c][0].x, acc[c][0].y, acc[c][1].x, acc[c][1].y);
       }
       mbar_arrive(&s_tfull);  // every thread of the group: T holds block n's z stage
     }
