@@ -33,8 +33,13 @@ constexpr int kQueueThreads = 256;
 constexpr int kTileW = 4, kTileH = 8;  // pixels of one warp tile
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
-  return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
-                     fmaf(w, b.w - a.w, a.w));
+  // a + w (b - a) per channel, as packed float2 pairs (the same roundings as the scalar form)
+  const float2 ww = make_float2(w, w);
+  const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+  const float2 d0 = __fadd2_rn(make_float2(b.x, b.y), make_float2(-a.x, -a.y));
+  const float2 d1 = __fadd2_rn(make_float2(b.z, b.w), make_float2(-a.z, -a.w));
+  const float2 r0 = __ffma2_rn(ww, d0, a0), r1 = __ffma2_rn(ww, d1, a1);
+  return make_float4(r0.x, r0.y, r1.x, r1.y);
 }
 
 // FP32 ray set-up of pixel (px, py): unit direction d and entry distance t0; returns the number of
