@@ -42,7 +42,7 @@ WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degr
             "256-entry TF) + adjoint of the residual")
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by the
 # sha256 of the kernel source it was taken on; reported as null once the source changes.
-TRAFFIC = {"raycast": {"bytes": 395.28e6 + 17.12e6, "src_sha": "4ca865434f77119e"}}
+TRAFFIC = {"raycast": {"bytes": 395.19e6 + 17.23e6, "src_sha": "ccfac4a6e15beb36"}}
 # FP32 operations per ray-cast sample in the algorithm (FMA = 2): sample position 14, trilinear
 # interpolation of 4 channels 87, transfer function 18, headlight shading 20, compositing 15.
 RAY_FLOPS_PER_SAMPLE = 154
