@@ -861,8 +861,9 @@ contract3_tma_kernel(ContractParams prm, C3Smem L, int ks, int box_rows, const _
 // use), zero-padded, instead of loaded by TMA; the zero rows of A make the padding contribute nothing.
 constexpr int kZfPlane = 1024;   // samples of a 32 x 32 plane
 constexpr int kZfMaxRing = 16;
-constexpr int kZfGroup = 256;    // threads per warp group
-constexpr int kZfThreads = 2 * kZfGroup;
+constexpr int kZfGroup = 256;    // z group: 8 consumer warps
+constexpr int kZfYx = 224;       // y/x group: 7 warps
+constexpr int kZfThreads = kZfGroup + 32 + kZfYx;  // + the producer warp: 512 threads
 constexpr int kBarZ = 1, kBarYX = 2;  // named barriers of the two groups
 
 constexpr int kZfSets = 4;  // set-up buffers (geometry, A, knots)
@@ -879,7 +880,7 @@ ZfSmem zf_layout(int mode, int CP, int ks, int R) {
   for (int p = 0; p < kZfSets; ++p) { L.knots[p] = o; if (mode != kFit) o += 3 * kKnotMax; }
   o = round4(o);
   L.T = o; o += CP * kZfPlane;
-  L.U = L.T;  // U overwrites T once the y stage has read all of it
+  L.U = o; o += round4(CP * CP * 33);
   L.ring = o; o += 252 + R * ks * kZfPlane;  // slack for 1024-byte alignment
   L.ks = ks;
   L.R = R;
@@ -887,12 +888,12 @@ ZfSmem zf_layout(int mode, int CP, int ks, int R) {
   return L;
 }
 
-__device__ __forceinline__ void group_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kZfGroup) : "memory");
+__device__ __forceinline__ void group_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // true in every thread of the group if `pred` holds in any of them
-__device__ __forceinline__ bool group_any(int id, bool pred) {
+__device__ __forceinline__ bool group_any(int id, int count, bool pred) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred q, o;\n\t"
@@ -900,7 +901,7 @@ __device__ __forceinline__ bool group_any(int id, bool pred) {
       "bar.red.or.pred o, %2, %3, q;\n\t"
       "selp.u32 %0, 1, 0, o;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)pred), "r"(id), "r"(kZfGroup)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
       : "memory");
   return r != 0;
 }
@@ -911,15 +912,15 @@ __device__ __forceinline__ bool group_any(int id, bool pred) {
 template <int CP, int MODE>
 __device__ void zf_setup(const ContractParams& prm, const int* A, float* kn, float* sm, const C3Geom& g, int t,
                          int* s_bad) {
-  for (int e = t; e < 3 * 32 * CP; e += kZfGroup) sm[A[0] + e] = 0.f;
+  for (int e = t; e < 3 * 32 * CP; e += kZfYx) sm[A[0] + e] = 0.f;
   if (MODE != kFit)
     for (int a = 0; a < 3; ++a)
-      for (int i = t; i < g.C[a] + g.p[a] + 1; i += kZfGroup) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
-  group_sync(kBarYX);
+      for (int i = t; i < g.C[a] + g.p[a] + 1; i += kZfYx) kn[a * kKnotMax + i] = prm.knots[g.koff[a] + i];
+  group_sync(kBarYX, kZfYx);
   if (MODE == kFit) {
     for (int a = 0; a < 3; ++a) {
       const EncClass& c = prm.classes[g.cls[a]];
-      for (int e = t; e < c.n * c.C; e += kZfGroup) {
+      for (int e = t; e < c.n * c.C; e += kZfYx) {
         const int i = e / c.C, col = e - i * c.C;
         sm[A[a] + i * CP + col] = prm.pinv[c.pinv_off + e];
       }
@@ -941,7 +942,7 @@ __device__ void zf_setup(const ContractParams& prm, const int* A, float* kn, flo
       for (int r = 0; r <= g.p[a]; ++r) sm[A[a] + i * CP + s - g.p[a] + r] = N[r];
     }
   }
-  group_sync(kBarYX);
+  group_sync(kBarYX, kZfYx);
 }
 
 // z stage over the kc planes of one slab (rows of 32 in the 128-byte-swizzled layout): thread t of
@@ -985,36 +986,39 @@ __device__ __forceinline__ void zf_y_fma(float2 (&acc)[CP / 2], const float* Ay,
 
 template <int CP>
 __device__ void zf_stage_y(const float* T, const float* Ay, float* U, int Cy, int Cz, int ny, int t) {
-  const int e0 = t, e1 = t + kZfGroup;
-  const bool h0 = e0 < Cz * 32, h1 = e1 < Cz * 32;  // uniform across a warp (Cz * 32 is a multiple of 32)
-  float2 a0[CP / 2], a1[CP / 2];
+  // columns e (c = e >> 5, i = e & 31) in pairs e, e + kZfYx sharing the loads of Ay; a pair's second
+  // column exists or not for a whole warp (Cz * 32 is a multiple of 32)
+  for (int e0 = t; e0 < Cz * 32; e0 += 2 * kZfYx) {
+    const int e1 = e0 + kZfYx;
+    const bool h1 = e1 < Cz * 32;
+    float2 a0[CP / 2], a1[CP / 2];
 #pragma unroll
-  for (int b = 0; b < CP / 2; ++b) a0[b] = a1[b] = make_float2(0.f, 0.f);
-  const float* t0 = T + (e0 >> 5) * kZfPlane + (e0 & 31);
-  const float* t1 = T + (e1 >> 5) * kZfPlane + (e1 & 31);
-  if (h1) {
+    for (int b = 0; b < CP / 2; ++b) a0[b] = a1[b] = make_float2(0.f, 0.f);
+    const float* t0 = T + (e0 >> 5) * kZfPlane + (e0 & 31);
+    const float* t1 = T + (e1 >> 5) * kZfPlane + (e1 & 31);
+    if (h1) {
 #pragma unroll 2
-    for (int j = 0; j < ny; ++j) {
-      const float v0 = t0[j * 32], v1 = t1[j * 32];
-      zf_y_fma<CP>(a0, Ay, j, v0);
-      zf_y_fma<CP>(a1, Ay, j, v1);
-    }
-  } else if (h0) {
+      for (int j = 0; j < ny; ++j) {
+        const float v0 = t0[j * 32], v1 = t1[j * 32];
+        zf_y_fma<CP>(a0, Ay, j, v0);
+        zf_y_fma<CP>(a1, Ay, j, v1);
+      }
+    } else {
 #pragma unroll 4
-    for (int j = 0; j < ny; ++j) zf_y_fma<CP>(a0, Ay, j, t0[j * 32]);
-  }
-  group_sync(kBarYX);  // all of T has been read
-#pragma unroll
-  for (int b = 0; b < CP; ++b)
-    if (b < Cy) {
-      if (h0) U[((e0 >> 5) * Cy + b) * 33 + (e0 & 31)] = (b & 1) ? a0[b >> 1].y : a0[b >> 1].x;
-      if (h1) U[((e1 >> 5) * Cy + b) * 33 + (e1 & 31)] = (b & 1) ? a1[b >> 1].y : a1[b >> 1].x;
+      for (int j = 0; j < ny; ++j) zf_y_fma<CP>(a0, Ay, j, t0[j * 32]);
     }
+#pragma unroll
+    for (int b = 0; b < CP; ++b)
+      if (b < Cy) {
+        U[((e0 >> 5) * Cy + b) * 33 + (e0 & 31)] = (b & 1) ? a0[b >> 1].y : a0[b >> 1].x;
+        if (h1) U[((e1 >> 5) * Cy + b) * 33 + (e1 & 31)] = (b & 1) ? a1[b >> 1].y : a1[b >> 1].x;
+      }
+  }
 }
 
 template <int CP>
 __device__ void zf_stage_x(const float* U, const float* Ax, float* out, int Cx, int Cy, int Cz, int nx, int t) {
-  for (int q = t; q < Cz * Cy; q += kZfGroup) {
+  for (int q = t; q < Cz * Cy; q += kZfYx) {
     float2 acc[CP / 2];
 #pragma unroll
     for (int a = 0; a < CP / 2; ++a) acc[a] = make_float2(0.f, 0.f);
@@ -1032,10 +1036,11 @@ template <int CP, int MODE>
 __global__ void __launch_bounds__(kZfThreads, 1)
 contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtensorMap xmap) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ __align__(8) uint64_t s_full[kZfMaxRing];
+  __shared__ __align__(8) uint64_t s_full[kZfMaxRing], s_empty[kZfMaxRing];
   __shared__ __align__(8) uint64_t s_tfull, s_tfree, s_ready[kZfSets];
   __shared__ C3Geom s_g[kZfSets], s_built[kZfSets];  // geometry of the buffer's block / of its A matrices
   __shared__ int s_bad[kZfSets], s_rebuild[kZfSets], s_has[kZfSets];
+  __shared__ int s_zabort;  // a z warp gave up waiting for a slab
   const int tid = threadIdx.x;
   const int R = L.R, ks = L.ks;
   float4* ring = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(sm + L.ring) + 1023) & ~uintptr_t(1023));
@@ -1044,54 +1049,32 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
   auto tma_block = [](const C3Geom& g) { return g.valid && !g.bad && g.n[0] == 32 && g.n[1] == 32; };
 
   if (tid == 0) {
-    for (int r = 0; r < R; ++r) mbar_init(&s_full[r], 1);
+    for (int r = 0; r < R; ++r) {
+      mbar_init(&s_full[r], 1);
+      mbar_init(&s_empty[r], kZfGroup / 32);  // one arrival per z warp
+    }
     mbar_init(&s_tfull, kZfGroup);
     mbar_init(&s_tfree, 1);
     for (int p = 0; p < kZfSets; ++p) {
       mbar_init(&s_ready[p], 1);
       s_has[p] = 0;
     }
+    s_zabort = 0;
     fence_mbar_init();
   }
-  __syncthreads();  // the last CTA-wide barrier: from here on each group synchronises on its own
+  __syncthreads();  // the last CTA-wide barrier: from here on each role synchronises on its own
 
   if (tid < kZfGroup) {
-    // ------------------------------ z group ------------------------------
-    const int64_t rows_per_slot = prm.slot_stride / 32;
-    // producer (thread 0): the next slab to issue is slab p_slab of the CTA's block number p_n
-    int p_n = 0, p_slab = 0;
-    uint32_t issued = 0, consumed = 0;  // `consumed` is the same in every thread of the group
-    // Fill the ring up to R slabs ahead, into block n + 1 at most (its set-up, published on s_ready,
-    // gives the geometry; it cannot be overwritten before the group has finished block n + 1).
-    auto produce = [&](int n) {
-      while (issued < consumed + (uint32_t)R && p_n <= n + 1) {
-        const int pp = p_n % kZfSets;
-        if (!mbar_test_wait(&s_ready[pp], (p_n / kZfSets) & 1)) break;
-        const C3Geom& pg = s_g[pp];
-        if (!pg.valid) break;
-        if (tma_block(pg) && p_slab * ks < pg.n[2]) {
-          const uint32_t slot = issued % R;
-          mbar_arrive_expect_tx(&s_full[slot], slab_bytes);
-          const int64_t row = (int64_t)pg.slot * rows_per_slot + (int64_t)p_slab * ks * 32;
-          tma_load_2d(ring + slot * slab_f4, &xmap, &s_full[slot], 0, (int)row);
-          ++issued;
-          if (++p_slab * ks < pg.n[2]) continue;
-        }
-        ++p_n;
-        p_slab = 0;
-      }
-    };
-    auto fail = [&]() {  // a wait gave up: report, let this group's copies land, leave
-      if (tid == 0) {
-        flag(prm.status, MFA_DEV_TIMEOUT);
-        for (uint32_t q = consumed; q < issued; ++q) mbar_wait_bounded(&s_full[q % R], (q / R) & 1);
-      }
+    // ------------------------------ z group (consumers) ------------------------------
+    const int lane = tid & 31;
+    uint32_t consumed = 0;  // the same sequence in every warp of the group
+    auto fail = [&]() {
+      if (tid == 0) flag(prm.status, MFA_DEV_TIMEOUT);
     };
     for (int n = 0;; ++n) {
       const int p = n % kZfSets;
       // set-up of block n (geometry, A)
-      if (group_any(kBarZ, !mbar_wait_bounded(&s_ready[p], (n / kZfSets) & 1))) { fail(); return; }
-      if (tid == 0) produce(n);
+      if (group_any(kBarZ, kZfGroup, !mbar_wait_bounded(&s_ready[p], (n / kZfSets) & 1))) { fail(); return; }
       const C3Geom g = s_g[p];
       if (!g.valid) break;
       const bool skip = g.bad || s_bad[p];
@@ -1105,36 +1088,42 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
       auto take_t = [&]() {
         if (own_t) return true;
         own_t = true;
-        return !group_any(kBarZ, !mbar_wait_bounded(&s_tfree, (n - 1) & 1));
+        return !group_any(kBarZ, kZfGroup, !mbar_wait_bounded(&s_tfree, (n - 1) & 1));
       };
       if (!tmab && nz > 0 && !take_t()) { fail(); return; }
       float2 acc[CP][2];
 #pragma unroll
       for (int c = 0; c < CP; ++c) acc[c][0] = acc[c][1] = make_float2(0.f, 0.f);
-      const int step = tmab ? ks : min(ks, CP);  // a hand-filled slab must fit T (CP planes)
-      for (int k0 = 0; k0 < nz; k0 += step) {
-        const int kc = min(step, nz - k0);
-        const float4* buf;
-        if (tmab) {
-          if (tid == 0) produce(n);
+      if (tmab) {
+        // each warp consumes the ring at its own pace and hands every slab back on its empty barrier
+        for (int k0 = 0; k0 < nz; k0 += ks) {
           const uint32_t slot = consumed % R;
-          const bool got = mbar_wait_bounded(&s_full[slot], (consumed / R) & 1);
+          const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&s_full[slot], (consumed / R) & 1));
           ++consumed;
-          if (group_any(kBarZ, !got)) { fail(); return; }
-          buf = ring + slot * slab_f4;
-        } else {
-          const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
-          const int nx = g.n[0], ny = g.n[1];
+          if (!got) {  // the block's remaining slabs are abandoned; the group leaves below
+            if (lane == 0) atomicExch(&s_zabort, 1);
+            break;
+          }
+          if (!skip) zf_stage_z<CP>(ring + slot * slab_f4, Az, k0, min(ks, nz - k0), acc);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&s_empty[slot]);
+        }
+        if (group_any(kBarZ, kZfGroup, s_zabort != 0)) { fail(); return; }
+      } else {
+        const int step = min(ks, CP);  // a hand-filled slab must fit T (CP planes)
+        const float* X = prm.x + (int64_t)g.slot * prm.slot_stride;
+        const int nx = g.n[0], ny = g.n[1];
+        for (int k0 = 0; k0 < nz; k0 += step) {
+          const int kc = min(step, nz - k0);
           for (int e = tid; e < kc * kZfPlane; e += kZfGroup) {
             const int row = e >> 5, i = e & 31, kl = row >> 5, j = row & 31;
             const float v = (i < nx && j < ny) ? X[((int64_t)(k0 + kl) * ny + j) * nx + i] : 0.f;
             T[row * 32 + (((i >> 2) ^ (row & 7)) << 2) + (i & 3)] = v;
           }
-          group_sync(kBarZ);
-          buf = reinterpret_cast<const float4*>(T);
+          group_sync(kBarZ, kZfGroup);
+          if (!skip) zf_stage_z<CP>(reinterpret_cast<const float4*>(T), Az, k0, kc, acc);
+          group_sync(kBarZ, kZfGroup);
         }
-        if (!skip) zf_stage_z<CP>(buf, Az, k0, kc, acc);
-        group_sync(kBarZ);  // the slab's buffer may be refilled from here on
       }
       if (!take_t()) { fail(); return; }
       if (!skip && nz > 0) {
@@ -1147,9 +1136,47 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
       }
       mbar_arrive(&s_tfull);  // every thread of the group: T holds block n's z stage
     }
+  } else if (tid < kZfGroup + 32) {
+    // ------------------------------ producer warp ------------------------------
+    // Lane 0 issues the TMA slabs of the CTA's blocks in order, each into the ring slot the z warps
+    // have handed back. A block's geometry comes from its published set-up (never overwritten before
+    // the z group has consumed the block, so a register copy taken after the wait stays valid).
+    if (tid != kZfGroup) return;
+    const int64_t rows_per_slot = prm.slot_stride / 32;
+    uint32_t issued = 0;
+    // the CTA must not end with a copy in flight: before leaving, the producer waits (bounded) until its
+    // last R copies have landed; a copy's phase, once complete, stays complete until the slot is reused
+    auto land = [&]() {
+      for (uint32_t q = issued > (uint32_t)R ? issued - R : 0; q < issued; ++q)
+        mbar_wait_bounded(&s_full[q % R], (q / R) & 1);
+    };
+    auto drain = [&]() {  // a wait gave up: report, let the copies in flight land, leave
+      flag(prm.status, MFA_DEV_TIMEOUT);
+      land();
+    };
+    for (int m = 0;; ++m) {
+      const int pp = m % kZfSets;
+      if (!mbar_wait_bounded(&s_ready[pp], (m / kZfSets) & 1)) { drain(); return; }
+      const C3Geom& pg = s_g[pp];
+      if (!pg.valid) break;
+      if (!tma_block(pg)) continue;
+      const int64_t row0 = (int64_t)pg.slot * rows_per_slot;
+      const int nzp = pg.n[2];
+      for (int k0 = 0; k0 < nzp; k0 += ks) {
+        const uint32_t slot = issued % R;
+        if (issued >= (uint32_t)R && !mbar_wait_bounded(&s_empty[slot], ((issued / R) - 1) & 1)) {
+          drain();
+          return;
+        }
+        mbar_arrive_expect_tx(&s_full[slot], slab_bytes);
+        tma_load_2d(ring + slot * slab_f4, &xmap, &s_full[slot], 0, (int)(row0 + (int64_t)k0 * 32));
+        ++issued;
+      }
+    }
+    land();
   } else {
     // ------------------------------ y/x group ------------------------------
-    const int t = tid - kZfGroup;
+    const int t = tid - kZfGroup - 32;
     // thread 0 of the group: geometry of block m into buffer m % 4, and whether its A must be built
     auto fetch = [&](int m) {
       const int b = m % kZfSets;
@@ -1165,7 +1192,7 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
     };
     auto build = [&](int m) {  // the group: A of block m when needed, then publish the set-up
       const int b = m % kZfSets;
-      group_sync(kBarYX);
+      group_sync(kBarYX, kZfYx);
       if (s_rebuild[b]) {
         zf_setup<CP, MODE>(prm, L.A[b], sm + L.knots[b], sm, s_g[b], t, &s_bad[b]);
         if (t == 0) {
@@ -1181,20 +1208,19 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
     }
     for (int n = 0;; ++n) {
       const int b = n % kZfSets;
-      if (t == 0) fetch(n + kZfSets - 1);  // buffer of block n - 1, which both groups are done with
+      if (t == 0) fetch(n + kZfSets - 1);  // buffer of block n - 1, which every role is done with
       const C3Geom g = s_g[b];
       if (!g.valid) break;
       const bool ok = mbar_wait_bounded(&s_tfull, n & 1);
-      if (group_any(kBarYX, !ok)) {
+      if (group_any(kBarYX, kZfYx, !ok)) {
         if (t == 0) flag(prm.status, MFA_DEV_TIMEOUT);
         return;
       }
       const bool work = !g.bad && !s_bad[b] && g.n[2] > 0;
       if (work) zf_stage_y<CP>(sm + L.T, sm + L.A[b][1], sm + L.U, g.C[1], g.C[2], g.n[1], t);
-      group_sync(kBarYX);
+      group_sync(kBarYX, kZfYx);
+      if (t == 0) mbar_arrive(&s_tfree);  // T may take block n + 1
       if (work) zf_stage_x<CP>(sm + L.U, sm + L.A[b][0], prm.out + g.cpoff, g.C[0], g.C[1], g.C[2], g.n[0], t);
-      group_sync(kBarYX);
-      if (t == 0) mbar_arrive(&s_tfree);  // T (and U in it) may take block n + 1
       build(n + kZfSets - 1);
     }
   }
@@ -1293,7 +1319,7 @@ static int contract3_zfirst(mfa_ctx* ctx, const ContractParams& prm, cudaStream_
   auto depth = [&](int ks) {
     int R = 0;
     for (int r = kZfMaxRing; r >= 2 && !R; --r)
-      if ((size_t)zf_layout(prm.mode, CP, ks, r).total * 4 + 1024 <= kMaxDynSmem) R = r;  // room for static smem
+      if ((size_t)zf_layout(prm.mode, CP, ks, r).total * 4 + 2048 <= kMaxDynSmem) R = r;  // room for static smem
     return R;
   };
   int ks = 0, R = 0;
