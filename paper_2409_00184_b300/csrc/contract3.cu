@@ -997,7 +997,7 @@ __device__ void zf_stage_y(const float* T, const float* Ay, float* U, int Cy, in
     const float* t0 = T + (e0 >> 5) * kZfPlane + (e0 & 31);
     const float* t1 = T + (e1 >> 5) * kZfPlane + (e1 & 31);
     if (h1) {
-#pragma unroll 2
+#pragma unroll 4
       for (int j = 0; j < ny; ++j) {
         const float v0 = t0[j * 32], v1 = t1[j * 32];
         zf_y_fma<CP>(a0, Ay, j, v0);
@@ -1039,7 +1039,7 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
   __shared__ __align__(8) uint64_t s_full[kZfMaxRing], s_empty[kZfMaxRing];
   __shared__ __align__(8) uint64_t s_tfull, s_tfree, s_ready[kZfSets];
   __shared__ C3Geom s_g[kZfSets], s_built[kZfSets];  // geometry of the buffer's block / of its A matrices
-  __shared__ int s_bad[kZfSets], s_rebuild[kZfSets], s_has[kZfSets];
+  __shared__ int s_bad[kZfSets], s_rebuild[kZfSets], s_has[kZfSets];  // s_rebuild: 0 keep, 1 build, 2 copy
   __shared__ int s_zabort;  // a z warp gave up waiting for a slab
   const int tid = threadIdx.x;
   const int R = L.R, ks = L.ks;
@@ -1177,28 +1177,40 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
   } else {
     // ------------------------------ y/x group ------------------------------
     const int t = tid - kZfGroup - 32;
-    // thread 0 of the group: geometry of block m into buffer m % 4, and whether its A must be built
-    auto fetch = [&](int m) {
-      const int b = m % kZfSets;
-      c3_fetch(prm, blockIdx.x + m * (int)gridDim.x, s_g[b]);
-      const C3Geom& g = s_g[b];
-      const C3Geom& h = s_built[b];
-      bool same = s_has[b] != 0;
+    // one thread: geometry of block m into buffer m % 4, and how its A comes about: kept
+    // (the buffer's previous block had the same class, or degree, C, n and knots), copied from the
+    // buffer of block m - 1 (the same key), or built
+    auto same_key = [](const C3Geom& g, const C3Geom& h) {
+      bool same = true;
       for (int a = 0; a < 3 && same; ++a)
         same = MODE == kFit ? g.cls[a] == h.cls[a]
                             : (g.p[a] == h.p[a] && g.C[a] == h.C[a] && g.n[a] == h.n[a] && g.koff[a] == h.koff[a]);
-      s_rebuild[b] = g.valid && !g.bad && !same;
-      if (s_rebuild[b]) s_bad[b] = 0;
+      return same;
+    };
+    auto fetch = [&](int m) {
+      const int b = m % kZfSets, bp = (m + kZfSets - 1) % kZfSets;
+      c3_fetch(prm, blockIdx.x + m * (int)gridDim.x, s_g[b]);
+      const C3Geom& g = s_g[b];
+      int how = 0;
+      if (g.valid && !g.bad && !(s_has[b] && same_key(g, s_built[b])))
+        how = (m > 0 && s_has[bp] && same_key(g, s_built[bp])) ? 2 : 1;
+      s_rebuild[b] = how;
+      if (how == 1) s_bad[b] = 0;
+      if (how == 2) s_bad[b] = s_bad[bp];
     };
     auto build = [&](int m) {  // the group: A of block m when needed, then publish the set-up
-      const int b = m % kZfSets;
+      const int b = m % kZfSets, bp = (m + kZfSets - 1) % kZfSets;
       group_sync(kBarYX, kZfYx);
-      if (s_rebuild[b]) {
+      const int how = s_rebuild[b];
+      if (how == 1) {
         zf_setup<CP, MODE>(prm, L.A[b], sm + L.knots[b], sm, s_g[b], t, &s_bad[b]);
-        if (t == 0) {
-          s_built[b] = s_g[b];
-          s_has[b] = 1;
-        }
+      } else if (how == 2) {  // buffer bp holds block m - 1's A (rebuilt only after this one)
+        for (int e = t; e < 3 * 32 * CP; e += kZfYx) sm[L.A[b][0] + e] = sm[L.A[bp][0] + e];
+        group_sync(kBarYX, kZfYx);
+      }
+      if (how && t == 0) {
+        s_built[b] = s_g[b];
+        s_has[b] = 1;
       }
       if (t == 0) mbar_arrive(&s_ready[b]);
     };
@@ -1206,9 +1218,11 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
       if (t == 0) fetch(m);
       build(m);
     }
+    // the fetch for block n + 3 runs on the group's last warp during the x stage, which has the fewest
+    // rows there (none for C <= 12); it writes the buffer of block n - 1, which every role is done with
+    const int fetcher = kZfYx - 32;
     for (int n = 0;; ++n) {
       const int b = n % kZfSets;
-      if (t == 0) fetch(n + kZfSets - 1);  // buffer of block n - 1, which every role is done with
       const C3Geom g = s_g[b];
       if (!g.valid) break;
       const bool ok = mbar_wait_bounded(&s_tfull, n & 1);
@@ -1220,6 +1234,7 @@ contract3_zf_kernel(ContractParams prm, ZfSmem L, const __grid_constant__ CUtens
       if (work) zf_stage_y<CP>(sm + L.T, sm + L.A[b][1], sm + L.U, g.C[1], g.C[2], g.n[1], t);
       group_sync(kBarYX, kZfYx);
       if (t == 0) mbar_arrive(&s_tfree);  // T may take block n + 1
+      if (t == fetcher) fetch(n + kZfSets - 1);
       if (work) zf_stage_x<CP>(sm + L.U, sm + L.A[b][0], prm.out + g.cpoff, g.C[0], g.C[1], g.C[2], g.n[0], t);
       build(n + kZfSets - 1);
     }
