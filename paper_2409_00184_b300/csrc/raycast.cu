@@ -136,6 +136,30 @@ __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n,
       }
 }
 
+// The eight corners of a cell that spans two bricks on some axis, for bricks of 2^L voxels: per axis the
+// brick step (0 or 1) and local coordinate of the two corner planes are formed once with shifts and
+// masks; every corner then costs one table lookup and one load.
+template <int L, bool CUBES>
+__device__ __forceinline__ void corners_seam(const RaycastParams& prm, int ix, int iy, int iz, float4 (&c)[2][2][2]) {
+  constexpr int n = 1 << L;
+  const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
+  const int sx = lx == n - 1, sy = ly == n - 1, sz = lz == n - 1;  // the +1 plane lies in the next brick
+  const int lxd[2] = {lx, sx ? 0 : lx + 1}, lyd[2] = {ly, sy ? 0 : ly + 1}, lzd[2] = {lz, sz ? 0 : lz + 1};
+  const int t0 = ((iz >> L) * prm.B[1] + (iy >> L)) * prm.B[0] + (ix >> L);
+  const int tx[2] = {0, sx}, ty[2] = {0, sy * prm.B[0]}, tz[2] = {0, sz * prm.B[0] * prm.B[1]};
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int dx = e & 1, dy = (e >> 1) & 1, dz = e >> 2;
+    const int slot = __ldg(prm.table + t0 + tz[dz] + ty[dy] + tx[dx]);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (slot >= 0 && slot < prm.nslots) {
+      const int vox = CUBES ? cube_index(lxd[dx], lyd[dy], lzd[dz], n, n) : (((lzd[dz] << L) + lyd[dy]) << L) + lxd[dx];
+      v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + vox);
+    }
+    c[dz][dy][dx] = v;
+  }
+}
+
 // Adds the warp's marched samples to the statistics counter (lane = linear thread index mod 32).
 __device__ __forceinline__ void count_marched(const RaycastParams& prm, unsigned long long m, int lane) {
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
@@ -247,7 +271,7 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
       while (k < K) {
         float4 c[2][2][2];
         if (slot == -2) {
-          corners_general<CUBES ? 1 : 0>(prm, n, ix, iy, iz, c);
+          corners_seam<L, CUBES>(prm, ix, iy, iz, c);
         } else if (slot >= 0 && slot < prm.nslots && CUBES) {
           // cube layout: the two x, y and z corner planes of the cell
           const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
