@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
   if (px < prm.W && py < prm.H) {
     float d[3], t0;
     const int K = ray_setup(prm, px, py, d, t0);
-    const int n = prm.brick_n, n2 = n * n;
+    const int n = prm.brick_n;
     const int Nx = prm.B[0] * n, Ny = prm.B[1] * n, Nz = prm.B[2] * n;
     const float inv_range = 1.0f / (prm.vmax - prm.vmin);
     const float tfs = (float)(prm.tf_n - 1);
