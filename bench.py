@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--layout", choices=["rows", "apron"], default="rows",
+                    help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
+                         "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
+                         "decode)")
     ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct", "outofcore"],
                     default="step",
                     help="step: the default 512^3 step; frames: adaptive-NCP frames replayed from a CUDA graph "
@@ -159,10 +163,12 @@ def src_sha(name):
 
 
 class Workload:
-    def __init__(self, mfa, ctx, seed):
+    def __init__(self, mfa, ctx, seed, layout="rows"):
         self.mfa, self.ctx = mfa, ctx
         B = (N_FIELD // BRICK) ** 3
         self.B, self.vox = B, BRICK ** 3
+        self.apron = layout == "apron"
+        self.stride = mfa.apron_voxels(BRICK) if self.apron else self.vox  # cache slot stride (voxels)
         field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
         self.D = synth.blocks_from_field(field, BRICK).contiguous().view(B, self.vox)
         del field
@@ -170,7 +176,7 @@ class Workload:
         self.bs = synth.make_block_set([(NCP,) * 3] * B, [(DEGREE,) * 3] * B, [(BRICK,) * 3] * B, [zero] * B)
         self.blk = mfa.DeviceBlocks(self.bs)
         self.plan = mfa.EncodePlan(ctx, self.blk)
-        self.cache = torch.empty(B * self.vox * 4, device="cuda")
+        self.cache = torch.empty(B * self.stride * 4, device="cuda")
         nb = N_FIELD // BRICK
         self.table = torch.arange(B, dtype=torch.int32, device="cuda").view(nb, nb, nb)
         self.tf = torch.from_numpy(synth.transfer_function(seed)).cuda()
@@ -188,10 +194,14 @@ class Workload:
         m.encode_blocks(c, self.plan, D, v, self.B, blk.cps)
         if ev:
             ev[1].record()
-        m.decode_compare_blocks(c, blk, self.cache, v, self.B, D, v, residual=self.R, rmse=self.rmse)
+        m.decode_compare_blocks(c, blk, self.cache, self.stride, self.B, D, v, residual=self.R, rmse=self.rmse,
+                                flags=m.DECODE_APRON if self.apron else 0)
+        if self.apron:
+            m.fill_aprons(c, self.cache, self.stride, self.B, self.table, BRICK)
         if ev:
             ev[2].record()
-        m.raycast(c, self.cache, v, self.B, self.table, BRICK, self.view, self.tf, self.image)
+        m.raycast(c, self.cache, self.stride, self.B, self.table, BRICK, self.view, self.tf, self.image,
+                  apron=self.apron)
         if ev:
             ev[3].record()
         m.adjoint_blocks(c, blk, self.R, v, self.B, self.grad)
@@ -217,7 +227,8 @@ def check_against_oracle(w, nblocks=12, nvox=400, seed=5):
     from oracle import encode as oenc
     g = synth.rng(seed)
     knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
-    cache = w.cache.view(w.B, w.vox, 4)
+    cache = w.cache.view(w.B, w.stride, 4)
+    px, py = (w.mfa.apron_pitch(BRICK), BRICK + 1) if w.apron else (BRICK, BRICK)  # row pitch, rows per plane
     cps = w.blk.cps.view(w.B, NCP ** 3)
     got, want, cperr = [], [], 0.0
     for b in g.choice(w.B, nblocks, replace=False):
@@ -225,7 +236,7 @@ def check_against_oracle(w, nblocks=12, nvox=400, seed=5):
         P = oenc.fit_separable(Db, knots, (DEGREE,) * 3)
         cperr = max(cperr, float(np.abs(cps[b].cpu().numpy().reshape(P.shape) - P).max() / (P.max() - P.min())))
         kji = g.integers(0, BRICK, size=(nvox, 3))
-        lin = torch.as_tensor((kji[:, 0] * BRICK + kji[:, 1]) * BRICK + kji[:, 2], device="cuda")
+        lin = torch.as_tensor((kji[:, 0] * py + kji[:, 1]) * px + kji[:, 2], device="cuda")
         got.append(cache[b][lin].cpu().numpy())
         want.append(odec.decode_voxels(P, knots, (DEGREE,) * 3, (BRICK,) * 3, kji))
     got, want = np.concatenate(got).astype(np.float64), np.concatenate(want)
@@ -759,7 +770,7 @@ def main():
     from paper_2409_00184_b300 import mfa
     ctx = mfa.Context(local)
     seed = synth.BASE_SEED + 2 + rank
-    w = Workload(mfa, ctx, seed)
+    w = Workload(mfa, ctx, seed, args.layout)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -886,7 +897,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": K,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
+                "config": {"workload": WORKLOAD, "layout": args.layout, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
                            "l2": "inputs larger than L2 (512 MB samples, 2.15 GB cache); no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,

@@ -39,7 +39,13 @@
  *     Voxels of a slot are [z][y][x] (x fastest), or with MFA_DECODE_CUBES (blocks with even
  *     n per axis) in 2x2x2-voxel cubes: voxel (x, y, z) at 8*(((z/2)*(n_y/2) + y/2)*(n_x/2) + x/2)
  *     + 4*(z%2) + 2*(y%2) + x%2, so the 8 voxels of a cube (128 bytes of float4) share a cache
- *     line; a block with an odd n sets MFA_DEV_BAD_DESC and is skipped.
+ *     line; a block with an odd n sets MFA_DEV_BAD_DESC and is skipped. With MFA_DECODE_APRON
+ *     the slot holds A_x(n_y+1)(n_z+1) voxels with A_x = n_x+1 rounded up to even, voxel (x, y, z)
+ *     at ((z*(n_y+1) + y)*A_x + x): for an even n_x and an even slot stride every row starts on a
+ *     32-byte sector. The decode writes x < n_x,
+ *     y < n_y, z < n_z; mfa_fill_aprons writes the planes x = n_x, y = n_y, z = n_z from the
+ *     neighbouring bricks and zeros the padding columns n_x < x < A_x (a block whose apron volume
+ *     exceeds slot_stride_voxels sets MFA_DEV_BAD_RANGE and is skipped).
  */
 #ifndef MFA_H
 #define MFA_H
@@ -78,6 +84,7 @@ extern "C" {
 #define MFA_DECODE_VALUE_ONLY  0x1u /* write f only: 1 float per voxel instead of 4       */
 #define MFA_DECODE_LIST_SLOTS  0x2u /* with a list: item m goes to slot m (not desc.slot) */
 #define MFA_DECODE_CUBES       0x4u /* cache voxels in the cube layout (see Layouts); FP32 only */
+#define MFA_DECODE_APRON       0x8u /* cache voxels with a one-voxel apron (see Layouts); FP32 only */
 
 /* ---- fixed limits -------------------------------------------------------------------- */
 #define MFA_MAX_DEGREE 3
@@ -222,6 +229,7 @@ typedef struct {
 #define MFA_FRAME_SORT_BY_COST 0x1u /* order the visible list by decreasing max(C) first     */
 #define MFA_FRAME_RAYCAST      0x2u /* build the brick table and ray-cast after the decode   */
 #define MFA_FRAME_CUBES        0x4u /* decode into (and ray-cast from) the cube layout        */
+#define MFA_FRAME_APRON        0x8u /* decode with aprons, fill them, ray-cast with aprons    */
 
 /* Everything a frame reads; pointers and sizes are fixed when the graph is captured. Per frame
  * the caller writes the visible block ids into d_list[0 .. *d_count) (device memory, count <=
@@ -366,11 +374,28 @@ int mfa_raycast(mfa_ctx* ctx,
  * the same, bit for bit, as mfa_raycast's over the same voxels in the [z][y][x] layout: only
  * the addresses of the eight corner loads change. Unknown flags: MFA_ERR_INVALID_ARG. */
 #define MFA_RAYCAST_CUBES 0x1u
+/* MFA_RAYCAST_APRON: the cache bricks carry the one-voxel apron that MFA_DECODE_APRON and
+ * mfa_fill_aprons produce (slot_stride_voxels >= A(brick_n+1)^2 with A = brick_n+1 rounded up to
+ * even, else MFA_ERR_INVALID_ARG); every cell then reads its eight corners from its own
+ * slot. Same image, bit for bit, as mfa_raycast over the same voxels. */
+#define MFA_RAYCAST_APRON 0x2u
 int mfa_raycast_ex(mfa_ctx* ctx,
                    const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
                    const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
                    const mfa_view* view, const float* d_tf, int32_t tf_n,
                    float* d_image, uint32_t flags, void* stream);
+
+/* Writes the apron of every brick of d_brick_table (layout of MFA_DECODE_APRON, bricks of brick_n^3
+ * voxels in slots of at least A(brick_n+1)^2, A = brick_n+1 rounded up to even): voxel
+ * (x, y, z) of brick (bx, by, bz) with
+ * x, y or z equal to brick_n (and x, y, z <= brick_n) becomes voxel (x mod brick_n, y mod brick_n,
+ * z mod brick_n) of brick (bx + [x = n], by + [y = n], bz + [z = n]), or zero when that brick lies
+ * outside the volume or is absent (-1); the padding voxels brick_n < x < A become zero. Reads interior
+ * voxels only and writes apron and padding voxels only, 4 floats each. Bricks with slot -1 are
+ * skipped. Returns MFA_ERR_INVALID_ARG for null or misaligned pointers, brick_n outside
+ * 2 .. MFA_MAX_NSAMP, a slot stride below A(brick_n+1)^2 or bad brick_dims. */
+int mfa_fill_aprons(mfa_ctx* ctx, float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                    const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n, void* stream);
 
 /* Algorithm 4 with per-sample queries of the micro-models instead of a decoded cache: the same rays,
  * transfer function, shading and compositing as mfa_raycast, but every sample evaluates the value

@@ -77,6 +77,11 @@ __device__ __forceinline__ int cube_index(int x, int y, int z, int nx, int ny) {
   return ((((z >> 1) * (ny >> 1) + (y >> 1)) * (nx >> 1) + (x >> 1)) << 3) | ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
 }
 
+// Row pitch of a brick of n voxels per row in the apron layout (MFA_DECODE_APRON): n + 1 voxels rounded up
+// to even, so that rows of float4 voxels start on 32-byte sectors (for an even slot stride) and the apron
+// column x = n with its padding fills whole sectors.
+__host__ __device__ constexpr int apron_pitch(int n) { return (n + 2) & ~1; }
+
 // Sample parameter u_i = i/(n-1), rounded once (IEEE division).
 __device__ __forceinline__ float sample_param(int i, int n) {
   return __fdiv_rn((float)i, (float)(n - 1));

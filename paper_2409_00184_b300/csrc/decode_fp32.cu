@@ -55,8 +55,11 @@ static DecodeSmem decode_smem_layout(bool value_only, int maxC, int maxN, int ks
   return L;
 }
 
-template <int PMAX, bool VALUE_ONLY, bool COMPARE, bool CUBES>
-__global__ void __launch_bounds__(kDecodeThreads)
+// LAYOUT of the cache: kLayoutRows [z][y][x], kLayoutCubes, kLayoutApron ([z][y][x] in rows of apron_pitch(n), planes of n + 1 rows)
+enum CacheLayout { kLayoutRows = 0, kLayoutCubes = 1, kLayoutApron = 2 };
+
+template <int PMAX, bool VALUE_ONLY, bool COMPARE, int LAYOUT>
+__global__ void __launch_bounds__(kDecodeThreads, LAYOUT == kLayoutApron ? 4 : 0)  // 0: no minimum
 decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_unit, s_bad, s_item;
@@ -100,6 +103,9 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
         }
         if (!bad && COMPARE && (int64_t)s_g.n[0] * s_g.n[1] * s_g.n[2] > prm.data_stride) bad = MFA_DEV_BAD_RANGE;
         if (!bad && (prm.flags & MFA_DECODE_CUBES) && ((s_g.n[0] | s_g.n[1] | s_g.n[2]) & 1)) bad = MFA_DEV_BAD_DESC;
+        if (!bad && (prm.flags & MFA_DECODE_APRON) &&
+            (int64_t)apron_pitch(s_g.n[0]) * (s_g.n[1] + 1) * (s_g.n[2] + 1) > prm.slot_stride)
+          bad = MFA_DEV_BAD_RANGE;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
       }
     }
@@ -235,12 +241,19 @@ decode_fp32_kernel(DecodeParams prm, DecodeSmem L) {
           const float Nx[4] = {Nx4.x, Nx4.y, Nx4.z, Nx4.w}, dNx[4] = {dNx4.x, dNx4.y, dNx4.z, dNx4.w};
           const int rows = ny * kc;
           const int64_t base = (int64_t)s_g.slot * prm.slot_stride + (int64_t)k0 * ny * nx + i;
-          // cache index of row r's voxel: [z][y][x], or the cube layout
+          // cache index of row r's voxel: [z][y][x], the cube layout, or [z][y][x] with rows of
+          // apron_pitch(nx) and planes of ny + 1 rows (apron)
           const int64_t sbase = (int64_t)s_g.slot * prm.slot_stride;
+          const float inv_ny = 1.0f / (float)ny;
+          // apron: row r = kl * ny + j of the chunk sits at ((k0 + kl) * (ny + 1) + j) * ax + i, which is
+          // a0 + (r + kl) * ax
+          // (offsets inside a slot stay below 65^3, so 32 bits hold them)
+          const int ax = apron_pitch(nx), a0 = k0 * (ny + 1) * ax + i;
           auto cidx = [&](int r) -> int64_t {
-            if (!CUBES) return base + (int64_t)r * nx;
-            const int kl = r / ny, j = r - kl * ny;
-            return sbase + cube_index(i, j, k0 + kl, nx, ny);
+            if (LAYOUT == kLayoutRows) return base + (int64_t)r * nx;
+            const int kl = __float2int_rz(((float)r + 0.5f) * inv_ny);  // r / ny, exact for r < 2^12
+            if (LAYOUT == kLayoutCubes) return sbase + cube_index(i, r - kl * ny, k0 + kl, nx, ny);
+            return sbase + (a0 + (r + kl) * ax);
           };
           const int64_t dbase = COMPARE ? (int64_t)s_g.slot * prm.data_stride + (int64_t)k0 * ny * nx + i : 0;
           // rows in chunks of kPrefetch per thread: with COMPARE the chunk's samples D are loaded before its
@@ -359,9 +372,12 @@ __global__ void rmse_finish_kernel(DecodeParams prm, int max_items) {
 template <int PMAX, bool VO>
 static cudaError_t launch_one(mfa_ctx* ctx, const DecodeParams& prm, const DecodeSmem& L, int ctas_per_sm,
                               cudaStream_t stream) {
-  const bool cubes = (prm.flags & MFA_DECODE_CUBES) != 0;
-  auto kern = prm.data ? (cubes ? decode_fp32_kernel<PMAX, VO, true, true> : decode_fp32_kernel<PMAX, VO, true, false>)
-                       : (cubes ? decode_fp32_kernel<PMAX, VO, false, true> : decode_fp32_kernel<PMAX, VO, false, false>);
+  const int layout = (prm.flags & MFA_DECODE_CUBES) ? kLayoutCubes : (prm.flags & MFA_DECODE_APRON) ? kLayoutApron : kLayoutRows;
+  auto pick = [&](auto rows, auto cubes, auto apron) { return layout == kLayoutCubes ? cubes : layout == kLayoutApron ? apron : rows; };
+  auto kern = prm.data ? pick(decode_fp32_kernel<PMAX, VO, true, kLayoutRows>, decode_fp32_kernel<PMAX, VO, true, kLayoutCubes>,
+                              decode_fp32_kernel<PMAX, VO, true, kLayoutApron>)
+                       : pick(decode_fp32_kernel<PMAX, VO, false, kLayoutRows>, decode_fp32_kernel<PMAX, VO, false, kLayoutCubes>,
+                              decode_fp32_kernel<PMAX, VO, false, kLayoutApron>);
   const size_t smem = (size_t)L.total * 4;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -96,9 +96,12 @@ int mfa_frame_graph_create(mfa_ctx* ctx, mfa_frame_graph** out, const mfa_frame_
   if (!fd->d_desc || !fd->d_list || !fd->d_count || !fd->d_knots || !fd->d_cps || !fd->d_cache ||
       fd->nblocks < 1 || fd->list_capacity < 1 || fd->slot_stride_voxels < 1)
     return MFA_ERR_INVALID_ARG;
-  if (fd->flags & ~(MFA_FRAME_SORT_BY_COST | MFA_FRAME_RAYCAST | MFA_FRAME_CUBES)) return MFA_ERR_INVALID_ARG;
+  if (fd->flags & ~(MFA_FRAME_SORT_BY_COST | MFA_FRAME_RAYCAST | MFA_FRAME_CUBES | MFA_FRAME_APRON))
+    return MFA_ERR_INVALID_ARG;
   const bool rc = (fd->flags & MFA_FRAME_RAYCAST) != 0;
   const bool cubes = (fd->flags & MFA_FRAME_CUBES) != 0;
+  const bool apron = (fd->flags & MFA_FRAME_APRON) != 0;
+  if (cubes && apron) return MFA_ERR_INVALID_ARG;
   if (rc && (!fd->d_brick_table || !fd->view || !fd->d_tf || !fd->d_image)) return MFA_ERR_INVALID_ARG;
   if (rc && (int64_t)fd->brick_dims[0] * fd->brick_dims[1] * fd->brick_dims[2] != fd->nblocks)
     return MFA_ERR_INVALID_ARG;
@@ -127,16 +130,19 @@ int mfa_frame_graph_create(mfa_ctx* ctx, mfa_frame_graph** out, const mfa_frame_
     status = mfa_decode_blocks(ctx, fd->d_desc, fd->nblocks, fd->d_list, fd->list_capacity, fd->d_count,
                                fd->d_knots, fd->knots_len, fd->d_cps, fd->cps_len, fd->d_cache,
                                fd->slot_stride_voxels, fd->list_capacity, &fd->bounds, MFA_PREC_FP32,
-                               MFA_DECODE_LIST_SLOTS | (cubes ? MFA_DECODE_CUBES : 0u), s);
+                               MFA_DECODE_LIST_SLOTS | (cubes ? MFA_DECODE_CUBES : 0u) | (apron ? MFA_DECODE_APRON : 0u), s);
   if (status == MFA_OK && rc) {
     brick_table_kernel<<<1, 1024, 0, s>>>(fd->d_list, fd->list_capacity, fd->d_count, fd->nblocks,
                                           fd->d_brick_table);
     ctx->launches++;
     if (cudaGetLastError() != cudaSuccess) status = MFA_ERR_CUDA;
+    if (status == MFA_OK && apron)
+      status = mfa_fill_aprons(ctx, fd->d_cache, fd->slot_stride_voxels, fd->list_capacity, fd->d_brick_table,
+                               fd->brick_dims, fd->brick_n, s);
     if (status == MFA_OK)
       status = mfa_raycast_ex(ctx, fd->d_cache, fd->slot_stride_voxels, fd->list_capacity, fd->d_brick_table,
                               fd->brick_dims, fd->brick_n, fd->view, fd->d_tf, fd->tf_n, fd->d_image,
-                              cubes ? MFA_RAYCAST_CUBES : 0u, s);
+                              cubes ? MFA_RAYCAST_CUBES : apron ? MFA_RAYCAST_APRON : 0u, s);
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(s, &graph);

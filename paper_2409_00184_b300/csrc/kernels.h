@@ -75,9 +75,22 @@ struct RaycastParams {
   float step_voxels, opacity_max, ka, kd, ks, shininess, vmin, vmax;
   unsigned long long* samples;  // marched samples are added here (one atomic per warp)
   bool cubes = false;           // cache bricks in the cube layout (MFA_RAYCAST_CUBES)
+  bool apron = false;           // cache bricks with a one-voxel apron (MFA_RAYCAST_APRON)
 };
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream);
+
+// Apron planes of every brick of a brick table (MFA_DECODE_APRON layout, bricks of n^3 in (n+1)^3).
+struct ApronParams {
+  float4* cache;
+  int64_t slot_stride;
+  int64_t nslots;
+  const int32_t* table;
+  int B[3];
+  int n;
+};
+
+int apron_fill(mfa_ctx* ctx, const ApronParams& prm, cudaStream_t stream);
 
 // Micro-models queried per sample by the direct ray caster (prm.table holds block indices).
 struct DirectModels {

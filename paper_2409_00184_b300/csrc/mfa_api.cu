@@ -149,10 +149,12 @@ int decode_entry(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, co
   if (!ctx || !bounds_ok(bounds)) return MFA_ERR_INVALID_ARG;
   if (nblocks < 0 || list_len < 0 || knots_len < 0 || cps_len < 0 || slot_stride_voxels < 1 || nslots < 0)
     return MFA_ERR_INVALID_ARG;
-  if (flags & ~(MFA_DECODE_VALUE_ONLY | MFA_DECODE_LIST_SLOTS | MFA_DECODE_CUBES)) return MFA_ERR_INVALID_ARG;
+  if (flags & ~(MFA_DECODE_VALUE_ONLY | MFA_DECODE_LIST_SLOTS | MFA_DECODE_CUBES | MFA_DECODE_APRON))
+    return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_DECODE_CUBES) && (flags & MFA_DECODE_APRON)) return MFA_ERR_INVALID_ARG;
   if ((flags & MFA_DECODE_LIST_SLOTS) && !d_list) return MFA_ERR_INVALID_ARG;
   if (precision < MFA_PREC_FP32 || precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
-  if ((flags & MFA_DECODE_CUBES) && precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
+  if ((flags & (MFA_DECODE_CUBES | MFA_DECODE_APRON)) && precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
   const int items = d_list ? list_len : nblocks;
   if (items == 0 && !d_count) return MFA_OK;
   if (!d_desc || !d_knots || !d_cps || !d_cache || nblocks == 0) return MFA_ERR_INVALID_ARG;
@@ -335,7 +337,11 @@ int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxel
                    const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, uint32_t flags,
                    void* stream) {
   if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
-  if ((flags & ~MFA_RAYCAST_CUBES) || ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1))) return MFA_ERR_INVALID_ARG;
+  if ((flags & ~(MFA_RAYCAST_CUBES | MFA_RAYCAST_APRON)) || ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1)))
+    return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_RAYCAST_CUBES) && (flags & MFA_RAYCAST_APRON)) return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_RAYCAST_APRON) && slot_stride_voxels < (int64_t)apron_pitch(brick_n) * (brick_n + 1) * (brick_n + 1))
+    return MFA_ERR_INVALID_ARG;
   if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
     return MFA_ERR_INVALID_ARG;
   if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
@@ -354,7 +360,27 @@ int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxel
   prm.image = reinterpret_cast<float4*>(d_image);
   prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
   prm.cubes = (flags & MFA_RAYCAST_CUBES) != 0;
+  prm.apron = (flags & MFA_RAYCAST_APRON) != 0;
   return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
+}
+
+int mfa_fill_aprons(mfa_ctx* ctx, float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
+                    const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n, void* stream) {
+  if (!ctx || !d_cache || !d_brick_table || !brick_dims) return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_cache, 16) || !aligned(d_brick_table, 4)) return MFA_ERR_INVALID_ARG;
+  if (brick_n < 2 || brick_n > MFA_MAX_NSAMP || nslots < 0 ||
+      slot_stride_voxels < (int64_t)apron_pitch(brick_n) * (brick_n + 1) * (brick_n + 1))
+    return MFA_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
+  ApronParams prm;
+  prm.cache = reinterpret_cast<float4*>(d_cache);
+  prm.slot_stride = slot_stride_voxels;
+  prm.nslots = nslots;
+  prm.table = d_brick_table;
+  for (int a = 0; a < 3; ++a) prm.B[a] = brick_dims[a];
+  prm.n = brick_n;
+  return apron_fill(ctx, prm, static_cast<cudaStream_t>(stream));
 }
 
 int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,

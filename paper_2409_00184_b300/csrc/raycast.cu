@@ -106,17 +106,21 @@ __device__ __forceinline__ float4 trilinear(const float4 (&c)[2][2][2], float wx
                lerp4(lerp4(c[1][0][0], c[1][0][1], wx), lerp4(c[1][1][0], c[1][1][1], wx), wy), wz);
 }
 
-// Index of brick-local voxel (x, y, z) in its slot: [z][y][x], or the cube layout.
-__device__ __forceinline__ int brick_voxel(bool cubes, int n, int x, int y, int z) {
-  return cubes ? cube_index(x, y, z, n, n) : (z * n + y) * n + x;
+// Index of brick-local voxel (x, y, z) in its slot: [z][y][x] (rows of n; with an apron rows of
+// apron_pitch(n) and planes of n + 1 rows), or the cube layout.
+__device__ __forceinline__ int brick_voxel(bool cubes, bool apron, int n, int x, int y, int z) {
+  if (cubes) return cube_index(x, y, z, n, n);
+  if (apron) return (z * (n + 1) + y) * apron_pitch(n) + x;
+  return (z * n + y) * n + x;
 }
 
 // The eight corners of the cell at voxel (ix, iy, iz) when it spans two bricks on some axis (or the
 // brick size is not a power of two): one table lookup per corner.
-template <int LAYOUT>  // 0: [z][y][x], 1: cubes, -1: as prm.cubes says
+template <int LAYOUT>  // 0: [z][y][x], 1: cubes, 2: apron, -1: as prm says
 __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n, int ix, int iy, int iz,
                                                 float4 (&c)[2][2][2]) {
   const bool cubes = LAYOUT < 0 ? prm.cubes : LAYOUT == 1;
+  const bool apron = LAYOUT < 0 ? prm.apron : LAYOUT == 2;
   const int bx0 = ix / n, by0 = iy / n, bz0 = iz / n;
   const int lx0 = ix - bx0 * n, ly0 = iy - by0 * n, lz0 = iz - bz0 * n;
 #pragma unroll
@@ -131,7 +135,7 @@ __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n,
         const int slot = __ldg(prm.table + (bz * prm.B[1] + by) * prm.B[0] + bx);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (slot >= 0 && slot < prm.nslots)
-          v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + brick_voxel(cubes, n, lx, ly, lz));
+          v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + brick_voxel(cubes, apron, n, lx, ly, lz));
         c[dz][dy][dx] = v;
       }
 }
@@ -139,9 +143,9 @@ __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n,
 // The eight corners of a cell that spans two bricks on some axis, for bricks of 2^L voxels: per axis the
 // brick step (0 or 1) and local coordinate of the two corner planes are formed once with shifts and
 // masks; every corner then costs one table lookup and one load.
-template <int L, bool CUBES>
+template <int L, int LAYOUT>  // 0: [z][y][x], 1: cubes, 2: apron (rows of apron_pitch(2^L), planes of 2^L + 1)
 __device__ __forceinline__ void corners_seam(const RaycastParams& prm, int ix, int iy, int iz, float4 (&c)[2][2][2]) {
-  constexpr int n = 1 << L;
+  constexpr int n = 1 << L, P = n + 1, PX = apron_pitch(n);
   const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
   const int sx = lx == n - 1, sy = ly == n - 1, sz = lz == n - 1;  // the +1 plane lies in the next brick
   const int lxd[2] = {lx, sx ? 0 : lx + 1}, lyd[2] = {ly, sy ? 0 : ly + 1}, lzd[2] = {lz, sz ? 0 : lz + 1};
@@ -153,7 +157,9 @@ __device__ __forceinline__ void corners_seam(const RaycastParams& prm, int ix, i
     const int slot = __ldg(prm.table + t0 + tz[dz] + ty[dy] + tx[dx]);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (slot >= 0 && slot < prm.nslots) {
-      const int vox = CUBES ? cube_index(lxd[dx], lyd[dy], lzd[dz], n, n) : (((lzd[dz] << L) + lyd[dy]) << L) + lxd[dx];
+      const int vox = LAYOUT == 1   ? cube_index(lxd[dx], lyd[dy], lzd[dz], n, n)
+                      : LAYOUT == 2 ? (lzd[dz] * P + lyd[dy]) * PX + lxd[dx]
+                                    : (((lzd[dz] << L) + lyd[dy]) << L) + lxd[dx];
       v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + vox);
     }
     c[dz][dy][dx] = v;
@@ -191,14 +197,17 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
       const int bx0 = ix / n, by0 = iy / n, bz0 = iz / n;
       const int lx0 = ix - bx0 * n, ly0 = iy - by0 * n, lz0 = iz - bz0 * n;
       float4 c[2][2][2];
-      if (lx0 < n - 1 && ly0 < n - 1 && lz0 < n - 1) {
-        const int slot = __ldg(prm.table + (bz0 * prm.B[1] + by0) * prm.B[0] + bx0);
+      const bool inside = lx0 < n - 1 && ly0 < n - 1 && lz0 < n - 1;
+      const int slot0 = prm.apron || inside ? __ldg(prm.table + (bz0 * prm.B[1] + by0) * prm.B[0] + bx0) : -1;
+      // an apron keeps every cell of a present brick in that brick; an absent brick has no apron
+      if (inside || (prm.apron && slot0 >= 0 && slot0 < prm.nslots)) {
+        const int slot = slot0;
         if (slot >= 0 && slot < prm.nslots) {
           const float4* sb = prm.cache + (int64_t)slot * prm.slot_stride;
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             c[e >> 2][(e >> 1) & 1][e & 1] =
-                __ldg(sb + brick_voxel(prm.cubes, n, lx0 + (e & 1), ly0 + ((e >> 1) & 1), lz0 + (e >> 2)));
+                __ldg(sb + brick_voxel(prm.cubes, prm.apron, n, lx0 + (e & 1), ly0 + ((e >> 1) & 1), lz0 + (e >> 2)));
         } else {
 #pragma unroll
           for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -215,8 +224,11 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
   count_marched(prm, (unsigned long long)marched, tid & 31);
 }
 
-template <int L, bool CUBES>
+// LAYOUT of the cache bricks: 0 [z][y][x], 1 cubes, 2 [z][y][x] with a one-voxel apron (pitch 2^L + 1)
+template <int L, int LAYOUT>
 __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(RaycastParams prm, uint32_t* counter) {
+  constexpr bool CUBES = LAYOUT == 1, APRON = LAYOUT == 2;
+  constexpr int P = (1 << L) + 1, PX = apron_pitch(1 << L);  // apron: rows per plane, row pitch
   constexpr int n = 1 << L, n2 = n * n;
   extern __shared__ float4 s_tf[];  // tf_n entries
   for (int e = threadIdx.x; e < prm.tf_n; e += kQueueThreads) s_tf[e] = prm.tf[e];
@@ -259,7 +271,8 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
         wx = gx - (float)ix;
         wy = gy - (float)iy;
         wz = gz - (float)iz;
-        const bool one = (ix & (n - 1)) < n - 1 && (iy & (n - 1)) < n - 1 && (iz & (n - 1)) < n - 1;
+        // with an apron every cell lies in its lower corner's brick
+        const bool one = APRON || ((ix & (n - 1)) < n - 1 && (iy & (n - 1)) < n - 1 && (iz & (n - 1)) < n - 1);
         slot = -2;  // -2: spans bricks
         if (one) slot = __ldg(prm.table + ((iz >> L) * prm.B[1] + (iy >> L)) * prm.B[0] + (ix >> L));
       };
@@ -270,8 +283,17 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
       int k = 0;
       while (k < K) {
         float4 c[2][2][2];
-        if (slot == -2) {
-          corners_seam<L, CUBES>(prm, ix, iy, iz, c);
+        if (!APRON && slot == -2) {
+          corners_seam<L, LAYOUT>(prm, ix, iy, iz, c);
+        } else if (slot >= 0 && slot < prm.nslots && APRON) {
+          const float4* base = prm.cache + (int64_t)slot * prm.slot_stride +
+                               ((iz & (n - 1)) * P + (iy & (n - 1))) * PX + (ix & (n - 1));
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(base + (e >> 2) * P * PX + ((e >> 1) & 1) * PX + (e & 1));
+        } else if (APRON && (((ix & (n - 1)) == n - 1) | ((iy & (n - 1)) == n - 1) | ((iz & (n - 1)) == n - 1))) {
+          // an absent brick has no apron: a seam cell reads the neighbouring bricks' corners directly
+          corners_seam<L, LAYOUT>(prm, ix, iy, iz, c);
         } else if (slot >= 0 && slot < prm.nslots && CUBES) {
           // cube layout: the two x, y and z corner planes of the cell
           const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
 template <int L>
 int launch_queue(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {
   const size_t smem = (size_t)prm.tf_n * sizeof(float4);
-  auto kern = prm.cubes ? raycast_queue_kernel<L, true> : raycast_queue_kernel<L, false>;
+  auto kern = prm.apron ? raycast_queue_kernel<L, 2> : prm.cubes ? raycast_queue_kernel<L, 1> : raycast_queue_kernel<L, 0>;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQueueThreads, smem) != cudaSuccess)
     return MFA_ERR_CUDA;

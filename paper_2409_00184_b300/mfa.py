@@ -17,8 +17,8 @@ OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVICE, ERR_IO = -1, -2, -3, -4, -5, -6, -7
 DEV_BAD_DESC, DEV_BAD_KNOTS, DEV_BAD_RANGE, DEV_BAD_LIST, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4, 8, 16, 32
 PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
-DECODE_VALUE_ONLY, DECODE_LIST_SLOTS, DECODE_CUBES = 1, 2, 4
-RAYCAST_CUBES = 1
+DECODE_VALUE_ONLY, DECODE_LIST_SLOTS, DECODE_CUBES, DECODE_APRON = 1, 2, 4, 8
+RAYCAST_CUBES, RAYCAST_APRON = 1, 2
 MAX_DEGREE, MAX_NCP, MAX_NSAMP = 3, 32, 64
 
 
@@ -53,7 +53,7 @@ class FrameDesc(ctypes.Structure):
                 ("tf_n", ctypes.c_int32), ("d_image", ctypes.c_void_p)]
 
 
-FRAME_SORT_BY_COST, FRAME_RAYCAST, FRAME_CUBES = 1, 2, 4
+FRAME_SORT_BY_COST, FRAME_RAYCAST, FRAME_CUBES, FRAME_APRON = 1, 2, 4, 8
 
 DESC_DTYPE = np.dtype({"names": ["degree", "ncp", "nsamp", "slot", "knot_off", "cp_off"],
                        "formats": [("<i4", 3), ("<i4", 3), ("<i4", 3), "<i4", ("<i8", 3), "<i8"],
@@ -68,7 +68,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
            "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
            "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop",
-           "mfa_raycast_ex"]
+           "mfa_raycast_ex", "mfa_fill_aprons"]
 
 
 def _load():
@@ -118,6 +118,7 @@ def _load():
                                        ctypes.POINTER(View), P, I32, P, P]),
         "mfa_raycast_ex": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32,
                                           ctypes.POINTER(View), P, I32, P, ctypes.c_uint32, P]),
+        "mfa_fill_aprons": (ctypes.c_int, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_int32 * 3), I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -158,6 +159,16 @@ def _stream(stream):
 def _need(t, n, what):
     if t.numel() < n:
         raise ValueError(f"{what}: {t.numel()} elements, the call touches {n}")
+
+
+def apron_pitch(n):
+    """Row pitch (voxels) of a brick with n voxels per row in the DECODE_APRON layout: n + 1 rounded up to even."""
+    return (n + 2) & ~1
+
+
+def apron_voxels(n):
+    """Smallest slot stride (voxels) of an n^3 brick in the DECODE_APRON layout."""
+    return apron_pitch(n) * (n + 1) ** 2
 
 
 def model_bytes(ncp, degree):
@@ -496,22 +507,34 @@ def raycast_direct(ctx, blocks, table, brick_n, view, tf, image, cps=None, strea
            "mfa_raycast_direct")
 
 
-def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None, cubes=False):
-    """mfa_raycast (mfa_raycast_ex with MFA_RAYCAST_CUBES when `cubes`): table is an int32 (Bz, By, Bx)
-    CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
+def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None, cubes=False,
+            apron=False):
+    """mfa_raycast (mfa_raycast_ex with MFA_RAYCAST_CUBES or MFA_RAYCAST_APRON): table is an int32
+    (Bz, By, Bx) CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
     Bz, By, Bx = table.shape
     _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
     _need(cache, nslots * slot_stride * 4, "cache")
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
     vw = make_view(view)
-    if cubes:
+    if cubes or apron:
+        flags = (RAYCAST_CUBES if cubes else 0) | (RAYCAST_APRON if apron else 0)
         _check(lib.mfa_raycast_ex(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
-                                  brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), RAYCAST_CUBES,
+                                  brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), flags,
                                   _stream(stream)), "mfa_raycast_ex")
     else:
         _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
                                brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
                "mfa_raycast")
+
+
+def fill_aprons(ctx, cache, slot_stride, nslots, table, brick_n, stream=None):
+    """mfa_fill_aprons: the apron planes of every brick of `table` (int32 (Bz, By, Bx) CUDA tensor) in a cache
+    decoded with DECODE_APRON (slot_stride >= apron_voxels(brick_n) voxels of 4 floats)."""
+    Bz, By, Bx = table.shape
+    _need(cache, nslots * slot_stride * 4, "cache")
+    dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
+    _check(lib.mfa_fill_aprons(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
+                               brick_n, _stream(stream)), "mfa_fill_aprons")
 
 
 class FrameGraph:
@@ -520,12 +543,13 @@ class FrameGraph:
     (device int32 tensors) before each launch()."""
 
     def __init__(self, ctx, blocks, list_buf, count_buf, cache, slot_stride, sort=True,
-                 table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None, cubes=False):
+                 table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None, cubes=False,
+                 apron=False):
         self.ctx = ctx
         self._keep = [blocks, list_buf, count_buf, cache, table, tf, image]
         cap = list_buf.numel()
         _need(cache, cap * slot_stride * 4, "cache")
-        flags = (FRAME_SORT_BY_COST if sort else 0) | (FRAME_CUBES if cubes else 0)
+        flags = (FRAME_SORT_BY_COST if sort else 0) | (FRAME_CUBES if cubes else 0) | (FRAME_APRON if apron else 0)
         self._view = None
         fd = FrameDesc()
         fd.d_desc, fd.nblocks = _ptr(blocks.desc), blocks.n
