@@ -38,11 +38,11 @@ N_FIELD, BRICK, NCP, DEGREE = 512, 32, 12, 2
 IMG = 1024
 METRIC = "Gvoxel/s MFA decode (value+grad), % roofline, max err vs FP64 oracle"
 WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degree 2, 12^3 control points: "
-            "LS encode + value/gradient decode fused with residual and RMSE + 1024^2 ray cast (1 sample/voxel, "
-            "256-entry TF) + adjoint of the residual")
-# dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by the
-# sha256 of the kernel source it was taken on; reported as null once the source changes.
-TRAFFIC = {"raycast": {"bytes": 395.19e6 + 17.23e6, "src_sha": "ccfac4a6e15beb36"}}
+            "LS encode + value/gradient decode fused with residual and RMSE (apron layout: + neighbour-plane fill) "
+            "+ 1024^2 ray cast (1 sample/voxel, 256-entry TF) + adjoint of the residual")
+# dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by kernel and
+# cache layout, with the sha256 of the kernel source it was taken on; reported as null once the source changes.
+TRAFFIC = {("raycast", "apron"): {"bytes": 455.87e6 + 18.05e6, "src_sha": "26d0410bb7e630c0"}}
 # FP32 operations per ray-cast sample in the algorithm (FMA = 2): sample position 14, trilinear
 # interpolation of 4 channels 87, transfer function 18, headlight shading 20, compositing 15.
 RAY_FLOPS_PER_SAMPLE = 154
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--layout", choices=["rows", "apron"], default="rows",
+    ap.add_argument("--layout", choices=["rows", "apron"], default="apron",
                     help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
                          "decode)")
@@ -824,7 +824,7 @@ def main():
     kernels["raycast"]["l1_frac"] = kernels["raycast"]["l1_GB_s"] / L1_PEAK_GBS
     dom = max(names, key=lambda n: per[n])
     src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "raycast": "raycast.cu", "adjoint": "contract3.cu"}[dom]
-    tr = TRAFFIC.get(dom)
+    tr = TRAFFIC.get((dom, args.layout))
     traffic = tr["bytes"] if tr and tr["src_sha"] == src_sha(src) else None
     if dom == "raycast":
         achieved = kernels["raycast"]["TFLOP_s"]
@@ -898,7 +898,8 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "layout": args.layout, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
-                           "l2": "inputs larger than L2 (512 MB samples, 2.15 GB cache); no flush",
+                           "l2": f"inputs larger than L2 (512 MB samples, {w.cache.numel() * 4 / 1e9:.2f} GB cache); "
+                                 "no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
