@@ -336,17 +336,19 @@ def run_frames(args):
         counts[f] = len(v)
     lst = torch.zeros(cap, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    cache = torch.empty(cap * n ** 3 * 4, device="cuda")
+    apron = args.layout == "apron"
+    S = mfa.apron_voxels(n) if apron else n ** 3  # cache slot stride (voxels)
+    cache = torch.empty(cap * S * 4, device="cuda")
     lst.copy_(all_lists[0])
     cnt.copy_(counts[0:1])
-    tune = autotune.tune_decode(ctx, blk, cache, n ** 3, cap, list_=lst, count=cnt, flags=mfa.DECODE_LIST_SLOTS,
-                                iters=3, warmup=1)
+    tune = autotune.tune_decode(ctx, blk, cache, S, cap, list_=lst, count=cnt,
+                                flags=mfa.DECODE_LIST_SLOTS | (mfa.DECODE_APRON if apron else 0), iters=3, warmup=1)
     table = torch.zeros(len(bs), dtype=torch.int32, device="cuda")
     tf = torch.from_numpy(synth.transfer_function(seed)).cuda()
     image = torch.empty(IMG, IMG, 4, device="cuda")
     views = [synth.orbit_view(f, fov_y_deg=fov) for f in range(frames)]
-    graphs = [mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True, table=table, brick_dims=(B, B, B),
-                             brick_n=n, view=v, tf=tf, image=image) for v in views]
+    graphs = [mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, table=table, brick_dims=(B, B, B),
+                             brick_n=n, view=v, tf=tf, image=image, apron=apron) for v in views]
     stream = torch.cuda.current_stream()
     for f in range(max(3, args.warmup)):
         lst.copy_(all_lists[f % frames]); cnt.copy_(counts[f % frames: f % frames + 1]); graphs[f % frames].launch()
@@ -369,7 +371,7 @@ def run_frames(args):
     samples = ctx.ray_samples(reset=True) / frames
     ms = [ev[f].elapsed_time(ev[f + 1]) for f in range(frames)]
     # the same frames without the ray cast (ordering + decode only), for the per-stage split
-    dgraph = mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True)
+    dgraph = mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, apron=apron)
     for f in range(3):
         dgraph.launch()
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -390,8 +392,10 @@ def run_frames(args):
             "config": {"workload": "adaptive-NCP frames: 1024^3 flame stand-in, 32768 blocks of 32^3, C in {4..24} by "
                                    "gradient energy, ~6000 visible per frame (32-frame orbit), cost-ordered persistent "
                                    "decode + 1024^2 ray cast replayed from a CUDA graph",
-                       "visible_mean": float(np.mean([len(v) for v in lists])), "tiling": tune},
+                       "layout": args.layout, "visible_mean": float(np.mean([len(v) for v in lists])),
+                       "tiling": tune},
             "stages": {"decode_ms_per_frame": dms, "raycast_ms_per_frame": total / frames - dms,
+                       "raycast_stage": "brick table" + (" + apron fill" if apron else "") + " + ray cast",
                        "ray_samples_per_frame": samples,
                        "raycast_Gsample_s": samples / ((total / frames - dms) * 1e-3) / 1e9,
                        "raycast_TFLOP_s": samples * RAY_FLOPS_PER_SAMPLE / ((total / frames - dms) * 1e-3) / 1e12},
