@@ -712,7 +712,7 @@ def run_outofcore(args):
     tf = torch.from_numpy(synth.transfer_function(seed)).cuda()
     out = {}
     for mode in ("prefetch", "no_prefetch"):
-        ooc = OutOfCoreRenderer(ctx, path, 8000, (B, B, B), n, tf, IMG, IMG)
+        ooc = OutOfCoreRenderer(ctx, path, 8000, (B, B, B), n, tf, IMG, IMG, apron=args.layout == "apron")
         torch.cuda.synchronize()
         stats = []
         t0 = time.perf_counter()
@@ -741,7 +741,8 @@ def run_outofcore(args):
             "config": {"workload": "1024^3 flame stand-in, 32768 micro-models (C in {4..24}) in a store file "
                                    f"({store_mb:.0f} MB written in "
                                    f"{store_s:.1f} s), 8000-model LRU cache, 32-frame orbit, ~6600 visible per frame",
-                       "visible_mean": float(np.mean([len(v) for v in vis])), "store_seconds": store_s},
+                       "layout": args.layout, "visible_mean": float(np.mean([len(v) for v in vis])),
+                       "store_seconds": store_s},
             "modes": out}
     print(json.dumps(line))
     ctx.close()

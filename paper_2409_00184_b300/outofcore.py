@@ -28,17 +28,21 @@ def extrapolate_view(prev, cur):
 class OutOfCoreRenderer:
     """Renders frames of a brick grid whose micro-models live in a store file, through a host LRU cache
     of `capacity` models. brick_dims = (Bx, By, Bz); n = samples per brick axis; model b of the store is
-    brick b (id = (bz*By + by)*Bx + bx)."""
+    brick b (id = (bz*By + by)*Bx + bx). With `apron` the slots use the apron layout (mfa.DECODE_APRON): the
+    decode is followed by the fill of the neighbour planes, and every ray-cast cell of a present brick reads
+    its corners from one slot (the image is the same bit for bit)."""
 
-    def __init__(self, ctx, store_path, capacity, brick_dims, n, tf, width, height, pinned=True, device="cuda"):
-        self.ctx, self.n, self.tf = ctx, n, tf
+    def __init__(self, ctx, store_path, capacity, brick_dims, n, tf, width, height, pinned=True, device="cuda",
+                 apron=True):
+        self.ctx, self.n, self.tf, self.apron = ctx, n, tf, apron
+        self.stride = mfa.apron_voxels(n) if apron else n ** 3  # cache slot stride (voxels)
         self.B = tuple(int(b) for b in brick_dims)
         self.cache = mfa.ModelCache(store_path, capacity, pinned=pinned)
         count, max_ncp, max_degree = self.cache.info()
         if count != self.B[0] * self.B[1] * self.B[2]:
             raise ValueError("the store must hold one model per brick")
         self.batch = mfa.DeviceBatch(capacity, max_ncp, max_degree, device=device)
-        self.slots = torch.empty(capacity * n ** 3 * 4, dtype=torch.float32, device=device)
+        self.slots = torch.empty(capacity * self.stride * 4, dtype=torch.float32, device=device)
         self.table_host = torch.full((self.B[2], self.B[1], self.B[0]), -1, dtype=torch.int32).pin_memory() \
             if pinned else torch.full((self.B[2], self.B[1], self.B[0]), -1, dtype=torch.int32)
         self.table = torch.full((self.B[2], self.B[1], self.B[0]), -1, dtype=torch.int32, device=device)
@@ -63,11 +67,13 @@ class OutOfCoreRenderer:
                                                                                             dtype=torch.int32)
         self.table.copy_(self.table_host, non_blocking=True)
         caching_ns = time.perf_counter_ns() - t0
-        n3 = self.n ** 3
-        mfa.decode_blocks(self.ctx, self.batch, self.slots, n3, len(visible), bounds=self.batch.bounds,
-                          stream=stream)
-        mfa.raycast(self.ctx, self.slots, n3, len(visible), self.table, self.n, view, self.tf, self.image,
-                    stream=stream)
+        S, nv = self.stride, len(visible)
+        mfa.decode_blocks(self.ctx, self.batch, self.slots, S, nv, bounds=self.batch.bounds,
+                          flags=mfa.DECODE_APRON if self.apron else 0, stream=stream)
+        if self.apron:
+            mfa.fill_aprons(self.ctx, self.slots, S, nv, self.table, self.n, stream=stream)
+        mfa.raycast(self.ctx, self.slots, S, nv, self.table, self.n, view, self.tf, self.image, stream=stream,
+                    apron=self.apron)
         self.done.record(stream)
         if predicted is not None:
             self.cache.prefetch_start(np.ascontiguousarray(predicted, dtype=np.int32))

@@ -53,9 +53,11 @@ def test_upload_reproduces_the_stored_models(mfa, ctx, tmp_path):
     cache.close()
 
 
-def test_out_of_core_frames_equal_in_core_frames(mfa, ctx, tmp_path):
+@pytest.mark.parametrize("apron", [True, False])
+def test_out_of_core_frames_equal_in_core_frames(mfa, ctx, tmp_path, apron):
     """128^3 flame, 512 bricks of 16^3 (C in {4, 6, 8, 12}); 6 orbit frames through a 200-model cache with
-    prefetching of the extrapolated next view, against decode + ray cast of the resident models."""
+    prefetching of the extrapolated next view (slots in the apron or the row layout), against decode + ray
+    cast of the resident models in the row layout."""
     from paper_2409_00184_b300.outofcore import OutOfCoreRenderer, extrapolate_view
     N, n, p = 128, 16, 2
     bs, B = flame_blockset(N, n, (4, 6, 8, 12), (50, 75, 90), p, synth.BASE_SEED + 3, "cpu")
@@ -66,7 +68,7 @@ def test_out_of_core_frames_equal_in_core_frames(mfa, ctx, tmp_path):
     views = [synth.orbit_view(f, fov_y_deg=fov, width=48, height=40) for f in range(6)]
     vis = [synth.visible_bricks(v, B) for v in views]
     assert max(len(v) for v in vis) <= 200
-    ooc = OutOfCoreRenderer(ctx, path, 200, (B, B, B), n, tf, 48, 40)
+    ooc = OutOfCoreRenderer(ctx, path, 200, (B, B, B), n, tf, 48, 40, apron=apron)
     blk = mfa.DeviceBlocks(bs)
     cache = torch.empty(200 * n ** 3 * 4, device="cuda")
     table = torch.full((B, B, B), -1, dtype=torch.int32, device="cuda")
