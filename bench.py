@@ -196,23 +196,28 @@ class Workload:
             ev[1].record()
         m.decode_compare_blocks(c, blk, self.cache, self.stride, self.B, D, v, residual=self.R, rmse=self.rmse,
                                 flags=m.DECODE_APRON if self.apron else 0)
+        if ev:
+            ev[2].record()
         if self.apron:
             m.fill_aprons(c, self.cache, self.stride, self.B, self.table, BRICK)
         if ev:
-            ev[2].record()
+            ev[3].record()
         m.raycast(c, self.cache, self.stride, self.B, self.table, BRICK, self.view, self.tf, self.image,
                   apron=self.apron)
         if ev:
-            ev[3].record()
+            ev[4].record()
         m.adjoint_blocks(c, blk, self.R, v, self.B, self.grad)
         if ev:
-            ev[4].record()
+            ev[5].record()
 
 
-def algorithmic_bytes(B):
+def algorithmic_bytes(B, apron):
     """Bytes each kernel must move at minimum per launch on this workload."""
     vox, cp = BRICK ** 3, NCP ** 3
+    n, p = BRICK, BRICK + 1
+    apron_vox = p * p + p * n + n * n  # planes x, y, z = n of one brick
     return {
+        "fill": B * apron_vox * 32 if apron else 0,   # read each apron voxel from a neighbour, write it
         "encode": B * (vox * 4 + cp * 4),              # read samples, write control points
         "decode": B * (vox * (16 + 4 + 4) + cp * 4 + 72 + 8),  # cache float4, read samples, write residual; CPs,
                                                                # descriptor, RMSE
@@ -792,7 +797,7 @@ def main():
 
     # ---- timed region: K steps, per-stage events on the launching stream ----
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     barrier()
@@ -808,7 +813,7 @@ def main():
     clk = clocks.stop()
     samples_per_step = ctx.ray_samples(reset=True) / K
     ms = start.elapsed_time(end) / K
-    names = ["encode", "decode", "raycast", "adjoint"]
+    names = ["encode", "decode", "fill", "raycast", "adjoint"]
     per = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)) for i, n in enumerate(names)}
     ms = max_over_ranks(ms, ws, "cuda")
     st = ctx.device_status()
@@ -819,8 +824,10 @@ def main():
 
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    algo = algorithmic_bytes(w.B)
-    kernels = {n: {"ms": per[n], "GB_s": algo[n] / (per[n] * 1e-3) / 1e9} for n in names}
+    algo = algorithmic_bytes(w.B, w.apron)
+    kernels = {n: {"ms": per[n], "GB_s": algo[n] / (per[n] * 1e-3) / 1e9 if algo[n] else 0.0} for n in names}
+    if not w.apron:
+        del kernels["fill"]
     kernels["decode"]["Gvoxel_s"] = voxels / (per["decode"] * 1e-3) / 1e9
     kernels["raycast"]["Gsample_s"] = samples_per_step / (per["raycast"] * 1e-3) / 1e9
     kernels["raycast"]["samples_per_frame"] = samples_per_step
@@ -828,7 +835,8 @@ def main():
     kernels["raycast"]["l1_GB_s"] = samples_per_step * RAY_L1_BYTES_PER_SAMPLE / (per["raycast"] * 1e-3) / 1e9
     kernels["raycast"]["l1_frac"] = kernels["raycast"]["l1_GB_s"] / L1_PEAK_GBS
     dom = max(names, key=lambda n: per[n])
-    src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "raycast": "raycast.cu", "adjoint": "contract3.cu"}[dom]
+    src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "fill": "apron.cu", "raycast": "raycast.cu",
+           "adjoint": "contract3.cu"}[dom]
     tr = TRAFFIC.get((dom, args.layout))
     traffic = tr["bytes"] if tr and tr["src_sha"] == src_sha(src) else None
     if dom == "raycast":
@@ -842,7 +850,9 @@ def main():
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": traffic,
                     "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"}
-    kernels["decode"]["hbm_frac"] = kernels["decode"]["GB_s"] / hbm
+    for n in ("decode", "fill"):
+        if n in kernels:
+            kernels[n]["hbm_frac"] = kernels[n]["GB_s"] / hbm
 
     # ---- end to end: host samples in pinned memory -> step -> image back to the host ----
     e2e = None
