@@ -142,12 +142,17 @@ def test_raycast_apron_matches_rows_bitwise(mfa, ctx, volume, which):
     assert np.array_equal(rows, apr)
 
 
-def test_raycast_apron_any_brick_size(mfa, ctx):
-    """Bricks of 6^3 (not a power of two: the per-pixel kernel)."""
-    g = synth.rng(15)
-    n, nb = 6, 3
+@pytest.mark.parametrize("holes", [False, True])
+@pytest.mark.parametrize("n", [5, 6])
+def test_raycast_apron_any_brick_size(mfa, ctx, n, holes):
+    """Bricks of 5^3 (pitch 6, no padding column) and 6^3 (pitch 8): not powers of two, the per-pixel
+    kernel; with absent bricks, cells whose own brick is absent read their present neighbours' corners."""
+    g = synth.rng(15 + n)
+    nb = 3
     cache = g.uniform(0, 1, (nb ** 3, n, n, n, 4)).astype(np.float32)
     table = g.permutation(nb ** 3).astype(np.int32).reshape(nb, nb, nb)
+    if holes:
+        table[g.random(table.shape) < 0.3] = -1
     tf = synth.transfer_function(synth.BASE_SEED + 3)
     view = synth.default_view(width=40, height=36)
     rows = _render(mfa, ctx, cache, n ** 3, nb ** 3, table, n, view, tf, False)
