@@ -375,9 +375,10 @@ int mfa_raycast(mfa_ctx* ctx,
  * the addresses of the eight corner loads change. Unknown flags: MFA_ERR_INVALID_ARG. */
 #define MFA_RAYCAST_CUBES 0x1u
 /* MFA_RAYCAST_APRON: the cache bricks carry the one-voxel apron that MFA_DECODE_APRON and
- * mfa_fill_aprons produce (slot_stride_voxels >= A(brick_n+1)^2 with A = brick_n+1 rounded up to
- * even, else MFA_ERR_INVALID_ARG); every cell then reads its eight corners from its own
- * slot. Same image, bit for bit, as mfa_raycast over the same voxels. */
+ * mfa_fill_aprons produce (brick_n <= MFA_MAX_NSAMP and slot_stride_voxels >= A(brick_n+1)^2 with
+ * A = brick_n+1 rounded up to even, else MFA_ERR_INVALID_ARG); every cell of a present brick then
+ * reads its eight corners from its own slot. Same image, bit for bit, as mfa_raycast over the same
+ * voxels. */
 #define MFA_RAYCAST_APRON 0x2u
 int mfa_raycast_ex(mfa_ctx* ctx,
                    const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,

@@ -80,7 +80,8 @@ struct RaycastParams {
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream);
 
-// Apron planes of every brick of a brick table (MFA_DECODE_APRON layout, bricks of n^3 in (n+1)^3).
+// Apron planes of every brick of a brick table (MFA_DECODE_APRON layout: bricks of n^3 voxels in slots of
+// n + 1 planes of n + 1 rows of apron_pitch(n) voxels).
 struct ApronParams {
   float4* cache;
   int64_t slot_stride;

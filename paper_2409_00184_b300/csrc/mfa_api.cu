@@ -340,11 +340,13 @@ int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxel
   if ((flags & ~(MFA_RAYCAST_CUBES | MFA_RAYCAST_APRON)) || ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1)))
     return MFA_ERR_INVALID_ARG;
   if ((flags & MFA_RAYCAST_CUBES) && (flags & MFA_RAYCAST_APRON)) return MFA_ERR_INVALID_ARG;
-  if ((flags & MFA_RAYCAST_APRON) && slot_stride_voxels < (int64_t)apron_pitch(brick_n) * (brick_n + 1) * (brick_n + 1))
-    return MFA_ERR_INVALID_ARG;
   if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
     return MFA_ERR_INVALID_ARG;
   if (brick_n < 2 || slot_stride_voxels < (int64_t)brick_n * brick_n * brick_n || nslots < 0 || tf_n < 2)
+    return MFA_ERR_INVALID_ARG;
+  if ((flags & MFA_RAYCAST_APRON) &&
+      (brick_n > MFA_MAX_NSAMP ||
+       slot_stride_voxels < (int64_t)apron_pitch(brick_n) * (brick_n + 1) * (brick_n + 1)))
     return MFA_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if (brick_dims[a] < 1 || (int64_t)brick_dims[a] * brick_n > (1 << 20)) return MFA_ERR_INVALID_ARG;
