@@ -229,7 +229,11 @@ typedef struct {
 #define MFA_FRAME_SORT_BY_COST 0x1u /* order the visible list by decreasing max(C) first     */
 #define MFA_FRAME_RAYCAST      0x2u /* build the brick table and ray-cast after the decode   */
 #define MFA_FRAME_CUBES        0x4u /* decode into (and ray-cast from) the cube layout        */
-#define MFA_FRAME_APRON        0x8u /* decode with aprons, fill them, ray-cast with aprons    */
+#define MFA_FRAME_APRON        0x8u /* decode into the apron layout; with MFA_FRAME_RAYCAST   */
+                                    /* also fill the aprons and ray-cast with them, which     */
+                                    /* needs slot_stride_voxels >= A(n+1)^2, A = n+1 rounded  */
+                                    /* up to even, n = brick_n (else creation returns         */
+                                    /* MFA_ERR_INVALID_ARG); not with MFA_FRAME_CUBES         */
 
 /* Everything a frame reads; pointers and sizes are fixed when the graph is captured. Per frame
  * the caller writes the visible block ids into d_list[0 .. *d_count) (device memory, count <=
