@@ -223,4 +223,11 @@ def test_apron_argument_checks(mfa, ctx):
     with pytest.raises(mfa.MfaError):
         mfa.raycast(ctx, cache, apron_voxels(8) - 1, 2, table, 8, synth.default_view(width=8, height=8), tf, img,
                     apron=True)
+    # a frame graph that fills and ray-casts with aprons needs the apron slot too (checked at creation)
+    lst = torch.arange(2, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([2], dtype=torch.int32, device="cuda")
+    tab = torch.empty(2, dtype=torch.int32, device="cuda")
+    with pytest.raises(mfa.MfaError):
+        mfa.FrameGraph(ctx, blk, lst, cnt, cache, 8 ** 3, sort=False, table=tab, brick_dims=(2, 1, 1), brick_n=8,
+                       view=synth.default_view(width=8, height=8), tf=tf, image=img, apron=True)
     assert ctx.device_status() == 0
