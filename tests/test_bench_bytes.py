@@ -1,0 +1,31 @@
+"""The algorithmic bytes behind the bench's roofline fractions, checked against their per-unit
+definitions: the decode writes 16 bytes of cache and 4 of residual and reads 4 of samples per voxel,
+plus the control points, the 72-byte descriptor and the 8-byte RMSE sum per block; the apron fill reads
+and writes 16 bytes per apron voxel, and the apron voxels of an n^3 brick are the (n+1)^3 cube less
+its n^3 interior."""
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_fill_bytes_cover_the_three_apron_planes():
+    n = bench.BRICK
+    planes = (n + 1) ** 2 + (n + 1) * n + n * n  # x = n (with its edges), then y = n, then z = n
+    assert planes == (n + 1) ** 3 - n ** 3
+    assert bench.algorithmic_bytes(4096, True)["fill"] == 4096 * planes * 32
+    assert bench.algorithmic_bytes(4096, False)["fill"] == 0
+
+
+def test_decode_and_contraction_bytes_per_block():
+    vox, cp = bench.BRICK ** 3, bench.NCP ** 3
+    b = bench.algorithmic_bytes(1, True)
+    assert b["decode"] == vox * (16 + 4 + 4) + cp * 4 + 72 + 8
+    assert b["encode"] == vox * 4 + cp * 4
+    assert b["adjoint"] == vox * 4 + cp * 4 + 72
+    # the step's 4096 blocks of 32^3 at C = 12: 24.2 bytes per voxel through the decode
+    assert abs(bench.algorithmic_bytes(4096, True)["decode"] / (4096 * vox) - 24.2) < 0.05
