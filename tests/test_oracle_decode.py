@@ -164,3 +164,17 @@ def test_linear_interpolation_special_case():
     assert np.max(np.abs(out[..., 0] - P)) < 1e-13  # n - 1 = 8: knots and FP32 sample params are exact
     # forward difference slope inside each interval: f_u = (n - 1) (P[a+1] - P[a]) on [u_a, u_{a+1})
     assert np.max(np.abs(out[:, :, :-1, 1] - (n - 1) * (P[:, :, 1:] - P[:, :, :-1]))) < 1e-12
+
+
+def test_decode_voxels_matches_decode_block_anisotropic():
+    """Selected voxels (k, j, i) decode to the same rows as the whole-grid decode indexed there, on an
+    anisotropic grid where any swap of the (k, j, i) -> (u, v, w) mapping lands on other samples."""
+    g = synth.rng(43)
+    degrees, ncp, n = (2, 3, 1), (5, 6, 4), (7, 11, 5)
+    knots = tuple(synth.random_clamped_knots(C, p, g, min_gap=0.1) for C, p in zip(ncp, degrees))
+    P = g.uniform(-1, 1, (ncp[2], ncp[1], ncp[0]))
+    full = decode.decode_block(P, knots, degrees, n)
+    kji = np.stack([g.integers(0, n[2], 60), g.integers(0, n[1], 60), g.integers(0, n[0], 60)], axis=1)
+    kji = np.concatenate([kji, [[0, 0, 0], [n[2] - 1, n[1] - 1, n[0] - 1], [n[2] - 1, 0, n[0] - 1]]])
+    sel = decode.decode_voxels(P, knots, degrees, n, kji)
+    assert np.array_equal(sel, full[kji[:, 0], kji[:, 1], kji[:, 2]])

@@ -162,3 +162,48 @@ def test_cross_level_searches_exactly_the_children_of_complex_blocks():
         parent = ((bz // 2) * cB[1] + by // 2) * cB[0] + bx // 2
         assert np.array_equal(fine["searched"], coarse["complex"][parent])
     assert any(r["complex"].any() for r in res) and any((~r["complex"] & r["searched"]).any() for r in res)
+
+
+@pytest.mark.parametrize("delta", [0.3, -2.5e-3])
+def test_rmse_of_a_known_offset(delta):
+    """RMSE (Table 1) of data that differ from the model by +-delta at every sample is exactly |delta|:
+    a sum instead of a mean, a mean over n instead of n^3, or a missing square root all fail."""
+    g = synth.rng(41)
+    degrees, ncp, n = (2, 3, 1), (5, 6, 3), (7, 5, 9)
+    knots = tuple(synth.random_clamped_knots(C, p, g, min_gap=0.1) for C, p in zip(ncp, degrees))
+    P = g.uniform(-1, 1, (ncp[2], ncp[1], ncp[0]))
+    f = decode.decode_block(P, knots, degrees, n)[..., 0]
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    s = np.where((i + 2 * j + 3 * k) % 2 == 0, 1.0, -1.0)
+    assert abs(s.sum()) > 0  # unbalanced: averaging r before squaring would not give |delta| either
+    D = f + delta * s
+    assert abs(encode.rmse(P, D, knots, degrees) - abs(delta)) < 1e-14
+
+
+def test_rmse_golden_trilinear():
+    """A residual worked by hand on a 3x2x2 trilinear model (tests/golden/rmse_trilinear_3x2x2.txt)."""
+    path = os.path.join(GOLDEN, "rmse_trilinear_3x2x2.txt")
+    rows = np.loadtxt(path)
+    expected = float([ln for ln in open(path) if ln.startswith("# rmse")][0].split()[2])
+    D = np.zeros((2, 2, 3))
+    for k, j, i, v in rows:
+        D[int(k), int(j), int(i)] = v
+    P = np.array([[[1 + 2 * a + 3 * b + 4 * c for a in (0, 1)] for b in (0, 1)] for c in (0, 1)], dtype=float)
+    knots = (np.array([0.0, 0.0, 1.0, 1.0]),) * 3
+    assert abs(encode.rmse(P, D, knots, (1, 1, 1)) - expected) < 1e-15
+
+
+def test_fit_separable_batch_matches_per_block_and_dense():
+    """The batched fit equals the per-block separable fit on every block, and the dense Kronecker
+    least squares (the definition) on tiny blocks."""
+    g = synth.rng(42)
+    degrees, ncp, n = (2, 1, 3), (4, 3, 5), (6, 5, 8)
+    knots = tuple(synth.random_clamped_knots(C, p, g, min_gap=0.1) for C, p in zip(ncp, degrees))
+    D = g.uniform(-1, 1, (5, n[2], n[1], n[0]))
+    Pb = encode.fit_separable_batch(D, knots, degrees)
+    assert Pb.shape == (5, ncp[2], ncp[1], ncp[0])
+    for b in range(len(D)):
+        Ps = encode.fit_separable(D[b], knots, degrees)
+        Pd = encode.fit_dense(D[b], knots, degrees)
+        assert np.max(np.abs(Pb[b] - Ps)) < 1e-12
+        assert np.max(np.abs(Pb[b] - Pd)) < 1e-10
