@@ -55,6 +55,29 @@ def evaluate_points(P, knots, degrees, uvw):
     return out
 
 
+def evaluate_points_multi(Ps, which, knots, degrees, uvw):
+    """:func:`evaluate_points` for points that belong to several blocks with the same knots and degrees.
+
+    Ps: (B, C_z, C_y, C_x) control points of the blocks; which: (M,) block of each point. Returns (M, 4)."""
+    Ps = np.asarray(Ps, dtype=np.float64)
+    which = np.asarray(which, dtype=np.int64)
+    uvw = np.atleast_2d(np.asarray(uvw, dtype=np.float64))
+    (tx, ty, tz), (px, py, pz) = knots, degrees
+    ox, Nx, dNx = _axis_terms(tx, px, uvw[:, 0])
+    oy, Ny, dNy = _axis_terms(ty, py, uvw[:, 1])
+    oz, Nz, dNz = _axis_terms(tz, pz, uvw[:, 2])
+    out = np.zeros((len(uvw), 4))
+    for dc in range(pz + 1):
+        for db in range(py + 1):
+            for da in range(px + 1):
+                cp = Ps[which, oz + dc, oy + db, ox + da]
+                out[:, 0] += Nx[:, da] * Ny[:, db] * Nz[:, dc] * cp
+                out[:, 1] += dNx[:, da] * Ny[:, db] * Nz[:, dc] * cp
+                out[:, 2] += Nx[:, da] * dNy[:, db] * Nz[:, dc] * cp
+                out[:, 3] += Nx[:, da] * Ny[:, db] * dNz[:, dc] * cp
+    return out
+
+
 def evaluate_points_dense(P, knots, degrees, uvw):
     """Same as :func:`evaluate_points` but summing every control point's term (all C^3)."""
     P = np.asarray(P, dtype=np.float64)

@@ -36,6 +36,7 @@ import math
 
 import numpy as np
 
+from . import bspline as _bspline
 from . import decode as _decode
 
 f32 = np.float32
@@ -97,7 +98,10 @@ def ray_setup(view, nodes):
 
 
 def fetch(cache, table, brick_n, g):
-    """Trilinear (f, f_u, f_v, f_w) at voxel coordinates g (M, 3) = (gx, gy, gz), FP64."""
+    """Trilinear (f, f_u, f_v, f_w) at voxel coordinates g (M, 3) = (gx, gy, gz), FP64.
+
+    cache is an array (slots, n, n, n, 4), or a function voxels(slot, iz, iy, ix) -> (M, 4) that gives the
+    nodes of the listed slots on demand (for volumes too large to decode in full)."""
     Bz, By, Bx = table.shape
     N = np.array([Bx * brick_n, By * brick_n, Bz * brick_n])
     g = np.clip(g, 0.0, (N - 1).astype(np.float64))
@@ -111,11 +115,44 @@ def fetch(cache, table, brick_n, g):
                 slot = table[iz // brick_n, iy // brick_n, ix // brick_n]
                 val = np.zeros((len(g), 4))
                 ok = slot >= 0
-                val[ok] = cache[slot[ok], iz[ok] % brick_n, iy[ok] % brick_n, ix[ok] % brick_n]
+                at = (slot[ok], iz[ok] % brick_n, iy[ok] % brick_n, ix[ok] % brick_n)
+                val[ok] = cache(*at) if callable(cache) else cache[at]
                 wt = ((w[:, 0] if dx else 1 - w[:, 0]) * (w[:, 1] if dy else 1 - w[:, 1])
                       * (w[:, 2] if dz else 1 - w[:, 2]))
                 out += wt[:, None] * val
     return out
+
+
+def decoded_nodes(groups, nslots):
+    """A cache given as a function (see :func:`fetch`): the nodes of decoded micro-models, computed on demand.
+
+    groups: list of (slots, Ps, knots, degrees, nsamp), the models of one group sharing knots, degrees and
+    sample grid; Ps (len(slots), C_z, C_y, C_x) holds the control points of the model in each listed slot.
+    A node (iz, iy, ix) of a slot is the model's value and parametric gradient at its sample parameters
+    (the decode of :mod:`oracle.decode`), rounded to FP32 as a cache stores it."""
+    group = np.full(nslots, -1, dtype=np.int64)
+    row = np.zeros(nslots, dtype=np.int64)
+    params = []
+    for gi, (slots, Ps, knots, degrees, nsamp) in enumerate(groups):
+        slots = np.asarray(slots, dtype=np.int64)
+        group[slots] = gi
+        row[slots] = np.arange(len(slots))
+        params.append(tuple(_bspline.sample_params(m) for m in nsamp))
+
+    def voxels(slot, iz, iy, ix):
+        out = np.zeros((len(slot), 4))
+        g = group[slot]
+        for gi in np.unique(g):
+            if gi < 0:
+                raise ValueError("a slot outside every group")
+            sel = g == gi
+            _, Ps, knots, degrees, _ = groups[gi]
+            ux, uy, uz = params[gi]
+            uvw = np.stack([ux[ix[sel]], uy[iy[sel]], uz[iz[sel]]], axis=1)
+            out[sel] = _decode.evaluate_points_multi(Ps, row[slot[sel]], knots, degrees, uvw)
+        return out.astype(np.float32).astype(np.float64)
+
+    return voxels
 
 
 def transfer(tf, f, vmin, vmax):
@@ -127,11 +164,14 @@ def transfer(tf, f, vmin, vmax):
     return tf[i0] * (1 - w) + tf[i0 + 1] * w
 
 
-def raycast(cache, table, brick_n, view, tf):
-    """Render an (H, W, 4) premultiplied RGBA image; cache: (slots, n, n, n, 4) as (f, f_u, f_v, f_w)."""
-    cache = np.asarray(cache, dtype=np.float64)
+def raycast(cache, table, brick_n, view, tf, pixels=None):
+    """Render an (H, W, 4) premultiplied RGBA image; cache: (slots, n, n, n, 4) as (f, f_u, f_v, f_w), or a
+    function of (slot, iz, iy, ix) as in :func:`fetch`. With pixels (flat indices y * W + x), only those rays
+    are marched and their (M, 4) colours returned, in the order given."""
+    if not callable(cache):
+        cache = np.asarray(cache, dtype=np.float64)
     table = np.asarray(table)
-    return _march(table.shape, brick_n, view, tf, lambda g: fetch(cache, table, brick_n, g))
+    return _march(table.shape, brick_n, view, tf, lambda g: fetch(cache, table, brick_n, g), pixels)
 
 
 def fetch_direct(blocks, table, brick_n, g):
@@ -171,8 +211,9 @@ def raycast_direct(blocks, table, brick_n, view, tf):
     return _march(table.shape, brick_n, view, tf, lambda g: fetch_direct(blocks, table, brick_n, g))
 
 
-def _march(table_shape, brick_n, view, tf, sample):
-    """Front-to-back marching of every pixel's ray; sample(g) gives (f, f_u, f_v, f_w) at voxel coords g."""
+def _march(table_shape, brick_n, view, tf, sample, pixels=None):
+    """Front-to-back marching of every pixel's ray (or of the listed pixels' rays only); sample(g) gives
+    (f, f_u, f_v, f_w) at voxel coords g."""
     tf = np.asarray(tf, dtype=np.float64)
     Bz, By, Bx = table_shape
     nodes = (Bx * brick_n, By * brick_n, Bz * brick_n)
@@ -181,6 +222,9 @@ def _march(table_shape, brick_n, view, tf, sample):
     d = d.reshape(-1, 3).astype(np.float64)
     t0 = t0.ravel().astype(np.float64)
     K = K.ravel()
+    if pixels is not None:  # march a subset of the rays: the per-ray set-up above is unchanged
+        pixels = np.asarray(pixels, dtype=np.int64).ravel()
+        d, t0, K = d[pixels], t0[pixels], K[pixels]
     eye = eye.astype(np.float64)
     dt = float(dt)
     step = float(np.float32(view.get("step_voxels", 1.0)))
@@ -191,8 +235,9 @@ def _march(table_shape, brick_n, view, tf, sample):
     half = np.array([(n - 1) / 2.0 for n in nodes])
     gscale = half / (brick_n - 1)  # d(world)/d(param): parametric gradient -> world gradient
 
-    color = np.zeros((H * W, 3))
-    alpha = np.zeros(H * W)
+    M = len(K)
+    color = np.zeros((M, 3))
+    alpha = np.zeros(M)
     active = K > 0
     k = 0
     while active.any():
@@ -216,4 +261,5 @@ def _march(table_shape, brick_n, view, tf, sample):
         alpha[idx] += wgt
         k += 1
         active[idx] = (k < K[idx]) & (alpha[idx] <= omax)
-    return np.concatenate([color, alpha[:, None]], axis=1).reshape(H, W, 4)
+    out = np.concatenate([color, alpha[:, None]], axis=1)
+    return out if pixels is not None else out.reshape(H, W, 4)

@@ -42,3 +42,27 @@ def gm_blocks_fitted(N, n, C, p, seed, device="cpu"):
     bs = synth.make_block_set([(C, C, C)] * B, [(p, p, p)] * B, [(n, n, n)] * B, list(P),
                               knots_list=[knots] * B)
     return bs, blocks
+
+
+def oracle_fit_all(blocks, C, p, chunk=256):
+    """Oracle least-squares control points (FP64) of every block of a (B, n, n, n) array, clamped uniform
+    knots read in FP32 as the library reads them; chunked to bound host memory."""
+    knots = tuple(np.float32(synth.clamped_uniform_knots(C, p)).astype(np.float64) for _ in range(3))
+    out = [encode.fit_separable_batch(np.asarray(blocks[i:i + chunk], dtype=np.float64), knots, (p, p, p))
+           for i in range(0, len(blocks), chunk)]
+    return np.concatenate(out)
+
+
+def node_groups(bs, slots_of=None):
+    """Groups for oracle.raycast.decoded_nodes: the BlockSet's blocks grouped by (knots, degree, grid); the
+    slot of block b is slots_of[b] (default: b)."""
+    keys = {}
+    for b in range(len(bs)):
+        k = (tuple(bs.knot_off[b]), tuple(bs.degree[b]), tuple(bs.ncp[b]), tuple(bs.nsamp[b]))
+        keys.setdefault(k, []).append(b)
+    groups = []
+    for k, ids in keys.items():
+        Ps = np.stack([bs.block_cps(b) for b in ids])
+        slots = np.asarray(ids if slots_of is None else [slots_of[b] for b in ids], dtype=np.int64)
+        groups.append((slots, Ps, bs.block_knots(ids[0]), tuple(int(x) for x in k[1]), tuple(int(x) for x in k[3])))
+    return groups

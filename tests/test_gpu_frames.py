@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import synth
-from gpu_util import TOL_FP32, rel_errors
+from gpu_util import TOL_FP32, node_groups, rel_errors
 from oracle import decode as odec
 from oracle import raycast as ocast
 
@@ -82,9 +82,9 @@ def test_frames_reduced_config3(mfa, ctx):
         tab = np.full(len(bs), -1, np.int32)
         tab[order] = np.arange(len(order), dtype=np.int32)
         assert np.array_equal(table.cpu().numpy(), tab)
-        # ray cast of the frame against the oracle's Algorithm 4 over the same FP32 cache
+        # ray cast of the frame against the oracle's Algorithm 4 over the oracle's decode (rounded to FP32)
         got = image.cpu().numpy()
-        want_img = ocast.raycast(c.reshape(cap, n, n, n, 4), tab.reshape(B, B, B), n, v, tf.cpu().numpy())
+        want_img = ocast.raycast(want_cache.astype(np.float32), tab.reshape(B, B, B), n, v, tf.cpu().numpy())
         d = np.abs(got - want_img).max(axis=-1)
         assert d.max() <= 1e-2 and (d <= 1e-4).mean() >= 0.999
     for g in graphs:
@@ -125,6 +125,49 @@ def test_frames_full_config3_sampled(mfa, ctx):
         ve, ge = rel_errors(np.concatenate(got), np.concatenate(want))
         assert ve <= TOL_FP32 and max(ge) <= TOL_FP32, (frame, ve, ge)
     g.close()
+
+
+def test_frame_full_config3_raycast_sampled_pixels(mfa, ctx):
+    """One frame of the adaptive-NCP workload as it is benchmarked: 1024^3 flame field, 32768 bricks with C in
+    {4..24}, ~6600 visible, cost-ordered decode into the apron layout, brick table, apron fill and 1024^2 ray
+    cast (O_max = 0.99) replayed from the frame graph; 2000 seeded pixels against the oracle's Algorithm 4
+    over its own decode of the visible models."""
+    N, n, p = 1024, 32, 2
+    seed = synth.BASE_SEED + 3
+    bs, B = flame_blockset(N, n, synth.FLAME_NCP_CLASSES, synth.FLAME_NCP_PERCENTILES, p, seed, "cuda")
+    torch.cuda.empty_cache()
+    blk = mfa.DeviceBlocks(bs)
+    fov = synth.fov_for_visible(6000, B)
+    view = synth.orbit_view(3, fov_y_deg=fov)
+    vis = synth.visible_bricks(view, B)
+    cap = len(vis)
+    S = mfa.apron_voxels(n)
+    lst = torch.from_numpy(vis.astype(np.int32)).cuda()
+    cnt = torch.tensor([len(vis)], dtype=torch.int32, device="cuda")
+    cache = torch.empty(cap * S * 4, device="cuda")
+    table = torch.zeros(len(bs), dtype=torch.int32, device="cuda")
+    tf = synth.transfer_function(seed)
+    image = torch.full((view["height"], view["width"], 4), float("nan"), device="cuda")
+    g = mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, table=table, brick_dims=(B, B, B), brick_n=n,
+                       view=view, tf=torch.from_numpy(tf).cuda(), image=image, apron=True)
+    g.launch()
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    got = image.view(-1, 4).cpu().numpy()
+    g.close()
+    del cache
+    assert not np.isnan(got).any()
+    tab = np.full(len(bs), -1, np.int32)
+    tab[vis] = vis  # the oracle's slots are the block ids
+    sub = synth.make_block_set(bs.ncp[vis], bs.degree[vis], bs.nsamp[vis], [bs.block_cps(b) for b in vis])
+    voxels = ocast.decoded_nodes(node_groups(sub, slots_of=vis), len(bs))
+    pix = synth.rng(72).choice(view["width"] * view["height"], 2000, replace=False)
+    want = ocast.raycast(voxels, tab.reshape(B, B, B), n, view, tf, pixels=pix)
+    d = np.abs(got[pix] - want).max(axis=-1)
+    print(f"config-3 frame, {len(vis)} visible, 2000 pixels: max {d.max():.2e}, within 1e-4: {(d <= 1e-4).mean():.4f},"
+          f" lit: {(want[:, 3] > 0).mean():.3f}")
+    assert (want[:, 3] > 0).mean() > 0.3
+    assert d.max() <= 1e-2 and (d <= 1e-4).mean() >= 0.999
 
 
 def test_autotuner_installs_a_tiling_and_keeps_parity(mfa, ctx, tmp_path):

@@ -178,3 +178,17 @@ def test_decode_voxels_matches_decode_block_anisotropic():
     kji = np.concatenate([kji, [[0, 0, 0], [n[2] - 1, n[1] - 1, n[0] - 1], [n[2] - 1, 0, n[0] - 1]]])
     sel = decode.decode_voxels(P, knots, degrees, n, kji)
     assert np.array_equal(sel, full[kji[:, 0], kji[:, 1], kji[:, 2]])
+
+
+def test_evaluate_points_multi_matches_per_block():
+    """Points of several blocks evaluated together equal each block's own evaluation."""
+    g = synth.rng(44)
+    degrees, ncp = (3, 2, 1), (6, 4, 5)
+    knots = tuple(synth.random_clamped_knots(C, p, g, min_gap=0.1) for C, p in zip(ncp, degrees))
+    Ps = g.uniform(-1, 1, (4, ncp[2], ncp[1], ncp[0]))
+    uvw = np.concatenate([g.uniform(0, 1, (50, 3)), [[0, 0, 0], [1, 1, 1], [1, 0, 1]]])
+    which = g.integers(0, 4, len(uvw))
+    got = decode.evaluate_points_multi(Ps, which, knots, degrees, uvw)
+    for b in range(4):
+        sel = which == b
+        assert np.array_equal(got[sel], decode.evaluate_points(Ps[b], knots, degrees, uvw[sel]))

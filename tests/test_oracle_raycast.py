@@ -205,3 +205,65 @@ def test_direct_and_cache_renders_agree_on_linear_fields():
     b = raycast.raycast_direct(blocks, table, n, view, tf)
     assert np.max(np.abs(a - b)) < 1e-12
     assert a[..., 3].max() > 0.1
+
+
+def _mixed_volume(seed, B=3, n=6):
+    g = synth.rng(seed)
+    table = g.permutation(B ** 3).astype(np.int32).reshape(B, B, B)
+    table[g.random(table.shape) < 0.2] = -1
+    cache = np.zeros((B ** 3, n, n, n, 4))
+    cache[..., 0] = g.uniform(0, 1, cache.shape[:-1])
+    cache[..., 1:] = g.uniform(-2, 2, cache.shape[:-1] + (3,))
+    return cache, table, n
+
+
+def test_pixel_subset_equals_full_render():
+    """Marching only some rays gives exactly those pixels of the full render, with and without early
+    termination (the per-ray set-up and the sample sequence of a ray do not depend on the other rays)."""
+    cache, table, n = _mixed_volume(51)
+    tf = synth.transfer_function(5)
+    tf[:, 3] = np.clip(tf[:, 3] * 8, 0, 1)
+    for omax in (1.0, 0.9):
+        view = synth.default_view(width=23, height=17, opacity_max=omax)
+        full = raycast.raycast(cache, table, n, view, tf).reshape(-1, 4)
+        pix = synth.rng(52).choice(23 * 17, 60, replace=False)
+        sub = raycast.raycast(cache, table, n, view, tf, pixels=pix)
+        assert sub.shape == (60, 4)
+        assert np.array_equal(sub, full[pix])
+        assert (full[:, 3] > 0).sum() > 100
+
+
+def test_voxel_function_equals_cache_array():
+    """A cache given as a function of (slot, iz, iy, ix) renders the same image as the array it reads."""
+    cache, table, n = _mixed_volume(53)
+    tf = synth.transfer_function(6)
+    view = synth.default_view(width=19, height=13, opacity_max=0.95)
+    calls = []
+
+    def voxels(slot, iz, iy, ix):
+        calls.append(len(slot))
+        return cache[slot, iz, iy, ix]
+
+    a = raycast.raycast(cache, table, n, view, tf)
+    b = raycast.raycast(voxels, table, n, view, tf)
+    assert calls and np.array_equal(a, b)
+
+
+def test_decoded_nodes_equal_block_decodes():
+    """The on-demand node source returns each slot's decode (oracle.decode.decode_block) at the requested
+    nodes, rounded to FP32, for two groups of models with different knots, degrees and grids."""
+    from oracle import decode
+    g = synth.rng(54)
+    groups, full = [], {}
+    for slots, degrees, ncp, n in (([4, 0, 2], (2, 2, 2), (5, 5, 5), (6, 6, 6)), ([1, 3], (3, 1, 2), (4, 3, 5), (6, 6, 6))):
+        knots = tuple(synth.random_clamped_knots(C, p, g, min_gap=0.1) for C, p in zip(ncp, degrees))
+        Ps = g.uniform(-1, 1, (len(slots), ncp[2], ncp[1], ncp[0]))
+        groups.append((slots, Ps, knots, degrees, n))
+        for m, s in enumerate(slots):
+            full[s] = decode.decode_block(Ps[m], knots, degrees, n).astype(np.float32)
+    voxels = raycast.decoded_nodes(groups, 5)
+    slot = g.integers(0, 5, 400)
+    iz, iy, ix = g.integers(0, 6, 400), g.integers(0, 6, 400), g.integers(0, 6, 400)
+    got = voxels(slot, iz, iy, ix)
+    want = np.stack([full[s][z, y, x] for s, z, y, x in zip(slot, iz, iy, ix)]).astype(np.float64)
+    assert np.array_equal(got, want)
