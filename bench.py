@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-frames", action="store_true", help="leave out the adaptive-NCP frames sub-record")
     ap.add_argument("--layout", choices=["rows", "apron"], default="apron",
                     help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
@@ -221,7 +222,7 @@ def algorithmic_bytes(B, apron):
         "encode": B * (vox * 4 + cp * 4),              # read samples, write control points
         "decode": B * (vox * (16 + 4 + 4) + cp * 4 + 72 + 8),  # cache float4, read samples, write residual; CPs,
                                                                # descriptor, RMSE
-        "raycast": IMG * IMG * 16,                      # image write; cache reads are counted as traffic, not here
+        "raycast": IMG * IMG * 16,                      # image write; the step adds the cache sectors it reads
         "adjoint": B * (vox * 4 + cp * 4 + 72),        # read the residual, write the gradient
     }
 
@@ -253,73 +254,253 @@ def check_against_oracle(w, nblocks=12, nvox=400, seed=5):
             "normalisation": "value: max|df|/range(f); grad: max|d grad|/max|grad|; cps: max|dP|/range(P)"}
 
 
-def oracle_sample_time(D_blocks):
-    """Times the FP64 oracle (fit + decode + adjoint) on the given host sample blocks.
-
-    Returns (wall seconds, cores used) where cores = process CPU time / wall time (numpy may run
-    some library calls on several threads)."""
+def _oracle_blocks(D_blocks):
+    """The FP64 oracle's fit + decode + adjoint of each host block; returns the process CPU seconds."""
     from oracle import adjoint as oadj
     from oracle import decode as odec
     from oracle import encode as oenc
     knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
     deg, ns, nc = (DEGREE,) * 3, (BRICK,) * 3, (NCP,) * 3
-    t0, c0 = time.perf_counter(), time.process_time()
+    c0 = time.process_time()
     for Db in D_blocks:
         P = oenc.fit_separable(Db, knots, deg)
         f = odec.decode_block(P, knots, deg, ns)
         oadj.adjoint_block(f[..., 0] - Db, knots, deg, nc)
-    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-    return wall, max(1, round(cpu / wall))
+    return time.process_time() - c0
 
 
-def host_sample(seed, nblocks):
-    """The first `nblocks` blocks of the workload's field, generated on the host."""
+_WORKER_P = None
+
+
+def _set_worker_cps(P):
+    global _WORKER_P
+    _WORKER_P = P
+
+
+def _node_key(slot, iz, iy, ix):
+    n = BRICK
+    return ((np.asarray(slot, np.int64) * n + iz) * n + iy) * n + ix
+
+
+def _oracle_record(args):
+    """The oracle's Algorithm 4 over the listed pixels of the step's view, with the nodes decoded on demand
+    from the worker's control points (FP32 as the cache holds them); returns every node the rays read
+    (sorted keys, their values) and the pixels' colours. Not timed: it builds the sparse cache that the
+    timed ray cast reads."""
+    pixels, seed = args
+    from oracle import raycast as ocast
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
+    B = len(_WORKER_P)
+    nb = N_FIELD // BRICK
+    voxels = ocast.decoded_nodes([(np.arange(B), _WORKER_P, knots, (DEGREE,) * 3, (BRICK,) * 3)], B)
+    keys, vals = [], []
+
+    def recording(slot, iz, iy, ix):
+        v = voxels(slot, iz, iy, ix)
+        keys.append(_node_key(slot, iz, iy, ix))
+        vals.append(v)
+        return v
+
+    table = np.arange(B, dtype=np.int32).reshape(nb, nb, nb)
+    img = ocast.raycast(recording, table, BRICK, synth.default_view(IMG, IMG), synth.transfer_function(seed),
+                        pixels=pixels)
+    k = np.concatenate(keys) if keys else np.zeros(0, np.int64)
+    v = np.concatenate(vals) if vals else np.zeros((0, 4))
+    uk, first = np.unique(k, return_index=True)
+    return uk, v[first], img
+
+
+def _oracle_rays(args):
+    """The oracle's Algorithm 4 over the listed pixels, reading the nodes recorded by _oracle_record (a cache
+    of the decoded nodes the rays touch); returns ((M, 4) colours, process CPU seconds of the ray cast)."""
+    pixels, seed, uk, uv = args
+    from oracle import raycast as ocast
+    nb = N_FIELD // BRICK
+
+    def lookup(slot, iz, iy, ix):
+        return uv[np.searchsorted(uk, _node_key(slot, iz, iy, ix))]
+
+    table = np.arange(nb ** 3, dtype=np.int32).reshape(nb, nb, nb)
+    c0 = time.process_time()
+    img = ocast.raycast(lookup, table, BRICK, synth.default_view(IMG, IMG), synth.transfer_function(seed),
+                        pixels=pixels)
+    return img, time.process_time() - c0
+
+
+class OraclePool:
+    """The oracle run on every host core: a pool of single-threaded worker processes (spawned, so that no
+    worker inherits the parent's CUDA state), each taking whole blocks or whole rays. With cores = 1 the
+    work runs in this process."""
+
+    def __init__(self, cores, P_all):
+        self.cores = max(1, int(cores))
+        self.pool = None
+        _set_worker_cps(P_all)
+        if self.cores > 1:
+            import multiprocessing as mp
+            keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+            for k in keep:
+                os.environ[k] = "1"  # one BLAS thread per worker; the workers read it when they start
+            try:
+                self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_set_worker_cps, initargs=(P_all,))
+            finally:
+                for k, v in keep.items():
+                    if v is None:
+                        os.environ.pop(k, None)
+                    else:
+                        os.environ[k] = v
+
+    def blocks(self, D_blocks):
+        """Wall seconds of fit + decode + adjoint of every block."""
+        t0 = time.perf_counter()
+        if self.pool is None:
+            _oracle_blocks(D_blocks)
+        else:
+            parts = [D_blocks[i::self.cores] for i in range(self.cores)]
+            self.pool.map(_oracle_blocks, [p for p in parts if len(p)])
+        return time.perf_counter() - t0
+
+    def prepare_rays(self, pixels, seed):
+        """Splits the pixels over the workers and records the nodes each part's rays read (untimed)."""
+        self.parts = [pixels[i::self.cores] for i in range(self.cores)]
+        args = [(q, seed) for q in self.parts]
+        self.tables = [_oracle_record(a) for a in args] if self.pool is None else self.pool.map(_oracle_record, args)
+        self.npix, self.seed = len(pixels), seed
+
+    def rays(self):
+        """(colours of the prepared pixels, wall seconds) of the oracle ray cast over the recorded nodes."""
+        args = [(q, self.seed, t[0], t[1]) for q, t in zip(self.parts, self.tables)]
+        t0 = time.perf_counter()
+        outs = [_oracle_rays(a) for a in args] if self.pool is None else self.pool.map(_oracle_rays, args)
+        wall = time.perf_counter() - t0
+        img = np.zeros((self.npix, 4))
+        for i, ((o, _), t) in enumerate(zip(outs, self.tables)):
+            assert np.array_equal(o, t[2])  # the recorded nodes give the same render
+            img[i::self.cores] = o
+        return img, wall
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def oracle_fit_all(D_blocks):
+    """The oracle's least-squares control points of every block (FP64; the batched fit)."""
+    from oracle import encode as oenc
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
+    D = np.asarray(D_blocks)
+    return np.concatenate([oenc.fit_separable_batch(D[i:i + 256].astype(np.float64), knots, (DEGREE,) * 3)
+                           for i in range(0, len(D), 256)])
+
+
+def oracle_step_estimate(pool, D_sample):
+    """Seconds the oracle takes for one step, from a bounded sample: fit + decode + adjoint of the sample
+    blocks scaled to all blocks, plus the ray cast of the prepared pixels (over the decoded nodes they read)
+    scaled to the image. Also returns the sampled pixels' colours."""
+    B = (N_FIELD // BRICK) ** 3
+    tb = pool.blocks(D_sample)
+    img, tr = pool.rays()
+    return tb * B / len(D_sample) + tr * (IMG * IMG) / pool.npix, img
+
+
+def host_blocks(seed):
+    """Every block of the workload's field (generated on the device), as host float32 (B, n, n, n)."""
     field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
-    blocks = synth.blocks_from_field(field, BRICK)
-    idx = synth.rng(seed + 1).choice(blocks.shape[0], nblocks, replace=False)
-    out = [blocks[int(i)].double().cpu().numpy() for i in idx]
-    del field, blocks
+    blocks = synth.blocks_from_field(field, BRICK).cpu().numpy()
+    del field
     torch.cuda.empty_cache()
-    return out
+    return blocks
+
+
+def oracle_baselines(w, seed, timed=True):
+    """The oracle beside the step: its per-step time on one host core and on every host core (bounded
+    samples of blocks and pixels, scaled to the step), and the error of the step's image against the
+    oracle's render of the same pixels (the oracle's own fit, decode and ray cast of the step's samples)."""
+    blocks = w.D.view(w.B, BRICK, BRICK, BRICK).cpu().numpy()
+    P_all = oracle_fit_all(blocks)
+    g = synth.rng(seed + 1)
+    voxels = w.B * w.vox
+    cpu, runs = None, {}
+    ncpu = os.cpu_count() or 1
+    for cores in ((1, ncpu) if timed else (ncpu,)):
+        pool = OraclePool(cores, P_all)
+        D_sample = [blocks[int(i)].astype(np.float64) for i in g.choice(w.B, 16 * pool.cores, replace=False)]
+        pixels = g.choice(IMG * IMG, 256 * pool.cores, replace=False)
+        pool.prepare_rays(pixels, seed)
+        t, img = oracle_step_estimate(pool, D_sample)
+        pool.close()
+        runs[cores] = (t, img, pixels, len(D_sample))
+    t, img, pixels, nb = runs[ncpu]
+    got = w.image.view(-1, 4)[torch.as_tensor(pixels, device=w.image.device)].double().cpu().numpy()
+    d = np.abs(got - img).max(axis=1)
+    img_err = {"max": float(d.max()), "within_1e-4": float((d <= 1e-4).mean()), "pixels": len(pixels),
+               "normalisation": "max |dRGBA| over the sampled pixels (O_max 0.99), against the oracle's fit + "
+                                "decode + Algorithm 4 of the same samples"}
+    if timed:
+        t1, _, px1, nb1 = runs[1]
+        cpu = {"value": voxels / t / 1e9, "unit": "Gvoxel/s", "cores": ncpu, "kind": "oracle",
+               "single_core": {"value": voxels / t1 / 1e9, "unit": "Gvoxel/s", "cores": 1,
+                               "sample": f"{nb1} blocks, {len(px1)} pixels"},
+               "sample": f"FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks and Algorithm 4 over {len(pixels)} "
+                         f"of the 1024^2 pixels (over the oracle's decoded nodes those rays read), each scaled to the "
+                         f"whole step ({t:.0f} s per step on {ncpu} worker processes; {t1:.0f} s on one core)"}
+    return cpu, img_err
 
 
 def run_reference(args, ws, rank):
+    """The oracle on the host cores, on the step's workload: per step, fit + decode + adjoint of a sample of
+    the blocks and the ray cast of a sample of the pixels, each scaled to the whole step."""
     if rank != 0:
         return 0
-    torch.cuda.set_device(0)
     seed = synth.BASE_SEED + 2
+    torch.cuda.set_device(0)
+    blocks = host_blocks(seed)
+    P_all = oracle_fit_all(blocks)
+    pool = OraclePool(os.cpu_count() or 1, P_all)  # spawned workers: none inherits this process's CUDA state
+    g = synth.rng(seed + 1)
     budget = 150.0  # seconds for the whole run
     per_step = budget / max(1, args.steps + args.warmup)
-    probe = host_sample(seed, 2)
-    t1 = oracle_sample_time(probe)[0] / 2
-    nb = max(1, int(per_step / t1))
-    sample = host_sample(seed, nb)
+    # probe: seconds per block on one core; the ray sample is 256 pixels per core (their nodes recorded once)
+    t_b = pool.blocks([blocks[i].astype(np.float64) for i in range(pool.cores)])
+    pixels = g.choice(IMG * IMG, 256 * pool.cores, replace=False)
+    pool.prepare_rays(pixels, seed)
+    t_r = pool.rays()[1]
+    nb = max(pool.cores, int(max(0.0, per_step - t_r) / t_b) * pool.cores)
+    nr = len(pixels)
+    sample = [blocks[int(i)].astype(np.float64) for i in g.choice(len(blocks), nb, replace=False)]
     for _ in range(args.warmup):
-        oracle_sample_time(sample)
-    runs = [oracle_sample_time(sample) for _ in range(args.steps)]
-    dt = sum(r[0] for r in runs) / len(runs)
-    cores = max(r[1] for r in runs)
-    value = nb * BRICK ** 3 / dt / 1e9
+        oracle_step_estimate(pool, sample)
+    runs = [oracle_step_estimate(pool, sample)[0] for _ in range(args.steps)]
+    pool.close()
+    dt = sum(runs) / len(runs)
+    value = len(blocks) * BRICK ** 3 / dt / 1e9
+    sample_desc = (f"per step: FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks and Algorithm 4 over "
+                   f"{nr} of the 1024^2 pixels (reading the oracle's decoded nodes, recorded once), each scaled to "
+                   f"the whole step; {pool.cores} worker processes")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "blocks": (N_FIELD // BRICK) ** 3, "sample_blocks_per_step": nb},
-            "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
-                             "sample": f"FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks per step "
-                                       "(ray cast not in the sample)"},
+            "config": {"workload": WORKLOAD, "blocks": len(blocks), "sample_blocks_per_step": nb,
+                       "sample_pixels_per_step": nr},
+            "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": sample_desc},
             "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def run_frames(args):
+def frames_record(layout="apron", frames=32, warmup=3, ctx=None):
     """Adaptive-NCP frames: 1024^3 flame stand-in, 32768 blocks of 32^3, C in {4..24} by gradient energy,
-    control points = the field at Greville abscissae; per frame the ~6000 bricks in view along a 32-frame
+    control points = the field at Greville abscissae; per frame the ~6600 bricks in view along a 32-frame
     orbit are ordered by cost, decoded by the persistent queue and ray-cast at 1024^2, all replayed from
-    one CUDA graph with the tiling the autotuner picked for this batch."""
+    one CUDA graph with the tiling the autotuner picked for this batch. Returns the per-frame timings (the
+    whole frame, and the ordering + decode alone) with their rates."""
     from paper_2409_00184_b300 import autotune, mfa
-    torch.cuda.set_device(0)
-    ctx = mfa.Context(0)
+    own = ctx is None
+    if own:
+        ctx = mfa.Context(0)
     N, n, p, seed = 1024, 32, 2, synth.BASE_SEED + 3
     field = synth.flame_field(N, seed, device="cuda")
     blocks = synth.blocks_from_field(field, n)
@@ -331,7 +512,6 @@ def run_frames(args):
     bs = synth.make_block_set([(c, c, c) for c in ncp], [(p, p, p)] * len(ncp), [(n, n, n)] * len(ncp), cps)
     blk = mfa.DeviceBlocks(bs)
     fov = synth.fov_for_visible(6000, B)
-    frames = 32
     lists = [synth.visible_bricks(synth.orbit_view(f, fov_y_deg=fov), B) for f in range(frames)]
     cap = max(len(v) for v in lists)
     all_lists = torch.zeros(frames, cap, dtype=torch.int32, device="cuda")
@@ -341,7 +521,7 @@ def run_frames(args):
         counts[f] = len(v)
     lst = torch.zeros(cap, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    apron = args.layout == "apron"
+    apron = layout == "apron"
     S = mfa.apron_voxels(n) if apron else n ** 3  # cache slot stride (voxels)
     cache = torch.empty(cap * S * 4, device="cuda")
     lst.copy_(all_lists[0])
@@ -355,7 +535,7 @@ def run_frames(args):
     graphs = [mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, table=table, brick_dims=(B, B, B),
                              brick_n=n, view=v, tf=tf, image=image, apron=apron) for v in views]
     stream = torch.cuda.current_stream()
-    for f in range(max(3, args.warmup)):
+    for f in range(max(3, warmup)):
         lst.copy_(all_lists[f % frames]); cnt.copy_(counts[f % frames: f % frames + 1]); graphs[f % frames].launch()
     torch.cuda.synchronize()
     if ctx.device_status():
@@ -375,6 +555,8 @@ def run_frames(args):
     launches = ctx.launch_count() - n0
     samples = ctx.ray_samples(reset=True) / frames
     ms = [ev[f].elapsed_time(ev[f + 1]) for f in range(frames)]
+    for g in graphs:
+        g.close()
     # the same frames without the ray cast (ordering + decode only), for the per-stage split
     dgraph = mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, apron=apron)
     for f in range(3):
@@ -389,22 +571,48 @@ def run_frames(args):
         torch.cuda.synchronize()
         dms += d0.elapsed_time(d1)
     dms /= frames
-    vox = sum(len(v) for v in lists) * n ** 3
+    dgraph.close()
+    if ctx.device_status():
+        raise RuntimeError("device status after the frames")
+    nvis = [len(v) for v in lists]
+    vox = sum(nvis) * n ** 3
+    # algorithmic bytes of the decode per frame: 16 B per voxel written, the control points and descriptors read
+    dec_bytes = sum(int(n ** 3 * 16 + int(ncp[b]) ** 3 * 4 + 72) for v in lists for b in v) / frames
     total = sum(ms)
-    line = {"metric": METRIC, "value": vox / (total * 1e-3) / 1e9, "unit": "Gvoxel/s", "n_gpus": 1, "steps": frames,
-            "warmup": max(3, args.warmup), "ms_per_step": total / frames, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    rec = {"ms_per_frame": total / frames, "Gvoxel_s": vox / (total * 1e-3) / 1e9, "frames": frames,
+           "visible_mean": float(np.mean(nvis)), "layout": layout, "tiling": tune,
+           "decode_ms_per_frame": dms, "decode_Gvoxel_s": vox / frames / (dms * 1e-3) / 1e9,
+           "decode_GB_s": dec_bytes / (dms * 1e-3) / 1e9, "decode_hbm_frac": dec_bytes / (dms * 1e-3) / 1e9 / hbm,
+           "decode_stage": "cost ordering + persistent decode, replayed from a CUDA graph",
+           "raycast_ms_per_frame": total / frames - dms,
+           "raycast_stage": "brick table" + (" + apron fill" if apron else "") + " + ray cast",
+           "ray_samples_per_frame": samples,
+           "raycast_Gsample_s": samples / ((total / frames - dms) * 1e-3) / 1e9,
+           "gpu_launches": launches, "clocks": clk}
+    del cache, blk
+    torch.cuda.empty_cache()
+    if own:
+        ctx.close()
+    return rec
+
+
+def run_frames(args):
+    """The adaptive-NCP frames workload as its own bench line (see frames_record)."""
+    torch.cuda.set_device(0)
+    rec = frames_record(args.layout, 32, args.warmup)
+    line = {"metric": METRIC, "value": rec["Gvoxel_s"], "unit": "Gvoxel/s", "n_gpus": 1, "steps": rec["frames"],
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_frame"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "adaptive-NCP frames: 1024^3 flame stand-in, 32768 blocks of 32^3, C in {4..24} by "
-                                   "gradient energy, ~6000 visible per frame (32-frame orbit), cost-ordered persistent "
+                                   "gradient energy, ~6600 visible per frame (32-frame orbit), cost-ordered persistent "
                                    "decode + 1024^2 ray cast replayed from a CUDA graph",
-                       "layout": args.layout, "visible_mean": float(np.mean([len(v) for v in lists])),
-                       "tiling": tune},
-            "stages": {"decode_ms_per_frame": dms, "raycast_ms_per_frame": total / frames - dms,
-                       "raycast_stage": "brick table" + (" + apron fill" if apron else "") + " + ray cast",
-                       "ray_samples_per_frame": samples,
-                       "raycast_Gsample_s": samples / ((total / frames - dms) * 1e-3) / 1e9,
-                       "raycast_TFLOP_s": samples * RAY_FLOPS_PER_SAMPLE / ((total / frames - dms) * 1e-3) / 1e12},
-            "gpu_launches": launches, "clocks": clk}
+                       "layout": args.layout, "visible_mean": rec["visible_mean"], "tiling": rec["tiling"]},
+            "roofline": {"kernel": "decode (frames)", "bound": "hbm", "achieved": rec["decode_GB_s"],
+                         "peak": float(measured_peaks()[0]["hbm_gbs"]), "unit": "GB/s", "frac": rec["decode_hbm_frac"],
+                         "traffic": None},
+            "frames": rec, "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"]}
     print(json.dumps(line))
     return 0
 
@@ -834,22 +1042,29 @@ def main():
     kernels["raycast"]["TFLOP_s"] = samples_per_step * RAY_FLOPS_PER_SAMPLE / (per["raycast"] * 1e-3) / 1e12
     kernels["raycast"]["l1_GB_s"] = samples_per_step * RAY_L1_BYTES_PER_SAMPLE / (per["raycast"] * 1e-3) / 1e9
     kernels["raycast"]["l1_frac"] = kernels["raycast"]["l1_GB_s"] / L1_PEAK_GBS
+    # the cache bytes the ray cast must read at least once: its distinct 32-byte sectors, counted by the
+    # measuring instance of the same ray cast (outside the timed region), plus the image written
+    ctx.stats(reset=True)
+    m = w.mfa
+    m.raycast(ctx, w.cache, w.stride, w.B, w.table, BRICK, w.view, w.tf, w.image, apron=w.apron, count_sectors=True)
+    sectors = ctx.stats(reset=True)[m.STAT_RAY_SECTORS]
+    algo["raycast"] = sectors * 32 + IMG * IMG * 16
+    kernels["raycast"]["GB_s"] = algo["raycast"] / (per["raycast"] * 1e-3) / 1e9
+    kernels["raycast"]["hbm_frac"] = kernels["raycast"]["GB_s"] / hbm
+    kernels["raycast"]["touched_cache_bytes"] = sectors * 32
+    kernels["raycast"]["alu_frac"] = kernels["raycast"]["TFLOP_s"] / FP32_PEAK_TFLOPS
     dom = max(names, key=lambda n: per[n])
     src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "fill": "apron.cu", "raycast": "raycast.cu",
            "adjoint": "contract3.cu"}[dom]
     tr = TRAFFIC.get((dom, args.layout))
     traffic = tr["bytes"] if tr and tr["src_sha"] == src_sha(src) else None
+    achieved = algo[dom] / (per[dom] * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"}
     if dom == "raycast":
-        achieved = kernels["raycast"]["TFLOP_s"]
-        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz; achieved = marched samples "
-                                   f"x {RAY_FLOPS_PER_SAMPLE} FLOP / kernel time"}
-    else:
-        achieved = algo[dom] / (per[dom] * 1e-3) / 1e9
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": traffic,
-                    "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"}
+        roofline["algorithmic_bytes"] = ("distinct 32-byte cache sectors the ray cast reads (counted on the device "
+                                         "by the measuring instance of the same kernel) + the 16 MB image")
     for n in ("decode", "fill"):
         if n in kernels:
             kernels[n]["hbm_frac"] = kernels[n]["GB_s"] / hbm
@@ -898,15 +1113,16 @@ def main():
     err = None if args.no_check or rank != 0 else check_against_oracle(w)
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        nb = 64
-        sample = [w.D[int(b)].view(BRICK, BRICK, BRICK).double().cpu().numpy()
-                  for b in synth.rng(seed + 1).choice(w.B, nb, replace=False)]
-        t, cores = oracle_sample_time(sample)
-        cpu = {"value": nb * w.vox / t / 1e9, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
-               "host_cpus": os.cpu_count(),
-               "sample": f"FP64 oracle fit+decode+adjoint of {nb} of the 4096 blocks ({nb * w.vox} voxels, "
-                         f"{t:.1f} s wall); the ray-cast stage is not in the sample"}
+    if rank == 0 and ws == 1 and not (args.no_cpu_baseline and args.no_check):
+        cpu, img_err = oracle_baselines(w, seed, not args.no_cpu_baseline)
+        if err is not None:
+            err["image"] = img_err
+
+    frames = None
+    if rank == 0 and not args.no_frames:
+        del w.R, w.grad
+        torch.cuda.empty_cache()
+        frames = frames_record(args.layout, 32, args.warmup, ctx)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": K,
@@ -917,7 +1133,7 @@ def main():
                                  "no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk, "frames": frames}
         print(json.dumps(line))
     ctx.close()
     if ws > 1:

@@ -128,7 +128,9 @@ int64_t mfa_ctx_launch_count(const mfa_ctx* ctx);
 
 /* Device statistics kept by the context (64-bit counters, summed over launches). */
 #define MFA_STAT_RAY_SAMPLES 0   /* samples marched by mfa_raycast (after early termination) */
-#define MFA_NUM_STATS        1
+#define MFA_STAT_RAY_SECTORS 1   /* distinct 32-byte cache sectors read by a ray cast with
+                                    MFA_RAYCAST_COUNT_SECTORS (summed over such launches) */
+#define MFA_NUM_STATS        2
 /* Synchronises `stream` and copies the first `nstats` counters to stats[]; resets them if `reset`. */
 int mfa_ctx_read_stats(mfa_ctx* ctx, uint64_t* stats, int nstats, int reset, void* stream);
 
@@ -384,6 +386,14 @@ int mfa_raycast(mfa_ctx* ctx,
  * reads its eight corners from its own slot. Same image, bit for bit, as mfa_raycast over the same
  * voxels. */
 #define MFA_RAYCAST_APRON 0x2u
+/* MFA_RAYCAST_COUNT_SECTORS: a measuring variant of the same ray cast (same image, bit for bit) that
+ * also records every 32-byte sector of d_cache its corner loads read, and adds the number of distinct
+ * sectors to MFA_STAT_RAY_SECTORS: the cache bytes the ray cast must read at least once (its
+ * algorithmic bytes from memory). It is much slower (one atomic per corner load) and is meant for
+ * measurement, not rendering. The context allocates a bitmap of one bit per sector of the cache
+ * (nslots * slot_stride_voxels / 2 bits) on first use and keeps it until destroyed. Power-of-two
+ * brick_n from 8 to 64 only (the persistent queue kernel), else MFA_ERR_UNSUPPORTED. */
+#define MFA_RAYCAST_COUNT_SECTORS 0x4u
 int mfa_raycast_ex(mfa_ctx* ctx,
                    const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
                    const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,

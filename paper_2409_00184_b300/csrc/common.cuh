@@ -17,6 +17,8 @@ struct mfa_ctx {
   uint32_t* d_status = nullptr;   // device status word (MFA_DEV_* bits)
   uint32_t* d_counters = nullptr; // work-queue counters, one per concurrent launch kind
   unsigned long long* d_stats = nullptr;  // device statistics (MFA_STAT_*)
+  uint32_t* d_touched = nullptr;  // sector bitmap of MFA_RAYCAST_COUNT_SECTORS, grown on demand
+  int64_t touched_words = 0;
   int64_t launches = 0;           // kernels enqueued through this context
   int ntilings = 0;
   mfa_tiling_entry tilings[64];   // decode tile shapes keyed by batch bounds (autotuner)

@@ -15,50 +15,76 @@ namespace mfa {
 namespace {
 
 constexpr int kSortThreads = 1024;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kKeys = MFA_MAX_NCP + 1;
 
-// Stable counting sort of list[0 .. count) by decreasing cost key max(C_x, C_y, C_z) (largest
-// models first, so the persistent queue ends on short items). One CTA; tmp holds `capacity` ints.
+// Cost key of list entry b: ascending key = descending max(C_x, C_y, C_z).
+__device__ __forceinline__ int cost_key(const mfa_block_desc* desc, int nblocks, int b) {
+  if (b < 0 || b >= nblocks) return 0;
+  const mfa_block_desc& d = desc[b];
+  const int k = max(d.ncp[0], max(d.ncp[1], d.ncp[2]));
+  return MFA_MAX_NCP - min(max(k, 0), MFA_MAX_NCP);
+}
+
+// Stable counting sort of list[0 .. count) by decreasing cost key max(C_x, C_y, C_z) (largest models
+// first, so the persistent queue ends on short items). One CTA; tmp holds `capacity` ints. Each warp
+// owns one contiguous chunk of the list: it counts its chunk's keys, a scan over (key, warp) gives every
+// warp its first position per key, and the warp then scatters its chunk in order, 32 entries at a time,
+// ranking equal keys within a step by lane.
 __global__ void __launch_bounds__(kSortThreads) sort_by_cost_kernel(const mfa_block_desc* desc, int nblocks,
                                                                     int32_t* list, int capacity,
                                                                     const int32_t* d_count, int32_t* tmp,
                                                                     uint32_t* status) {
-  __shared__ int hist[MFA_MAX_NCP + 1];
-  __shared__ int base[MFA_MAX_NCP + 1];
-  const int tid = threadIdx.x;
+  __shared__ int pos[kSortWarps][kKeys];  // per warp and key: count, then next position
+  __shared__ int base[kKeys];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int count = d_count ? *d_count : capacity;
   if (count < 0 || count > capacity) {
     if (tid == 0) flag(status, MFA_DEV_BAD_LIST);
     count = max(0, min(count, capacity));
   }
-  if (tid <= MFA_MAX_NCP) hist[tid] = 0;
+  for (int e = tid; e < kSortWarps * kKeys; e += kSortThreads) pos[e / kKeys][e % kKeys] = 0;
   __syncthreads();
-  auto key = [&](int b) {
-    if (b < 0 || b >= nblocks) return 0;
-    const mfa_block_desc& d = desc[b];
-    int k = max(d.ncp[0], max(d.ncp[1], d.ncp[2]));
-    return MFA_MAX_NCP - min(max(k, 0), MFA_MAX_NCP);  // ascending key = descending cost
-  };
-  for (int m = tid; m < count; m += blockDim.x) {
-    tmp[m] = list[m];
-    atomicAdd(&hist[key(list[m])], 1);
+  const int chunk = (count + kSortWarps - 1) / kSortWarps;
+  const int m0 = min(count, warp * chunk), m1 = min(count, m0 + chunk);
+  for (int m = m0 + lane; m < m1; m += 32) {
+    const int b = list[m];
+    tmp[m] = b;
+    atomicAdd(&pos[warp][cost_key(desc, nblocks, b)], 1);
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < kKeys) {  // per key: offsets of the warps' chunks, and the key's total
     int acc = 0;
-    for (int k = 0; k <= MFA_MAX_NCP; ++k) { base[k] = acc; acc += hist[k]; }
+    for (int w = 0; w < kSortWarps; ++w) {
+      const int c = pos[w][tid];
+      pos[w][tid] = acc;
+      acc += c;
+    }
+    base[tid] = acc;
   }
   __syncthreads();
-  // stable scatter: one warp per key walks the list in order
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int k = warp; k <= MFA_MAX_NCP; k += blockDim.x >> 5) {
-    int pos = base[k];
-    for (int m0 = 0; m0 < count; m0 += 32) {
-      const int m = m0 + lane;
-      const bool mine = m < count && key(tmp[m]) == k;
-      const unsigned bal = __ballot_sync(0xffffffffu, mine);
-      if (mine) list[pos + __popc(bal & ((1u << lane) - 1u))] = tmp[m];
-      pos += __popc(bal);
+  if (tid == 0) {  // first position of every key: exclusive scan of the totals in key order
+    int acc = 0;
+    for (int k = 0; k < kKeys; ++k) {
+      const int c = base[k];
+      base[k] = acc;
+      acc += c;
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < kSortWarps * kKeys; e += kSortThreads) pos[e / kKeys][e % kKeys] += base[e % kKeys];
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+  for (int mb = m0; mb < m1; mb += 32) {
+    const int m = mb + lane;
+    const bool valid = m < m1;
+    const int b = valid ? tmp[m] : -1;
+    const int k = valid ? cost_key(desc, nblocks, b) : kKeys;  // kKeys: no entry
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    if (valid) list[pos[warp][k] + __popc(peers & below)] = b;
+    __syncwarp();
+    if (valid && (peers >> lane) == 1u) pos[warp][k] += __popc(peers);  // the highest lane of each key
+    __syncwarp();
   }
 }
 

@@ -76,6 +76,8 @@ struct RaycastParams {
   unsigned long long* samples;  // marched samples are added here (one atomic per warp)
   bool cubes = false;           // cache bricks in the cube layout (MFA_RAYCAST_CUBES)
   bool apron = false;           // cache bricks with a one-voxel apron (MFA_RAYCAST_APRON)
+  uint32_t* touched = nullptr;  // non-null: sector bitmap of the cache (MFA_RAYCAST_COUNT_SECTORS)
+  unsigned long long* sectors = nullptr;  // distinct sectors of the bitmap are added here
 };
 
 int raycast(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream);

@@ -59,6 +59,7 @@ void mfa_ctx_destroy(mfa_ctx* ctx) {
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
   cudaFree(ctx->d_stats);
+  cudaFree(ctx->d_touched);
   delete ctx;
 }
 
@@ -337,7 +338,8 @@ int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxel
                    const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, uint32_t flags,
                    void* stream) {
   if (!ctx || !d_cache || !d_brick_table || !brick_dims || !view || !d_tf || !d_image) return MFA_ERR_INVALID_ARG;
-  if ((flags & ~(MFA_RAYCAST_CUBES | MFA_RAYCAST_APRON)) || ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1)))
+  if ((flags & ~(MFA_RAYCAST_CUBES | MFA_RAYCAST_APRON | MFA_RAYCAST_COUNT_SECTORS)) ||
+      ((flags & MFA_RAYCAST_CUBES) && (brick_n & 1)))
     return MFA_ERR_INVALID_ARG;
   if ((flags & MFA_RAYCAST_CUBES) && (flags & MFA_RAYCAST_APRON)) return MFA_ERR_INVALID_ARG;
   if (!aligned(d_cache, 16) || !aligned(d_tf, 16) || !aligned(d_image, 16) || !aligned(d_brick_table, 4))
@@ -363,7 +365,23 @@ int mfa_raycast_ex(mfa_ctx* ctx, const float* d_cache, int64_t slot_stride_voxel
   prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
   prm.cubes = (flags & MFA_RAYCAST_CUBES) != 0;
   prm.apron = (flags & MFA_RAYCAST_APRON) != 0;
-  return raycast(ctx, prm, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (flags & MFA_RAYCAST_COUNT_SECTORS) {
+    if (prm.log2n < 3 || prm.log2n > 6) return MFA_ERR_UNSUPPORTED;
+    const int64_t words = ((nslots * slot_stride_voxels + 1) / 2 + 31) / 32;  // one bit per 32-byte sector
+    if (words > ctx->touched_words) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return MFA_ERR_CUDA;
+      cudaFree(ctx->d_touched);
+      ctx->d_touched = nullptr;
+      ctx->touched_words = 0;
+      if (cudaMalloc(&ctx->d_touched, (size_t)words * sizeof(uint32_t)) != cudaSuccess) return MFA_ERR_CUDA;
+      ctx->touched_words = words;
+    }
+    if (cudaMemsetAsync(ctx->d_touched, 0, (size_t)words * sizeof(uint32_t), s) != cudaSuccess) return MFA_ERR_CUDA;
+    prm.touched = ctx->d_touched;
+    prm.sectors = ctx->d_stats + MFA_STAT_RAY_SECTORS;
+  }
+  return raycast(ctx, prm, s);
 }
 
 int mfa_fill_aprons(mfa_ctx* ctx, float* d_cache, int64_t slot_stride_voxels, int64_t nslots,

@@ -147,10 +147,21 @@ __device__ __forceinline__ void corners_general(const RaycastParams& prm, int n,
       }
 }
 
+// One corner load of the queue kernel. The measuring instance (TOUCH) also sets the bit of the 32-byte
+// cache sector it reads in prm.touched.
+template <bool TOUCH>
+__device__ __forceinline__ float4 load_corner(const RaycastParams& prm, const float4* p) {
+  if (TOUCH) {
+    const int64_t sec = (p - prm.cache) >> 1;  // two float4 per sector
+    atomicOr(prm.touched + (sec >> 5), 1u << (sec & 31));
+  }
+  return __ldg(p);
+}
+
 // The eight corners of a cell that spans two bricks on some axis, for bricks of 2^L voxels: per axis the
 // brick step (0 or 1) and local coordinate of the two corner planes are formed once with shifts and
 // masks; every corner then costs one table lookup and one load.
-template <int L, int LAYOUT>  // 0: [z][y][x], 1: cubes, 2: apron (rows of apron_pitch(2^L), planes of 2^L + 1)
+template <int L, int LAYOUT, bool TOUCH>  // 0: [z][y][x], 1: cubes, 2: apron (rows of apron_pitch(2^L), planes of 2^L + 1)
 __device__ __forceinline__ void corners_seam(const RaycastParams& prm, int ix, int iy, int iz, float4 (&c)[2][2][2]) {
   constexpr int n = 1 << L, P = n + 1, PX = apron_pitch(n);
   const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
@@ -167,7 +178,7 @@ __device__ __forceinline__ void corners_seam(const RaycastParams& prm, int ix, i
       const int vox = LAYOUT == 1   ? cube_index(lxd[dx], lyd[dy], lzd[dz], n, n)
                       : LAYOUT == 2 ? (lzd[dz] * P + lyd[dy]) * PX + lxd[dx]
                                     : (((lzd[dz] << L) + lyd[dy]) << L) + lxd[dx];
-      v = __ldg(prm.cache + (int64_t)slot * prm.slot_stride + vox);
+      v = load_corner<TOUCH>(prm, prm.cache + (int64_t)slot * prm.slot_stride + vox);
     }
     c[dz][dy][dx] = v;
   }
@@ -231,8 +242,9 @@ __global__ void __launch_bounds__(kTile * kTile, 4) raycast_tile_kernel(RaycastP
   count_marched(prm, (unsigned long long)marched, tid & 31);
 }
 
-// LAYOUT of the cache bricks: 0 [z][y][x], 1 cubes, 2 [z][y][x] with a one-voxel apron (pitch 2^L + 1)
-template <int L, int LAYOUT>
+// LAYOUT of the cache bricks: 0 [z][y][x], 1 cubes, 2 [z][y][x] with a one-voxel apron (pitch 2^L + 1).
+// TOUCH: the measuring instance that records the cache sectors it reads (MFA_RAYCAST_COUNT_SECTORS).
+template <int L, int LAYOUT, bool TOUCH>
 __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(RaycastParams prm, uint32_t* counter) {
   constexpr bool CUBES = LAYOUT == 1, APRON = LAYOUT == 2;
   constexpr int P = (1 << L) + 1, PX = apron_pitch(1 << L);  // apron: rows per plane, row pitch
@@ -291,16 +303,16 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
       while (k < K) {
         float4 c[2][2][2];
         if (!APRON && slot == -2) {
-          corners_seam<L, LAYOUT>(prm, ix, iy, iz, c);
+          corners_seam<L, LAYOUT, TOUCH>(prm, ix, iy, iz, c);
         } else if (slot >= 0 && slot < prm.nslots && APRON) {
           const float4* base = prm.cache + (int64_t)slot * prm.slot_stride +
                                ((iz & (n - 1)) * P + (iy & (n - 1))) * PX + (ix & (n - 1));
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(base + (e >> 2) * P * PX + ((e >> 1) & 1) * PX + (e & 1));
+            c[e >> 2][(e >> 1) & 1][e & 1] = load_corner<TOUCH>(prm, base + (e >> 2) * P * PX + ((e >> 1) & 1) * PX + (e & 1));
         } else if (APRON && (((ix & (n - 1)) == n - 1) | ((iy & (n - 1)) == n - 1) | ((iz & (n - 1)) == n - 1))) {
           // an absent brick has no apron: a seam cell reads the neighbouring bricks' corners directly
-          corners_seam<L, LAYOUT>(prm, ix, iy, iz, c);
+          corners_seam<L, LAYOUT, TOUCH>(prm, ix, iy, iz, c);
         } else if (slot >= 0 && slot < prm.nslots && CUBES) {
           // cube layout: the two x, y and z corner planes of the cell
           const int lx = ix & (n - 1), ly = iy & (n - 1), lz = iz & (n - 1);
@@ -311,12 +323,13 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
           const float4* sb = prm.cache + (int64_t)slot * prm.slot_stride;
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(sb + oz[e >> 2] + oy[(e >> 1) & 1] + ox[e & 1]);
+            c[e >> 2][(e >> 1) & 1][e & 1] = load_corner<TOUCH>(prm, sb + oz[e >> 2] + oy[(e >> 1) & 1] + ox[e & 1]);
         } else if (slot >= 0 && slot < prm.nslots) {
           const float4* base = prm.cache + (int64_t)slot * prm.slot_stride +
                                ((((iz & (n - 1)) << L) + (iy & (n - 1))) << L) + (ix & (n - 1));
 #pragma unroll
-          for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = __ldg(base + (e >> 2) * n2 + ((e >> 1) & 1) * n + (e & 1));
+          for (int e = 0; e < 8; ++e)
+            c[e >> 2][(e >> 1) & 1][e & 1] = load_corner<TOUCH>(prm, base + (e >> 2) * n2 + ((e >> 1) & 1) * n + (e & 1));
         } else {
 #pragma unroll
           for (int e = 0; e < 8; ++e) c[e >> 2][(e >> 1) & 1][e & 1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -334,16 +347,36 @@ __global__ void __launch_bounds__(kQueueThreads, 3) raycast_queue_kernel(Raycast
   count_marched(prm, marched, lane);
 }
 
+// Adds the number of set bits of words[0 .. nwords) to *out.
+__global__ void count_bits_kernel(const uint32_t* __restrict__ words, int64_t nwords, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (int64_t)gridDim.x * blockDim.x)
+    c += __popc(words[i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+template <int L, bool TOUCH>
+auto queue_kernel(const RaycastParams& prm) {
+  return prm.apron ? raycast_queue_kernel<L, 2, TOUCH>
+                   : prm.cubes ? raycast_queue_kernel<L, 1, TOUCH> : raycast_queue_kernel<L, 0, TOUCH>;
+}
+
 template <int L>
 int launch_queue(mfa_ctx* ctx, const RaycastParams& prm, cudaStream_t stream) {
   const size_t smem = (size_t)prm.tf_n * sizeof(float4);
-  auto kern = prm.apron ? raycast_queue_kernel<L, 2> : prm.cubes ? raycast_queue_kernel<L, 1> : raycast_queue_kernel<L, 0>;
+  auto kern = prm.touched ? queue_kernel<L, true>(prm) : queue_kernel<L, false>(prm);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQueueThreads, smem) != cudaSuccess)
     return MFA_ERR_CUDA;
   uint32_t* counter = ctx->d_counters + kRaycastQueue;
   if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
   kern<<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, counter);
+  if (prm.touched) {
+    const int64_t words = ((prm.nslots * prm.slot_stride + 1) / 2 + 31) / 32;
+    count_bits_kernel<<<ctx->num_sms * 4, 256, 0, stream>>>(prm.touched, words, prm.sectors);
+    ctx->launches++;
+  }
   return MFA_OK;
 }
 

@@ -18,7 +18,8 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_DEVIC
 DEV_BAD_DESC, DEV_BAD_KNOTS, DEV_BAD_RANGE, DEV_BAD_LIST, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4, 8, 16, 32
 PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
 DECODE_VALUE_ONLY, DECODE_LIST_SLOTS, DECODE_CUBES, DECODE_APRON = 1, 2, 4, 8
-RAYCAST_CUBES, RAYCAST_APRON = 1, 2
+RAYCAST_CUBES, RAYCAST_APRON, RAYCAST_COUNT_SECTORS = 1, 2, 4
+STAT_RAY_SAMPLES, STAT_RAY_SECTORS, NUM_STATS = 0, 1, 2
 MAX_DEGREE, MAX_NCP, MAX_NSAMP = 3, 32, 64
 
 
@@ -213,10 +214,15 @@ class Context:
         _check(lib.mfa_selftest_wait_timeout(self.handle, int(polls), _stream(stream)), "mfa_selftest_wait_timeout")
 
     def ray_samples(self, reset=True, stream=None):
-        """Samples marched by mfa_raycast since the last reset (synchronises the stream)."""
-        v = (ctypes.c_uint64 * 1)()
-        _check(lib.mfa_ctx_read_stats(self.handle, v, 1, int(reset), _stream(stream)), "mfa_ctx_read_stats")
-        return int(v[0])
+        """Samples marched by mfa_raycast since the last reset (synchronises the stream; resets every
+        statistic)."""
+        return self.stats(reset, stream)[0]
+
+    def stats(self, reset=True, stream=None):
+        """Every MFA_STAT_* counter (ray samples, ray-cast sectors) since the last reset (synchronises)."""
+        v = (ctypes.c_uint64 * NUM_STATS)()
+        _check(lib.mfa_ctx_read_stats(self.handle, v, NUM_STATS, int(reset), _stream(stream)), "mfa_ctx_read_stats")
+        return [int(x) for x in v]
 
     def set_decode_tiling(self, bounds, ks=0, ctas_per_sm=0):
         _check(lib.mfa_ctx_set_decode_tiling(self.handle, ctypes.byref(bounds),
@@ -508,16 +514,17 @@ def raycast_direct(ctx, blocks, table, brick_n, view, tf, image, cps=None, strea
 
 
 def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, stream=None, cubes=False,
-            apron=False):
-    """mfa_raycast (mfa_raycast_ex with MFA_RAYCAST_CUBES or MFA_RAYCAST_APRON): table is an int32
-    (Bz, By, Bx) CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
+            apron=False, count_sectors=False):
+    """mfa_raycast (mfa_raycast_ex with MFA_RAYCAST_CUBES, MFA_RAYCAST_APRON or MFA_RAYCAST_COUNT_SECTORS):
+    table is an int32 (Bz, By, Bx) CUDA tensor; image a float32 (H, W, 4) CUDA tensor."""
     Bz, By, Bx = table.shape
     _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
     _need(cache, nslots * slot_stride * 4, "cache")
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
     vw = make_view(view)
-    if cubes or apron:
-        flags = (RAYCAST_CUBES if cubes else 0) | (RAYCAST_APRON if apron else 0)
+    if cubes or apron or count_sectors:
+        flags = ((RAYCAST_CUBES if cubes else 0) | (RAYCAST_APRON if apron else 0) |
+                 (RAYCAST_COUNT_SECTORS if count_sectors else 0))
         _check(lib.mfa_raycast_ex(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
                                   brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), flags,
                                   _stream(stream)), "mfa_raycast_ex")

@@ -72,6 +72,7 @@ def test_frames_reduced_config3(mfa, ctx):
         assert sorted(order.tolist()) == sorted(vis.tolist())
         keys = bs.ncp[order].max(axis=1)
         assert np.all(np.diff(keys) <= 0)
+        assert np.array_equal(order, vis[np.argsort(-bs.ncp[vis].max(axis=1), kind="stable")])
         c = cache.view(cap, n ** 3, 4).cpu().numpy()
         want_cache = np.zeros((cap, n, n, n, 4))
         for m, b in enumerate(order):
@@ -112,8 +113,7 @@ def test_frames_full_config3_sampled(mfa, ctx):
         g.launch()
         assert ctx.device_status() == 0
         order = lst[: len(vis)].cpu().numpy()
-        assert sorted(order.tolist()) == sorted(vis.tolist())
-        assert np.all(np.diff(bs.ncp[order].max(axis=1)) <= 0)
+        assert np.array_equal(order, vis[np.argsort(-bs.ncp[vis].max(axis=1), kind="stable")])
         c = cache.view(cap, n ** 3, 4)
         got, want = [], []
         for m in rng.choice(len(order), 48, replace=False):

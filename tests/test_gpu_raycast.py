@@ -187,3 +187,68 @@ def test_raycast_direct_model_queries_match_oracle(mfa, ctx, N, n, holes):
     cache = np.stack(oracle_decode_set(bs)).astype(np.float32)
     via_cache = ocast.raycast(cache, table, n, view, tf)
     print(f"N={N} n={n} holes={holes}: max |direct - cache| = {np.max(np.abs(want - via_cache)):.2e}")
+
+
+def _touched_sectors_host(view, B, n, stride, apron):
+    """Distinct 32-byte cache sectors the eight corner loads of every sample read, replaying the FP32 sample
+    positions the kernel forms (g = (fma(t_s, d, eye) + 1) * half + k * dg, one FMA per axis) with the
+    oracle's FP32 ray set-up. Identity brick table, early termination off."""
+    N = B * n
+    d, t0, dt, K, eye = ocast.ray_setup(view, (N, N, N))
+    f32 = np.float32
+    half = f32((N - 1) / 2.0)
+
+    def fma(a, b, c):  # FP32 fused multiply-add: exact product and sum in FP64, one rounding (ties aside)
+        return (np.float64(a) * np.float64(b) + np.float64(c)).astype(f32)
+
+    ts = fma(f32(0.5), dt, t0)
+    gb = [((fma(ts, d[..., a], eye[a]) + f32(1.0)) * half).astype(f32) for a in range(3)]
+    dg = [((dt * d[..., a]).astype(f32) * half).astype(f32) for a in range(3)]
+    A = (n + 1 + 1) // 2 * 2 if apron else n
+    P = n + 1 if apron else n
+    secs = set()
+    for y, x in zip(*np.nonzero(K > 0)):
+        k = np.arange(K[y, x], dtype=np.float64)
+        g = [np.clip(fma(k.astype(f32), dg[a][y, x], gb[a][y, x]), 0, N - 1) for a in range(3)]
+        i = [np.minimum(g[a].astype(np.int64), N - 2) for a in range(3)]
+        slot = ((i[2] // n) * B + i[1] // n) * B + i[0] // n
+        for e in range(8):
+            dx, dy, dz = e & 1, (e >> 1) & 1, e >> 2
+            lx, ly, lz = i[0] % n + dx, i[1] % n + dy, i[2] % n + dz
+            if not apron:  # a corner beyond the brick reads the neighbour's first plane
+                sl = (((i[2] + dz) // n) * B + (i[1] + dy) // n) * B + (i[0] + dx) // n
+                vox = sl * stride + (((i[2] + dz) % n) * n + (i[1] + dy) % n) * n + (i[0] + dx) % n
+            else:
+                vox = slot * stride + (lz * P + ly) * A + lx
+            secs.update((vox >> 1).tolist())
+    return len(secs)
+
+
+@pytest.mark.parametrize("apron", [False, True])
+def test_raycast_sector_count(mfa, ctx, apron):
+    """MFA_RAYCAST_COUNT_SECTORS renders the same image bit for bit and counts the distinct 32-byte cache
+    sectors of the corner loads: equal to a host replay of the kernel's sample cells (to 0.5 %: a sample
+    exactly on a cell boundary may round the other way), and below the cache's sector count."""
+    n, B = 16, 2
+    cache = _fitted_volume(B * n, n, synth.BASE_SEED + 15)
+    table = torch.arange(B ** 3, dtype=torch.int32, device="cuda").view(B, B, B)
+    tf = torch.from_numpy(synth.transfer_function(synth.BASE_SEED + 2)).cuda()
+    view = synth.default_view(width=48, height=40, opacity_max=1.0)
+    S = mfa.apron_voxels(n) if apron else n ** 3
+    dev = torch.zeros(B ** 3, S, 4, device="cuda")
+    if apron:
+        A = mfa.apron_pitch(n)
+        dev[:, : (n + 1) * (n + 1) * A].view(B ** 3, n + 1, n + 1, A, 4)[:, :n, :n, :n] = torch.from_numpy(cache).cuda()
+        mfa.fill_aprons(ctx, dev, S, B ** 3, table, n)
+    else:
+        dev.copy_(torch.from_numpy(cache.reshape(B ** 3, S, 4)))
+    img = [torch.full((40, 48, 4), float("nan"), device="cuda") for _ in range(2)]
+    ctx.stats(reset=True)
+    mfa.raycast(ctx, dev, S, B ** 3, table, n, view, tf, img[0], apron=apron)
+    mfa.raycast(ctx, dev, S, B ** 3, table, n, view, tf, img[1], apron=apron, count_sectors=True)
+    st = ctx.stats(reset=True)
+    assert ctx.device_status() == 0
+    assert torch.equal(img[0], img[1])
+    want = _touched_sectors_host(view, B, n, S, apron)
+    assert abs(st[mfa.STAT_RAY_SECTORS] - want) <= 0.005 * want, (st, want)
+    assert st[mfa.STAT_RAY_SECTORS] <= B ** 3 * S // 2
