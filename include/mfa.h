@@ -324,6 +324,56 @@ int mfa_select_ncp(mfa_ctx* ctx, const double* d_errors, int32_t ncand, const in
 int mfa_lod_gather(mfa_ctx* ctx, const float* d_field, const int32_t dims[3], int32_t n, int32_t stride,
                    const int32_t* d_ids, int32_t nblocks, float* d_out, int64_t slot_stride, void* stream);
 
+/* mfa_lod_gather with flags. MFA_LOD_SHARED_BOUNDARY: the blocks of a level share their boundary
+ * samples (Sec. 4.2: neighbouring blocks share one sample on the boundary in x, y and z, which keeps
+ * the micro-models C0 across blocks): block (bx, by, bz) spans (n-1)*stride intervals from node
+ * (bx, by, bz)*(n-1)*stride, its last samples being the next block's first, and each dims[a] - 1 must
+ * be a positive multiple of (n-1)*stride (else MFA_ERR_INVALID_ARG). Without the flag, as
+ * mfa_lod_gather. Unknown flags: MFA_ERR_INVALID_ARG. */
+#define MFA_LOD_SHARED_BOUNDARY 0x1u
+int mfa_lod_gather_ex(mfa_ctx* ctx, const float* d_field, const int32_t dims[3], int32_t n, int32_t stride,
+                      const int32_t* d_ids, int32_t nblocks, float* d_out, int64_t slot_stride, uint32_t flags,
+                      void* stream);
+
+/* ---- levels of detail chosen by distance (Sec. 5.1.3) and rendered by model queries ------------ */
+/* A multi-resolution volume of `levels` levels of shared-boundary micro-blocks with n samples per axis
+ * (MFA_LOD_SHARED_BOUNDARY): level l = 0 (finest) .. levels-1 has B_l = fine_blocks / 2^l blocks per
+ * axis, each spanning (n-1)*2^l intervals of the finest grid of N = fine_blocks*(n-1) + 1 nodes per axis,
+ * which maps onto [-1, 1]^3. Global block ids list level 0 first, each level z-major:
+ * id = off_l + (bz*B_l + by)*B_l + bx with off_l the number of blocks of the finer levels. */
+#define MFA_MAX_LEVELS 8
+
+/* For a point of view `eye` (world coordinates), the level of detail of every part of the volume by the
+ * distance from the eye to the block centroids (Sec. 5.1.3: four ranges [0, 0.8], [0.8, 1.6], [1.6, 2.4],
+ * [2.4, inf), the nearest taking the finest level): walking from the coarsest level down, a block of
+ * level l >= 1 is taken when its centroid lies at distance >= ranges[l-1], else its eight children are
+ * examined; level 0 is taken where no coarser block was. The distance test is decided in FP32, one
+ * rounded operation at a time: c_a = (2*g0_a + E)/(N - 1) - 1 with g0 the block's first node and E its
+ * extent in finest nodes, d^2 = ((c_x - e_x)^2 + (c_y - e_y)^2) + (c_z - e_z)^2 against ranges[l-1]^2.
+ * Writes d_table[(fz*B0 + fy)*B0 + fx] = the global id of the block covering finest block (fx, fy, fz),
+ * B0 = fine_blocks (int32, B0^3 entries, caller-owned). ranges: levels-1 host floats (NULL when levels
+ * is 1). MFA_ERR_INVALID_ARG for null or misaligned pointers, n outside [2, MFA_MAX_NSAMP], levels
+ * outside [1, MFA_MAX_LEVELS], fine_blocks not a multiple of 2^(levels-1), a negative or non-finite
+ * range or eye coordinate, or a grid of 2^23 finest intervals or more. */
+int mfa_lod_select(mfa_ctx* ctx, const float eye[3], int32_t fine_blocks, int32_t n, int32_t levels,
+                   const float* ranges, int32_t* d_table, void* stream);
+
+/* Algorithm 4 over a multi-resolution volume with per-sample queries of the selected micro-models
+ * (valueMicroModel / gradientMicroModel of Sec. 4.3.3 on the blocks mfa_lod_select chose): the camera,
+ * marching, transfer function, shading, compositing and early termination of mfa_raycast, on the
+ * finest grid of N = fine_blocks*(n-1) + 1 nodes per axis (one sample per finest node spacing at
+ * step_voxels 1). A sample at finest-node coordinates g lies in finest block min(floor(g/(n-1)),
+ * fine_blocks - 1) per axis; d_table gives the global id of the block that covers it (its level l,
+ * first node g0 and extent E = (n-1)*2^l follow from the id), and the sample is that model's value and
+ * gradient at u = (g - g0)/E clamped to [0, 1] (gradient / E in node units). d_desc[id] describes block
+ * id: n samples per axis (else MFA_DEV_BAD_DESC and the block reads as zero), degree, NCP, knots and
+ * control points as for mfa_decode_blocks; nblocks must cover every id of the levels. Other arguments
+ * and checks as mfa_raycast_direct. */
+int mfa_raycast_lod(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,
+                    int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
+                    const int32_t* d_table, int32_t fine_blocks, int32_t n, int32_t levels, const mfa_view* view,
+                    const float* d_tf, int32_t tf_n, float* d_image, void* stream);
+
 /* Allocation-free least-squares encode. The paper has no counterpart to this entry point: it
  * exists for callers that cannot call cudaMalloc - a process whose device memory is reserved
  * by another runtime's memory pool, so that a fresh allocation fails or has to wait for that
@@ -336,11 +386,13 @@ int mfa_lod_gather(mfa_ctx* ctx, const float* d_field, const int32_t dims[3], in
  *   - The batch's scratch need, 256 bytes + 168 per axis class + 24 per block + 4*C*n per axis
  *     class (pseudo-inverse) + 20*n per axis class (basis table), each part rounded up to 256
  *     bytes, must fit the 2 MiB; a larger batch returns MFA_ERR_CAPACITY and enqueues nothing.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture on that device.
+ *   - Every call looks up the array's device address on the current device (cudaGetSymbolAddress).
  *   - The call copies the host descriptors into the array, enqueues the fit on `stream` and then
- *     synchronises `stream`; it returns MFA_ERR_DEVICE if a device-side check failed (the status
- *     word, e.g. MFA_DEV_NOT_SPD), else MFA_OK.
+ *     synchronises `stream` and copies the status word back synchronously, so it must not be called
+ *     while any stream on the device is being captured into a CUDA graph.
+ *   - It returns MFA_ERR_DEVICE if a device-side check failed, else MFA_OK. Which check failed (the
+ *     MFA_DEV_* bits, e.g. MFA_DEV_NOT_SPD) is not returned; a caller that needs it runs the same
+ *     batch through a context (mfa_encode_plan_create, mfa_encode_blocks, mfa_ctx_device_status).
  *   - Every call uses the same array; it clears the status word and counter itself. Calls whose
  *     work overlaps on the GPU (other threads, other streams) race on the array: serialise them.
  * Arguments as for mfa_encode_plan_create (h_desc, nblocks, h_knots, knots_len, cps_len) and

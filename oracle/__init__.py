@@ -23,6 +23,10 @@ What each module computes, and the passage it follows:
   0.5*||decode(P) - D||^2 with respect to P.
 * ``raycast``  - front-to-back direct volume rendering with early termination
   (Algorithm 4) over a bricked value+gradient cache.
+* ``multires`` - shared-boundary micro-blocks of every level of detail (Sec. 4.2),
+  the selection of a level per block by the distance from the point of view
+  (Sec. 5.1.3), Algorithm 4 over the selected models, and the MSE / PSNR image
+  metrics of Sec. 5.2.
 
 Parity pins (tests/test_oracle_*.py) tie every function to something other than
 itself: partition of unity, Bernstein closed forms, polynomial reproduction, endpoint
@@ -31,4 +35,4 @@ dot-product identity and closed-form ray compositing. The ray caster is pinned o
 by those closed-form cases; elsewhere it is "parity unpinned" beyond them.
 """
 
-from . import bspline, decode, encode, adjoint, raycast  # noqa: F401
+from . import bspline, decode, encode, adjoint, raycast, multires  # noqa: F401

@@ -211,12 +211,15 @@ def raycast_direct(blocks, table, brick_n, view, tf):
     return _march(table.shape, brick_n, view, tf, lambda g: fetch_direct(blocks, table, brick_n, g))
 
 
-def _march(table_shape, brick_n, view, tf, sample, pixels=None):
+def _march(table_shape, brick_n, view, tf, sample, pixels=None, nodes=None, gscale=None):
     """Front-to-back marching of every pixel's ray (or of the listed pixels' rays only); sample(g) gives
-    (f, f_u, f_v, f_w) at voxel coords g."""
+    (f, f_u, f_v, f_w) at voxel coords g. By default the volume is the brick grid (B_a * brick_n nodes per
+    axis) and the gradient is parametric per brick; `nodes` and `gscale` (world gradient per sampled
+    gradient unit) replace both."""
     tf = np.asarray(tf, dtype=np.float64)
-    Bz, By, Bx = table_shape
-    nodes = (Bx * brick_n, By * brick_n, Bz * brick_n)
+    if nodes is None:
+        Bz, By, Bx = table_shape
+        nodes = (Bx * brick_n, By * brick_n, Bz * brick_n)
     H, W = int(view["height"]), int(view["width"])
     d, t0, dt, K, eye = ray_setup(view, nodes)
     d = d.reshape(-1, 3).astype(np.float64)
@@ -233,7 +236,8 @@ def _march(table_shape, brick_n, view, tf, sample, pixels=None):
     shin = float(np.float32(view["shininess"]))
     vmin, vmax = float(np.float32(view["vmin"])), float(np.float32(view["vmax"]))
     half = np.array([(n - 1) / 2.0 for n in nodes])
-    gscale = half / (brick_n - 1)  # d(world)/d(param): parametric gradient -> world gradient
+    if gscale is None:
+        gscale = half / (brick_n - 1)  # d(world)/d(param): parametric gradient -> world gradient
 
     M = len(K)
     color = np.zeros((M, 3))

@@ -13,7 +13,6 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <new>
 #include <vector>
 
@@ -281,21 +280,14 @@ constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;
 static __device__ __align__(256) unsigned char g_encode_scratch[kNoAllocScratchBytes];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-
 // Device address of g_encode_scratch on the current device. In host code the array's name is
-// only a host-side stand-in, so the address comes from cudaGetSymbolAddress, once per device.
-int scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return MFA_ERR_CAPACITY;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_encode_scratch) != cudaSuccess || !p) return MFA_ERR_CUDA;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[dev];
+// only a host-side stand-in, so the address comes from cudaGetSymbolAddress. It is looked up on
+// every call (the lookup is cheap): after a device reset the module is loaded again and the
+// array's address may change, so a stored address could go stale.
+int scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_encode_scratch) != cudaSuccess || !p) return MFA_ERR_CUDA;
+  *out = static_cast<unsigned char*>(p);
   return MFA_OK;
 }
 }  // namespace
@@ -331,7 +323,7 @@ extern "C" int mfa_encode_blocks_noalloc(const mfa_block_desc* h_desc, int32_t n
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MFA_ERR_CUDA;
   unsigned char* base = nullptr;
-  rc = scratch_address(dev, &base);
+  rc = scratch_address(&base);
   if (rc != MFA_OK) return rc;
   mfa_ctx local;  // host-side view for the launchers; its device pointers point into the scratch
   local.device = dev;

@@ -109,6 +109,18 @@ struct DirectModels {
 
 int raycast_direct(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, cudaStream_t stream);
 
+// Levels of a multi-resolution volume of shared-boundary micro-blocks (mfa_lod_select, mfa_raycast_lod).
+struct LodLevels {
+  int B0;      // finest blocks per axis
+  int n;       // samples per block and axis
+  int levels;
+  int off[MFA_MAX_LEVELS];  // first global id of every level
+};
+
+// Algorithm 4 with per-sample queries of the models prm.table selects per finest block (global ids).
+int raycast_lod(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, const LodLevels& lv,
+                cudaStream_t stream);
+
 struct AdjointParams {
   const mfa_block_desc* desc;
   int nblocks;

@@ -1,4 +1,5 @@
 // C-ABI entry points: context, host-side argument checks, dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -267,7 +268,10 @@ int mfa_adjoint_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nbloc
 
 namespace {
 // Host checks of the view and the brick grid, and the FP32 camera/march parameters of a ray cast.
-int view_params(mfa::RaycastParams& prm, const int32_t brick_dims[3], int32_t brick_n, const mfa_view* view) {
+// nodes > 0: the volume has `nodes` nodes on every axis (a shared-boundary grid) and the samples carry
+// gradients in node units; otherwise brick_dims[a]*brick_n nodes and gradients per brick parameter.
+int view_params(mfa::RaycastParams& prm, const int32_t brick_dims[3], int32_t brick_n, const mfa_view* view,
+                int64_t nodes = 0) {
   if (view->width < 1 || view->height < 1 || view->width > 16384 || view->height > 16384) return MFA_ERR_INVALID_ARG;
   if (!(view->fov_y_deg > 0.f && view->fov_y_deg < 180.f) || !(view->step_voxels > 0.f) ||
       !(view->vmax > view->vmin))
@@ -291,10 +295,10 @@ int view_params(mfa::RaycastParams& prm, const int32_t brick_dims[3], int32_t br
   int nmax = 0;
   for (int a = 0; a < 3; ++a) {
     prm.B[a] = brick_dims[a];
-    const int N = brick_dims[a] * brick_n;
+    const int N = nodes > 0 ? (int)nodes : brick_dims[a] * brick_n;
     nmax = N > nmax ? N : nmax;
     prm.half[a] = (float)((N - 1) / 2.0);
-    prm.gscale[a] = (float)((N - 1) / 2.0 / (brick_n - 1));
+    prm.gscale[a] = nodes > 0 ? prm.half[a] : (float)((N - 1) / 2.0 / (brick_n - 1));
     prm.eye[a] = view->eye[a];
     prm.fwd[a] = (float)f[a];
     prm.right[a] = (float)r[a];
@@ -444,3 +448,56 @@ int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nbloc
 }
 
 }  // extern "C"
+
+extern "C" int mfa_raycast_lod(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,
+                               int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
+                               const int32_t* d_table, int32_t fine_blocks, int32_t n, int32_t levels,
+                               const mfa_view* view, const float* d_tf, int32_t tf_n, float* d_image, void* stream) {
+  if (!ctx || !d_desc || !d_knots || !d_cps || !bounds || !d_table || !view || !d_tf || !d_image)
+    return MFA_ERR_INVALID_ARG;
+  if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_cps, 4) || !aligned(d_tf, 16) ||
+      !aligned(d_image, 16) || !aligned(d_table, 4))
+    return MFA_ERR_INVALID_ARG;
+  if (nblocks < 0 || knots_len < 0 || cps_len < 0 || n < 2 || n > MFA_MAX_NSAMP || tf_n < 2 || levels < 1 ||
+      levels > MFA_MAX_LEVELS || fine_blocks < 1 || fine_blocks % (1 << (levels - 1)) != 0 ||
+      (int64_t)fine_blocks * (n - 1) + 1 > (1 << 20))
+    return MFA_ERR_INVALID_ARG;
+  if (bounds->max_degree < 1 || bounds->max_degree > MFA_MAX_DEGREE || bounds->max_ncp < 2 ||
+      bounds->max_ncp > MFA_MAX_NCP || bounds->max_nsamp < n || bounds->max_nsamp > MFA_MAX_NSAMP)
+    return MFA_ERR_INVALID_ARG;
+  LodLevels lv;
+  lv.B0 = fine_blocks;
+  lv.n = n;
+  lv.levels = levels;
+  int64_t acc = 0;
+  for (int l = 0; l < MFA_MAX_LEVELS; ++l) {
+    lv.off[l] = (int)std::min<int64_t>(acc, 0x7fffffff);
+    if (l < levels) {
+      const int64_t Bl = fine_blocks >> l;
+      acc += Bl * Bl * Bl;
+    }
+  }
+  if (acc > 0x7fffffff) return MFA_ERR_CAPACITY;
+  const int32_t dims[3] = {fine_blocks, fine_blocks, fine_blocks};
+  RaycastParams prm;
+  const int vs = view_params(prm, dims, n, view, (int64_t)fine_blocks * (n - 1) + 1);
+  if (vs != MFA_OK) return vs;
+  prm.cache = nullptr;
+  prm.slot_stride = 0;
+  prm.nslots = 0;
+  prm.table = d_table;
+  prm.tf = reinterpret_cast<const float4*>(d_tf);
+  prm.tf_n = tf_n;
+  prm.image = reinterpret_cast<float4*>(d_image);
+  prm.samples = ctx->d_stats + MFA_STAT_RAY_SAMPLES;
+  DirectModels m;
+  m.desc = d_desc;
+  m.nblocks = nblocks;
+  m.knots = d_knots;
+  m.knots_len = knots_len;
+  m.cps = d_cps;
+  m.cps_len = cps_len;
+  m.bounds = *bounds;
+  m.status = ctx->d_status;
+  return raycast_lod(ctx, prm, m, lv, static_cast<cudaStream_t>(stream));
+}

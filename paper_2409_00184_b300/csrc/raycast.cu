@@ -543,6 +543,100 @@ __global__ void __launch_bounds__(kQueueThreads) raycast_direct_kernel(RaycastPa
   count_marched(prm, marched, lane);
 }
 
+// The selected model's (f, df/dg) at finest-node coordinates gv (node-unit gradient) of a multi-resolution
+// volume: the finest block holding gv, the global id the table gives it, and that block's level, first
+// node and extent, from which u = (g - g0)/E.
+__device__ __forceinline__ float4 sample_lod(const RaycastParams& prm, const DirectModels& m, const LodLevels& lv,
+                                             const float (&gv)[3], ModelGeom& cur) {
+  const int nm1 = lv.n - 1;
+  int fb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) fb[a] = min((int)(gv[a] / (float)nm1), lv.B0 - 1);
+  const int id = __ldg(prm.table + ((int64_t)fb[2] * lv.B0 + fb[1]) * lv.B0 + fb[0]);
+  if (id < 0 || id >= m.nblocks) {
+    flag(m.status, MFA_DEV_BAD_LIST);
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int l = 0;
+  while (l + 1 < lv.levels && id >= lv.off[l + 1]) ++l;
+  const int local = id - lv.off[l], Bl = lv.B0 >> l, E = nm1 << l;
+  const int b[3] = {local % Bl, (local / Bl) % Bl, local / (Bl * Bl)};
+  float u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = fminf(fmaxf((gv[a] - (float)(b[a] * E)) / (float)E, 0.f), 1.f);
+  if (id != cur.block) load_model(m, lv.n, id, cur);
+  if (!cur.ok) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 v = eval_model(m, cur, u[0], u[1], u[2]);
+  const float inv = 1.0f / (float)E;
+  return make_float4(v.x, v.y * inv, v.z * inv, v.w * inv);
+}
+
+__global__ void __launch_bounds__(kQueueThreads) raycast_lod_kernel(RaycastParams prm, DirectModels models,
+                                                                    LodLevels lv, uint32_t* counter) {
+  extern __shared__ float4 s_tf[];  // tf_n entries
+  for (int e = threadIdx.x; e < prm.tf_n; e += kQueueThreads) s_tf[e] = prm.tf[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int tiles_x = (prm.W + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * ((prm.H + kTileH - 1) / kTileH);
+  const float Nmax = (float)(lv.B0 * (lv.n - 1));
+  const float inv_range = 1.0f / (prm.vmax - prm.vmin);
+  const float tfs = (float)(prm.tf_n - 1);
+  unsigned long long marched = 0;
+  ModelGeom cur;
+  cur.block = -1;
+  cur.ok = false;
+
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = (int)atomicAdd(counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= ntiles) break;
+    const int px = (tile % tiles_x) * kTileW + tile_dx(lane);
+    const int py = (tile / tiles_x) * kTileH + tile_dy(lane);
+    if (px < prm.W && py < prm.H) {
+      float d[3], t0;
+      const int K = ray_setup(prm, px, py, d, t0);
+      float gb[3], dg[3];
+      const float ts = fmaf(0.5f, prm.dt, t0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gb[a] = (fmaf(ts, d[a], prm.eye[a]) + 1.0f) * prm.half[a];
+        dg[a] = prm.dt * d[a] * prm.half[a];
+      }
+      float cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+      int k = 0;
+      while (k < K) {
+        const float kf = (float)k;
+        float gv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gv[a] = fminf(fmaxf(fmaf(kf, dg[a], gb[a]), 0.f), Nmax);
+        const float4 s = sample_lod(prm, models, lv, gv, cur);
+        ++k;
+        if (composite(prm, s_tf, s, d, inv_range, tfs, cr, cg, cb, A)) break;
+      }
+      prm.image[(int64_t)py * prm.W + px] = make_float4(cr, cg, cb, A);
+      marched += (unsigned long long)k;
+    }
+  }
+  count_marched(prm, marched, lane);
+}
+
+int raycast_lod(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, const LodLevels& lv,
+                cudaStream_t stream) {
+  if (prm.tf_n > kMaxTf) return MFA_ERR_CAPACITY;
+  const size_t smem = (size_t)prm.tf_n * sizeof(float4);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_lod_kernel, kQueueThreads, smem) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  uint32_t* counter = ctx->d_counters + kRaycastQueue;
+  if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
+  raycast_lod_kernel<<<ctx->num_sms * (per_sm > 0 ? per_sm : 1), kQueueThreads, smem, stream>>>(prm, models, lv,
+                                                                                                 counter);
+  ctx->launches++;
+  return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+}
+
 int raycast_direct(mfa_ctx* ctx, const RaycastParams& prm, const DirectModels& models, cudaStream_t stream) {
   if (prm.tf_n > kMaxTf) return MFA_ERR_CAPACITY;
   const size_t smem = (size_t)prm.tf_n * sizeof(float4);

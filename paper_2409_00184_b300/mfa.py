@@ -20,6 +20,7 @@ PREC_FP32, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16 = 0, 1, 2, 3
 DECODE_VALUE_ONLY, DECODE_LIST_SLOTS, DECODE_CUBES, DECODE_APRON = 1, 2, 4, 8
 RAYCAST_CUBES, RAYCAST_APRON, RAYCAST_COUNT_SECTORS = 1, 2, 4
 STAT_RAY_SAMPLES, STAT_RAY_SECTORS, NUM_STATS = 0, 1, 2
+LOD_SHARED_BOUNDARY = 1
 MAX_DEGREE, MAX_NCP, MAX_NSAMP = 3, 32, 64
 
 
@@ -69,7 +70,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
            "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
            "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop",
-           "mfa_raycast_ex", "mfa_fill_aprons"]
+           "mfa_raycast_ex", "mfa_fill_aprons", "mfa_lod_gather_ex", "mfa_lod_select", "mfa_raycast_lod"]
 
 
 def _load():
@@ -99,6 +100,10 @@ def _load():
         "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
         "mfa_selftest_wait_timeout": (ctypes.c_int, [P, I32, P]),
         "mfa_lod_gather": (ctypes.c_int, [P, P, ctypes.POINTER(I32), I32, I32, P, I32, P, I64, P]),
+        "mfa_lod_gather_ex": (ctypes.c_int, [P, P, ctypes.POINTER(I32), I32, I32, P, I32, P, I64, U32, P]),
+        "mfa_lod_select": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float * 3), I32, I32, I32, P, P, P]),
+        "mfa_raycast_lod": (ctypes.c_int, [P, P, I32, P, I64, P, I64, ctypes.POINTER(Bounds), P, I32, I32, I32,
+                                           ctypes.POINTER(View), P, I32, P, P]),
         "mfa_raycast_direct": (ctypes.c_int, [P, P, I32, P, I64, P, I64, ctypes.POINTER(Bounds), P,
                                               ctypes.POINTER(I32), I32, P, P, I32, P, P]),
         "mfa_store_write": (ctypes.c_int, [ctypes.c_char_p, P, I32, P, I64, P, I64]),
@@ -394,15 +399,20 @@ def select_ncp(ctx, errors, ncps, bound, out=None, stream=None):
     return out
 
 
-def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=None):
-    """mfa_lod_gather: the n^3 micro-blocks of one level of detail (every stride-th sample of blocks of
-    n*stride samples per axis) of a float32 CUDA field of shape (Nz, Ny, Nx). ids: int32 CUDA tensor of
-    block ids (None = the first nblocks, default all). Returns a float32 tensor (len, n^3)."""
+def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=None, shared=False):
+    """mfa_lod_gather (mfa_lod_gather_ex with MFA_LOD_SHARED_BOUNDARY when shared): the n^3 micro-blocks of
+    one level of detail (every stride-th sample of blocks of n*stride samples per axis, or of (n-1)*stride
+    intervals sharing their boundary samples) of a float32 CUDA field of shape (Nz, Ny, Nx). ids: int32
+    CUDA tensor of block ids (None = the first nblocks, default all). Returns a float32 tensor (len, n^3)."""
     if field.dim() != 3:
         raise ValueError("field: (Nz, Ny, Nx) tensor")
     Nz, Ny, Nx = field.shape
-    span = n * stride
-    total = (Nx // span) * (Ny // span) * (Nz // span)
+    if shared:
+        span = (n - 1) * stride
+        total = ((Nx - 1) // span) * ((Ny - 1) // span) * ((Nz - 1) // span)
+    else:
+        span = n * stride
+        total = (Nx // span) * (Ny // span) * (Nz // span)
     count = ids.numel() if ids is not None else (total if nblocks is None else nblocks)
     if out is None:
         out = torch.empty((count, n ** 3), dtype=torch.float32, device=field.device)
@@ -410,9 +420,35 @@ def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=N
     dims = (ctypes.c_int32 * 3)(Nx, Ny, Nz)
     if count == 0:
         return out
-    _check(lib.mfa_lod_gather(ctx.handle, _ptr(field), dims, n, stride, _ptr(ids), count, _ptr(out), n ** 3,
-                              _stream(stream)), "mfa_lod_gather")
+    _check(lib.mfa_lod_gather_ex(ctx.handle, _ptr(field), dims, n, stride, _ptr(ids), count, _ptr(out), n ** 3,
+                                 LOD_SHARED_BOUNDARY if shared else 0, _stream(stream)), "mfa_lod_gather_ex")
     return out
+
+
+def lod_select(ctx, eye, fine_blocks, n, levels, ranges=(0.8, 1.6, 2.4), table=None, stream=None):
+    """mfa_lod_select: int32 CUDA tensor (B0, B0, B0) [z][y][x] of the global id of the block that covers every
+    finest block for a point of view (levels of detail by distance, ranges[l-1] for level l >= 1)."""
+    if table is None:
+        table = torch.empty((fine_blocks,) * 3, dtype=torch.int32, device="cuda")
+    _need(table, fine_blocks ** 3, "table")
+    e = (ctypes.c_float * 3)(*[float(x) for x in eye])
+    r = (ctypes.c_float * max(1, len(ranges)))(*[float(x) for x in ranges])
+    _check(lib.mfa_lod_select(ctx.handle, ctypes.byref(e), fine_blocks, n, levels, r if levels > 1 else None,
+                              _ptr(table), _stream(stream)), "mfa_lod_select")
+    return table
+
+
+def raycast_lod(ctx, blocks, table, fine_blocks, n, levels, view, tf, image, cps=None, stream=None):
+    """mfa_raycast_lod: Algorithm 4 with per-sample queries of the models `table` (from lod_select) picks in a
+    DeviceBlocks batch holding every level's blocks by global id; image a float32 (H, W, 4) CUDA tensor."""
+    cps = blocks.cps if cps is None else cps
+    _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
+    _need(table, fine_blocks ** 3, "table")
+    v = make_view(view)
+    _check(lib.mfa_raycast_lod(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
+                               _ptr(cps), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table), fine_blocks, n, levels,
+                               ctypes.byref(v), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+           "mfa_raycast_lod")
 
 
 def store_write(path, bs):

@@ -49,6 +49,33 @@ def test_noalloc_encode_matches_plan_encode_twice():
     ctx.close()
 
 
+def test_noalloc_encode_without_rmse_takes_the_zfirst_fit():
+    """Without an RMSE buffer, with at most 16 control points and 32 samples per axis, 16-byte-aligned data and
+    a slot stride that is a multiple of 32, the fit runs on the z-first kernel, which reads the pseudo-inverses
+    and basis tables from the fixed scratch: two calls in a row against the plan-based encode."""
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    for seed in (904, 905):
+        bs = synth.random_block_set(40, seed, nsamp_choices=(16, 32), ncp_choices=(4, 6, 8, 12, 16))
+        stride = 32 ** 3
+        data = synth.rng(seed).uniform(-1, 1, (len(bs), stride)).astype(np.float32)
+        blk = mfa.DeviceBlocks(bs)
+        D = torch.from_numpy(data.ravel()).cuda()
+        assert D.data_ptr() % 16 == 0
+        plan = mfa.EncodePlan(ctx, blk)
+        want = torch.full((blk.cps_len,), float("nan"), device="cuda")
+        mfa.encode_blocks(ctx, plan, D, stride, len(bs), want)
+        assert ctx.device_status() == 0
+        plan.close()
+        got = torch.full((blk.cps_len,), float("nan"), device="cuda")
+        mfa.encode_blocks_noalloc(blk, D, stride, len(bs), got)
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        assert np.all(np.isfinite(g))
+        assert np.abs(g - w).max() <= 1e-5 * max(1.0, np.abs(w).max())
+    ctx.close()
+
+
 def test_noalloc_encode_rejects_a_batch_beyond_its_scratch():
     from paper_2409_00184_b300 import mfa
     torch.cuda.set_device(0)
