@@ -68,7 +68,8 @@ def parse():
                     help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
                          "decode)")
-    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct", "outofcore"],
+    ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct", "outofcore",
+                                           "lodrender"],
                     default="step",
                     help="step: the default 512^3 step; frames: adaptive-NCP frames replayed from a CUDA graph "
                          "(1024^3, ~6000 visible blocks); gd: gradient-descent fit (256^3, 512 blocks); "
@@ -76,7 +77,9 @@ def parse():
                          "ncp: Eq. 4 NCP search over every NCP in [3, 32] (512^3, 4096 blocks); "
                          "lod: Algorithm 1 cross-level encode of a 512^3 flame over 4 levels of detail; "
                          "direct: ray cast with per-sample micro-model queries vs the decoded cache; "
-                         "outofcore: frames through a model store and a host LRU cache with prefetching")
+                         "outofcore: frames through a model store and a host LRU cache with prefetching; "
+                         "lodrender: 4 levels of shared-boundary micro-blocks chosen by distance per frame and "
+                         "rendered by per-sample model queries, with PSNR against the finest level")
     return ap.parse_args()
 
 
@@ -447,6 +450,14 @@ def oracle_baselines(w, seed, timed=True):
                          f"of the 1024^2 pixels (over the oracle's decoded nodes those rays read), each scaled to the "
                          f"whole step ({t:.0f} s per step on {ncpu} worker processes; {t1:.0f} s on one core)"}
     return cpu, img_err
+
+
+def image_quality(got, want):
+    """MSE and PSNR (Sec. 5.2's image metrics, peak 1) of sampled pixels against the oracle's render of them."""
+    from oracle import multires as omr
+    got = np.asarray(got, dtype=np.float64)
+    return {"pixels": len(want), "mse": omr.mse(got, want), "psnr_db": omr.psnr(got, want),
+            "max_abs": float(np.abs(got - want).max())}
 
 
 def run_reference(args, ws, rank):
@@ -878,6 +889,15 @@ def run_direct(args):
     if ctx.device_status():
         raise RuntimeError("device status after the ray casts")
     diff = (img_direct - w.image).abs()
+    # the oracle's Algorithm 4 with per-sample queries of its own fit of the same samples, on sampled pixels
+    from oracle import multires as omr
+    from oracle import raycast as ocast
+    P_all = oracle_fit_all(w.D.view(w.B, BRICK, BRICK, BRICK).cpu().numpy())
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, DEGREE)).astype(np.float64) for _ in range(3))
+    pix = synth.rng(11).choice(IMG * IMG, 128, replace=False)
+    want = ocast.raycast_direct(lambda b: (P_all[b], knots, (DEGREE,) * 3), table.cpu().numpy(), BRICK, w.view,
+                                synth.transfer_function(synth.BASE_SEED + 2), pixels=pix)
+    got = img_direct.view(-1, 4)[torch.as_tensor(pix, device="cuda")].cpu().numpy()
     line = {"metric": "Algorithm 4 with per-sample micro-model queries: Gsample/s (no decoded cache)",
             "value": s_direct / (ms_direct * 1e-3) / 1e9, "unit": "Gsample/s", "n_gpus": 1, "steps": K, "warmup": 2,
             "ms_per_step": ms_direct, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -887,7 +907,9 @@ def run_direct(args):
             "samples_direct": s_direct, "samples_cache": s_cache,
             "cache_path": {"decode_ms": ms_dec, "raycast_ms": ms_cache, "total_ms": ms_dec + ms_cache,
                            "Gsample_s": s_cache / (ms_cache * 1e-3) / 1e9},
-            "image_diff": {"max": float(diff.max()), "mean": float(diff.mean())}}
+            "image_diff": {"max": float(diff.max()), "mean": float(diff.mean()),
+                           "psnr_db_direct_vs_cache": omr.psnr(img_direct.cpu().numpy(), w.image.cpu().numpy())},
+            "image_quality_vs_oracle": image_quality(got, want)}
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -936,6 +958,8 @@ def run_outofcore(args):
             stats.append(ooc.frame(vis[f], views[f], predicted=pred))
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        if mode == "prefetch":
+            last_image = ooc.image.clone()
         ooc.close()
         if ctx.device_status():
             raise RuntimeError("device status after the out-of-core frames")
@@ -948,6 +972,20 @@ def run_outofcore(args):
                      "read_MB": sum(s["bytes_read"] + s["prefetched_bytes"] for s in stats) / 1e6}
     os.unlink(path)
     pf = out["prefetch"]
+    # the last frame against the oracle's Algorithm 4 over its own decode of the visible models (sampled pixels)
+    from oracle import raycast as ocast
+    last = vis[-1]
+    groups = []
+    for c in np.unique(ncp[last]):
+        ids = last[ncp[last] == c]
+        groups.append((ids, np.stack([bs.block_cps(int(b)) for b in ids]), bs.block_knots(int(ids[0])), (p, p, p),
+                       (n, n, n)))
+    tab = np.full(B ** 3, -1, np.int64)
+    tab[last] = last
+    pix = synth.rng(12).choice(IMG * IMG, 256, replace=False)
+    want = ocast.raycast(ocast.decoded_nodes(groups, B ** 3), tab.reshape(B, B, B), n, views[-1],
+                         tf.cpu().numpy(), pixels=pix)
+    got = last_image.view(-1, 4)[torch.as_tensor(pix, device="cuda")].cpu().numpy()
     line = {"metric": "out-of-core frame time (caching + decode + ray cast), 1024^2", "value": pf["ms_per_frame"],
             "unit": "ms/frame", "n_gpus": 1, "steps": frames, "warmup": 0, "ms_per_step": pf["ms_per_frame"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -956,7 +994,120 @@ def run_outofcore(args):
                                    f"{store_s:.1f} s), 8000-model LRU cache, 32-frame orbit, ~6600 visible per frame",
                        "layout": args.layout, "visible_mean": float(np.mean([len(v) for v in vis])),
                        "store_seconds": store_s},
-            "modes": out}
+            "modes": out, "image_quality_vs_oracle": image_quality(got, want)}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def run_lodrender(args):
+    """Multi-resolution rendering (Sec. 4.3 with the LODs of Sec. 5.1.3): a 1025^3 Gaussian-mixture + noise field
+    cut into shared-boundary micro-blocks of 33^3 at 4 levels (32^3, 16^3, 8^3, 4^3 blocks), all fitted (degree 2,
+    12^3 control points); per frame of a 32-frame orbit the levels are chosen by distance (mfa_lod_select) and
+    the frame is rendered at 512^2 by per-sample queries of the chosen models (mfa_raycast_lod). Beside it the
+    same frames from the finest level only, and the PSNR between the two (the paper's quality measure of a
+    multi-resolution render); the first frame is also checked against the oracle on sampled pixels."""
+    from oracle import encode as oenc
+    from oracle import multires as omr
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    N, n, levels, C, p, W = 1025, 33, 4, NCP, DEGREE, 512
+    B0 = (N - 1) // (n - 1)
+    seed = synth.BASE_SEED + 6
+    field = synth.gm_noise_field(N, seed, device="cuda")
+    vox = n ** 3
+    counts = [(B0 >> l) ** 3 for l in range(levels)]
+    total = sum(counts)
+    D = torch.empty(total * vox, device="cuda")
+    o = 0
+    for lvl in range(levels):
+        mfa.lod_gather(ctx, field, n, 1 << lvl, out=D[o * vox:(o + counts[lvl]) * vox].view(counts[lvl], vox),
+                       shared=True)
+        o += counts[lvl]
+    zero = np.zeros((C, C, C))
+    bs = synth.make_block_set([(C,) * 3] * total, [(p,) * 3] * total, [(n,) * 3] * total, [zero] * total)
+    blk = mfa.DeviceBlocks(bs)
+    plan = mfa.EncodePlan(ctx, blk)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mfa.encode_blocks(ctx, plan, D, vox, total, blk.cps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    encode_ms = e0.elapsed_time(e1)
+    del D
+    torch.cuda.empty_cache()
+    tf = synth.transfer_function(seed)
+    tf_d = torch.from_numpy(tf).cuda()
+    frames = 32
+    views = [synth.orbit_view(f, radius=1.5, fov_y_deg=60.0, width=W, height=W) for f in range(frames)]
+    img = torch.empty(W, W, 4, device="cuda")
+    ref = torch.empty(W, W, 4, device="cuda")
+    table = torch.empty((B0,) * 3, dtype=torch.int32, device="cuda")
+    fine = torch.arange(B0 ** 3, dtype=torch.int32, device="cuda").view(B0, B0, B0)
+    for _ in range(max(1, args.warmup)):
+        mfa.lod_select(ctx, views[0]["eye"], B0, n, levels, table=table)
+        mfa.raycast_lod(ctx, blk, table, B0, n, levels, views[0], tf_d, img)
+    torch.cuda.synchronize()
+    ms_lod, ms_fine, psnr, per_level, bytes_sel = [], [], [], np.zeros(levels), []
+    ctx.ray_samples(reset=True)
+    for v in views:
+        e0.record(stream)
+        mfa.lod_select(ctx, v["eye"], B0, n, levels, table=table)
+        mfa.raycast_lod(ctx, blk, table, B0, n, levels, v, tf_d, img)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_lod.append(e0.elapsed_time(e1))
+        samples = ctx.ray_samples(reset=True)
+        e0.record(stream)
+        mfa.raycast_lod(ctx, blk, fine, B0, n, levels, v, tf_d, ref)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_fine.append(e0.elapsed_time(e1))
+        ctx.ray_samples(reset=True)
+        psnr.append(omr.psnr(img.cpu().numpy(), ref.cpu().numpy()))
+        used = torch.unique(table).cpu().numpy()
+        lv = np.searchsorted(np.cumsum(counts), used, side="right")
+        per_level += np.bincount(lv, minlength=levels)
+        bytes_sel.append(len(used) * int(mfa.model_bytes(C, p)))
+    if ctx.device_status():
+        raise RuntimeError("device status after the LOD frames")
+    # frame 0 against the oracle's render of its own fits of the same samples, on sampled pixels
+    host = field.cpu().numpy()
+    del field
+    knots = tuple(np.float32(synth.clamped_uniform_knots(C, p)).astype(np.float64) for _ in range(3))
+    fits = {}
+
+    def models(bid):
+        if bid not in fits:
+            lvl, g0, E = omr.block_geometry(bid, B0, n, levels)
+            s = 1 << lvl
+            blkD = host[g0[2]:g0[2] + E + 1:s, g0[1]:g0[1] + E + 1:s, g0[0]:g0[0] + E + 1:s].astype(np.float64)
+            fits[bid] = (oenc.fit_separable(blkD, knots, (p, p, p)), knots, (p, p, p))
+        return fits[bid]
+
+    t0 = omr.select_lod(views[0]["eye"], B0, n, levels)
+    mfa.lod_select(ctx, views[0]["eye"], B0, n, levels, table=table)
+    mfa.raycast_lod(ctx, blk, table, B0, n, levels, views[0], tf_d, img)
+    same_table = bool(np.array_equal(table.cpu().numpy(), t0))
+    pix = synth.rng(13).choice(W * W, 96, replace=False)
+    want = omr.raycast_lod(models, t0, n, levels, views[0], tf, pixels=pix)
+    got = img.view(-1, 4)[torch.as_tensor(pix, device="cuda")].cpu().numpy()
+    line = {"metric": "LOD-selected per-sample model queries (Algorithm 4): ms per 512^2 frame",
+            "value": float(np.mean(ms_lod)), "unit": "ms/frame", "n_gpus": 1, "steps": frames, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(ms_lod)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1025^3 Gaussian-mixture+noise field, shared-boundary micro-blocks of 33^3 at 4 levels "
+                                   "(32768 + 4096 + 512 + 64), degree 2, 12^3 control points; levels by distance "
+                                   "(ranges 0.8, 1.6, 2.4 in [-1,1]^3) along a 32-frame orbit of radius 1.5, 512^2",
+                       "blocks": total, "encode_ms_all_levels": encode_ms},
+            "finest_only_ms_per_frame": float(np.mean(ms_fine)),
+            "psnr_db_vs_finest": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
+            "models_per_frame_by_level": (per_level / frames).tolist(),
+            "model_bytes_per_frame": {"lod": float(np.mean(bytes_sel)), "finest": B0 ** 3 * int(mfa.model_bytes(C, p))},
+            "selection_equals_oracle_frame0": same_table,
+            "image_quality_vs_oracle_frame0": image_quality(got, want)}
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -981,6 +1132,8 @@ def main():
         return run_direct(args) if rank == 0 else 0
     if args.workload == "outofcore":
         return run_outofcore(args) if rank == 0 else 0
+    if args.workload == "lodrender":
+        return run_lodrender(args) if rank == 0 else 0
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist

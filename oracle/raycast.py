@@ -205,10 +205,11 @@ def fetch_direct(blocks, table, brick_n, g):
     return out
 
 
-def raycast_direct(blocks, table, brick_n, view, tf):
-    """Render with a per-sample query of the micro-models (see fetch_direct) instead of a decoded cache."""
+def raycast_direct(blocks, table, brick_n, view, tf, pixels=None):
+    """Render with a per-sample query of the micro-models (see fetch_direct) instead of a decoded cache; with
+    pixels, only those rays (as in :func:`raycast`)."""
     table = np.asarray(table)
-    return _march(table.shape, brick_n, view, tf, lambda g: fetch_direct(blocks, table, brick_n, g))
+    return _march(table.shape, brick_n, view, tf, lambda g: fetch_direct(blocks, table, brick_n, g), pixels)
 
 
 def _march(table_shape, brick_n, view, tf, sample, pixels=None, nodes=None, gscale=None):

@@ -233,6 +233,23 @@ def test_pixel_subset_equals_full_render():
         assert (full[:, 3] > 0).sum() > 100
 
 
+def test_direct_pixel_subset_equals_full_render():
+    """The per-sample-query renderer marches a subset of rays exactly as in its full render."""
+    g = synth.rng(55)
+    B, n, C, p = 2, 6, 4, 2
+    knots = tuple(synth.clamped_uniform_knots(C, p) for _ in range(3))
+    Ps = g.uniform(0, 1, (B ** 3, C, C, C))
+    table = np.arange(B ** 3, dtype=np.int32).reshape(B, B, B)
+    table[1, 0, 1] = -1
+    tf = synth.transfer_function(8)
+    view = synth.default_view(width=15, height=11, opacity_max=0.95)
+    models = lambda b: (Ps[b], knots, (p, p, p))  # noqa: E731
+    full = raycast.raycast_direct(models, table, n, view, tf).reshape(-1, 4)
+    pix = g.choice(15 * 11, 30, replace=False)
+    assert np.array_equal(raycast.raycast_direct(models, table, n, view, tf, pixels=pix), full[pix])
+    assert (full[:, 3] > 0).sum() > 40
+
+
 def test_voxel_function_equals_cache_array():
     """A cache given as a function of (slot, iz, iy, ix) renders the same image as the array it reads."""
     cache, table, n = _mixed_volume(53)
