@@ -208,7 +208,13 @@ int mfa_basis_tables(mfa_ctx* ctx, const mfa_block_desc* d_desc,
  * Written to d_grad_cps at the block's cp_off (same layout as the control points);
  * overwrites, does not accumulate. With d_cps non-NULL the residual is formed in the
  * kernel instead: R = decode_value(d_cps) - d_residual (d_residual then holds the data
- * samples D), which is the gradient of 0.5*||decode(P) - D||^2. */
+ * samples D), which is the gradient of 0.5*||decode(P) - D||^2.
+ * precision: MFA_PREC_FP32 (CUDA cores, any supported shape), or MFA_PREC_BF16 /
+ * MFA_PREC_SPLIT_BF16 on the tensor cores (BF16 operands, split-BF16 A*B ~ Ahi*Bhi + Ahi*Blo +
+ * Alo*Bhi, FP32 accumulation) for bounds with max_nsamp = 32 and max_ncp <= 16, d_cps NULL,
+ * d_residual 16-byte aligned and slot_stride_voxels a multiple of 4 (otherwise, and for
+ * MFA_PREC_FP16, MFA_ERR_UNSUPPORTED and nothing is enqueued); a block of another shape in such a
+ * batch sets MFA_DEV_BAD_DESC and is skipped. */
 int mfa_adjoint_blocks(mfa_ctx* ctx,
                        const mfa_block_desc* d_desc, int32_t nblocks,
                        const float* d_knots, int64_t knots_len,
@@ -295,6 +301,18 @@ int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
                        const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
                        float* d_cps_out, double* d_rmse /* nullable, one per block */,
                        void* stream);
+
+/* mfa_encode_blocks in a chosen arithmetic (the same least-squares fit of Algorithm 1's model()).
+ * MFA_PREC_FP32: mfa_encode_blocks. MFA_PREC_BF16 / MFA_PREC_SPLIT_BF16: the three pseudo-inverse
+ * contractions P = D x_1 Px x_2 Py x_3 Pz run on the tensor cores with BF16 operands (split-BF16:
+ * A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi, each stage's FP32 result split again) and FP32 accumulation; the
+ * pseudo-inverses are the plan's (FP64-built, stored FP32). For plans whose blocks all have 32 samples
+ * and at most 16 control points per axis, with d_rmse NULL, d_data 16-byte aligned and
+ * slot_stride_voxels a multiple of 4; otherwise (and for MFA_PREC_FP16) MFA_ERR_UNSUPPORTED and nothing
+ * is enqueued. Other checks as mfa_encode_blocks. */
+int  mfa_encode_blocks_ex(mfa_ctx* ctx, const mfa_encode_plan* plan,
+                          const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
+                          float* d_cps_out, double* d_rmse, int32_t precision, void* stream);
 
 /* In-level adaptive encoding, Eq. 4 (Sec. 4.2.2): NCP* = the smallest NCP whose error is below the
  * bound e. d_errors holds, candidate-major, one error per (candidate, block):

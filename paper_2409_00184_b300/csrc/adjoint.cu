@@ -230,7 +230,8 @@ cudaError_t launch_adj(mfa_ctx* ctx, const AdjointParams& prm, const AdjSmem& L,
 
 int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream) {
   // the dense contraction kernel first (N^T R, or M P - N^T D for the fused gradient); this banded
-  // gather kernel only serves block shapes whose buffers do not fit that kernel's shared memory
+  // gather kernel only serves block shapes whose buffers do not fit that kernel's shared memory. The
+  // 16-bit precisions run on the tensor-core contraction only.
   {
     ContractParams c;
     std::memset(&c, 0, sizeof(c));
@@ -252,6 +253,7 @@ int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream) {
     c.maxN = prm.bounds.max_nsamp;
     c.pmax = prm.bounds.max_degree;
     c.rows32 = prm.bounds.max_nsamp == 32;
+    if (prm.precision != MFA_PREC_FP32) return contract_tc(ctx, c, prm.precision, stream);
     const int rc = contract3(ctx, c, stream);
     if (rc != MFA_ERR_CAPACITY && rc != MFA_ERR_UNSUPPORTED) return rc;
   }

@@ -193,6 +193,29 @@ int run_fit(mfa_ctx* ctx, int nblocks, int maxC, int maxN, const EncItem* items,
   return contract3(ctx, prm, s);
 }
 
+// The fit on the tensor cores (BF16 / split-BF16, no RMSE pass): the same items, classes and pools.
+int run_fit_tc(mfa_ctx* ctx, int nblocks, int maxC, int maxN, const EncItem* items, const EncClass* classes,
+               float* pinv, const float* data, int64_t slot_stride, int64_t nslots, float* cps_out, int precision,
+               cudaStream_t s) {
+  ContractParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.mode = kFit;
+  prm.nblocks = nblocks;
+  prm.items = items;
+  prm.classes = classes;
+  prm.pinv = pinv;
+  prm.x = data;
+  prm.slot_stride = slot_stride;
+  prm.nslots = nslots;
+  prm.out = cps_out;
+  prm.status = ctx->d_status;
+  prm.counter = ctx->d_counters + kEncodeQueue;
+  prm.maxC = maxC;
+  prm.maxN = maxN;
+  prm.pmax = MFA_MAX_DEGREE;
+  return contract_tc(ctx, prm, precision, s);
+}
+
 }  // namespace
 }  // namespace mfa
 
@@ -268,6 +291,21 @@ int mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_
   return run_fit(ctx, plan->nblocks, plan->maxC, plan->maxN, plan->d_items, plan->d_classes, plan->d_pinv,
                  plan->d_tabs, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse,
                  static_cast<cudaStream_t>(stream), plan->rows32);
+}
+
+int mfa_encode_blocks_ex(mfa_ctx* ctx, const mfa_encode_plan* plan, const float* d_data, int64_t slot_stride_voxels,
+                         int64_t nslots, float* d_cps_out, double* d_rmse, int32_t precision, void* stream) {
+  if (precision == MFA_PREC_FP32)
+    return mfa_encode_blocks(ctx, plan, d_data, slot_stride_voxels, nslots, d_cps_out, d_rmse, stream);
+  if (precision != MFA_PREC_BF16 && precision != MFA_PREC_SPLIT_BF16 && precision != MFA_PREC_FP16)
+    return MFA_ERR_INVALID_ARG;
+  if (!ctx || !plan || plan->ctx != ctx || !d_data || !d_cps_out) return MFA_ERR_INVALID_ARG;
+  if (slot_stride_voxels < plan->max_vox || nslots <= plan->max_slot) return MFA_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_data) & 3) || (reinterpret_cast<uintptr_t>(d_cps_out) & 3))
+    return MFA_ERR_INVALID_ARG;
+  if (precision == MFA_PREC_FP16 || d_rmse) return MFA_ERR_UNSUPPORTED;
+  return run_fit_tc(ctx, plan->nblocks, plan->maxC, plan->maxN, plan->d_items, plan->d_classes, plan->d_pinv, d_data,
+                    slot_stride_voxels, nslots, d_cps_out, precision, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

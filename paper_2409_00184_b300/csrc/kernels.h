@@ -135,6 +135,7 @@ struct AdjointParams {
   mfa_bounds bounds;
   uint32_t* status;
   uint32_t* counter;
+  int precision = MFA_PREC_FP32;  // FP32: CUDA-core kernels; BF16 / split-BF16: the tensor-core contraction
 };
 
 int adjoint(mfa_ctx* ctx, const AdjointParams& prm, cudaStream_t stream);
@@ -194,5 +195,11 @@ struct ContractParams {
 
 // Returns MFA_ERR_CAPACITY (without launching) when the block shapes do not fit shared memory.
 int contract3(mfa_ctx* ctx, ContractParams prm, cudaStream_t stream);
+
+// The fit (without RMSE) and the adjoint on the tensor cores in BF16 or split-BF16 (precision MFA_PREC_BF16 /
+// MFA_PREC_SPLIT_BF16): 32 samples and at most 16 control points per axis, 16-byte-aligned sample grids with a
+// slot stride that is a multiple of 4 floats; MFA_ERR_UNSUPPORTED (nothing launched) for any other call. A
+// block of another shape in the batch sets MFA_DEV_BAD_DESC and is skipped.
+int contract_tc(mfa_ctx* ctx, const ContractParams& prm, int precision, cudaStream_t stream);
 
 }  // namespace mfa

@@ -246,8 +246,9 @@ int mfa_adjoint_blocks(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nbloc
   if (!aligned(d_desc, 8) || !aligned(d_knots, 4) || !aligned(d_residual, 4) || !aligned(d_grad_cps, 4) ||
       (d_cps && !aligned(d_cps, 4)))
     return MFA_ERR_INVALID_ARG;
-  if (precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
+  if (precision == MFA_PREC_FP16) return MFA_ERR_UNSUPPORTED;
   AdjointParams prm;
+  prm.precision = precision;
   prm.desc = d_desc;
   prm.nblocks = nblocks;
   prm.knots = d_knots;

@@ -70,7 +70,8 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_ctx_read_stats", "mfa_select_ncp", "mfa_selftest_wait_timeout", "mfa_lod_gather",
            "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
            "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop",
-           "mfa_raycast_ex", "mfa_fill_aprons", "mfa_lod_gather_ex", "mfa_lod_select", "mfa_raycast_lod"]
+           "mfa_raycast_ex", "mfa_fill_aprons", "mfa_lod_gather_ex", "mfa_lod_select", "mfa_raycast_lod",
+           "mfa_encode_blocks_ex"]
 
 
 def _load():
@@ -96,6 +97,7 @@ def _load():
         "mfa_encode_plan_create": (ctypes.c_int, [P, ctypes.POINTER(P), P, I32, P, I64, I64]),
         "mfa_encode_plan_destroy": (None, [P]),
         "mfa_encode_blocks": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
+        "mfa_encode_blocks_ex": (ctypes.c_int, [P, P, P, I64, I64, P, P, I32, P]),
         "mfa_encode_blocks_noalloc": (ctypes.c_int, [P, I32, P, I64, P, I64, I64, P, I64, P, P]),
         "mfa_select_ncp": (ctypes.c_int, [P, P, I32, P, I64, ctypes.c_double, P, P]),
         "mfa_selftest_wait_timeout": (ctypes.c_int, [P, I32, P]),
@@ -355,14 +357,19 @@ class EncodePlan:
             pass
 
 
-def encode_blocks(ctx, plan, data, slot_stride, nslots, cps_out, rmse=None, stream=None):
-    """mfa_encode_blocks: least-squares control points (and FP64 RMSE per block) from sample grids."""
+def encode_blocks(ctx, plan, data, slot_stride, nslots, cps_out, rmse=None, stream=None, precision=PREC_FP32):
+    """mfa_encode_blocks (mfa_encode_blocks_ex for another precision): least-squares control points (and FP64
+    RMSE per block, FP32 only) from sample grids."""
     _need(data, nslots * slot_stride, "data")
     _need(cps_out, plan.cps_len, "cps_out")
     if rmse is not None:
         _need(rmse, plan.nblocks, "rmse")
-    _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
-                                 _ptr(rmse), _stream(stream)), "mfa_encode_blocks")
+    if precision == PREC_FP32:
+        _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
+                                     _ptr(rmse), _stream(stream)), "mfa_encode_blocks")
+    else:
+        _check(lib.mfa_encode_blocks_ex(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
+                                        _ptr(rmse), precision, _stream(stream)), "mfa_encode_blocks_ex")
 
 
 def encode_blocks_noalloc(blocks, data, slot_stride, nslots, cps_out, rmse=None, stream=None):
