@@ -742,6 +742,29 @@ def run_precision(args):
                           "hbm_frac": algo / (ms * 1e-3) / 1e9 / hbm,
                           "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
                           "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm)}
+    # the fit (without RMSE) and the adjoint of the same blocks in each precision: 4 B/voxel read + C^3 written
+    D = synth.blocks_from_field(synth.gm_noise_field(N_FIELD, seed, device="cuda"), BRICK).contiguous().view(-1)
+    R = torch.empty_like(D).uniform_(-1, 1, generator=torch.Generator(device="cuda").manual_seed(seed))
+    P_tmp = torch.empty(blk.cps_len, device="cuda")
+    c_algo = B * (vox * 4 + NCP ** 3 * 4 + 72)
+    contraction = {}
+    for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16)):
+        for what, fn in (("fit", lambda: mfa.encode_blocks(ctx, plan, D, vox, B, P_tmp, precision=prec)),
+                         ("adjoint", lambda: mfa.adjoint_blocks(ctx, blk, R, vox, B, P_tmp, precision=prec))):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(K):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            contraction[f"{what}_{name}"] = {"ms": ms, "GB_s": c_algo / (ms * 1e-3) / 1e9,
+                                             "hbm_frac": c_algo / (ms * 1e-3) / 1e9 / hbm}
+    if ctx.device_status():
+        raise RuntimeError("device status after the contractions")
     launches = ctx.launch_count() - n0
     clk = clocks.stop()
     sp = variants["split_bf16"]
@@ -757,6 +780,9 @@ def run_precision(args):
                          "unit": "GB/s", "frac": sp["hbm_frac"], "traffic": None,
                          "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"},
             "variants": variants, "split_vs_fp32_speedup": variants["fp32"]["ms"] / sp["ms"],
+            "contraction": contraction,
+            "contraction_split_vs_fp32_speedup": {
+                w: contraction[f"{w}_fp32"]["ms"] / contraction[f"{w}_split_bf16"]["ms"] for w in ("fit", "adjoint")},
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
     ctx.close()

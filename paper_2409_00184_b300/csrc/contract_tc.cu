@@ -8,13 +8,14 @@
 //   stage x  T1[(k,j)][a] = sum_i X[(k,j)][i] Ax[i][a]   M = 1024 rows (8 tiles), K = i, N = 16 columns
 //   stage y  T2[(k,a)][b] = sum_j T1[(k,j)][a] Ay[j][b]   M = 512 rows (4 tiles),  K = j
 //   stage z  Y[(b,a)][c]  = sum_k T2[(k,a)][b] Az[k][c]   M = 256 rows (2 tiles),  K = k
-// K = 32 is two MMA steps of 16. The sample grid arrives in two batches of 16 planes: each thread loads its
-// share of a batch into registers (coalesced 16-byte loads), splits it into BF16 hi (and lo) parts and
-// writes the stage-x A operand; the next batch (and, after the last one, the next block's first batch) is
-// loaded while the MMAs of the current one run. Stage outputs are read from tensor memory, split again and
-// written transposed as the next stage's A operand; the B operands (the three A_a^T, zero beyond C) are
-// built per block. One thread issues the MMAs; completion is an mbarrier armed by tcgen05.commit and waited
-// on with a bounded poll that reports MFA_DEV_TIMEOUT.
+// K = 32 is two MMA steps of 16. The sample grid arrives in four batches of 8 planes: each thread loads its
+// share of a batch (coalesced 16-byte loads), splits it into BF16 hi (and lo) parts and writes the stage-x A
+// operand. Stage outputs are read from tensor memory, split again and written transposed as the next stage's
+// A operand (stage y in two halves of 16 planes); the B operands (the three A_a^T, zero beyond C) are built
+// per block. One 32 KB operand region serves every A operand in turn, and a CTA (one warpgroup) holds 128
+// tensor-memory columns, so four CTAs share an SM and one's loads and conversions overlap the others' MMAs.
+// One thread issues the MMAs; completion is an mbarrier armed by tcgen05.commit and waited on with a
+// bounded poll that reports MFA_DEV_TIMEOUT.
 #include <algorithm>
 #include <cuda_bf16.h>
 
@@ -25,24 +26,30 @@
 namespace mfa {
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 128;           // one warpgroup: warp w reads tensor-memory lanes 32w .. 32w+31
 constexpr int kTcN = 32;                  // samples per axis (the contraction's K)
 constexpr int kTcC = 16;                  // padded control points per axis (the MMA N)
-constexpr uint32_t kLBO32 = 128, kSBO32 = 512;  // K-major core-matrix strides for K = 32
-constexpr int kRowB = 64;                 // bytes of one operand row (32 x 16-bit)
-constexpr int kBatchRows = 512;           // 16 planes x 32 rows
-constexpr int kF4PerThread = kBatchRows * 8 / kTcThreads;  // float4 loads per thread and batch (16)
+// K-major core-matrix strides for K = 32: the four K-adjacent core matrices (8 rows x 16 bytes) of a row group
+// lie 144 bytes apart instead of back to back, so the same row of consecutive K chunks falls in different
+// shared-memory banks (a warp writing one row's 32 K entries, or one K entry of 8 rows, hits no bank twice).
+constexpr uint32_t kLBO32 = 144, kSBO32 = 4 * kLBO32;
+constexpr int kOpRows = 256;              // rows of the operand region (two 128-row tiles)
+constexpr int kBatches = 4;               // 8 planes (256 rows of 32 samples) per batch
+constexpr int kF4Round = 8;               // float4 loads per thread in flight
+constexpr int kF4PerThread = kOpRows * 8 / kTcThreads;  // float4 loads per thread and batch (16)
 
-// Shared-memory layout (bytes): every operand is stored hi, then lo at +half its region.
-constexpr int kA1 = 0, kA1Lo = kBatchRows * kRowB;                  // stage-x A: 512 rows
-constexpr int kA2 = kA1 + 2 * kBatchRows * kRowB, kA2Lo = 512 * kRowB;  // stage-y A: 512 rows (k,a)
-constexpr int kA3 = kA2 + 2 * 512 * kRowB, kA3Lo = 256 * kRowB;       // stage-z A: 256 rows (b,a)
-constexpr int kB = kA3 + 2 * 256 * kRowB, kBLo = kTcC * kRowB;        // B_x, B_y, B_z: 16 rows each
-constexpr int kBasisOff = kB + 3 * 2 * kTcC * kRowB;                 // adjoint: per axis and sample
-constexpr int kTcSmem = kBasisOff + 3 * kTcN * 32 + 1024;            // + slack for 1024-byte alignment
-static_assert(kTcSmem <= 227 * 1024, "shared memory budget");
-// tensor-memory columns: T1 8 x 16, T2 4 x 16, Y 2 x 16
-constexpr uint32_t kT1 = 0, kT2 = 128, kT3 = 192, kTcCols = 256;
+// Shared-memory layout (bytes). One operand region serves the stage-x A (a batch), the stage-y A (half of
+// its rows) and the stage-z A in turn: each is written only after the MMAs that read the previous one have
+// completed. Every operand is stored hi, then lo at +half its region.
+constexpr int kOp = 0, kOpLo = kOpRows / 8 * kSBO32;                  // 256 rows: 18 KB (+18 KB lo)
+constexpr int kB = kOp + 2 * kOpLo, kBLo = kTcC / 8 * kSBO32;        // B_x, B_y, B_z: 16 rows each (+lo)
+constexpr int kBasisOff = kB + 3 * 2 * kBLo;                         // adjoint: per axis and sample
+constexpr int kTcUsed = kBasisOff + 3 * kTcN * 32 + 1024;            // + slack for 1024-byte alignment
+// requested per CTA: at most four CTAs share an SM (4 x 128 tensor-memory columns)
+constexpr int kTcSmem = 48 * 1024;
+static_assert(kTcUsed <= kTcSmem, "shared memory budget");
+// tensor-memory columns: T1 8 tiles x 16 (then T2 over the first 64, Y over the next 32)
+constexpr uint32_t kT1 = 0, kT2 = 0, kT3 = 64, kTcCols = 128;
 
 struct TcBand {  // one sample of one axis: first nonzero basis index and the p+1 values there
   int off;
@@ -112,16 +119,15 @@ __device__ __forceinline__ uint32_t load_tc_item(const ContractParams& prm, int 
 }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(ContractParams prm) {
+__global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ TcGeom s_g[2];
+  __shared__ TcGeom s_g;
   __shared__ float s_kn[3][kKnotMax];
   __shared__ int s_bad;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, group = warp >> 2;
   TcBand* band = reinterpret_cast<TcBand*>(sm + kBasisOff);  // [axis][sample]
 
   if (warp == 0) {
@@ -136,13 +142,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(ContractPara
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
   const uint32_t sbase = smem_addr(sm);
   const uint32_t idesc = idesc_f16(128, kTcC, true);
   uint32_t phase = 0;
   bool timed_out = false;
 
-  // D (+)= A * B^T over K = 32 (two steps of 16), A and B at byte offsets with their lo parts further on
-  auto mma32 = [&](uint32_t d, uint32_t a, uint32_t a_lo, uint32_t b) {
+  // D (+)= A * B^T over K = 32 (two steps of 16); A at byte offset a in the operand region, B at offset b
+  auto mma32 = [&](uint32_t d, uint32_t a, uint32_t b) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const uint32_t ko = s * 2 * kLBO32;
@@ -151,9 +158,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(ContractPara
       if (SPLIT) {
         mma_f16(d, desc_kmajor(sbase + a + ko, kLBO32, kSBO32), desc_kmajor(sbase + b + kBLo + ko, kLBO32, kSBO32),
                 idesc, 1);
-        mma_f16(d, desc_kmajor(sbase + a + a_lo + ko, kLBO32, kSBO32), desc_kmajor(sbase + b + ko, kLBO32, kSBO32),
+        mma_f16(d, desc_kmajor(sbase + a + kOpLo + ko, kLBO32, kSBO32), desc_kmajor(sbase + b + ko, kLBO32, kSBO32),
                 idesc, 1);
       }
+    }
+  };
+  // the two 128-row tiles of the operand region against B, into tensor-memory columns d0 and d1
+  auto mma_tiles = [&](uint32_t d0, uint32_t d1, uint32_t b) {
+    if (tid == 0) {
+      mma32(tmem + d0, kOp, b);
+      mma32(tmem + d1, kOp + 16 * kSBO32, b);
+      mma_commit(&s_bar);
     }
   };
   auto wait_mma = [&]() {  // all threads
@@ -172,51 +187,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(ContractPara
     __syncthreads();
     tc_fence_after();
   };
-  // thread 0: the next valid work item into s_g[buf] (ok = 0 when the queue is empty)
-  auto fetch = [&](int buf) {
-    for (;;) {
-      const int item = (int)atomicAdd(prm.counter, 1u);
-      if (item >= prm.nblocks) {
-        s_g[buf].ok = 0;
-        return;
+
+  for (;;) {
+    if (tid == 0) {  // the next valid work item (ok = 0 when the queue is empty)
+      for (;;) {
+        const int item = (int)atomicAdd(prm.counter, 1u);
+        if (item >= prm.nblocks) {
+          s_g.ok = 0;
+          break;
+        }
+        const uint32_t bad = load_tc_item(prm, item, s_g);
+        if (!bad) break;
+        flag(prm.status, bad);
       }
-      const uint32_t bad = load_tc_item(prm, item, s_g[buf]);
-      if (!bad) return;
-      flag(prm.status, bad);
+      s_bad = 0;
     }
-  };
-  float4 xr[kF4PerThread];
-  // this thread's share of batch h (16 planes) of the block in s_g[buf]
-  auto load_batch = [&](int buf, int h) {
-    const float4* src = reinterpret_cast<const float4*>(prm.x + (int64_t)s_g[buf].slot * prm.slot_stride +
-                                                        (int64_t)h * kBatchRows * kTcN);
-#pragma unroll
-    for (int s = 0; s < kF4PerThread; ++s) xr[s] = __ldg(src + s * kTcThreads + tid);
-  };
-  auto store_batch = [&]() {
-#pragma unroll
-    for (int s = 0; s < kF4PerThread; ++s) {
-      const int e = s * kTcThreads + tid, row = e >> 3, k4 = (e & 7) * 4;
-      const uint32_t o = kA1 + off32(row, k4);
-      put_pair<SPLIT>(sm, o, kA1Lo, xr[s].x, xr[s].y);
-      put_pair<SPLIT>(sm, o + 4, kA1Lo, xr[s].z, xr[s].w);
-    }
-  };
-
-  if (tid == 0) fetch(0);
-  __syncthreads();
-  int cur = 0;
-  if (s_g[0].ok) load_batch(0, 0);
-
-  while (s_g[cur].ok && !timed_out) {
-    const TcGeom& g = s_g[cur];
+    __syncthreads();
+    if (!s_g.ok || timed_out) break;
+    const TcGeom& g = s_g;
     // ---- B operands: B_a[c][i] = A_a[i][c] for c < C_a, else 0 ----
     if (prm.mode == kAdjoint) {
       if (tid < 3 * kKnotMax) {
         const int a = tid / kKnotMax, i = tid - a * kKnotMax;
         if (i < g.C[a] + g.p[a] + 1) s_kn[a][i] = prm.knots[g.koff[a] + i];
       }
-      if (tid == 0) s_bad = 0;
       __syncthreads();
       if (tid < 3 && !knots_ok(s_kn[tid], g.p[tid], g.C[tid])) {
         atomicOr(&s_bad, 1);
@@ -248,84 +242,93 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(ContractPara
           if (d >= 0 && d <= g.p[a]) v = b.N[d];
         }
       }
-      put_one<SPLIT>(sm, kB + a * 2 * kTcC * kRowB + off32(c, i), kBLo, v);
+      put_one<SPLIT>(sm, kB + a * 2 * kBLo + off32(c, i), kBLo, v);
     }
-    const bool skip = prm.mode == kAdjoint && s_bad;  // s_bad is only read after the barriers above
-    // ---- stage x, two batches of 16 planes; the next loads are in flight while the MMAs run ----
-    for (int h = 0; h < 2 && !timed_out; ++h) {
-      store_batch();
-      operands_ready();
-      if (tid == 0 && !skip) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          mma32(tmem + kT1 + 16 * (4 * h + t), kA1 + t * 16 * kSBO32, kA1Lo, kB);
-      }
-      if (tid == 0) {
-        if (h == 1) fetch(cur ^ 1);  // the next block, whose first batch loads during this block's stages
-        if (!skip) mma_commit(&s_bar);
-      }
+    if (prm.mode == kAdjoint && s_bad) {  // (s_bad is read after the barriers above)
       __syncthreads();
-      if (h == 0) load_batch(cur, 1);
-      else if (s_g[cur ^ 1].ok) load_batch(cur ^ 1, 0);
-      if (!skip) wait_mma();
+      continue;
+    }
+    // ---- stage x: four batches of 8 planes (256 rows of 32 samples) through the operand region ----
+    // Each batch is loaded in two rounds of kF4Round float4 per thread; the first round of the next batch is
+    // in flight while the current batch's MMAs run.
+    const float4* src = reinterpret_cast<const float4*>(prm.x + (int64_t)g.slot * prm.slot_stride);
+    float4 xr[kF4Round];
+    auto load_round = [&](int h, int s0) {
+#pragma unroll
+      for (int s = 0; s < kF4Round; ++s) xr[s] = __ldg(src + (h * kF4PerThread + s0 + s) * kTcThreads + tid);
+    };
+    auto store_round = [&](int s0) {
+#pragma unroll
+      for (int s = 0; s < kF4Round; ++s) {
+        const int e = (s0 + s) * kTcThreads + tid, row = e >> 3, k4 = (e & 7) * 4;
+        const uint32_t o = kOp + off32(row, k4);
+        put_pair<SPLIT>(sm, o, kOpLo, xr[s].x, xr[s].y);
+        put_pair<SPLIT>(sm, o + 4, kOpLo, xr[s].z, xr[s].w);
+      }
+    };
+    static_assert(kF4PerThread == 2 * kF4Round, "two rounds per batch");
+    load_round(0, 0);
+    for (int h = 0; h < kBatches && !timed_out; ++h) {
+      if (h > 0) wait_mma();  // the previous batch's MMAs have read the region
+      if (timed_out) break;
+      store_round(0);
+      load_round(h, kF4Round);
+      store_round(kF4Round);
+      operands_ready();
+      mma_tiles(kT1 + 32 * h, kT1 + 32 * h + 16, kB);
+      if (h + 1 < kBatches) load_round(h + 1, 0);
     }
     if (timed_out) break;
-    if (!skip) {
-      // ---- T1 -> A2: row (k,a) = 16k + a, K = j ----
+    wait_mma();
+    if (timed_out) break;
+    // ---- stage y in two halves of 16 planes: T1 (row (k,j) = 32k + j) -> operand rows 16(k - 16 half) + a ----
+    for (int half = 0; half < 2 && !timed_out; ++half) {
 #pragma unroll
       for (int tt = 0; tt < 4; ++tt) {
-        const int t = group + 2 * tt, k = 4 * t + quarter, j = lane;
+        const int t = 4 * half + tt, kl = 4 * tt + warp;  // T1 tile t, row 32 warp + lane: k = 4t + warp
         uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + kT1 + 16 * t, r);
+        tmem_ld16(tlane + kT1 + 16 * t, r);
         tmem_ld_wait();
 #pragma unroll
-        for (int a = 0; a < kTcC; ++a) put_one<SPLIT>(sm, kA2 + off32(16 * k + a, j), kA2Lo, __uint_as_float(r[a]));
+        for (int a = 0; a < kTcC; ++a) put_one<SPLIT>(sm, kOp + off32(16 * kl + a, lane), kOpLo, __uint_as_float(r[a]));
       }
       operands_ready();
-      if (tid == 0) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) mma32(tmem + kT2 + 16 * u, kA2 + u * 16 * kSBO32, kA2Lo, kB + 2 * kTcC * kRowB);
-        mma_commit(&s_bar);
-      }
+      mma_tiles(kT2 + 32 * half, kT2 + 32 * half + 16, kB + 2 * kBLo);
       wait_mma();
-      if (timed_out) break;
-      // ---- T2 -> A3: T2 row (k,a) = 128u + 32q + lane; A3 row (b,a) = 16b + a, K = k ----
+    }
+    if (timed_out) break;
+    // ---- stage z: T2 (row (k,a) = 16k + a) -> operand rows (b,a) = 16b + a, K = k ----
 #pragma unroll
-      for (int uu = 0; uu < 2; ++uu) {
-        const int u = group + 2 * uu, R = 128 * u + 32 * quarter + lane, k = R >> 4, a = R & 15;
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + kT2 + 16 * u, r);
-        tmem_ld_wait();
+    for (int u = 0; u < 4; ++u) {
+      const int R = 128 * u + 32 * warp + lane, k = R >> 4, a = R & 15;
+      uint32_t r[16];
+      tmem_ld16(tlane + kT2 + 16 * u, r);
+      tmem_ld_wait();
 #pragma unroll
-        for (int b = 0; b < kTcC; ++b) put_one<SPLIT>(sm, kA3 + off32(16 * b + a, k), kA3Lo, __uint_as_float(r[b]));
-      }
-      operands_ready();
-      if (tid == 0) {
+      for (int b = 0; b < kTcC; ++b) put_one<SPLIT>(sm, kOp + off32(16 * b + a, k), kOpLo, __uint_as_float(r[b]));
+    }
+    operands_ready();
+    mma_tiles(kT3, kT3 + 16, kB + 4 * kBLo);
+    wait_mma();
+    if (timed_out) break;
+    // ---- Y row (b,a) = 128v + 32 warp + lane, columns c -> out[cp_off + (c Cy + b) Cx + a] ----
 #pragma unroll
-        for (int v = 0; v < 2; ++v) mma32(tmem + kT3 + 16 * v, kA3 + v * 16 * kSBO32, kA3Lo, kB + 4 * kTcC * kRowB);
-        mma_commit(&s_bar);
-      }
-      wait_mma();
-      if (timed_out) break;
-      // ---- Y row (b,a) = 128v + 32q + lane, columns c -> out[cp_off + (c Cy + b) Cx + a] ----
-      {
-        const int R = 128 * group + 32 * quarter + lane, b = R >> 4, a = R & 15;
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + kT3 + 16 * group, r);
-        tmem_ld_wait();
-        const int Cx = g.C[0], Cy = g.C[1], Cz = g.C[2];
-        if (a < Cx && b < Cy) {
-          float* out = prm.out + g.cp_off + (int64_t)b * Cx + a;
+    for (int v = 0; v < 2; ++v) {
+      const int R = 128 * v + 32 * warp + lane, b = R >> 4, a = R & 15;
+      uint32_t r[16];
+      tmem_ld16(tlane + kT3 + 16 * v, r);
+      tmem_ld_wait();
+      const int Cx = g.C[0], Cy = g.C[1], Cz = g.C[2];
+      if (a < Cx && b < Cy) {
+        float* out = prm.out + g.cp_off + (int64_t)b * Cx + a;
 #pragma unroll
-          for (int c = 0; c < kTcC; ++c)
-            if (c < Cz) out[(int64_t)c * Cy * Cx] = __uint_as_float(r[c]);
-        }
+        for (int c = 0; c < kTcC; ++c)
+          if (c < Cz) out[(int64_t)c * Cy * Cx] = __uint_as_float(r[c]);
       }
     }
     tc_fence_before();
-    __syncthreads();  // the operands, s_g[cur] and the tensor memory are reused by the next block
+    __syncthreads();  // the operands, s_g and the tensor memory are reused by the next block
     tc_fence_after();
-    cur ^= 1;
   }
   tc_fence_before();
   __syncthreads();
@@ -337,8 +340,22 @@ int launch_contract_tc(mfa_ctx* ctx, const ContractParams& prm, cudaStream_t str
   if (cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
       cudaSuccess)
     return MFA_ERR_CUDA;
+  if (cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  // resident CTAs per SM from the kernel's registers and shared memory (and the SM's register file and
+  // shared memory), at most four: every resident CTA holds 128 of the SM's 512 tensor-memory columns
+  cudaFuncAttributes fa;
+  int smem_sm = 0, regs_sm = 0;
+  if (cudaFuncGetAttributes(&fa, contract_tc_kernel<SPLIT>) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  const int by_regs = regs_sm / std::max(1, fa.numRegs * kTcThreads);
+  const int by_smem = smem_sm / (int)(kTcSmem + fa.sharedSizeBytes + 1024);
+  const int per_sm = std::max(1, std::min(512 / (int)kTcCols, std::min(by_regs, by_smem)));
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
-  const int grid = std::min(ctx->num_sms, prm.nblocks);
+  const int grid = std::min(ctx->num_sms * per_sm, prm.nblocks);
   contract_tc_kernel<SPLIT><<<grid, kTcThreads, kTcSmem, stream>>>(prm);
   ctx->launches++;
   return cudaGetLastError() == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
