@@ -42,7 +42,7 @@ WORKLOAD = ("512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degr
             "+ 1024^2 ray cast (1 sample/voxel, 256-entry TF) + adjoint of the residual")
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed by kernel and
 # cache layout, with the sha256 of the kernel source it was taken on; reported as null once the source changes.
-TRAFFIC = {("raycast", "apron"): {"bytes": 455.31e6 + 17.15e6, "src_sha": "d540ec71a9b54445"}}
+TRAFFIC = {("raycast", "apron"): {"bytes": 455153408 + 16834048, "src_sha": "65523ff5aba58011"}}
 # FP32 operations per ray-cast sample in the algorithm (FMA = 2): sample position 14, trilinear
 # interpolation of 4 channels 87, transfer function 18, headlight shading 20, compositing 15.
 RAY_FLOPS_PER_SAMPLE = 154
