@@ -289,8 +289,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
         uint32_t r[16];
         tmem_ld16(tlane + kT1 + 16 * t, r);
         tmem_ld_wait();
+        // Lanes j and j^1 trade values so that each writes one 32-bit word (K = j & ~1 and its successor):
+        // the even lane the word of row (kl, a), the odd lane that of row (kl, a + 8). Those two rows lie
+        // in different bank halves, so the warp's 32 words hit 32 banks.
+        const bool even = (lane & 1) == 0;
 #pragma unroll
-        for (int a = 0; a < kTcC; ++a) put_one<SPLIT>(sm, kOp + off32(16 * kl + a, lane), kOpLo, __uint_as_float(r[a]));
+        for (int a = 0; a < kTcC / 2; ++a) {
+          const float va = __uint_as_float(r[a]), vb = __uint_as_float(r[a + 8]);
+          const float got = __shfl_xor_sync(0xffffffffu, even ? vb : va, 1);
+          const int row = 16 * kl + (even ? a : a + 8);
+          put_pair<SPLIT>(sm, kOp + off32(row, lane & ~1), kOpLo, even ? va : got, even ? got : vb);
+        }
       }
       operands_ready();
       mma_tiles(kT2 + 32 * half, kT2 + 32 * half + 16, kB + 2 * kBLo);
