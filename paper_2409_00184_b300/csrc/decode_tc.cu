@@ -89,6 +89,15 @@ __device__ __forceinline__ void put(unsigned char* base, uint32_t off, uint32_t 
   *reinterpret_cast<uint16_t*>(base + off) = h;
   if (PREC == kSplit) *reinterpret_cast<uint16_t*>(base + lo_delta + off) = to16<PREC>(x - from16<PREC>(h));
 }
+// Writes two consecutive K entries (x0 first) as one 32-bit word and, for split-BF16, their remainders.
+template <int PREC>
+__device__ __forceinline__ void put2(unsigned char* base, uint32_t off, uint32_t lo_delta, float x0, float x1) {
+  const uint16_t h0 = to16<PREC>(x0), h1 = to16<PREC>(x1);
+  *reinterpret_cast<uint32_t*>(base + off) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+  if (PREC == kSplit)
+    *reinterpret_cast<uint32_t*>(base + lo_delta + off) =
+        (uint32_t)to16<PREC>(x0 - from16<PREC>(h0)) | ((uint32_t)to16<PREC>(x1 - from16<PREC>(h1)) << 16);
+}
 // Writes 8 consecutive K entries of one operand row (16 bytes) and, for split-BF16, their remainders.
 template <int PREC>
 __device__ __forceinline__ void put8(unsigned char* base, uint32_t off, uint32_t lo_delta, const uint32_t* x) {
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     for (int e = tid; e < 2 * 64 * kK; e += kThreadsTC) {
       const int which = e / (64 * kK), rem = e - which * (64 * kK), n = rem / kK, c = rem - (rem / kK) * kK;
       const int axis = which == 0 ? 1 : 0;
-      const TcBasis tb = bas[axis * kN + (n & 31)];
+      const TcBasis& tb = bas[axis * kN + (n & 31)];
       const int d = c - tb.off;
       float v = 0.f;
       if (n < 32) { if (d >= 0 && d <= 3 && c < s_g.C[axis]) v = tb.N[d]; }
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         const int kl = n & 7;
         float v = 0.f;
         if ((n < 8) == (which == 0)) {
-          const TcBasis tb = bas[2 * kN + k0 + kl];
+          const TcBasis& tb = bas[2 * kN + k0 + kl];
           const int d = c - tb.off;
           if (d >= 0 && d <= 3) {
             if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
@@ -322,13 +331,21 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         tmem_ld16(ta, r0);
         tmem_ld16(ta + 32, r1);
         tmem_ld_wait();
+        // Lanes L and L + 16 hold the same (k, a) at b and b + 1 (adjacent K): they trade values so that
+        // the lower lane writes the 32-bit words (b, b + 1) of chains 0 and 1, the upper one those of chains 2
+        // and 3.
+        const bool low = (lane & 16) == 0;
+        unsigned char* dst0 = sm + L::Ty + (low ? 0 : 2 * kOp128);
+        unsigned char* dst1 = sm + L::Ty + (low ? kOp128 : 3 * kOp128);
 #pragma unroll
         for (int kl = 0; kl < kKS; ++kl) {
-          const uint32_t off = kmajor_off(kl * 16 + a, b, kLBO, kSBO);
-          put<PREC>(sm + L::Ty, off, L::dTy, __uint_as_float(r0[kl]));
-          put<PREC>(sm + L::Ty + kOp128, off, L::dTy, __uint_as_float(r1[8 + kl]));
-          put<PREC>(sm + L::Ty + 2 * kOp128, off, L::dTy, __uint_as_float(r1[kl]));
-          put<PREC>(sm + L::Ty + 3 * kOp128, off, L::dTy, __uint_as_float(r0[8 + kl]));
+          const float v0 = __uint_as_float(r0[kl]), v1 = __uint_as_float(r1[8 + kl]);
+          const float v2 = __uint_as_float(r1[kl]), v3 = __uint_as_float(r0[8 + kl]);
+          const float g0 = __shfl_xor_sync(0xffffffffu, low ? v2 : v0, 16);
+          const float g1 = __shfl_xor_sync(0xffffffffu, low ? v3 : v1, 16);
+          const uint32_t off = kmajor_off(kl * 16 + a, b & ~1, kLBO, kSBO);
+          put2<PREC>(dst0, off, L::dTy, low ? v0 : g0, low ? g0 : v2);
+          put2<PREC>(dst1, off, L::dTy, low ? v1 : g1, low ? g1 : v3);
         }
       }
       operands_ready();
