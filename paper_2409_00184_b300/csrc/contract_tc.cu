@@ -283,12 +283,14 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
     if (timed_out) break;
     // ---- stage y in two halves of 16 planes: T1 (row (k,j) = 32k + j) -> operand rows 16(k - 16 half) + a ----
     for (int half = 0; half < 2 && !timed_out; ++half) {
+      uint32_t r4[4][16];  // the half's four tiles are loaded together, then one wait
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt) tmem_ld16(tlane + kT1 + 16 * (4 * half + tt), r4[tt]);
+      tmem_ld_wait();
 #pragma unroll
       for (int tt = 0; tt < 4; ++tt) {
-        const int t = 4 * half + tt, kl = 4 * tt + warp;  // T1 tile t, row 32 warp + lane: k = 4t + warp
-        uint32_t r[16];
-        tmem_ld16(tlane + kT1 + 16 * t, r);
-        tmem_ld_wait();
+        const int kl = 4 * tt + warp;  // T1 tile 4 half + tt, row 32 warp + lane: k = 4t + warp
+        const uint32_t* r = r4[tt];
         // Lanes j and j^1 trade values so that each writes one 32-bit word (K = j & ~1 and its successor):
         // the even lane the word of row (kl, a), the odd lane that of row (kl, a + 8). Those two rows lie
         // in different bank halves, so the warp's 32 words hit 32 banks.
@@ -307,14 +309,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
     }
     if (timed_out) break;
     // ---- stage z: T2 (row (k,a) = 16k + a) -> operand rows (b,a) = 16b + a, K = k ----
+    {
+      uint32_t r4[4][16];  // the four tiles are loaded together, then one wait
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int R = 128 * u + 32 * warp + lane, k = R >> 4, a = R & 15;
-      uint32_t r[16];
-      tmem_ld16(tlane + kT2 + 16 * u, r);
+      for (int u = 0; u < 4; ++u) tmem_ld16(tlane + kT2 + 16 * u, r4[u]);
       tmem_ld_wait();
 #pragma unroll
-      for (int b = 0; b < kTcC; ++b) put_one<SPLIT>(sm, kOp + off32(16 * b + a, k), kOpLo, __uint_as_float(r[b]));
+      for (int u = 0; u < 4; ++u) {
+        const int R = 128 * u + 32 * warp + lane, k = R >> 4, a = R & 15;
+#pragma unroll
+        for (int b = 0; b < kTcC; ++b) put_one<SPLIT>(sm, kOp + off32(16 * b + a, k), kOpLo, __uint_as_float(r4[u][b]));
+      }
     }
     operands_ready();
     mma_tiles(kT3, kT3 + 16, kB + 4 * kBLo);

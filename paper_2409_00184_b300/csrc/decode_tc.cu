@@ -361,16 +361,18 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       if (timed_out) break;
       // readout y: warp (quarter c, group g) holds chain c, sample j = lane, planes k = 4g .. 4g+3;
       // stage-x A of chain c: element (row 32k + j, K = a), 16 consecutive K entries = two 16-byte stores
+      {  // the four loads are issued together, then one wait
+        uint32_t r[4][16];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const int kl = 4 * group + kk;
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * kl, r);
+        for (int kk = 0; kk < 4; ++kk) tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * (4 * group + kk), r[kk]);
         tmem_ld_wait();
-        const uint32_t off = kmajor_off(kl * 32 + lane, 0, kLBO, kSBO);
         unsigned char* base = sm + L::R1 + quarter * kOp256;
-        put8<PREC>(base, off, L::dAx, r);
-        put8<PREC>(base, off + kLBO, L::dAx, r + 8);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kmajor_off((4 * group + kk) * 32 + lane, 0, kLBO, kSBO);
+          put8<PREC>(base, off, L::dAx, r[kk]);
+          put8<PREC>(base, off + kLBO, L::dAx, r[kk] + 8);
+        }
       }
       operands_ready();
       // ---- stage x per 128-row tile: f | f_u | f_v | f_w in columns 0..127 of the tile ----
