@@ -127,8 +127,10 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   constexpr bool bf = PREC != kFP16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ int s_item, s_bad;
+  __shared__ int s_item, s_bad, s_same;
   __shared__ BlockGeom s_g;
+  __shared__ int64_t s_key[9];  // knots, degrees and sizes of the block whose bases are in shared memory
+  __shared__ int s_key_ok;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
+    s_key_ok = 0;
   }
   // the zero rows of the stage-y basis buffers are written once; the basis rows per block
   for (int e = tid * 16; e < 2 * kOpZ * L::NL; e += kThreadsTC * 16)
@@ -211,21 +214,34 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
           for (int a = 0; a < 3; ++a)
             if (s_g.n[a] != kN || s_g.C[a] > kK) bad = MFA_DEV_BAD_DESC;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
+        // the bases, difference scales and basis operands only depend on (knots, degree, C) per axis: a block
+        // that repeats the previous block's keeps them
+        const int64_t key[9] = {s_g.knot_off[0], s_g.knot_off[1], s_g.knot_off[2], s_g.p[0], s_g.p[1], s_g.p[2],
+                                s_g.C[0], s_g.C[1], s_g.C[2]};
+        bool same = s_key_ok && !bad;
+        for (int q = 0; q < 9; ++q) same = same && s_key[q] == key[q];
+        s_same = same;
+        if (!bad && !same) {
+          for (int q = 0; q < 9; ++q) s_key[q] = key[q];
+          s_key_ok = 0;  // valid once this block's set-up has passed its checks
+        }
       }
     }
     __syncthreads();
     if (s_item >= count || timed_out) break;
     if (s_bad) continue;
     const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
+    const bool same = s_same;
 
-    // ---- per block: knots, basis bands of degree p and p-1, difference scales, P ----
-    if (tid < 3 * kKnotMax) {
+    // ---- per block: knots, basis bands of degree p and p-1, difference scales (unless kept), P ----
+    if (!same && tid < 3 * kKnotMax) {
       const int a = tid / kKnotMax, i = tid - a * kKnotMax;
       if (i < s_g.C[a] + s_g.p[a] + 1) kn[tid] = prm.knots[s_g.knot_off[a] + i];
     }
     const int ncps = Cx * Cy * Cz;
     for (int e = tid; e < ncps; e += kThreadsTC) P[e] = __ldg(prm.cps + s_g.cp_off + e);
     __syncthreads();
+    if (!same) {
     if (tid < 3 && !knots_ok(kn + tid * kKnotMax, s_g.p[tid], s_g.C[tid])) {
       atomicOr(&s_bad, 1);
       flag(prm.status, MFA_DEV_BAD_KNOTS);
@@ -255,6 +271,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     }
     __syncthreads();
     if (s_bad) continue;
+    if (tid == 0) s_key_ok = 1;
     // stage-y A: rows 96..127 of the two zero-padded buffers = N_y(u_j) and N_y^(p-1)(u_j), K = b;
     // stage-x B: rows n < 32 = N_x(u_n), rows 32..63 = N_x^(p-1)(u_{n-32}), K = a
     for (int e = tid; e < 2 * 64 * kK; e += kThreadsTC) {
@@ -270,23 +287,28 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       else
         put<PREC>(sm + L::Bx, kmajor_off(n, c, kLBO, kSBO), L::dBx, v);
     }
-    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index)
-    for (int e = tid; e < 256 * kK; e += kThreadsTC) {
-      const int R = e >> 4, c = e & 15, b = R >> 4, a = R & 15;
-      float v0 = 0.f, vu = 0.f, vv = 0.f, vw = 0.f;
-      if (a < Cx && b < Cy && c < Cz) {
-        const int idx = (c * Cy + b) * Cx + a;
-        const float p0 = P[idx];
-        v0 = p0;
-        if (a < Cx - 1) vu = dsc[a] * (P[idx + 1] - p0);
-        if (b < Cy - 1) vv = dsc[kN + b] * (P[idx + Cx] - p0);
-        if (c < Cz - 1) vw = dsc[2 * kN + c] * (P[idx + Cy * Cx] - p0);
+    }  // !same
+    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index), two K at a time
+    for (int e = tid; e < 256 * kK / 2; e += kThreadsTC) {
+      const int R = e >> 3, c0 = 2 * (e & 7), b = R >> 4, a = R & 15;
+      float v0[2] = {0.f, 0.f}, vu[2] = {0.f, 0.f}, vv[2] = {0.f, 0.f}, vw[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + h;
+        if (a < Cx && b < Cy && c < Cz) {
+          const int idx = (c * Cy + b) * Cx + a;
+          const float p0 = P[idx];
+          v0[h] = p0;
+          if (a < Cx - 1) vu[h] = dsc[a] * (P[idx + 1] - p0);
+          if (b < Cy - 1) vv[h] = dsc[kN + b] * (P[idx + Cx] - p0);
+          if (c < Cz - 1) vw[h] = dsc[2 * kN + c] * (P[idx + Cy * Cx] - p0);
+        }
       }
-      const uint32_t off = kmajor_off(R, c, kLBO, kSBO);
-      put<PREC>(sm + L::Az, off, L::dAz, v0);
-      put<PREC>(sm + L::Az + kOp256, off, L::dAz, vu);
-      put<PREC>(sm + L::Az + 2 * kOp256, off, L::dAz, vv);
-      put<PREC>(sm + L::Az + 3 * kOp256, off, L::dAz, vw);
+      const uint32_t off = kmajor_off(R, c0, kLBO, kSBO);
+      put2<PREC>(sm + L::Az, off, L::dAz, v0[0], v0[1]);
+      put2<PREC>(sm + L::Az + kOp256, off, L::dAz, vu[0], vu[1]);
+      put2<PREC>(sm + L::Az + 2 * kOp256, off, L::dAz, vv[0], vv[1]);
+      put2<PREC>(sm + L::Az + 3 * kOp256, off, L::dAz, vw[0], vw[1]);
     }
     // (P in R1 is dead from here on: R1 becomes the stage-x operand and the readout staging)
 
