@@ -1032,7 +1032,8 @@ def run_lodrender(args):
     12^3 control points); per frame of a 32-frame orbit the levels are chosen by distance (mfa_lod_select) and
     the frame is rendered at 512^2 by per-sample queries of the chosen models (mfa_raycast_lod). Beside it the
     same frames from the finest level only, and the PSNR between the two (the paper's quality measure of a
-    multi-resolution render); the first frame is also checked against the oracle on sampled pixels."""
+    multi-resolution render, with SSIM on every fourth frame); the first frame is also checked against the
+    oracle on sampled pixels."""
     from oracle import encode as oenc
     from oracle import multires as omr
     from paper_2409_00184_b300 import mfa
@@ -1076,7 +1077,7 @@ def run_lodrender(args):
         mfa.lod_select(ctx, views[0]["eye"], B0, n, levels, table=table)
         mfa.raycast_lod(ctx, blk, table, B0, n, levels, views[0], tf_d, img)
     torch.cuda.synchronize()
-    ms_lod, ms_fine, psnr, per_level, bytes_sel = [], [], [], np.zeros(levels), []
+    ms_lod, ms_fine, psnr, ssim, per_level, bytes_sel = [], [], [], [], np.zeros(levels), []
     ctx.ray_samples(reset=True)
     for v in views:
         e0.record(stream)
@@ -1092,7 +1093,10 @@ def run_lodrender(args):
         torch.cuda.synchronize()
         ms_fine.append(e0.elapsed_time(e1))
         ctx.ray_samples(reset=True)
-        psnr.append(omr.psnr(img.cpu().numpy(), ref.cpu().numpy()))
+        a_img, b_img = img.cpu().numpy(), ref.cpu().numpy()
+        psnr.append(omr.psnr(a_img, b_img))
+        if len(psnr) % 4 == 1:
+            ssim.append(omr.ssim(a_img, b_img))
         used = torch.unique(table).cpu().numpy()
         lv = np.searchsorted(np.cumsum(counts), used, side="right")
         per_level += np.bincount(lv, minlength=levels)
@@ -1130,6 +1134,7 @@ def run_lodrender(args):
                        "blocks": total, "encode_ms_all_levels": encode_ms},
             "finest_only_ms_per_frame": float(np.mean(ms_fine)),
             "psnr_db_vs_finest": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
+            "ssim_vs_finest": {"mean": float(np.mean(ssim)), "min": float(np.min(ssim)), "frames": len(ssim)},
             "models_per_frame_by_level": (per_level / frames).tolist(),
             "model_bytes_per_frame": {"lod": float(np.mean(bytes_sel)), "finest": B0 ** 3 * int(mfa.model_bytes(C, p))},
             "selection_equals_oracle_frame0": same_table,

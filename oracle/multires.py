@@ -5,7 +5,7 @@ sharing one sample on their common boundary (for C0 continuity), and downsamples
 micro-block resolution of its level. Sec. 5.1.3 renders with four LODs chosen per micro-block by the
 distance from the point of view to the block's centroid, over the distance ranges [0, 0.8], [0.8, 1.6],
 [1.6, 2.4] and [2.4, inf) in a volume rescaled to [-1, 1]^3; the nearest range takes the finest level.
-Sec. 5.2 compares rendered images by MSE and PSNR.
+Sec. 5.2 compares rendered images by MSE, PSNR and SSIM.
 
 Readings used here (the paper gives the rules, not the bookkeeping):
 
@@ -157,3 +157,47 @@ def psnr(a, b, peak=1.0):
     """Peak signal-to-noise ratio in dB, 10 log10(peak^2 / MSE); infinite for equal images."""
     m = mse(a, b)
     return float("inf") if m == 0.0 else float(10.0 * np.log10(peak * peak / m))
+
+
+def gaussian_window(size=11, sigma=1.5):
+    """Normalised 1-D Gaussian weights of the structural-similarity window."""
+    x = np.arange(size) - (size - 1) / 2.0
+    w = np.exp(-0.5 * (x / sigma) ** 2)
+    return w / w.sum()
+
+
+def _filter_valid(img, w):
+    """Separable weighted sums of every size x size window of a 2-D image (valid windows only)."""
+    k = len(w)
+    H, W = img.shape
+    rows = np.zeros((H - k + 1, W))
+    for i in range(k):
+        rows += w[i] * img[i:H - k + 1 + i, :]
+    out = np.zeros((H - k + 1, W - k + 1))
+    for j in range(k):
+        out += w[j] * rows[:, j:W - k + 1 + j]
+    return out
+
+
+def ssim(a, b, peak=1.0, size=11, sigma=1.5, k1=0.01, k2=0.03):
+    """Structural similarity (the third image metric of Sec. 5.2) in its usual form: per channel, the local
+    means, variances and covariance under an 11 x 11 Gaussian window (sigma 1.5) over every valid window,
+    SSIM = (2 mu_a mu_b + c1)(2 s_ab + c2) / ((mu_a^2 + mu_b^2 + c1)(s_a^2 + s_b^2 + c2)) with
+    c1 = (k1 peak)^2, c2 = (k2 peak)^2, averaged over the windows and then over the channels.
+    a, b: (H, W) or (H, W, channels)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.ndim == 2:
+        a, b = a[..., None], b[..., None]
+    w = gaussian_window(size, sigma)
+    c1, c2 = (k1 * peak) ** 2, (k2 * peak) ** 2
+    vals = []
+    for ch in range(a.shape[2]):
+        x, y = a[..., ch], b[..., ch]
+        mx, my = _filter_valid(x, w), _filter_valid(y, w)
+        sxx = _filter_valid(x * x, w) - mx * mx
+        syy = _filter_valid(y * y, w) - my * my
+        sxy = _filter_valid(x * y, w) - mx * my
+        m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+        vals.append(m.mean())
+    return float(np.mean(vals))

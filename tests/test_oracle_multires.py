@@ -173,3 +173,39 @@ def test_mse_and_psnr_closed_forms():
     b[0, 0, 0] += 0.6  # one channel of one pixel off by 0.6: MSE = 0.36 / 252
     assert abs(multires.mse(a, b) - 0.36 / 252) < 1e-15
     assert abs(multires.psnr(a, b, peak=2.0) - 10 * math.log10(4 * 252 / 0.36)) < 1e-10
+
+
+def _ssim_brute(a, b, size=11, sigma=1.5, c1=1e-4, c2=9e-4):
+    """SSIM of one channel with every window's weighted statistics summed directly (no separable filter)."""
+    x = np.arange(size) - (size - 1) / 2.0
+    g = np.exp(-0.5 * (x / sigma) ** 2)
+    w2 = np.outer(g, g) / np.outer(g, g).sum()
+    H, W = a.shape
+    vals = []
+    for i in range(H - size + 1):
+        for j in range(W - size + 1):
+            pa, pb = a[i:i + size, j:j + size], b[i:i + size, j:j + size]
+            ma, mb = (w2 * pa).sum(), (w2 * pb).sum()
+            va = (w2 * (pa - ma) ** 2).sum()
+            vb = (w2 * (pb - mb) ** 2).sum()
+            cab = (w2 * (pa - ma) * (pb - mb)).sum()
+            vals.append(((2 * ma * mb + c1) * (2 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2)))
+    return np.mean(vals)
+
+
+def test_ssim_against_per_window_sums_and_closed_forms():
+    """SSIM (Sec. 5.2): equal to the per-window weighted sums written out, 1 for equal images, symmetric, the
+    closed form (2 c c' + c1) / (c^2 + c'^2 + c1) for two constant images, and below 1 for a noisy copy."""
+    g = synth.rng(64)
+    a = g.uniform(0, 1, (17, 19))
+    b = np.clip(a + g.normal(0, 0.05, a.shape), 0, 1)
+    assert abs(multires.ssim(a, b) - _ssim_brute(a, b)) < 1e-12
+    assert abs(multires.ssim(a, a) - 1.0) < 1e-12
+    assert abs(multires.ssim(a, b) - multires.ssim(b, a)) < 1e-12
+    assert multires.ssim(a, b) < 0.99
+    c, d = 0.3, 0.7
+    want = (2 * c * d + 1e-4) / (c * c + d * d + 1e-4)
+    assert abs(multires.ssim(np.full((15, 15), c), np.full((15, 15), d)) - want) < 1e-12
+    rgba = g.uniform(0, 1, (16, 14, 4))
+    per = [multires.ssim(rgba[..., k], rgba[..., k] * 0.9) for k in range(4)]
+    assert abs(multires.ssim(rgba, rgba * 0.9) - np.mean(per)) < 1e-12
