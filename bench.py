@@ -1269,30 +1269,30 @@ def main():
         s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s2.record(stream)
         copy_stream.wait_event(s2)
-        with torch.cuda.stream(copy_stream):
-            Ddev[0].copy_(hostD, non_blocking=True)
-            copied[0].record(copy_stream)
+        m = w.mfa
+        m.copy_to_device(Ddev[0], hostD, stream=copy_stream)
+        copied[0].record(copy_stream)
         for k in range(Ke):
             b = k % 2
             if k + 1 < Ke:
                 nb = 1 - b
                 if k >= 1:
                     copy_stream.wait_event(used[nb])  # step k-1 has finished reading that buffer
-                with torch.cuda.stream(copy_stream):
-                    Ddev[nb].copy_(hostD, non_blocking=True)
-                    copied[nb].record(copy_stream)
+                m.copy_to_device(Ddev[nb], hostD, stream=copy_stream)
+                copied[nb].record(copy_stream)
             stream.wait_event(copied[b])
             w.step(D=Ddev[b])
             used[b].record(stream)
-            hostImg.copy_(w.image, non_blocking=True)
+            m.copy_to_host(hostImg, w.image, stream=stream)
         e2.record(stream)
         barrier()
         ms_e2e = max_over_ranks(s2.elapsed_time(e2) / Ke, ws, "cuda")
         e2e = {"value": job_throughput(ws, voxels, ms_e2e), "unit": "Gvoxel/s",
                "h2d_bytes_per_step": hostD.numel() * 4, "d2h_bytes_per_step": hostImg.numel() * 4,
                "ms_per_step": ms_e2e,
-               "pipelining": "pinned host samples copied each step on a second stream into one of two device "
-                             "buffers, overlapping the previous step; image read back after each step"}
+               "pipelining": "pinned host samples copied each step (mfa_copy_to_device) on a second stream into "
+                             "one of two device buffers, overlapping the previous step; image read back after "
+                             "each step (mfa_copy_to_host)"}
 
     err = None if args.no_check or rank != 0 else check_against_oracle(w)
 

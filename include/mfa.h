@@ -151,6 +151,15 @@ int mfa_ctx_get_decode_tiling(const mfa_ctx* ctx, const mfa_bounds* key, mfa_dec
  * Returns -1 for NCP < 1 or degree < 0. */
 int64_t mfa_model_bytes(int32_t ncp, int32_t degree);
 
+/* Host <-> device copies of caller-owned buffers on `stream`, for callers whose sample grids and images
+ * live in host memory (the paper's pipeline moves the visible micro-models to the GPU and the frame back,
+ * Sec. 4.3): mfa_copy_to_device copies `bytes` from host h_src to device d_dst, mfa_copy_to_host from
+ * device d_src to host h_dst. Asynchronous with respect to the host when the host buffer is page-locked
+ * (otherwise the copy completes before the call returns). MFA_ERR_INVALID_ARG for null pointers or
+ * bytes < 0 (0 bytes: nothing is enqueued), MFA_ERR_CUDA if the copy cannot be enqueued. */
+int mfa_copy_to_device(void* d_dst, const void* h_src, int64_t bytes, void* stream);
+int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream);
+
 /* ---- decode (Algorithm 4's value and gradient queries, batched on sample grids) ----- */
 /* Decodes blocks into the cache: for each selected block b and sample (i, j, k),
  *   f   = sum_{a,b,c} N_a(u_i) N_b(v_j) N_c(w_k) P_abc,  and f_u, f_v, f_w with N' in the

@@ -133,6 +133,24 @@ int mfa_ctx_get_decode_tiling(const mfa_ctx* ctx, const mfa_bounds* key, mfa_dec
   return MFA_ERR_INVALID_ARG;
 }
 
+int mfa_copy_to_device(void* d_dst, const void* h_src, int64_t bytes, void* stream) {
+  if (!d_dst || !h_src || bytes < 0) return MFA_ERR_INVALID_ARG;
+  if (bytes == 0) return MFA_OK;
+  return cudaMemcpyAsync(d_dst, h_src, (size_t)bytes, cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? MFA_OK
+             : MFA_ERR_CUDA;
+}
+
+int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream) {
+  if (!h_dst || !d_src || bytes < 0) return MFA_ERR_INVALID_ARG;
+  if (bytes == 0) return MFA_OK;
+  return cudaMemcpyAsync(h_dst, d_src, (size_t)bytes, cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? MFA_OK
+             : MFA_ERR_CUDA;
+}
+
 int64_t mfa_model_bytes(int32_t ncp, int32_t degree) {
   if (ncp < 1 || degree < 0) return -1;
   const int64_t c = ncp;

@@ -71,7 +71,7 @@ SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_de
            "mfa_raycast_direct", "mfa_decode_compare_blocks", "mfa_store_write", "mfa_cache_create", "mfa_cache_destroy", "mfa_cache_info",
            "mfa_cache_lookup", "mfa_cache_upload", "mfa_cache_prefetch_start", "mfa_cache_prefetch_stop",
            "mfa_raycast_ex", "mfa_fill_aprons", "mfa_lod_gather_ex", "mfa_lod_select", "mfa_raycast_lod",
-           "mfa_encode_blocks_ex"]
+           "mfa_encode_blocks_ex", "mfa_copy_to_device", "mfa_copy_to_host"]
 
 
 def _load():
@@ -89,6 +89,8 @@ def _load():
         "mfa_ctx_set_decode_tiling": (ctypes.c_int, [P, ctypes.POINTER(Bounds), ctypes.POINTER(DecodeTiling)]),
         "mfa_ctx_get_decode_tiling": (ctypes.c_int, [P, ctypes.POINTER(Bounds), ctypes.POINTER(DecodeTiling)]),
         "mfa_model_bytes": (I64, [I32, I32]),
+        "mfa_copy_to_device": (ctypes.c_int, [P, P, I64, P]),
+        "mfa_copy_to_host": (ctypes.c_int, [P, P, I64, P]),
         "mfa_decode_blocks": (ctypes.c_int, [P, P, I32, P, I32, P, P, I64, P, I64, P, I64, I64,
                                              ctypes.POINTER(Bounds), I32, U32, P]),
         "mfa_basis_tables": (ctypes.c_int, [P, P, P, I64, P, P, P]),
@@ -164,6 +166,14 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _host_ptr(t):
+    if t.is_cuda:
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _need(t, n, what):
     if t.numel() < n:
         raise ValueError(f"{what}: {t.numel()} elements, the call touches {n}")
@@ -182,6 +192,24 @@ def apron_voxels(n):
 def model_bytes(ncp, degree):
     """Eq. 2 model size in bytes."""
     return int(lib.mfa_model_bytes(ncp, degree))
+
+
+def copy_to_device(dst, src, stream=None):
+    """mfa_copy_to_device: the bytes of host tensor src (page-locked for an asynchronous copy) into CUDA
+    tensor dst."""
+    if dst.numel() * dst.element_size() < src.numel() * src.element_size():
+        raise ValueError("destination smaller than source")
+    _check(lib.mfa_copy_to_device(_ptr(dst), _host_ptr(src), src.numel() * src.element_size(), _stream(stream)),
+           "mfa_copy_to_device")
+
+
+def copy_to_host(dst, src, stream=None):
+    """mfa_copy_to_host: the bytes of CUDA tensor src into host tensor dst (page-locked for an asynchronous
+    copy)."""
+    if dst.numel() * dst.element_size() < src.numel() * src.element_size():
+        raise ValueError("destination smaller than source")
+    _check(lib.mfa_copy_to_host(_host_ptr(dst), _ptr(src), src.numel() * src.element_size(), _stream(stream)),
+           "mfa_copy_to_host")
 
 
 class Context:

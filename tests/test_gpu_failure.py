@@ -48,3 +48,23 @@ def test_selftest_argument_checks(mfa, ctx):
         with pytest.raises(mfa.MfaError):
             ctx.selftest_wait_timeout(polls)
     assert ctx.device_status() == 0
+
+
+def test_host_device_copies_round_trip():
+    """mfa_copy_to_device / mfa_copy_to_host move pinned host bytes to the device and back unchanged, and
+    refuse null pointers and negative sizes."""
+    import ctypes
+    import torch
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    h = torch.arange(1 << 20, dtype=torch.float32).pin_memory()
+    d = torch.empty_like(h, device="cuda")
+    back = torch.zeros_like(h).pin_memory()
+    s = torch.cuda.Stream()
+    mfa.copy_to_device(d, h, stream=s)
+    mfa.copy_to_host(back, d, stream=s)
+    s.synchronize()
+    assert torch.equal(back, h)
+    assert mfa.lib.mfa_copy_to_device(None, ctypes.c_void_p(h.data_ptr()), 4, None) == mfa.ERR_INVALID_ARG
+    assert mfa.lib.mfa_copy_to_host(ctypes.c_void_p(back.data_ptr()), ctypes.c_void_p(d.data_ptr()), -1,
+                                    None) == mfa.ERR_INVALID_ARG
