@@ -6,7 +6,10 @@
 // from an atomic queue and decoded in four slabs of 8 z-planes; every index is padded to 16 and basis
 // rows are written densely (zero outside each band). The stage-z operands (P and its differences) do
 // not depend on the slab and are built once per block. One kernel per precision; BF16 and FP16 keep no
-// "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns). Derivatives use the B-spline derivative identity: d/du sum_a N_{a,p}(u) c_a =
+// "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns).
+// Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per block for all 32 planes
+// (N = 64) into columns 256..511; the slabs then start at stage y. Derivatives use the B-spline derivative
+// identity: d/du sum_a N_{a,p}(u) c_a =
 // sum_a N_{a,p-1}(u) q_a with q_a = p (c_{a+1} - c_a) / (t_{a+p+1} - t_{a+1}) on the knots
 // t_1 .. t_{C+p-1}. The four outputs are four independent chains of mode products on the control points
 // P and their FP32 differences DxP, DyP, DzP, taken before any rounding: every 16-bit operand is then a
@@ -42,9 +45,14 @@ constexpr int kKS = 8;       // z-planes per slab
 constexpr int kSlabs = kN / kKS;
 constexpr int kRowBytes = 32;                  // one K-major operand row: 16 x 16-bit
 constexpr uint32_t kLBO = 128, kSBO = 256;     // core-matrix strides for K = 16
-constexpr int kTmemCols = 256;
 
 enum Prec { kBF16 = 0, kFP16 = 1, kSplit = 2 };
+// Split-BF16 runs one CTA per SM (its shared memory) and takes all 512 tensor-memory columns: its stage z runs
+// once per block, for all 32 planes, into columns 256..511. BF16 and FP16 run two CTAs of 256 columns each
+// and a stage z per slab.
+template <int PREC> constexpr bool kZOnce = PREC == kSplit;
+template <int PREC> constexpr uint32_t kTmemColsOf = kZOnce<PREC> ? 512 : 256;
+constexpr uint32_t kZCols = 256;  // first column of the whole-block stage-z result
 
 constexpr int kOp256 = 256 * kRowBytes, kOp128 = 128 * kRowBytes, kOp64 = 64 * kRowBytes, kOp16 = 16 * kRowBytes;
 constexpr int kZRows = 224;                   // stage-y basis buffer: 96 zero rows, 32 basis rows, 96 zero rows
@@ -59,8 +67,11 @@ struct TcLayout {
   static constexpr int Az = 0;                             // stage z A: chains 0..3, per block
   static constexpr int R1 = Az + 4 * kOp256 * NL;          // stage x A; aliases P (block set-up) and staging
   static constexpr int R1Bytes = std::max(4 * kOp256 * NL, std::max(kPBytes, kStageBytes));
-  static constexpr int Bz = R1 + R1Bytes;                  // B_z0 = [N_z | 0], B_z1 = [0 | N_z^(p-1)], B_z2 = [0 | N_z]
-  static constexpr int Ty = Bz + 3 * kOp16 * NL;           // stage y B: chains 0..3, rows (k,a), K = b
+  // stage z B, per slab (16 rows: 8 planes) or per block (64 rows: 32 planes):
+  // B_z0 = [N_z | 0], B_z1 = [0 | N_z^(p-1)], B_z2 = [0 | N_z]
+  static constexpr int BzOp = kZOnce<PREC> ? kOp64 : kOp16;
+  static constexpr int Bz = R1 + R1Bytes;
+  static constexpr int Ty = Bz + 3 * BzOp * NL;            // stage y B: chains 0..3, rows (k,a), K = b
   static constexpr int Zy = Ty + 4 * kOp128 * NL;          // stage y A: N_y and N_y^(p-1), zero-padded
   static constexpr int Bx = Zy + 2 * kOpZ * NL;            // stage x B: rows [N_x ; N_x^(p-1)]
   static constexpr int Basis = Bx + kOp64 * NL;            // per axis and sample: TcBasis (48 B)
@@ -68,7 +79,7 @@ struct TcLayout {
   static constexpr int Dsc = Knots + 3 * kKnotMax * 4;     // per axis: p / (t_{c+p+1} - t_{c+1})
   static constexpr int Total = Dsc + 3 * kN * 4 + 1024;    // + slack for 1024-byte alignment
   // lo-part distances (0 when unused)
-  static constexpr int dAz = 4 * kOp256, dAx = 4 * kOp256, dBz = 3 * kOp16, dTy = 4 * kOp128, dZy = 2 * kOpZ, dBx = kOp64;
+  static constexpr int dAz = 4 * kOp256, dAx = 4 * kOp256, dBz = 3 * BzOp, dTy = 4 * kOp128, dZy = 2 * kOpZ, dBx = kOp64;
   static_assert(Total <= 227 * 1024, "shared memory budget");
 };
 
@@ -125,6 +136,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   using L = TcLayout<PREC>;
   constexpr bool split = PREC == kSplit;
   constexpr bool bf = PREC != kFP16;
+  constexpr bool zonce = kZOnce<PREC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ int s_item, s_bad, s_same;
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   float* dsc = reinterpret_cast<float*>(sm + L::Dsc);          // [axis][control index]
 
   if (warp == 0) {
-    tmem_alloc(&s_tmem, kTmemCols);
+    tmem_alloc(&s_tmem, kTmemColsOf<PREC>);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -287,6 +299,22 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       else
         put<PREC>(sm + L::Bx, kmajor_off(n, c, kLBO, kSBO), L::dBx, v);
     }
+    // per-block stage-z B: rows n < 32 of B_z0 = N_z(u_n); rows 32..63 of B_z1 = N_z^(p-1)(u_{n-32}) and of
+    // B_z2 = N_z(u_{n-32}); K = c
+    if (zonce)
+      for (int e = tid; e < 3 * 64 * kK; e += kThreadsTC) {
+        const int which = e / (64 * kK), n = (e >> 4) & 63, c = e & 15;
+        float v = 0.f;
+        if ((n < 32) == (which == 0)) {
+          const TcBasis& tb = bas[2 * kN + (n & 31)];
+          const int d = c - tb.off;
+          if (d >= 0 && d <= 3) {
+            if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
+            else if (c < Cz) v = tb.N[d];
+          }
+        }
+        put<PREC>(sm + L::Bz + which * kOp64, kmajor_off(n, c, kLBO, kSBO), L::dBz, v);
+      }
     }  // !same
     // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index), two K at a time
     for (int e = tid; e < 256 * kK / 2; e += kThreadsTC) {
@@ -311,9 +339,29 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       put2<PREC>(sm + L::Az + 3 * kOp256, off, L::dAz, vw[0], vw[1]);
     }
     // (P in R1 is dead from here on: R1 becomes the stage-x operand and the readout staging)
+    if (zonce) {
+      operands_ready();
+      // ---- stage z for all 32 planes, per 128-row tile t at column 256 + 128t:
+      //      [chain 0 | chain 3 | chain 2 | chain 1], 32 planes each ----
+      if (tid == 0) {
+        for (int t = 0; t < 2; ++t) {
+          const uint32_t ro = t * 16 * kSBO, d = tmem + kZCols + 128 * t;
+          mma(d, L::Az + ro, L::Az + L::dAz + ro, L::Bz, L::Bz + L::dBz, 64, 0);
+          mma(d, L::Az + 3 * kOp256 + ro, L::Az + 3 * kOp256 + L::dAz + ro, L::Bz + kOp64, L::Bz + kOp64 + L::dBz,
+              64, 1);
+          mma(d + 64, L::Az + 2 * kOp256 + ro, L::Az + 2 * kOp256 + L::dAz + ro, L::Bz, L::Bz + L::dBz, 64, 0);
+          mma(d + 64, L::Az + kOp256 + ro, L::Az + kOp256 + L::dAz + ro, L::Bz + 2 * kOp64,
+              L::Bz + 2 * kOp64 + L::dBz, 64, 1);
+        }
+        mma_commit(&s_bar);
+      }
+      wait_mma();
+      if (timed_out) break;
+    }
 
     for (int slab = 0; slab < kSlabs && !timed_out; ++slab) {
       const int k0 = slab * kKS;
+      if (!zonce) {
       for (int e = tid; e < 3 * 16 * kK; e += kThreadsTC) {  // B_z0, B_z1, B_z2: 16 x 16 each
         const int which = e >> 8, n = (e >> 4) & 15, c = e & 15;
         const int kl = n & 7;
@@ -345,13 +393,23 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       }
       wait_mma();
       if (timed_out) break;
-      // readout z -> stage-y B of chain c: element (row 16k + a, K = b); every entry of all 128 rows is written
+      }  // !zonce
+      // readout z -> stage-y B of chain c: element (row 16k + a, K = b); every entry of all 128 rows is written.
+      // r0 = [chain 0 | chain 3], r1 = [chain 2 | chain 1] of planes k0 .. k0+7
       {
         const int R = 128 * group + 32 * quarter + lane, b = R >> 4, a = R & 15;
         uint32_t r0[16], r1[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 16 * group;
-        tmem_ld16(ta, r0);
-        tmem_ld16(ta + 32, r1);
+        if (zonce) {
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + kZCols + 128 * group + k0;
+          tmem_ld8(ta, *reinterpret_cast<uint32_t(*)[8]>(r0));
+          tmem_ld8(ta + 32, *reinterpret_cast<uint32_t(*)[8]>(r0 + 8));
+          tmem_ld8(ta + 64, *reinterpret_cast<uint32_t(*)[8]>(r1));
+          tmem_ld8(ta + 96, *reinterpret_cast<uint32_t(*)[8]>(r1 + 8));
+        } else {
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 16 * group;
+          tmem_ld16(ta, r0);
+          tmem_ld16(ta + 32, r1);
+        }
         tmem_ld_wait();
         // Lanes L and L + 16 hold the same (k, a) at b and b + 1 (adjacent K): they trade values so that
         // the lower lane writes the 32-bit words (b, b + 1) of chains 0 and 1, the upper one those of chains 2
@@ -449,7 +507,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) tmem_dealloc(tmem, kTmemColsOf<PREC>);
 }
 
 template <int PREC>
@@ -462,8 +520,8 @@ int launch_tc(mfa_ctx* ctx, DecodeParams prm, cudaStream_t stream) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_tc_kernel<PREC>, kThreadsTC, smem) != cudaSuccess)
     return MFA_ERR_CUDA;
-  // every resident CTA holds 256 of the SM's 512 tensor-memory columns
-  per_sm = std::max(1, std::min(per_sm, 512 / kTmemCols));
+  // the resident CTAs share the SM's 512 tensor-memory columns
+  per_sm = std::max(1, std::min(per_sm, (int)(512 / kTmemColsOf<PREC>)));
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
   decode_tc_kernel<PREC><<<ctx->num_sms * per_sm, kThreadsTC, smem, stream>>>(prm);
   ctx->launches++;
