@@ -171,9 +171,10 @@ int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream
  * with MFA_DECODE_VALUE_ONLY, at d_cache + (slot*slot_stride_voxels + voxel)*width.
  * d_cache must be 16-byte aligned. knots_len / cps_len are the array lengths (floats),
  * used for the range checks. precision: MFA_PREC_FP32 (any supported shape) or, on the tensor
- * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 for batches with 32 samples and at
- * most 16 control points per axis (max_nsamp = 32, max_ncp <= 16, no VALUE_ONLY; otherwise
- * MFA_ERR_UNSUPPORTED; a block of another shape in such a batch sets MFA_DEV_BAD_DESC). */
+ * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 for batches with at most 16
+ * control points per axis and any sample counts (max_ncp <= 16, no VALUE_ONLY, row layout;
+ * otherwise MFA_ERR_UNSUPPORTED; a block with more than 16 control points on an axis in such a
+ * batch sets MFA_DEV_BAD_DESC). */
 int mfa_decode_blocks(mfa_ctx* ctx,
                       const mfa_block_desc* d_desc, int32_t nblocks,
                       const int32_t* d_list, int32_t list_len, const int32_t* d_count,

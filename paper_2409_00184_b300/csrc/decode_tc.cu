@@ -2,9 +2,11 @@
 // (Sec. 4.2 model, Algorithm 4 value and gradient queries) as dense 16-bit MMAs with FP32 accumulation
 // in tensor memory, for BF16, FP16 and split-BF16 operands.
 //
-// Work unit = one block with 32 samples and at most 16 control points per axis (K = 16 per MMA), taken
-// from an atomic queue and decoded in four slabs of 8 z-planes; every index is padded to 16 and basis
-// rows are written densely (zero outside each band). The stage-z operands (P and its differences) do
+// Work unit = one sub-cube of at most 32 samples per axis of a block with at most 16 control points per
+// axis (K = 16 per MMA), taken from an atomic queue and decoded in slabs of 8 z-planes (four for 32
+// planes); a block of n samples per axis has ceil(n / 32) sub-cubes per axis (n up to 64). Every index is
+// padded to 16 control points and 32 samples; basis rows are written densely (zero outside each band and
+// for the samples past the sub-cube's end). The stage-z operands (P and its differences) do
 // not depend on the slab and are built once per block. One kernel per precision; BF16 and FP16 keep no
 // "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns).
 // Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per block for all 32 planes
@@ -39,7 +41,7 @@ namespace mfa {
 namespace {
 
 constexpr int kThreadsTC = 256;
-constexpr int kN = 32;       // samples per axis on this path
+constexpr int kN = 32;       // samples per axis of one work unit (sub-cube)
 constexpr int kK = 16;       // padded control points per axis (one MMA K step)
 constexpr int kKS = 8;       // z-planes per slab
 constexpr int kSlabs = kN / kKS;
@@ -140,8 +142,9 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ int s_item, s_bad, s_same;
+  __shared__ int s_w0[3];       // first sample of the sub-cube per axis
   __shared__ BlockGeom s_g;
-  __shared__ int64_t s_key[9];  // knots, degrees and sizes of the block whose bases are in shared memory
+  __shared__ int64_t s_key[15];  // knots, degrees, sizes and sub-cube of the unit whose bases are in shared memory
   __shared__ int s_key_ok;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
@@ -177,6 +180,9 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     if (blockIdx.x == 0 && tid == 0) flag(prm.status, MFA_DEV_BAD_LIST);
     count = max(0, min(count, prm.list_len));
   }
+  // work units: every item has Sa^3 sub-cubes (Sa = ceil(max_nsamp / 32)); those past a block's own n are empty
+  const int Sa = (prm.bounds.max_nsamp + kN - 1) / kN, S = Sa * Sa * Sa;
+  const int units = count * S;
 
   // D (+)= A * B^T for operands at byte offsets a, b (lo parts at a_lo, b_lo); acc0 = accumulate into D
   auto mma = [&](uint32_t d, uint32_t a, uint32_t a_lo, uint32_t b, uint32_t b_lo, int N, uint32_t acc0) {
@@ -209,8 +215,11 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     if (tid == 0) {
       s_item = (int)atomicAdd(prm.counter, 1u);
       s_bad = 0;
-      const int item = s_item;
-      if (item < count) {
+      if (s_item < units) {
+        const int item = s_item / S, sub = s_item - item * S;
+        s_w0[0] = (sub % Sa) * kN;
+        s_w0[1] = ((sub / Sa) % Sa) * kN;
+        s_w0[2] = (sub / (Sa * Sa)) * kN;
         const int b = prm.list ? prm.list[item] : item;
         const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
         uint32_t bad = 0;
@@ -221,29 +230,35 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
           if (item >= prm.nslots) bad = MFA_DEV_BAD_RANGE;
           s_g.slot = item;
         }
-        // this path decodes 32 samples and at most 16 control points per axis
+        // this path decodes at most 16 control points per axis
         if (!bad)
           for (int a = 0; a < 3; ++a)
-            if (s_g.n[a] != kN || s_g.C[a] > kK) bad = MFA_DEV_BAD_DESC;
+            if (s_g.C[a] > kK) bad = MFA_DEV_BAD_DESC;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
-        // the bases, difference scales and basis operands only depend on (knots, degree, C) per axis: a block
-        // that repeats the previous block's keeps them
-        const int64_t key[9] = {s_g.knot_off[0], s_g.knot_off[1], s_g.knot_off[2], s_g.p[0], s_g.p[1], s_g.p[2],
-                                s_g.C[0], s_g.C[1], s_g.C[2]};
-        bool same = s_key_ok && !bad;
-        for (int q = 0; q < 9; ++q) same = same && s_key[q] == key[q];
+        // a sub-cube past the block's own sample count has nothing to decode
+        if (!bad && (s_w0[0] >= s_g.n[0] || s_w0[1] >= s_g.n[1] || s_w0[2] >= s_g.n[2])) s_bad = 1;
+        // the bases, difference scales and basis operands only depend on (knots, degree, C, n, sub-cube) per
+        // axis: a unit that repeats the previous unit's keeps them
+        const int64_t key[15] = {s_g.knot_off[0], s_g.knot_off[1], s_g.knot_off[2], s_g.p[0], s_g.p[1], s_g.p[2],
+                                 s_g.C[0],        s_g.C[1],        s_g.C[2],        s_g.n[0], s_g.n[1], s_g.n[2],
+                                 s_w0[0],         s_w0[1],         s_w0[2]};
+        bool same = s_key_ok && !s_bad;
+        for (int q = 0; q < 15; ++q) same = same && s_key[q] == key[q];
         s_same = same;
-        if (!bad && !same) {
-          for (int q = 0; q < 9; ++q) s_key[q] = key[q];
-          s_key_ok = 0;  // valid once this block's set-up has passed its checks
+        if (!s_bad && !same) {
+          for (int q = 0; q < 15; ++q) s_key[q] = key[q];
+          s_key_ok = 0;  // valid once this unit's set-up has passed its checks
         }
       }
     }
     __syncthreads();
-    if (s_item >= count || timed_out) break;
+    if (s_item >= units || timed_out) break;
     if (s_bad) continue;
     const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
     const bool same = s_same;
+    // z-slabs of this sub-cube; a block of 32^3 samples is one whole sub-cube
+    const int nslab = (min(kN, s_g.n[2] - s_w0[2]) + kKS - 1) / kKS;
+    const bool whole = s_g.n[0] == kN && s_g.n[1] == kN && s_g.n[2] == kN;
 
     // ---- per block: knots, basis bands of degree p and p-1, difference scales (unless kept), P ----
     if (!same && tid < 3 * kKnotMax) {
@@ -262,16 +277,20 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       const int a = tid / kN, i = tid - a * kN;
       const int p = s_g.p[a];
       const float* t = kn + a * kKnotMax;
-      const float u = sample_param(i, kN);
-      const int s = find_span(t, p, s_g.C[a], u);
-      float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1], Nm[MFA_MAX_DEGREE + 1], dNm[MFA_MAX_DEGREE + 1];
-      basis_funs<MFA_MAX_DEGREE>(t, p, s, u, N, dN);
-      // degree p-1 on the knots t_1 .. t_{C+p-1}: span s-1, nonzero functions s-p .. s-1
-      basis_funs<MFA_MAX_DEGREE>(t + 1, p - 1, s - 1, u, Nm, dNm);
       TcBasis tb;
-      tb.off = s - p;
+      tb.off = 0;
       tb.pad[0] = tb.pad[1] = tb.pad[2] = 0;
-      for (int r = 0; r < 4; ++r) { tb.N[r] = N[r]; tb.Nm[r] = Nm[r]; }
+      for (int r = 0; r < 4; ++r) { tb.N[r] = 0.f; tb.Nm[r] = 0.f; }
+      if (s_w0[a] + i < s_g.n[a]) {  // a sample of this sub-cube (the rows past its end stay zero)
+        const float u = sample_param(s_w0[a] + i, s_g.n[a]);
+        const int s = find_span(t, p, s_g.C[a], u);
+        float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1], Nm[MFA_MAX_DEGREE + 1], dNm[MFA_MAX_DEGREE + 1];
+        basis_funs<MFA_MAX_DEGREE>(t, p, s, u, N, dN);
+        // degree p-1 on the knots t_1 .. t_{C+p-1}: span s-1, nonzero functions s-p .. s-1
+        basis_funs<MFA_MAX_DEGREE>(t + 1, p - 1, s - 1, u, Nm, dNm);
+        tb.off = s - p;
+        for (int r = 0; r < 4; ++r) { tb.N[r] = N[r]; tb.Nm[r] = Nm[r]; }
+      }
       bas[a * kN + i] = tb;
       // difference scale of control index i (i < C-1)
       float sc = 0.f;
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       if (timed_out) break;
     }
 
-    for (int slab = 0; slab < kSlabs && !timed_out; ++slab) {
+    for (int slab = 0; slab < nslab && !timed_out; ++slab) {
       const int k0 = slab * kKS;
       if (!zonce) {
       for (int e = tid; e < 3 * 16 * kK; e += kThreadsTC) {  // B_z0, B_z1, B_z2: 16 x 16 each
@@ -469,11 +488,12 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       }
       wait_mma();
       if (timed_out) break;
-      // readout x: warp group g takes tile g; each warp stages its 32 rows, 8 voxels at a time
+      // readout x: warp group g takes tile g; each warp stages its 32 rows, 8 voxels at a time, and writes
+      // the voxels inside the sub-cube: row (k, j) of the tile is voxel row (w0_z + k0 + k, w0_y + j)
       {
         float4* stg = reinterpret_cast<float4*>(sm + L::R1 + warp * 32 * 128);
-        float4* out = reinterpret_cast<float4*>(prm.cache) + (int64_t)s_g.slot * prm.slot_stride +
-                      (int64_t)k0 * kN * kN;
+        float4* out = reinterpret_cast<float4*>(prm.cache) + (int64_t)s_g.slot * prm.slot_stride;
+
         for (int h = 0; h < 2; ++h) {
           uint32_t f[16], fu[16], fv[16], fw[16];
           const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 128 * group + 16 * h;
@@ -494,8 +514,14 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
 #pragma unroll
             for (int it = 0; it < 8; ++it) {
               const int rr = 4 * it + (lane >> 3), v = lane & 7;
-              const int Rg = 128 * group + 32 * quarter + rr;
-              __stcs(out + (int64_t)Rg * kN + 16 * h + 8 * half + v, stg[rr * 8 + (v ^ (rr & 7))]);
+              const int Rg = 128 * group + 32 * quarter + rr, i = 16 * h + 8 * half + v;
+              if (whole) {  // row (k, j) of the tile at (k0 + k) 32^2 + 32 j
+                __stcs(out + (k0 * kN * kN + Rg * kN + i), stg[rr * 8 + (v ^ (rr & 7))]);
+              } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the block
+                const int kz = s_w0[2] + k0 + (Rg >> 5), jy = s_w0[1] + (Rg & 31), ix = s_w0[0] + i;
+                if (kz < s_g.n[2] && jy < s_g.n[1] && ix < s_g.n[0])
+                  __stcs(out + ((kz * s_g.n[1] + jy) * s_g.n[0] + ix), stg[rr * 8 + (v ^ (rr & 7))]);
+              }
             }
             __syncwarp();
           }
@@ -531,7 +557,7 @@ int launch_tc(mfa_ctx* ctx, DecodeParams prm, cudaStream_t stream) {
 }  // namespace
 
 int decode_tc(mfa_ctx* ctx, DecodeParams prm, int precision, cudaStream_t stream) {
-  if (prm.bounds.max_nsamp != kN || prm.bounds.max_ncp > kK) return MFA_ERR_UNSUPPORTED;
+  if (prm.bounds.max_ncp > kK || prm.bounds.max_nsamp > 2 * kN) return MFA_ERR_UNSUPPORTED;
   if (prm.flags & MFA_DECODE_VALUE_ONLY) return MFA_ERR_UNSUPPORTED;
   prm.ks = kKS;
   prm.slabs = kSlabs;

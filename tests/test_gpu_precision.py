@@ -56,7 +56,7 @@ def test_tensor_core_decode_fitted_blocks(mfa, ctx, name, degree):
 
 @pytest.mark.parametrize("name", ["split", "bf16"])
 def test_tensor_core_decode_mixed_shapes(mfa, ctx, name):
-    """Anisotropic C in 2..16, degrees 1..3, non-uniform knots, all with 32 samples per axis."""
+    """Anisotropic C in 2..16, degrees 1..3, non-uniform knots, all with 32 samples per axis (one sub-cube)."""
     bs = synth.random_block_set(20, 601, ncp_choices=(2, 3, 4, 7, 12, 16), degree_choices=(1, 2, 3),
                                 nsamp_choices=(32,), nonuniform=True)
     got = _decode(mfa, ctx, bs, _prec(mfa, name))
@@ -81,19 +81,60 @@ def test_tensor_core_list_slots_and_shape_checks(mfa, ctx):
         ve, ge = rel_errors(c[m].reshape(32, 32, 32, 4), oracle_decode_set(bs, [b])[0])
         assert ve <= 1e-4 and max(ge) <= 1e-4
     assert np.all(np.isnan(c[2]))
-    # shapes outside the tensor-core path: host refusal, or a per-block device flag
-    small = synth.random_block_set(2, 603, ncp_choices=(4,), nsamp_choices=(16,), degree_choices=(2,))
-    sblk = mfa.DeviceBlocks(small)
+    # shapes outside the tensor-core path (more than 16 control points on an axis): host refusal when the
+    # bounds say so, a per-block device flag when a block breaks the bounds it was launched with
+    big = synth.random_block_set(2, 603, ncp_choices=(20,), nsamp_choices=(24,), degree_choices=(2,))
+    bblk = mfa.DeviceBlocks(big)
     with pytest.raises(mfa.MfaError) as e:
-        mfa.decode_blocks(ctx, sblk, torch.zeros(2 * 16 ** 3 * 4, device="cuda"), 16 ** 3, 2,
+        mfa.decode_blocks(ctx, bblk, torch.zeros(2 * bblk.slot_voxels * 4, device="cuda"), bblk.slot_voxels, 2,
                           precision=mfa.PREC_BF16)
     assert e.value.code == mfa.ERR_UNSUPPORTED
-    mixed = synth.random_block_set(2, 604, ncp_choices=(4,), nsamp_choices=(16,), degree_choices=(2,))
-    mixed.nsamp[1] = 32
+    ncp = [(4, 4, 4), (4, 17, 4), (4, 4, 4)]
+    gm = synth.rng(605)
+    mixed = synth.make_block_set(ncp, [(2, 2, 2)] * 3, [(16, 16, 16)] * 3,
+                                 [gm.uniform(-1, 1, size=c[::-1]) for c in ncp])
     mblk = mfa.DeviceBlocks(mixed)
-    mfa.decode_blocks(ctx, mblk, torch.zeros(2 * mblk.slot_voxels * 4, device="cuda"), mblk.slot_voxels, 2,
-                      precision=mfa.PREC_BF16)
-    assert ctx.device_status() & mfa.DEV_BAD_DESC
+    cache = torch.full((3 * mblk.slot_voxels * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, mblk, cache, mblk.slot_voxels, 3, precision=mfa.PREC_BF16, bounds=mfa.Bounds(2, 16, 16))
+    assert ctx.device_status() & mfa.DEV_BAD_DESC  # reading the status clears it
+    c = cache.view(3, mblk.slot_voxels, 4).cpu().numpy()
+    want = oracle_decode_set(mixed, [0, 2])
+    for m, b in enumerate([0, 2]):
+        ve, ge = rel_errors(c[mixed.slot[b]].reshape(16, 16, 16, 4), want[m])
+        assert ve <= 1e-2 and max(ge) <= 1e-2
+    assert np.all(np.isnan(c[mixed.slot[1]]))
+
+
+@pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
+def test_tensor_core_decode_any_sample_count(mfa, ctx, name):
+    """Sample counts other than 32 (2 .. 64 per axis, anisotropic, non-uniform knots): a block of n samples is
+    decoded as ceil(n/32)^3 sub-cubes whose rows past n are zero and never stored."""
+    bs = synth.random_block_set(14, 606, ncp_choices=(2, 3, 5, 9, 16), degree_choices=(1, 2, 3),
+                                nsamp_choices=(2, 7, 16, 31, 33, 48, 64), nonuniform=True)
+    got = _decode(mfa, ctx, bs, _prec(mfa, name))
+    assert ctx.device_status() == 0
+    want = oracle_decode_set(bs)
+    for b in range(len(bs)):
+        nx, ny, nz = (int(v) for v in bs.nsamp[b])
+        vox = nx * ny * nz
+        ve, ge = rel_errors(got[bs.slot[b]][:vox].reshape(nz, ny, nx, 4), want[b])
+        assert ve <= TOL[name] and max(ge) <= TOL[name], (b, bs.nsamp[b], ve, ge)
+        assert np.all(np.isnan(got[bs.slot[b]][vox:]))  # nothing written past the block's voxels
+
+
+def test_tensor_core_decode_config1(mfa, ctx):
+    """Config 1 on the tensor cores: one block of 16^3 control points (degree 2, Gaussian-mixture samples)
+    decoded on a 64^3 grid in split-BF16 (eight 32^3 sub-cubes), every voxel against the oracle."""
+    C, p, n = 16, 2, 64
+    g = synth.rng(synth.BASE_SEED + 1)
+    cps = g.uniform(0.0, 1.0, size=(C, C, C))
+    t = synth.clamped_uniform_knots(C, p)
+    bs = synth.make_block_set([(C, C, C)], [(p, p, p)], [(n, n, n)], [cps], [(t, t, t)])
+    got = _decode(mfa, ctx, bs, mfa.PREC_SPLIT_BF16)
+    assert ctx.device_status() == 0
+    ve, ge = rel_errors(got[0].reshape(n, n, n, 4), oracle_decode_set(bs)[0])
+    print(f"config 1 split-BF16: value {ve:.2e}, gradient {max(ge):.2e}")
+    assert ve <= TOL["split"] and max(ge) <= TOL["split"], (ve, ge)
 
 
 def test_config4_full_size_sampled(mfa, ctx):
