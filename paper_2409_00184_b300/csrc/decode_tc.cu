@@ -2,11 +2,13 @@
 // (Sec. 4.2 model, Algorithm 4 value and gradient queries) as dense 16-bit MMAs with FP32 accumulation
 // in tensor memory, for BF16, FP16 and split-BF16 operands.
 //
-// Work unit = one sub-cube of at most 32 samples per axis of a block with at most 16 control points per
-// axis (K = 16 per MMA), taken from an atomic queue and decoded in slabs of 8 z-planes (four for 32
-// planes); a block of n samples per axis has ceil(n / 32) sub-cubes per axis (n up to 64). Every index is
-// padded to 16 control points and 32 samples; basis rows are written densely (zero outside each band and
-// for the samples past the sub-cube's end). The stage-z operands (P and its differences) do
+// Work unit = one sub-cube of a block, taken from an atomic queue and decoded in slabs of 8 z-planes (four
+// for 32 planes). Per axis a sub-cube has 32 samples when the axis has at most 16 control points, else 16
+// samples; it only touches the window of control points c0 .. c0+W-1 that its samples' bands cover, and
+// W <= 16 holds for uniform knots up to about 24 control points (a wider window, possible only for strongly
+// clustered knots, sets MFA_DEV_BAD_DESC for that sub-cube). So every MMA has K = 16 (the window, padded);
+// every index is padded to 16 control points and 32 samples, and basis rows are written densely (zero
+// outside each band and for the samples past the sub-cube's end). n is at most 64 per axis. The stage-z operands (P and its differences) do
 // not depend on the slab and are built once per block. One kernel per precision; BF16 and FP16 keep no
 // "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns).
 // Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per block for all 32 planes
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ int s_item, s_bad, s_same;
-  __shared__ int s_w0[3];       // first sample of the sub-cube per axis
+  __shared__ int s_w0[3], s_m[3];  // first sample and number of samples of the sub-cube per axis
+  __shared__ int s_c0[3];          // first control point of the sub-cube's window per axis
   __shared__ BlockGeom s_g;
   __shared__ int64_t s_key[15];  // knots, degrees, sizes and sub-cube of the unit whose bases are in shared memory
   __shared__ int s_key_ok;
@@ -180,8 +183,11 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     if (blockIdx.x == 0 && tid == 0) flag(prm.status, MFA_DEV_BAD_LIST);
     count = max(0, min(count, prm.list_len));
   }
-  // work units: every item has Sa^3 sub-cubes (Sa = ceil(max_nsamp / 32)); those past a block's own n are empty
-  const int Sa = (prm.bounds.max_nsamp + kN - 1) / kN, S = Sa * Sa * Sa;
+  // work units: every item has Sa^3 sub-cube positions G apart per axis (G = 16 when some axis may have more
+  // than 16 control points, else 32; Sa = ceil(max_nsamp / G)); a block takes the positions on its own
+  // sub-cube grid (32 or 16 samples per axis) inside its n, the others are empty
+  const int G = prm.bounds.max_ncp > kK ? kN / 2 : kN;
+  const int Sa = (prm.bounds.max_nsamp + G - 1) / G, S = Sa * Sa * Sa;
   const int units = count * S;
 
   // D (+)= A * B^T for operands at byte offsets a, b (lo parts at a_lo, b_lo); acc0 = accumulate into D
@@ -217,9 +223,9 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       s_bad = 0;
       if (s_item < units) {
         const int item = s_item / S, sub = s_item - item * S;
-        s_w0[0] = (sub % Sa) * kN;
-        s_w0[1] = ((sub / Sa) % Sa) * kN;
-        s_w0[2] = (sub / (Sa * Sa)) * kN;
+        s_w0[0] = (sub % Sa) * G;
+        s_w0[1] = ((sub / Sa) % Sa) * G;
+        s_w0[2] = (sub / (Sa * Sa)) * G;
         const int b = prm.list ? prm.list[item] : item;
         const bool list_slots = (prm.flags & MFA_DECODE_LIST_SLOTS) != 0;
         uint32_t bad = 0;
@@ -230,13 +236,14 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
           if (item >= prm.nslots) bad = MFA_DEV_BAD_RANGE;
           s_g.slot = item;
         }
-        // this path decodes at most 16 control points per axis
-        if (!bad)
-          for (int a = 0; a < 3; ++a)
-            if (s_g.C[a] > kK) bad = MFA_DEV_BAD_DESC;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
-        // a sub-cube past the block's own sample count has nothing to decode
-        if (!bad && (s_w0[0] >= s_g.n[0] || s_w0[1] >= s_g.n[1] || s_w0[2] >= s_g.n[2])) s_bad = 1;
+        // positions off the block's sub-cube grid, or past its own sample count, have nothing to decode
+        if (!bad)
+          for (int a = 0; a < 3; ++a) {
+            const int E = s_g.C[a] <= kK ? kN : kN / 2;
+            if (s_w0[a] % E != 0 || s_w0[a] >= s_g.n[a]) s_bad = 1;
+            s_m[a] = min(E, s_g.n[a] - s_w0[a]);
+          }
         // the bases, difference scales and basis operands only depend on (knots, degree, C, n, sub-cube) per
         // axis: a unit that repeats the previous unit's keeps them
         const int64_t key[15] = {s_g.knot_off[0], s_g.knot_off[1], s_g.knot_off[2], s_g.p[0], s_g.p[1], s_g.p[2],
@@ -256,19 +263,20 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     if (s_bad) continue;
     const int Cx = s_g.C[0], Cy = s_g.C[1], Cz = s_g.C[2];
     const bool same = s_same;
-    // z-slabs of this sub-cube; a block of 32^3 samples is one whole sub-cube
-    const int nslab = (min(kN, s_g.n[2] - s_w0[2]) + kKS - 1) / kKS;
-    const bool whole = s_g.n[0] == kN && s_g.n[1] == kN && s_g.n[2] == kN;
+    // z-slabs of this sub-cube; a block of 32^3 samples and at most 16 control points per axis is one whole
+    // sub-cube
+    const int nslab = (s_m[2] + kKS - 1) / kKS;
+    const bool whole = s_g.n[0] == kN && s_g.n[1] == kN && s_g.n[2] == kN && s_m[0] == kN && s_m[1] == kN &&
+                       s_m[2] == kN;
 
-    // ---- per block: knots, basis bands of degree p and p-1, difference scales (unless kept), P ----
-    if (!same && tid < 3 * kKnotMax) {
+    // ---- per unit: knots, basis bands of degree p and p-1, control windows, difference scales (unless
+    //      kept), the window of P ----
+    if (!same) {
+    if (tid < 3 * kKnotMax) {
       const int a = tid / kKnotMax, i = tid - a * kKnotMax;
       if (i < s_g.C[a] + s_g.p[a] + 1) kn[tid] = prm.knots[s_g.knot_off[a] + i];
     }
-    const int ncps = Cx * Cy * Cz;
-    for (int e = tid; e < ncps; e += kThreadsTC) P[e] = __ldg(prm.cps + s_g.cp_off + e);
     __syncthreads();
-    if (!same) {
     if (tid < 3 && !knots_ok(kn + tid * kKnotMax, s_g.p[tid], s_g.C[tid])) {
       atomicOr(&s_bad, 1);
       flag(prm.status, MFA_DEV_BAD_KNOTS);
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       tb.off = 0;
       tb.pad[0] = tb.pad[1] = tb.pad[2] = 0;
       for (int r = 0; r < 4; ++r) { tb.N[r] = 0.f; tb.Nm[r] = 0.f; }
-      if (s_w0[a] + i < s_g.n[a]) {  // a sample of this sub-cube (the rows past its end stay zero)
+      if (i < s_m[a]) {  // a sample of this sub-cube (the rows past its end stay zero)
         const float u = sample_param(s_w0[a] + i, s_g.n[a]);
         const int s = find_span(t, p, s_g.C[a], u);
         float N[MFA_MAX_DEGREE + 1], dN[MFA_MAX_DEGREE + 1], Nm[MFA_MAX_DEGREE + 1], dNm[MFA_MAX_DEGREE + 1];
@@ -301,8 +309,20 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       dsc[a * kN + i] = sc;
     }
     __syncthreads();
+    // control window per axis: from the first sample's band to the last one's (spans do not decrease)
+    if (tid < 3 && !s_bad) {
+      const int c0 = bas[tid * kN].off, last = bas[tid * kN + s_m[tid] - 1].off;
+      s_c0[tid] = c0;
+      if (last + s_g.p[tid] + 1 - c0 > kK) {
+        atomicOr(&s_bad, 1);
+        flag(prm.status, MFA_DEV_BAD_DESC);
+      }
+    }
+    __syncthreads();
     if (s_bad) continue;
+    if (tid < 3 * kN && tid % kN < s_m[tid / kN]) bas[tid].off -= s_c0[tid / kN];  // band offsets in the window
     if (tid == 0) s_key_ok = 1;
+    __syncthreads();
     // stage-y A: rows 96..127 of the two zero-padded buffers = N_y(u_j) and N_y^(p-1)(u_j), K = b;
     // stage-x B: rows n < 32 = N_x(u_n), rows 32..63 = N_x^(p-1)(u_{n-32}), K = a
     for (int e = tid; e < 2 * 64 * kK; e += kThreadsTC) {
@@ -311,8 +331,9 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       const TcBasis& tb = bas[axis * kN + (n & 31)];
       const int d = c - tb.off;
       float v = 0.f;
-      if (n < 32) { if (d >= 0 && d <= 3 && c < s_g.C[axis]) v = tb.N[d]; }
-      else if (d >= 0 && d <= 3 && c < s_g.C[axis] - 1) v = tb.Nm[d];
+      const int cw = c + s_c0[axis];  // control index
+      if (n < 32) { if (d >= 0 && d <= 3 && cw < s_g.C[axis]) v = tb.N[d]; }
+      else if (d >= 0 && d <= 3 && cw < s_g.C[axis] - 1) v = tb.Nm[d];
       if (which == 0)
         put<PREC>(sm + L::Zy + (n < 32 ? 0 : kOpZ), kmajor_off(96 + (n & 31), c, kLBO, kSBO), L::dZy, v);
       else
@@ -326,29 +347,39 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         float v = 0.f;
         if ((n < 32) == (which == 0)) {
           const TcBasis& tb = bas[2 * kN + (n & 31)];
-          const int d = c - tb.off;
+          const int d = c - tb.off, cw = c + s_c0[2];
           if (d >= 0 && d <= 3) {
-            if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
-            else if (c < Cz) v = tb.N[d];
+            if (which == 1) { if (cw < Cz - 1) v = tb.Nm[d]; }
+            else if (cw < Cz) v = tb.N[d];
           }
         }
         put<PREC>(sm + L::Bz + which * kOp64, kmajor_off(n, c, kLBO, kSBO), L::dBz, v);
       }
     }  // !same
-    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index), two K at a time
+    {  // the window of P: local (c, b, a) at (16 c + b) 16 + a, control (c0_z + c, c0_y + b, c0_x + a)
+    const int x0 = s_c0[0], y0 = s_c0[1], z0 = s_c0[2];
+    const int Wx = min(kK, Cx - x0), Wy = min(kK, Cy - y0), Wz = min(kK, Cz - z0);
+    for (int e = tid; e < kK * kK * kK; e += kThreadsTC) {
+      const int c = e >> 8, b = (e >> 4) & 15, a = e & 15;
+      if (a < Wx && b < Wy && c < Wz) P[e] = __ldg(prm.cps + s_g.cp_off + ((z0 + c) * Cy + y0 + b) * Cx + x0 + a);
+    }
+    __syncthreads();
+    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index in the window), two
+    // K at a time. A difference whose second point lies past the window is never used (its degree p-1 basis
+    // function is zero on the sub-cube's samples) and is written as 0.
     for (int e = tid; e < 256 * kK / 2; e += kThreadsTC) {
       const int R = e >> 3, c0 = 2 * (e & 7), b = R >> 4, a = R & 15;
       float v0[2] = {0.f, 0.f}, vu[2] = {0.f, 0.f}, vv[2] = {0.f, 0.f}, vw[2] = {0.f, 0.f};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = c0 + h;
-        if (a < Cx && b < Cy && c < Cz) {
-          const int idx = (c * Cy + b) * Cx + a;
+        if (a < Wx && b < Wy && c < Wz) {
+          const int idx = (c * kK + b) * kK + a;
           const float p0 = P[idx];
           v0[h] = p0;
-          if (a < Cx - 1) vu[h] = dsc[a] * (P[idx + 1] - p0);
-          if (b < Cy - 1) vv[h] = dsc[kN + b] * (P[idx + Cx] - p0);
-          if (c < Cz - 1) vw[h] = dsc[2 * kN + c] * (P[idx + Cy * Cx] - p0);
+          if (a + 1 < Wx) vu[h] = dsc[x0 + a] * (P[idx + 1] - p0);
+          if (b + 1 < Wy) vv[h] = dsc[kN + y0 + b] * (P[idx + kK] - p0);
+          if (c + 1 < Wz) vw[h] = dsc[2 * kN + z0 + c] * (P[idx + kK * kK] - p0);
         }
       }
       const uint32_t off = kmajor_off(R, c0, kLBO, kSBO);
@@ -356,6 +387,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       put2<PREC>(sm + L::Az + kOp256, off, L::dAz, vu[0], vu[1]);
       put2<PREC>(sm + L::Az + 2 * kOp256, off, L::dAz, vv[0], vv[1]);
       put2<PREC>(sm + L::Az + 3 * kOp256, off, L::dAz, vw[0], vw[1]);
+    }
     }
     // (P in R1 is dead from here on: R1 becomes the stage-x operand and the readout staging)
     if (zonce) {
@@ -387,10 +419,10 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         float v = 0.f;
         if ((n < 8) == (which == 0)) {
           const TcBasis& tb = bas[2 * kN + k0 + kl];
-          const int d = c - tb.off;
+          const int d = c - tb.off, cw = c + s_c0[2];
           if (d >= 0 && d <= 3) {
-            if (which == 1) { if (c < Cz - 1) v = tb.Nm[d]; }
-            else if (c < Cz) v = tb.N[d];
+            if (which == 1) { if (cw < Cz - 1) v = tb.Nm[d]; }
+            else if (cw < Cz) v = tb.N[d];
           }
         }
         put<PREC>(sm + L::Bz + which * kOp16, kmajor_off(n, c, kLBO, kSBO), L::dBz, v);
@@ -517,10 +549,11 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
               const int Rg = 128 * group + 32 * quarter + rr, i = 16 * h + 8 * half + v;
               if (whole) {  // row (k, j) of the tile at (k0 + k) 32^2 + 32 j
                 __stcs(out + (k0 * kN * kN + Rg * kN + i), stg[rr * 8 + (v ^ (rr & 7))]);
-              } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the block
-                const int kz = s_w0[2] + k0 + (Rg >> 5), jy = s_w0[1] + (Rg & 31), ix = s_w0[0] + i;
-                if (kz < s_g.n[2] && jy < s_g.n[1] && ix < s_g.n[0])
-                  __stcs(out + ((kz * s_g.n[1] + jy) * s_g.n[0] + ix), stg[rr * 8 + (v ^ (rr & 7))]);
+              } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the sub-cube
+                const int kl = k0 + (Rg >> 5), j = Rg & 31;
+                if (kl < s_m[2] && j < s_m[1] && i < s_m[0])
+                  __stcs(out + (((s_w0[2] + kl) * s_g.n[1] + s_w0[1] + j) * s_g.n[0] + s_w0[0] + i),
+                         stg[rr * 8 + (v ^ (rr & 7))]);
               }
             }
             __syncwarp();
@@ -557,7 +590,7 @@ int launch_tc(mfa_ctx* ctx, DecodeParams prm, cudaStream_t stream) {
 }  // namespace
 
 int decode_tc(mfa_ctx* ctx, DecodeParams prm, int precision, cudaStream_t stream) {
-  if (prm.bounds.max_ncp > kK || prm.bounds.max_nsamp > 2 * kN) return MFA_ERR_UNSUPPORTED;
+  if (prm.bounds.max_nsamp > 2 * kN) return MFA_ERR_UNSUPPORTED;
   if (prm.flags & MFA_DECODE_VALUE_ONLY) return MFA_ERR_UNSUPPORTED;
   prm.ks = kKS;
   prm.slabs = kSlabs;

@@ -81,28 +81,30 @@ def test_tensor_core_list_slots_and_shape_checks(mfa, ctx):
         ve, ge = rel_errors(c[m].reshape(32, 32, 32, 4), oracle_decode_set(bs, [b])[0])
         assert ve <= 1e-4 and max(ge) <= 1e-4
     assert np.all(np.isnan(c[2]))
-    # shapes outside the tensor-core path (more than 16 control points on an axis): host refusal when the
-    # bounds say so, a per-block device flag when a block breaks the bounds it was launched with
-    big = synth.random_block_set(2, 603, ncp_choices=(20,), nsamp_choices=(24,), degree_choices=(2,))
-    bblk = mfa.DeviceBlocks(big)
+    # outside the tensor-core path: a value-only decode (host refusal), and a sub-cube whose samples' bands
+    # cover more than 16 control points (clustered knots: a per-block device flag, the other blocks decode)
     with pytest.raises(mfa.MfaError) as e:
-        mfa.decode_blocks(ctx, bblk, torch.zeros(2 * bblk.slot_voxels * 4, device="cuda"), bblk.slot_voxels, 2,
-                          precision=mfa.PREC_BF16)
+        mfa.decode_blocks(ctx, blk, torch.zeros(3 * 32 ** 3, device="cuda"), 32 ** 3, 3,
+                          precision=mfa.PREC_BF16, flags=mfa.DECODE_VALUE_ONLY)
     assert e.value.code == mfa.ERR_UNSUPPORTED
-    ncp = [(4, 4, 4), (4, 17, 4), (4, 4, 4)]
+    C, p = 24, 2
+    uni = synth.clamped_uniform_knots(C, p)
+    clustered = np.concatenate([np.zeros(p + 1), np.linspace(0.01, 0.3, C - p - 1), np.ones(p + 1)])
     gm = synth.rng(605)
-    mixed = synth.make_block_set(ncp, [(2, 2, 2)] * 3, [(16, 16, 16)] * 3,
-                                 [gm.uniform(-1, 1, size=c[::-1]) for c in ncp])
+    mixed = synth.make_block_set([(C, C, C)] * 3, [(p, p, p)] * 3, [(32, 32, 32)] * 3,
+                                 [gm.uniform(-1, 1, size=(C, C, C)) for _ in range(3)],
+                                 [(uni, uni, uni), (uni, clustered, uni), (uni, uni, uni)])
     mblk = mfa.DeviceBlocks(mixed)
     cache = torch.full((3 * mblk.slot_voxels * 4,), float("nan"), device="cuda")
-    mfa.decode_blocks(ctx, mblk, cache, mblk.slot_voxels, 3, precision=mfa.PREC_BF16, bounds=mfa.Bounds(2, 16, 16))
+    mfa.decode_blocks(ctx, mblk, cache, mblk.slot_voxels, 3, precision=mfa.PREC_BF16)
     assert ctx.device_status() & mfa.DEV_BAD_DESC  # reading the status clears it
     c = cache.view(3, mblk.slot_voxels, 4).cpu().numpy()
     want = oracle_decode_set(mixed, [0, 2])
     for m, b in enumerate([0, 2]):
-        ve, ge = rel_errors(c[mixed.slot[b]].reshape(16, 16, 16, 4), want[m])
+        ve, ge = rel_errors(c[mixed.slot[b]].reshape(32, 32, 32, 4), want[m])
         assert ve <= 1e-2 and max(ge) <= 1e-2
-    assert np.all(np.isnan(c[mixed.slot[1]]))
+    # the flagged block's sub-cubes with y < 16 (the window of 22 control points) are not written
+    assert np.all(np.isnan(c[mixed.slot[1]].reshape(32, 32, 32, 4)[:, :16]))
 
 
 @pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
@@ -120,6 +122,40 @@ def test_tensor_core_decode_any_sample_count(mfa, ctx, name):
         ve, ge = rel_errors(got[bs.slot[b]][:vox].reshape(nz, ny, nx, 4), want[b])
         assert ve <= TOL[name] and max(ge) <= TOL[name], (b, bs.nsamp[b], ve, ge)
         assert np.all(np.isnan(got[bs.slot[b]][vox:]))  # nothing written past the block's voxels
+
+
+@pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
+def test_tensor_core_decode_more_than_16_control_points(mfa, ctx, name):
+    """C up to 24 per axis (uniform knots, n >= 32, degrees 1..3, mixed with C <= 16): axes with C > 16 are
+    decoded in 16-sample sub-cubes, each over the window of at most 16 control points its bands cover."""
+    bs = synth.random_block_set(12, 607, ncp_choices=(4, 12, 17, 20, 24), degree_choices=(1, 2, 3),
+                                nsamp_choices=(32, 40, 64))
+    got = _decode(mfa, ctx, bs, _prec(mfa, name))
+    assert ctx.device_status() == 0
+    want = oracle_decode_set(bs)
+    assert int(np.max(bs.ncp)) > 16
+    for b in range(len(bs)):
+        nx, ny, nz = (int(v) for v in bs.nsamp[b])
+        vox = nx * ny * nz
+        ve, ge = rel_errors(got[bs.slot[b]][:vox].reshape(nz, ny, nx, 4), want[b])
+        assert ve <= TOL[name] and max(ge) <= TOL[name], (b, bs.ncp[b], bs.nsamp[b], ve, ge)
+
+
+def test_tensor_core_decode_adaptive_ncp(mfa, ctx):
+    """Blocks of the adaptive-NCP batch's classes ({4, 6, 8, 12, 16, 20, 24} per axis, degree 2, 32^3
+    samples) in one split-BF16 launch against the oracle."""
+    g = synth.rng(608)
+    classes = (4, 6, 8, 12, 16, 20, 24)
+    ncp = [tuple(int(v) for v in g.choice(classes, 3)) for _ in range(24)]
+    ncp[0] = (24, 24, 24)
+    bs = synth.make_block_set(ncp, [(2, 2, 2)] * len(ncp), [(32, 32, 32)] * len(ncp),
+                              [g.uniform(0, 1, size=c[::-1]) for c in ncp])
+    got = _decode(mfa, ctx, bs, mfa.PREC_SPLIT_BF16)
+    assert ctx.device_status() == 0
+    want = np.stack(oracle_decode_set(bs))
+    ve, ge = rel_errors(got.reshape(len(bs), 32, 32, 32, 4), want)
+    print(f"adaptive NCP split-BF16: value {ve:.2e}, gradient {max(ge):.2e}")
+    assert ve <= TOL["split"] and max(ge) <= TOL["split"], (ve, ge)
 
 
 def test_tensor_core_decode_config1(mfa, ctx):
