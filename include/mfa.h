@@ -171,10 +171,13 @@ int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream
  * with MFA_DECODE_VALUE_ONLY, at d_cache + (slot*slot_stride_voxels + voxel)*width.
  * d_cache must be 16-byte aligned. knots_len / cps_len are the array lengths (floats),
  * used for the range checks. precision: MFA_PREC_FP32 (any supported shape) or, on the tensor
- * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 for batches with at most 16
- * control points per axis and any sample counts (max_ncp <= 16, no VALUE_ONLY, row layout;
- * otherwise MFA_ERR_UNSUPPORTED; a block with more than 16 control points on an axis in such a
- * batch sets MFA_DEV_BAD_DESC). */
+ * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 (row layout, no VALUE_ONLY;
+ * otherwise MFA_ERR_UNSUPPORTED). The tensor-core decode takes a block in sub-cubes of 32
+ * samples per axis, or 16 on an axis with more than 16 control points; every sub-cube's samples
+ * must have their nonzero basis functions within 16 consecutive control points per axis. That
+ * holds for every block with at most 16 control points per axis, and for uniform knots with up
+ * to 24 control points when n >= 32. A sub-cube that breaks it sets MFA_DEV_BAD_DESC and is not
+ * written. */
 int mfa_decode_blocks(mfa_ctx* ctx,
                       const mfa_block_desc* d_desc, int32_t nblocks,
                       const int32_t* d_list, int32_t list_len, const int32_t* d_count,

@@ -47,7 +47,7 @@ struct DecodeTuning {
 
 int decode_fp32(mfa_ctx* ctx, DecodeParams prm, const DecodeTuning& tune, cudaStream_t stream);
 
-// Tensor-core decode (BF16, FP16, split-BF16); MFA_ERR_UNSUPPORTED unless C <= 16 per axis.
+// Tensor-core decode (BF16, FP16, split-BF16) over sub-cubes whose bands lie within 16 control points per axis.
 int decode_tc(mfa_ctx* ctx, DecodeParams prm, int precision, cudaStream_t stream);
 
 int basis_tables(mfa_ctx* ctx, const mfa_block_desc* d_desc, const float* d_knots, int64_t knots_len,
