@@ -68,6 +68,9 @@ def parse():
                     help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
                          "decode)")
+    ap.add_argument("--field", type=int, default=N_FIELD,
+                    help="edge of the synthetic field of the precision workload (a multiple of 32; default 512, "
+                         "the quoted configuration; smaller fields make small profiler captures)")
     ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct", "outofcore",
                                            "lodrender"],
                     default="step",
@@ -693,8 +696,11 @@ def run_precision(args):
     torch.cuda.set_device(0)
     ctx = mfa.Context(0)
     seed, p = synth.BASE_SEED + 2, 3
-    B, vox = (N_FIELD // BRICK) ** 3, BRICK ** 3
-    field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+    nf = args.field
+    if nf < BRICK or nf % BRICK:
+        raise SystemExit("--field must be a positive multiple of 32")
+    B, vox = (nf // BRICK) ** 3, BRICK ** 3
+    field = synth.gm_noise_field(nf, seed, device="cuda")
     D = synth.blocks_from_field(field, BRICK).contiguous().view(-1)
     del field
     zero = np.zeros((NCP, NCP, NCP))
@@ -743,7 +749,7 @@ def run_precision(args):
                           "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
                           "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm)}
     # the fit (without RMSE) and the adjoint of the same blocks in each precision: 4 B/voxel read + C^3 written
-    D = synth.blocks_from_field(synth.gm_noise_field(N_FIELD, seed, device="cuda"), BRICK).contiguous().view(-1)
+    D = synth.blocks_from_field(synth.gm_noise_field(nf, seed, device="cuda"), BRICK).contiguous().view(-1)
     R = torch.empty_like(D).uniform_(-1, 1, generator=torch.Generator(device="cuda").manual_seed(seed))
     P_tmp = torch.empty(blk.cps_len, device="cuda")
     c_algo = B * (vox * 4 + NCP ** 3 * 4 + 72)
@@ -772,9 +778,10 @@ def run_precision(args):
             "value": sp["Gvoxel_s"], "unit": "Gvoxel/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup),
             "ms_per_step": sp["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3 (split) / f32 accumulate", "data": "synthetic",
-            "config": {"workload": "512^3 Gaussian-mixture+noise field, 4096 micro-blocks of 32^3, degree 3, 12^3 "
-                                   "control points (library LS fit); value+gradient decode per precision",
-                       "l2": "cache 2.15 GB, larger than L2; no flush",
+            "config": {"workload": f"{nf}^3 Gaussian-mixture+noise field, {B} micro-blocks of 32^3, degree 3, "
+                                   "12^3 control points (library LS fit); value+gradient decode per precision",
+                       "l2": f"cache {B * vox * 16 / 1e9:.2f} GB" + (", larger than L2; no flush" if B * vox * 16 > 126e6
+                                                                      else ", smaller than L2"),
                        "error_sample": "12 blocks x 400 voxels; value: max|df|/range(f), grad: max|dg|/max|g|"},
             "roofline": {"kernel": "decode_tc (split-BF16)", "bound": "hbm", "achieved": sp["GB_s"], "peak": hbm,
                          "unit": "GB/s", "frac": sp["hbm_frac"], "traffic": None,

@@ -141,6 +141,27 @@ def test_tensor_core_decode_more_than_16_control_points(mfa, ctx, name):
         assert ve <= TOL[name] and max(ge) <= TOL[name], (b, bs.ncp[b], bs.nsamp[b], ve, ge)
 
 
+def test_tensor_core_list_count_with_sub_cubes(mfa, ctx):
+    """A device list and count with list slots, over blocks of several sub-cubes each (n = 48 and C up to 20:
+    27 sub-cube positions per item): every listed block lands in its list slot, unlisted slots stay unwritten."""
+    bs = synth.random_block_set(6, 609, ncp_choices=(5, 12, 20), degree_choices=(2, 3), nsamp_choices=(33, 48))
+    blk = mfa.DeviceBlocks(bs)
+    order = torch.tensor([4, 0, 5, 2], dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([3], dtype=torch.int32, device="cuda")
+    V = blk.slot_voxels
+    cache = torch.full((4 * V * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, cache, V, 4, precision=mfa.PREC_SPLIT_BF16, list_=order, count=cnt,
+                      flags=mfa.DECODE_LIST_SLOTS)
+    assert ctx.device_status() == 0
+    c = cache.view(4, V, 4).cpu().numpy()
+    want = oracle_decode_set(bs, [4, 0, 5])
+    for m, b in enumerate([4, 0, 5]):
+        nx, ny, nz = (int(v) for v in bs.nsamp[b])
+        ve, ge = rel_errors(c[m][:nx * ny * nz].reshape(nz, ny, nx, 4), want[m])
+        assert ve <= TOL["split"] and max(ge) <= TOL["split"], (b, ve, ge)
+    assert np.all(np.isnan(c[3]))
+
+
 def test_tensor_core_decode_adaptive_ncp(mfa, ctx):
     """Blocks of the adaptive-NCP batch's classes ({4, 6, 8, 12, 16, 20, 24} per axis, degree 2, 32^3
     samples) in one split-BF16 launch against the oracle."""
