@@ -31,8 +31,12 @@ What each module computes, and the passage it follows:
 Parity pins (tests/test_oracle_*.py) tie every function to something other than
 itself: partition of unity, Bernstein closed forms, polynomial reproduction, endpoint
 interpolation, finite differences, brute-force dense least squares, the adjoint
-dot-product identity and closed-form ray compositing. The ray caster is pinned only
-by those closed-form cases; elsewhere it is "parity unpinned" beyond them.
+dot-product identity, and for the ray caster closed forms of each of its steps (camera
+orientation and centre ray, chord length and sample positions, front-to-back sums,
+termination, opacity correction, transfer-function interpolation, shading, trilinear
+interpolation across bricks). The renderer's choices that the paper leaves open (camera
+model, lighting model, sampling rate) are readings stated in oracle/raycast.py; the pins
+fix the oracle to those readings, not the readings to the paper.
 """
 
 from . import bspline, decode, encode, adjoint, raycast, multires  # noqa: F401

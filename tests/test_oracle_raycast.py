@@ -1,8 +1,8 @@
-"""Pins for the oracle ray caster (Algorithm 4): closed-form compositing and shading cases.
-
-Beyond these cases the ray caster is parity-unpinned: its remaining behaviour is the
-reading of Algorithm 4 stated in the module docstring, checked only against the GPU.
-"""
+"""Pins for the oracle ray caster (Algorithm 4): closed forms for the camera (centre ray, image
+orientation), the ray/box chord and the sample positions, the front-to-back compositing order and its
+sums, early termination, opacity correction, transfer-function interpolation and clamping, headlight
+shading, trilinear interpolation across bricks, absent bricks and missed rays; the per-sample query
+renderer against polynomial fields and the cache renderer; pixel subsets against the full render."""
 
 import numpy as np
 
@@ -93,6 +93,54 @@ def test_center_pixel_ray_is_view_direction():
     d, _, _, _, _ = raycast.ray_setup(view, (64, 64, 64))
     fwd = -np.array(view["eye"]) / np.linalg.norm(view["eye"])
     assert np.max(np.abs(d[2, 3] - fwd)) < 1e-6
+
+
+def test_image_orientation():
+    """Eye on +z looking at the origin with up +y: pixel columns grow towards +x and row 0 is the top (+y).
+    With the bricks of x > 0 absent the right columns are black and the left ones are not; with the bricks
+    of y > 0 absent the top rows are black. (Rays through columns 5..7 of 8 stay at x > 0.27, beyond the
+    cells that touch x = 0; likewise rows 0..2 at y > 0.27.)"""
+    B, n = 2, 8
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([np.full(x.shape, 0.5), 0 * x, 0 * x, 0 * x], -1))
+    tf = _const_tf([1.0, 1.0, 1.0, 0.3])
+    tf[0] = 0.0  # an absent brick's nodes (value 0) are transparent
+    view = synth.default_view(width=8, height=8, eye=(0.0, 0.0, 3.0), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0))
+    right_absent = table.copy()
+    right_absent[:, :, 1] = -1  # table[bz, by, bx]
+    img = raycast.raycast(cache, right_absent, n, view, tf)
+    assert np.all(img[:, 5:] == 0)
+    assert np.all(img[:, :3, 3] > 0.1)
+    top_absent = table.copy()
+    top_absent[:, 1, :] = -1
+    img = raycast.raycast(cache, top_absent, n, view, tf)
+    assert np.all(img[:3] == 0)
+    assert np.all(img[5:, :, 3] > 0.1)
+
+
+def test_front_to_back_order_and_sample_positions():
+    """f = 0.3 + s g_z (node units) seen by the centre ray from +z: sample k sits at node z = N - 3/2 - k (the
+    first sample half a step inside the front face), and a transfer function whose red channel is the value
+    itself (alpha constant, no shading) gives the front-to-back sum
+    C = alpha sum_k r^k f_k = alpha (c0 S0 - s S1), r = 1 - alpha, f_k = c0 - s k, c0 = 0.3 + s (N - 3/2),
+    with the closed forms S0 = (1 - r^K)/(1 - r) and S1 = r (1 - K r^(K-1) + (K-1) r^K)/(1 - r)^2."""
+    B, n = 2, 8
+    N = B * n
+    s = 0.03
+    cache, table = _volume(B, n, lambda x, y, z: np.stack([0.3 + s * z, 0 * x, 0 * x, s * (n - 1) + 0 * x], -1))
+    alpha = float(np.float32(0.05))
+    m = 256
+    tf = np.stack([np.arange(m) / (m - 1), np.zeros(m), np.zeros(m), np.full(m, alpha)], 1).astype(np.float32)
+    view = _axis_view((0.0, 0.0, 3.0), opacity_max=1.0, vmin=0.0, vmax=1.0, ka=1.0, kd=0.0, ks=0.0)
+    img = raycast.raycast(cache, table, n, view, tf)
+    K = N - 1
+    r = 1.0 - alpha
+    S0 = (1 - r ** K) / (1 - r)
+    S1 = r * (1 - K * r ** (K - 1) + (K - 1) * r ** K) / (1 - r) ** 2
+    c0 = 0.3 + s * (N - 1.5)
+    assert abs(img[2, 2, 3] - (1 - r ** K)) < 1e-12
+    assert abs(img[2, 2, 0] - alpha * (c0 * S0 - s * S1)) < 1e-7
+    # the reversed (back-to-front) weighting, or samples on the nodes, would differ by far more
+    assert abs(alpha * (c0 * S0 - s * S1) - alpha * ((0.3 + 0.5 * s) * S0 + s * S1)) > 1e-3
 
 
 def test_opacity_correction_closed_form():
