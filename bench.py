@@ -505,12 +505,14 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def frames_record(layout="apron", frames=32, warmup=3, ctx=None):
+def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=False):
     """Adaptive-NCP frames: 1024^3 flame stand-in, 32768 blocks of 32^3, C in {4..24} by gradient energy,
     control points = the field at Greville abscissae; per frame the ~6600 bricks in view along a 32-frame
     orbit are ordered by cost, decoded by the persistent queue and ray-cast at 1024^2, all replayed from
     one CUDA graph with the tiling the autotuner picked for this batch. Returns the per-frame timings (the
-    whole frame, and the ordering + decode alone) with their rates."""
+    whole frame, and the ordering + decode alone) with their rates. With precisions, also the plain decode of
+    every frame's visible list (row layout, list slots) in FP32, split-BF16 and BF16, with the error of each
+    against the FP64 oracle on sampled voxels of frame 0."""
     from paper_2409_00184_b300 import autotune, mfa
     own = ctx is None
     if own:
@@ -590,6 +592,48 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None):
         raise RuntimeError("device status after the frames")
     nvis = [len(v) for v in lists]
     vox = sum(nvis) * n ** 3
+    prec_rec = None
+    if precisions:
+        from oracle import decode as odec
+        g = synth.rng(seed + 11)
+        f0 = lists[0]
+        pick = g.choice(len(f0), 12, replace=False)  # list positions (= cache slots) in frame 0
+        kji = g.integers(0, n, size=(400, 3))
+        lin = torch.as_tensor((kji[:, 0] * n + kji[:, 1]) * n + kji[:, 2], device="cuda")
+        want = np.concatenate([odec.decode_voxels(bs.block_cps(int(f0[m])), bs.block_knots(int(f0[m])),
+                                                  bs.degree[int(f0[m])], bs.nsamp[int(f0[m])], kji) for m in pick])
+        vr, gmax = want[:, 0].max() - want[:, 0].min(), np.abs(want[:, 1:]).max()
+        peaks_h = float(measured_peaks()[0]["hbm_gbs"])
+        dec_b = sum(int(n ** 3 * 16 + int(ncp[b]) ** 3 * 4 + 72) for v in lists for b in v) / frames
+        prec_rec = {"layout": "rows (the tensor-core decode writes the row layout)",
+                    "error_sample": "12 blocks of frame 0 x 400 voxels; value: max|df|/range(f), grad: max|dg|/max|g|"}
+        for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16)):
+            def one(f):
+                lst.copy_(all_lists[f]); cnt.copy_(counts[f: f + 1])
+                mfa.decode_blocks(ctx, blk, cache, n ** 3, cap, precision=prec, list_=lst, count=cnt,
+                                  flags=mfa.DECODE_LIST_SLOTS)
+            for f in range(3):
+                one(f)
+            pms = 0.0
+            for f in range(frames):
+                d0.record(stream)
+                one(f)
+                d1.record(stream)
+                torch.cuda.synchronize()
+                pms += d0.elapsed_time(d1)
+            pms /= frames
+            one(0)
+            torch.cuda.synchronize()
+            if ctx.device_status():
+                raise RuntimeError(f"device status after the {name} frame decode")
+            c4 = cache[: cap * n ** 3 * 4].view(cap, n ** 3, 4)
+            got = np.concatenate([c4[int(m)][lin].double().cpu().numpy() for m in pick])
+            prec_rec[name] = {"decode_ms_per_frame": pms, "Gvoxel_s": vox / frames / (pms * 1e-3) / 1e9,
+                              "hbm_frac": dec_b / (pms * 1e-3) / 1e9 / peaks_h,
+                              "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
+                              "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gmax)}
+        prec_rec["split_vs_fp32_speedup"] = prec_rec["fp32"]["decode_ms_per_frame"] / \
+            prec_rec["split_bf16"]["decode_ms_per_frame"]
     # algorithmic bytes of the decode per frame: 16 B per voxel written, the control points and descriptors read
     dec_bytes = sum(int(n ** 3 * 16 + int(ncp[b]) ** 3 * 4 + 72) for v in lists for b in v) / frames
     total = sum(ms)
@@ -605,6 +649,8 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None):
            "ray_samples_per_frame": samples,
            "raycast_Gsample_s": samples / ((total / frames - dms) * 1e-3) / 1e9,
            "gpu_launches": launches, "clocks": clk}
+    if prec_rec is not None:
+        rec["precisions"] = prec_rec
     del cache, blk
     torch.cuda.empty_cache()
     if own:
@@ -615,7 +661,7 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None):
 def run_frames(args):
     """The adaptive-NCP frames workload as its own bench line (see frames_record)."""
     torch.cuda.set_device(0)
-    rec = frames_record(args.layout, 32, args.warmup)
+    rec = frames_record(args.layout, 32, args.warmup, precisions=True)
     line = {"metric": METRIC, "value": rec["Gvoxel_s"], "unit": "Gvoxel/s", "n_gpus": 1, "steps": rec["frames"],
             "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_frame"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

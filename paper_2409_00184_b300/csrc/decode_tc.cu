@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   __shared__ int s_item, s_bad, s_same;
   __shared__ int s_w0[3], s_m[3];  // first sample and number of samples of the sub-cube per axis
   __shared__ int s_c0[3];          // first control point of the sub-cube's window per axis
+  __shared__ float s_lo[kThreadsTC / 32], s_hi[kThreadsTC / 32];  // per warp: least and greatest P loaded
+  __shared__ float s_mid;  // mid-range of the unit's window of P
   __shared__ BlockGeom s_g;
   __shared__ int64_t s_key[15];  // knots, degrees, sizes and sub-cube of the unit whose bases are in shared memory
   __shared__ int s_key_ok;
@@ -359,14 +361,31 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     {  // the window of P: local (c, b, a) at (16 c + b) 16 + a, control (c0_z + c, c0_y + b, c0_x + a)
     const int x0 = s_c0[0], y0 = s_c0[1], z0 = s_c0[2];
     const int Wx = min(kK, Cx - x0), Wy = min(kK, Cy - y0), Wz = min(kK, Cz - z0);
+    float lo = __int_as_float(0x7f800000), hi = -lo;
     for (int e = tid; e < kK * kK * kK; e += kThreadsTC) {
       const int c = e >> 8, b = (e >> 4) & 15, a = e & 15;
-      if (a < Wx && b < Wy && c < Wz) P[e] = __ldg(prm.cps + s_g.cp_off + ((z0 + c) * Cy + y0 + b) * Cx + x0 + a);
+      if (a < Wx && b < Wy && c < Wz) {
+        const float v = __ldg(prm.cps + s_g.cp_off + ((z0 + c) * Cy + y0 + b) * Cx + x0 + a);
+        P[e] = v;
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+      }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
     __syncthreads();
-    // stage-z A: chains P, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index in the window), two
-    // K at a time. A difference whose second point lies past the window is never used (its degree p-1 basis
-    // function is zero on the sub-cube's samples) and is written as 0.
+    // The value chain carries P - m, m the mid-range of the window's P, and the readout adds m back: the
+    // sub-cube's samples have all their nonzero basis functions in the window and they sum to 1, so
+    // f = m + sum N (P - m), while the 16-bit roundings now scale with |P - m| instead of |P|.
+    for (int w = 0; w < kThreadsTC / 32; ++w) { lo = fminf(lo, s_lo[w]); hi = fmaxf(hi, s_hi[w]); }
+    const float mid = 0.5f * (lo + hi);
+    if (tid == 0) s_mid = mid;  // read by the value readouts of this unit's slabs
+    // stage-z A: chains P - m, DxP, DyP, DzP at rows (b,a) = 16b + a, K = c (z control index in the window),
+    // two K at a time. A difference whose second point lies past the window is never used (its degree p-1
+    // basis function is zero on the sub-cube's samples) and is written as 0.
     for (int e = tid; e < 256 * kK / 2; e += kThreadsTC) {
       const int R = e >> 3, c0 = 2 * (e & 7), b = R >> 4, a = R & 15;
       float v0[2] = {0.f, 0.f}, vu[2] = {0.f, 0.f}, vv[2] = {0.f, 0.f}, vw[2] = {0.f, 0.f};
@@ -376,7 +395,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         if (a < Wx && b < Wy && c < Wz) {
           const int idx = (c * kK + b) * kK + a;
           const float p0 = P[idx];
-          v0[h] = p0;
+          v0[h] = p0 - mid;
           if (a + 1 < Wx) vu[h] = dsc[x0 + a] * (P[idx + 1] - p0);
           if (b + 1 < Wy) vv[h] = dsc[kN + y0 + b] * (P[idx + kK] - p0);
           if (c + 1 < Wz) vw[h] = dsc[2 * kN + z0 + c] * (P[idx + kK * kK] - p0);
@@ -539,7 +558,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
               const int q = 8 * half + v;
-              stg[lane * 8 + (v ^ (lane & 7))] = make_float4(__uint_as_float(f[q]), __uint_as_float(fu[q]),
+              stg[lane * 8 + (v ^ (lane & 7))] = make_float4(__uint_as_float(f[q]) + s_mid, __uint_as_float(fu[q]),
                                                              __uint_as_float(fv[q]), __uint_as_float(fw[q]));
             }
             __syncwarp();
