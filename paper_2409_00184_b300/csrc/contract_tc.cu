@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
   __shared__ TcGeom s_g;
   __shared__ float s_kn[3][kKnotMax];
   __shared__ int s_bad;
+  __shared__ float s_lo[kTcThreads / 32], s_hi[kTcThreads / 32];  // fit: per warp, least and greatest sample
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -250,14 +251,27 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
     }
     // ---- stage x: four batches of 8 planes (256 rows of 32 samples) through the operand region ----
     // Each batch is loaded in two rounds of kF4Round float4 per thread; the first round of the next batch is
-    // in flight while the current batch's MMAs run.
+    // in flight while the current batch's MMAs run. The fit contracts X - m, m the mid-range of the first
+    // round's samples (4 of the 32 planes), and adds m to every control point: the least-squares fit
+    // reproduces constants (the basis functions sum to 1), so P(X) = m + P(X - m), and the 16-bit roundings
+    // scale with the samples' spread rather than their offset.
     const float4* src = reinterpret_cast<const float4*>(prm.x + (int64_t)g.slot * prm.slot_stride);
     float4 xr[kF4Round];
+    float shift = 0.f;
     auto load_round = [&](int h, int s0) {
 #pragma unroll
       for (int s = 0; s < kF4Round; ++s) xr[s] = __ldg(src + (h * kF4PerThread + s0 + s) * kTcThreads + tid);
     };
     auto store_round = [&](int s0) {
+      if (prm.mode == kFit) {  // X - m, as packed FP32x2 subtractions
+        const float2 m2 = make_float2(-shift, -shift);
+#pragma unroll
+        for (int s = 0; s < kF4Round; ++s) {
+          const float2 a = __fadd2_rn(make_float2(xr[s].x, xr[s].y), m2);
+          const float2 b = __fadd2_rn(make_float2(xr[s].z, xr[s].w), m2);
+          xr[s] = make_float4(a.x, a.y, b.x, b.y);
+        }
+      }
 #pragma unroll
       for (int s = 0; s < kF4Round; ++s) {
         const int e = (s0 + s) * kTcThreads + tid, row = e >> 3, k4 = (e & 7) * 4;
@@ -268,6 +282,22 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
     };
     static_assert(kF4PerThread == 2 * kF4Round, "two rounds per batch");
     load_round(0, 0);
+    if (prm.mode == kFit) {
+      float lo = __int_as_float(0x7f800000), hi = -lo;
+#pragma unroll
+      for (int s = 0; s < kF4Round; ++s) {
+        lo = fminf(fminf(lo, fminf(xr[s].x, xr[s].y)), fminf(xr[s].z, xr[s].w));
+        hi = fmaxf(fmaxf(hi, fmaxf(xr[s].x, xr[s].y)), fmaxf(xr[s].z, xr[s].w));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
+      __syncthreads();
+      for (int w = 0; w < kTcThreads / 32; ++w) { lo = fminf(lo, s_lo[w]); hi = fmaxf(hi, s_hi[w]); }
+      shift = 0.5f * (lo + hi);
+    }
     for (int h = 0; h < kBatches && !timed_out; ++h) {
       if (h > 0) wait_mma();  // the previous batch's MMAs have read the region
       if (timed_out) break;
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
         float* out = prm.out + g.cp_off + (int64_t)b * Cx + a;
 #pragma unroll
         for (int c = 0; c < kTcC; ++c)
-          if (c < Cz) out[(int64_t)c * Cy * Cx] = __uint_as_float(r[c]);
+          if (c < Cz) out[(int64_t)c * Cy * Cx] = __uint_as_float(r[c]) + shift;
       }
     }
     tc_fence_before();
