@@ -278,6 +278,14 @@ def _oracle_blocks(D_blocks):
 _WORKER_P = None
 
 
+def _oracle_decode(items):
+    """The FP64 oracle's value+gradient decode of each (P, knots, degrees, nsamp); returns the count."""
+    from oracle import decode as odec
+    for P, knots, degrees, nsamp in items:
+        odec.decode_block(P, knots, degrees, nsamp)
+    return len(items)
+
+
 def _set_worker_cps(P):
     global _WORKER_P
     _WORKER_P = P
@@ -366,6 +374,16 @@ class OraclePool:
             self.pool.map(_oracle_blocks, [p for p in parts if len(p)])
         return time.perf_counter() - t0
 
+    def decode(self, items):
+        """Wall seconds of the oracle decode of every (P, knots, degrees, nsamp)."""
+        t0 = time.perf_counter()
+        if self.pool is None:
+            _oracle_decode(items)
+        else:
+            parts = [items[i::self.cores] for i in range(self.cores)]
+            self.pool.map(_oracle_decode, [p for p in parts if len(p)])
+        return time.perf_counter() - t0
+
     def prepare_rays(self, pixels, seed):
         """Splits the pixels over the workers and records the nodes each part's rays read (untimed)."""
         self.parts = [pixels[i::self.cores] for i in range(self.cores)]
@@ -390,6 +408,24 @@ class OraclePool:
             self.pool.close()
             self.pool.join()
             self.pool = None
+
+
+def oracle_decode_baseline(bs, ids, what):
+    """cpu_baseline of a decode workload: the FP64 oracle's decode of the listed blocks (4 per host core, a
+    bounded sample) on every host core, as voxels per second; `what` names what the sample stands for."""
+    ncpu = os.cpu_count() or 1
+    ids = [int(b) for b in ids][: 4 * ncpu]
+    items = [(bs.block_cps(b), bs.block_knots(b), tuple(int(v) for v in bs.degree[b]),
+              tuple(int(v) for v in bs.nsamp[b])) for b in ids]
+    pool = OraclePool(ncpu, None)
+    try:
+        t = pool.decode(items)
+    finally:
+        pool.close()
+    vox = sum(int(np.prod(bs.nsamp[b])) for b in ids)
+    return {"value": vox / t / 1e9, "unit": "Gvoxel/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"FP64 oracle value+gradient decode of {len(ids)} blocks ({what}) on {ncpu} worker processes: "
+                      f"{t:.1f} s"}
 
 
 def oracle_fit_all(D_blocks):
@@ -634,6 +670,8 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
                               "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gmax)}
         prec_rec["split_vs_fp32_speedup"] = prec_rec["fp32"]["decode_ms_per_frame"] / \
             prec_rec["split_bf16"]["decode_ms_per_frame"]
+        prec_rec["cpu_baseline"] = oracle_decode_baseline(
+            bs, f0[synth.rng(seed + 12).permutation(len(f0))], "a seeded sample of frame 0's visible blocks")
     # algorithmic bytes of the decode per frame: 16 B per voxel written, the control points and descriptors read
     dec_bytes = sum(int(n ** 3 * 16 + int(ncp[b]) ** 3 * 4 + 72) for v in lists for b in v) / frames
     total = sum(ms)
@@ -672,7 +710,8 @@ def run_frames(args):
             "roofline": {"kernel": "decode (frames)", "bound": "hbm", "achieved": rec["decode_GB_s"],
                          "peak": float(measured_peaks()[0]["hbm_gbs"]), "unit": "GB/s", "frac": rec["decode_hbm_frac"],
                          "traffic": None},
-            "frames": rec, "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"]}
+            "frames": rec, "cpu_baseline": rec["precisions"]["cpu_baseline"], "gpu_launches": rec["gpu_launches"],
+            "clocks": rec["clocks"]}
     print(json.dumps(line))
     return 0
 
@@ -819,6 +858,10 @@ def run_precision(args):
         raise RuntimeError("device status after the contractions")
     launches = ctx.launch_count() - n0
     clk = clocks.stop()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_decode_baseline(bs, synth.rng(seed + 9).choice(B, min(B, 64), replace=False),
+                                     f"a seeded sample of the {B} degree-3 blocks")
     sp = variants["split_bf16"]
     line = {"metric": "Gvoxel/s MFA decode (value+grad) per precision, max err vs FP64 oracle",
             "value": sp["Gvoxel_s"], "unit": "Gvoxel/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup),
@@ -836,7 +879,7 @@ def run_precision(args):
             "contraction": contraction,
             "contraction_split_vs_fp32_speedup": {
                 w: contraction[f"{w}_fp32"]["ms"] / contraction[f"{w}_split_bf16"]["ms"] for w in ("fit", "adjoint")},
-            "gpu_launches": launches, "clocks": clk}
+            "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
     ctx.close()
     return 0
