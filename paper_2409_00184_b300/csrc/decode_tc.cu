@@ -595,11 +595,21 @@ int launch_tc(mfa_ctx* ctx, DecodeParams prm, cudaStream_t stream) {
   if (cudaFuncSetAttribute(decode_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return MFA_ERR_CUDA;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_tc_kernel<PREC>, kThreadsTC, smem) != cudaSuccess)
+  // all of the SM's unified L1 / shared memory as shared memory, so that two BF16 / FP16 CTAs fit
+  if (cudaFuncSetAttribute(decode_tc_kernel<PREC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return MFA_ERR_CUDA;
-  // the resident CTAs share the SM's 512 tensor-memory columns
-  per_sm = std::max(1, std::min(per_sm, (int)(512 / kTmemColsOf<PREC>)));
+  // resident CTAs per SM from the kernel's registers and shared memory (and the SM's register file and shared
+  // memory); the resident CTAs share the SM's 512 tensor-memory columns
+  cudaFuncAttributes fa;
+  int smem_sm = 0, regs_sm = 0;
+  if (cudaFuncGetAttributes(&fa, decode_tc_kernel<PREC>) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device) != cudaSuccess)
+    return MFA_ERR_CUDA;
+  const int by_regs = regs_sm / std::max(1, fa.numRegs * kThreadsTC);
+  const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+  const int per_sm = std::max(1, std::min((int)(512 / kTmemColsOf<PREC>), std::min(by_regs, by_smem)));
   if (cudaMemsetAsync(prm.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return MFA_ERR_CUDA;
   decode_tc_kernel<PREC><<<ctx->num_sms * per_sm, kThreadsTC, smem, stream>>>(prm);
   ctx->launches++;
