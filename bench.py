@@ -547,8 +547,8 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
     orbit are ordered by cost, decoded by the persistent queue and ray-cast at 1024^2, all replayed from
     one CUDA graph with the tiling the autotuner picked for this batch. Returns the per-frame timings (the
     whole frame, and the ordering + decode alone) with their rates. With precisions, also the plain decode of
-    every frame's visible list (row layout, list slots) in FP32, split-BF16 and BF16, with the error of each
-    against the FP64 oracle on sampled voxels of frame 0."""
+    every frame's visible list (the frames' cache layout, list slots) in FP32, split-BF16 and BF16, with the
+    error of each against the FP64 oracle on sampled voxels of frame 0."""
     from paper_2409_00184_b300 import autotune, mfa
     own = ctx is None
     if own:
@@ -635,19 +635,20 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
         f0 = lists[0]
         pick = g.choice(len(f0), 12, replace=False)  # list positions (= cache slots) in frame 0
         kji = g.integers(0, n, size=(400, 3))
-        lin = torch.as_tensor((kji[:, 0] * n + kji[:, 1]) * n + kji[:, 2], device="cuda")
+        rows_pp, pitch = (n + 1, mfa.apron_pitch(n)) if apron else (n, n)
+        lin = torch.as_tensor((kji[:, 0] * rows_pp + kji[:, 1]) * pitch + kji[:, 2], device="cuda")
         want = np.concatenate([odec.decode_voxels(bs.block_cps(int(f0[m])), bs.block_knots(int(f0[m])),
                                                   bs.degree[int(f0[m])], bs.nsamp[int(f0[m])], kji) for m in pick])
         vr, gmax = want[:, 0].max() - want[:, 0].min(), np.abs(want[:, 1:]).max()
         peaks_h = float(measured_peaks()[0]["hbm_gbs"])
         dec_b = sum(int(n ** 3 * 16 + int(ncp[b]) ** 3 * 4 + 72) for v in lists for b in v) / frames
-        prec_rec = {"layout": "rows (the tensor-core decode writes the row layout)",
+        prec_rec = {"layout": layout,
                     "error_sample": "12 blocks of frame 0 x 400 voxels; value: max|df|/range(f), grad: max|dg|/max|g|"}
         for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16)):
             def one(f):
                 lst.copy_(all_lists[f]); cnt.copy_(counts[f: f + 1])
-                mfa.decode_blocks(ctx, blk, cache, n ** 3, cap, precision=prec, list_=lst, count=cnt,
-                                  flags=mfa.DECODE_LIST_SLOTS)
+                mfa.decode_blocks(ctx, blk, cache, S, cap, precision=prec, list_=lst, count=cnt,
+                                  flags=mfa.DECODE_LIST_SLOTS | (mfa.DECODE_APRON if apron else 0))
             for f in range(3):
                 one(f)
             pms = 0.0
@@ -662,7 +663,7 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
             torch.cuda.synchronize()
             if ctx.device_status():
                 raise RuntimeError(f"device status after the {name} frame decode")
-            c4 = cache[: cap * n ** 3 * 4].view(cap, n ** 3, 4)
+            c4 = cache.view(cap, S, 4)
             got = np.concatenate([c4[int(m)][lin].double().cpu().numpy() for m in pick])
             prec_rec[name] = {"decode_ms_per_frame": pms, "Gvoxel_s": vox / frames / (pms * 1e-3) / 1e9,
                               "hbm_frac": dec_b / (pms * 1e-3) / 1e9 / peaks_h,

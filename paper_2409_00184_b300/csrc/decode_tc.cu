@@ -238,6 +238,9 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
           if (item >= prm.nslots) bad = MFA_DEV_BAD_RANGE;
           s_g.slot = item;
         }
+        if (!bad && (prm.flags & MFA_DECODE_APRON) &&
+            (int64_t)apron_pitch(s_g.n[0]) * (s_g.n[1] + 1) * (s_g.n[2] + 1) > prm.slot_stride)
+          bad = MFA_DEV_BAD_RANGE;
         if (bad) { flag(prm.status, bad); s_bad = 1; }
         // positions off the block's sub-cube grid, or past its own sample count, have nothing to decode
         if (!bad)
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     // sub-cube
     const int nslab = (s_m[2] + kKS - 1) / kKS;
     const bool whole = s_g.n[0] == kN && s_g.n[1] == kN && s_g.n[2] == kN && s_m[0] == kN && s_m[1] == kN &&
-                       s_m[2] == kN;
+                       s_m[2] == kN && !(prm.flags & MFA_DECODE_APRON);
 
     // ---- per unit: knots, basis bands of degree p and p-1, control windows, difference scales (unless
     //      kept), the window of P ----
@@ -568,11 +571,15 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
               const int Rg = 128 * group + 32 * quarter + rr, i = 16 * h + 8 * half + v;
               if (whole) {  // row (k, j) of the tile at (k0 + k) 32^2 + 32 j
                 __stcs(out + (k0 * kN * kN + Rg * kN + i), stg[rr * 8 + (v ^ (rr & 7))]);
-              } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the sub-cube
+              } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the sub-cube; with an apron in
+                        // rows of apron_pitch(n_x) and planes of n_y + 1 rows
                 const int kl = k0 + (Rg >> 5), j = Rg & 31;
-                if (kl < s_m[2] && j < s_m[1] && i < s_m[0])
-                  __stcs(out + (((s_w0[2] + kl) * s_g.n[1] + s_w0[1] + j) * s_g.n[0] + s_w0[0] + i),
+                if (kl < s_m[2] && j < s_m[1] && i < s_m[0]) {
+                  const bool ap = (prm.flags & MFA_DECODE_APRON) != 0;
+                  const int rows = ap ? s_g.n[1] + 1 : s_g.n[1], pitch = ap ? apron_pitch(s_g.n[0]) : s_g.n[0];
+                  __stcs(out + (((s_w0[2] + kl) * rows + s_w0[1] + j) * pitch + s_w0[0] + i),
                          stg[rr * 8 + (v ^ (rr & 7))]);
+                }
               }
             }
             __syncwarp();

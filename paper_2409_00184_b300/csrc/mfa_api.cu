@@ -174,7 +174,7 @@ int decode_entry(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, co
   if ((flags & MFA_DECODE_CUBES) && (flags & MFA_DECODE_APRON)) return MFA_ERR_INVALID_ARG;
   if ((flags & MFA_DECODE_LIST_SLOTS) && !d_list) return MFA_ERR_INVALID_ARG;
   if (precision < MFA_PREC_FP32 || precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
-  if ((flags & (MFA_DECODE_CUBES | MFA_DECODE_APRON)) && precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
+  if ((flags & MFA_DECODE_CUBES) && precision != MFA_PREC_FP32) return MFA_ERR_UNSUPPORTED;
   const int items = d_list ? list_len : nblocks;
   if (items == 0 && !d_count) return MFA_OK;
   if (!d_desc || !d_knots || !d_cps || !d_cache || nblocks == 0) return MFA_ERR_INVALID_ARG;

@@ -210,10 +210,11 @@ def test_apron_argument_checks(mfa, ctx):
     cache = torch.full((2 * apron_voxels(8) * 4,), 3.0, device="cuda")
     with pytest.raises(mfa.MfaError):  # cubes and apron together
         mfa.decode_blocks(ctx, blk, cache, apron_voxels(8), 2, flags=mfa.DECODE_APRON | mfa.DECODE_CUBES)
-    with pytest.raises(mfa.MfaError):  # tensor-core precisions write the row layout only
-        mfa.decode_blocks(ctx, blk, cache, apron_voxels(8), 2, precision=mfa.PREC_BF16, flags=mfa.DECODE_APRON)
-    mfa.decode_blocks(ctx, blk, cache, apron_voxels(8) - 1, 2, flags=mfa.DECODE_APRON)  # slots one voxel short
-    assert ctx.device_status() == mfa.DEV_BAD_RANGE
+    with pytest.raises(mfa.MfaError):  # tensor-core precisions write the row or the apron layout, not cubes
+        mfa.decode_blocks(ctx, blk, cache, apron_voxels(8), 2, precision=mfa.PREC_BF16, flags=mfa.DECODE_CUBES)
+    for prec in (mfa.PREC_FP32, mfa.PREC_BF16):  # slots one voxel short
+        mfa.decode_blocks(ctx, blk, cache, apron_voxels(8) - 1, 2, precision=prec, flags=mfa.DECODE_APRON)
+        assert ctx.device_status() == mfa.DEV_BAD_RANGE
     assert bool((cache == 3.0).all())
     table = torch.zeros(1, 1, 1, dtype=torch.int32, device="cuda")
     with pytest.raises(mfa.MfaError):
@@ -231,3 +232,34 @@ def test_apron_argument_checks(mfa, ctx):
         mfa.FrameGraph(ctx, blk, lst, cnt, cache, 8 ** 3, sort=False, table=tab, brick_dims=(2, 1, 1), brick_n=8,
                        view=synth.default_view(width=8, height=8), tf=tf, image=img, apron=True)
     assert ctx.device_status() == 0
+
+
+@pytest.mark.parametrize("prec", ["split", "bf16"])
+@pytest.mark.parametrize("N,n,C", [(128, 32, 12), (64, 16, 8)])
+def test_tensor_core_decode_apron(mfa, ctx, prec, N, n, C):
+    """The tensor-core decode in the apron layout: the interior equals its row-layout decode bit for bit,
+    the apron planes are left to mfa_fill_aprons, and after the fill the apron ray cast equals the row
+    layout's bit for bit."""
+    precision = {"split": mfa.PREC_SPLIT_BF16, "bf16": mfa.PREC_BF16}[prec]
+    bs, _ = gm_blocks_fitted(N, n, C, 2, synth.BASE_SEED + 13)
+    blk = mfa.DeviceBlocks(bs)
+    B, P3 = len(bs), apron_voxels(n)
+    row = torch.full((B * n ** 3 * 4,), float("nan"), device="cuda")
+    apr = torch.full((B * P3 * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, row, n ** 3, B, precision=precision)
+    mfa.decode_blocks(ctx, blk, apr, P3, B, precision=precision, flags=mfa.DECODE_APRON)
+    assert ctx.device_status() == 0
+    r = row.view(B, n, n, n, 4).cpu().numpy()
+    a = apr.view(B, n + 1, n + 1, pitch(n), 4).cpu().numpy()
+    assert np.array_equal(a[:, :n, :n, :n], r)
+    assert np.isnan(a[:, n]).all() and np.isnan(a[:, :, n]).all() and np.isnan(a[:, :, :, n:]).all()
+    nb = N // n
+    table = np.arange(B, dtype=np.int32).reshape(nb, nb, nb)
+    mfa.fill_aprons(ctx, apr, P3, B, torch.from_numpy(table).cuda(), n)
+    assert ctx.device_status() == 0
+    tf = synth.transfer_function(synth.BASE_SEED + 2)
+    view = synth.default_view(width=64, height=48)
+    img_rows = _render(mfa, ctx, r, n ** 3, B, table, n, view, tf, False)
+    img_apr = _render(mfa, ctx, apr.cpu().numpy(), P3, B, table, n, view, tf, True)
+    assert img_rows[..., 3].max() > 0.1
+    assert np.array_equal(img_rows, img_apr)
