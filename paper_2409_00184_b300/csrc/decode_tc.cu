@@ -8,14 +8,15 @@
 // W <= 16 holds for uniform knots up to about 24 control points (a wider window, possible only for strongly
 // clustered knots, sets MFA_DEV_BAD_DESC for that sub-cube). So every MMA has K = 16 (the window, padded);
 // every index is padded to 16 control points and 32 samples, and basis rows are written densely (zero
-// outside each band and for the samples past the sub-cube's end). n is at most 64 per axis. The stage-z operands (P and its differences) do
-// not depend on the slab and are built once per block. One kernel per precision; BF16 and FP16 keep no
-// "lo" operands, which halves the shared memory and lets two CTAs share an SM (2 x 256 TMEM columns).
-// Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per block for all 32 planes
-// (N = 64) into columns 256..511; the slabs then start at stage y. Derivatives use the B-spline derivative
-// identity: d/du sum_a N_{a,p}(u) c_a =
-// sum_a N_{a,p-1}(u) q_a with q_a = p (c_{a+1} - c_a) / (t_{a+p+1} - t_{a+1}) on the knots
-// t_1 .. t_{C+p-1}. The four outputs are four independent chains of mode products on the control points
+// outside each band and for the samples past the sub-cube's end). n is at most 64 per axis. The output is
+// the row layout or the apron layout (MFA_DECODE_APRON). The stage-z operands (P and its differences) do
+// not depend on the slab and are built once per unit; the value chain carries P - m, m the mid-range of the
+// window, and the readout adds m back (the basis functions on the sub-cube sum to 1). One kernel per
+// precision; BF16 and FP16 keep no "lo" operands, which halves the shared memory and lets two CTAs share an
+// SM (2 x 256 TMEM columns). Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per
+// unit for all 32 planes (N = 64) into columns 256..511; the slabs then start at stage y. Derivatives use
+// the B-spline derivative identity: d/du sum_a N_{a,p}(u) c_a = sum_a N_{a,p-1}(u) q_a with
+// q_a = p (c_{a+1} - c_a) / (t_{a+p+1} - t_{a+1}) on the knots t_1 .. t_{C+p-1}. The four outputs are four independent chains of mode products on the control points
 // P and their FP32 differences DxP, DyP, DzP, taken before any rounding: every 16-bit operand is then a
 // weighted average of exact differences, and no product cancels against another.
 //   chain 0 (f):   P   x N_z x N_y x N_x          chain 1 (f_u): DxP x N_z x N_y       x N_x^(p-1)
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     // sub-cube
     const int nslab = (s_m[2] + kKS - 1) / kKS;
     const bool whole = s_g.n[0] == kN && s_g.n[1] == kN && s_g.n[2] == kN && s_m[0] == kN && s_m[1] == kN &&
-                       s_m[2] == kN && !(prm.flags & MFA_DECODE_APRON);
+                       s_m[2] == kN;
+    const bool apron = (prm.flags & MFA_DECODE_APRON) != 0;
 
     // ---- per unit: knots, basis bands of degree p and p-1, control windows, difference scales (unless
     //      kept), the window of P ----
@@ -569,14 +571,16 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
             for (int it = 0; it < 8; ++it) {
               const int rr = 4 * it + (lane >> 3), v = lane & 7;
               const int Rg = 128 * group + 32 * quarter + rr, i = 16 * h + 8 * half + v;
-              if (whole) {  // row (k, j) of the tile at (k0 + k) 32^2 + 32 j
-                __stcs(out + (k0 * kN * kN + Rg * kN + i), stg[rr * 8 + (v ^ (rr & 7))]);
+              if (whole) {  // row (k, j) of the tile at (k0 + k) 32^2 + 32 j, or with an apron at
+                            // ((k0 + k) 33 + j) apron_pitch(32)
+                constexpr int AP = apron_pitch(kN);
+                const int row = apron ? ((k0 + (Rg >> 5)) * (kN + 1) + (Rg & 31)) * AP : k0 * kN * kN + Rg * kN;
+                __stcs(out + (row + i), stg[rr * 8 + (v ^ (rr & 7))]);
               } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the sub-cube; with an apron in
                         // rows of apron_pitch(n_x) and planes of n_y + 1 rows
                 const int kl = k0 + (Rg >> 5), j = Rg & 31;
                 if (kl < s_m[2] && j < s_m[1] && i < s_m[0]) {
-                  const bool ap = (prm.flags & MFA_DECODE_APRON) != 0;
-                  const int rows = ap ? s_g.n[1] + 1 : s_g.n[1], pitch = ap ? apron_pitch(s_g.n[0]) : s_g.n[0];
+                  const int rows = apron ? s_g.n[1] + 1 : s_g.n[1], pitch = apron ? apron_pitch(s_g.n[0]) : s_g.n[0];
                   __stcs(out + (((s_w0[2] + kl) * rows + s_w0[1] + j) * pitch + s_w0[0] + i),
                          stg[rr * 8 + (v ^ (rr & 7))]);
                 }
