@@ -607,6 +607,7 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
     launches = ctx.launch_count() - n0
     samples = ctx.ray_samples(reset=True) / frames
     ms = [ev[f].elapsed_time(ev[f + 1]) for f in range(frames)]
+    last_fp32 = image.clone()  # the last frame's image, for the precision variants' image quality
     for g in graphs:
         g.close()
     # the same frames without the ray cast (ordering + decode only), for the per-stage split
@@ -669,6 +670,31 @@ def frames_record(layout="apron", frames=32, warmup=3, ctx=None, precisions=Fals
                               "hbm_frac": dec_b / (pms * 1e-3) / 1e9 / peaks_h,
                               "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
                               "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gmax)}
+            if prec != mfa.PREC_FP32:
+                # whole frames in this precision (graph replay: ordering, decode, brick table, fill, ray cast)
+                # and the last frame's image against the FP32 frame's (Sec. 5.2's MSE and PSNR)
+                from oracle import multires as omr
+                pg = [mfa.FrameGraph(ctx, blk, lst, cnt, cache, S, sort=True, table=table, brick_dims=(B, B, B),
+                                     brick_n=n, view=v, tf=tf, image=image, apron=apron, precision=prec)
+                      for v in views]
+                for f in range(3):
+                    lst.copy_(all_lists[f]); cnt.copy_(counts[f: f + 1]); pg[f].launch()
+                torch.cuda.synchronize()
+                fms = 0.0
+                for f in range(frames):
+                    lst.copy_(all_lists[f]); cnt.copy_(counts[f: f + 1])
+                    d0.record(stream)
+                    pg[f].launch()
+                    d1.record(stream)
+                    torch.cuda.synchronize()
+                    fms += d0.elapsed_time(d1)
+                for g2 in pg:
+                    g2.close()
+                if ctx.device_status():
+                    raise RuntimeError(f"device status after the {name} frames")
+                a, b2 = image.double().cpu().numpy(), last_fp32.double().cpu().numpy()
+                prec_rec[name].update({"frame_ms": fms / frames, "last_frame_vs_fp32": {
+                    "mse": omr.mse(a, b2), "psnr_db": omr.psnr(a, b2), "max_abs": float(np.abs(a - b2).max())}})
         prec_rec["split_vs_fp32_speedup"] = prec_rec["fp32"]["decode_ms_per_frame"] / \
             prec_rec["split_bf16"]["decode_ms_per_frame"]
         prec_rec["cpu_baseline"] = oracle_decode_baseline(

@@ -262,7 +262,9 @@ typedef struct {
  * m (the cache holds list_capacity slots of slot_stride_voxels float4). With MFA_FRAME_RAYCAST the
  * blocks are the bricks of a Bx*By*Bz volume (nblocks = Bx*By*Bz, brick id z-major) of brick_n^3
  * samples each; the graph rewrites d_brick_table (nblocks int32: list position or -1) and renders
- * into d_image as mfa_raycast does. */
+ * into d_image as mfa_raycast does. precision: MFA_PREC_* of the captured decode (0, a zeroed
+ * descriptor, is FP32); the tensor-core precisions take the row or the apron layout and the
+ * shapes mfa_decode_blocks gives them (otherwise creation returns MFA_ERR_UNSUPPORTED). */
 typedef struct {
   const mfa_block_desc* d_desc;
   int32_t nblocks;
@@ -285,6 +287,7 @@ typedef struct {
   const float* d_tf;
   int32_t tf_n;
   float* d_image;
+  int32_t precision;          /* MFA_PREC_* of the decode */
 } mfa_frame_desc;
 
 typedef struct mfa_frame_graph mfa_frame_graph;

@@ -128,6 +128,7 @@ int mfa_frame_graph_create(mfa_ctx* ctx, mfa_frame_graph** out, const mfa_frame_
   const bool cubes = (fd->flags & MFA_FRAME_CUBES) != 0;
   const bool apron = (fd->flags & MFA_FRAME_APRON) != 0;
   if (cubes && apron) return MFA_ERR_INVALID_ARG;
+  if (fd->precision < MFA_PREC_FP32 || fd->precision > MFA_PREC_SPLIT_BF16) return MFA_ERR_INVALID_ARG;
   if (rc && (!fd->d_brick_table || !fd->view || !fd->d_tf || !fd->d_image)) return MFA_ERR_INVALID_ARG;
   if (rc && (int64_t)fd->brick_dims[0] * fd->brick_dims[1] * fd->brick_dims[2] != fd->nblocks)
     return MFA_ERR_INVALID_ARG;
@@ -155,7 +156,7 @@ int mfa_frame_graph_create(mfa_ctx* ctx, mfa_frame_graph** out, const mfa_frame_
   if (status == MFA_OK)
     status = mfa_decode_blocks(ctx, fd->d_desc, fd->nblocks, fd->d_list, fd->list_capacity, fd->d_count,
                                fd->d_knots, fd->knots_len, fd->d_cps, fd->cps_len, fd->d_cache,
-                               fd->slot_stride_voxels, fd->list_capacity, &fd->bounds, MFA_PREC_FP32,
+                               fd->slot_stride_voxels, fd->list_capacity, &fd->bounds, fd->precision,
                                MFA_DECODE_LIST_SLOTS | (cubes ? MFA_DECODE_CUBES : 0u) | (apron ? MFA_DECODE_APRON : 0u), s);
   if (status == MFA_OK && rc) {
     brick_table_kernel<<<1, 1024, 0, s>>>(fd->d_list, fd->list_capacity, fd->d_count, fd->nblocks,

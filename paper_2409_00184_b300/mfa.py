@@ -52,7 +52,7 @@ class FrameDesc(ctypes.Structure):
                 ("d_cache", ctypes.c_void_p), ("slot_stride_voxels", ctypes.c_int64), ("bounds", Bounds),
                 ("flags", ctypes.c_uint32), ("d_brick_table", ctypes.c_void_p), ("brick_dims", ctypes.c_int32 * 3),
                 ("brick_n", ctypes.c_int32), ("view", ctypes.c_void_p), ("d_tf", ctypes.c_void_p),
-                ("tf_n", ctypes.c_int32), ("d_image", ctypes.c_void_p)]
+                ("tf_n", ctypes.c_int32), ("d_image", ctypes.c_void_p), ("precision", ctypes.c_int32)]
 
 
 FRAME_SORT_BY_COST, FRAME_RAYCAST, FRAME_CUBES, FRAME_APRON = 1, 2, 4, 8
@@ -622,7 +622,7 @@ class FrameGraph:
 
     def __init__(self, ctx, blocks, list_buf, count_buf, cache, slot_stride, sort=True,
                  table=None, brick_dims=None, brick_n=0, view=None, tf=None, image=None, cubes=False,
-                 apron=False):
+                 apron=False, precision=PREC_FP32):
         self.ctx = ctx
         self._keep = [blocks, list_buf, count_buf, cache, table, tf, image]
         cap = list_buf.numel()
@@ -636,6 +636,7 @@ class FrameGraph:
         fd.d_cps, fd.cps_len = _ptr(blocks.cps), blocks.cps.numel()
         fd.d_cache, fd.slot_stride_voxels = _ptr(cache), slot_stride
         fd.bounds = blocks.bounds
+        fd.precision = precision
         if view is not None:
             flags |= FRAME_RAYCAST
             _need(table, blocks.n, "table")
