@@ -171,8 +171,8 @@ int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream
  * with MFA_DECODE_VALUE_ONLY, at d_cache + (slot*slot_stride_voxels + voxel)*width.
  * d_cache must be 16-byte aligned. knots_len / cps_len are the array lengths (floats),
  * used for the range checks. precision: MFA_PREC_FP32 (any supported shape) or, on the tensor
- * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 (row or apron layout, no
- * VALUE_ONLY; otherwise MFA_ERR_UNSUPPORTED). The tensor-core decode takes a block in sub-cubes of 32
+ * cores, MFA_PREC_BF16 / MFA_PREC_FP16 / MFA_PREC_SPLIT_BF16 (row or apron layout, with or
+ * without VALUE_ONLY; the cube layout returns MFA_ERR_UNSUPPORTED). The tensor-core decode takes a block in sub-cubes of 32
  * samples per axis, or 16 on an axis with more than 16 control points; every sub-cube's samples
  * must have their nonzero basis functions within 16 consecutive control points per axis. That
  * holds for every block with at most 16 control points per axis, and for uniform knots with up

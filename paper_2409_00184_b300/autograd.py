@@ -21,26 +21,28 @@ from . import mfa
 
 
 class DecodeValue(torch.autograd.Function):
-    """f = decode_value(P) on each block's sample grid (slot-addressed, slot_stride floats per slot)."""
+    """f = decode_value(P) on each block's sample grid (slot-addressed, slot_stride floats per slot). The
+    forward decode and the backward adjoint run in `precision` (FP32 on the CUDA cores, or BF16 /
+    split-BF16 on the tensor cores, where the adjoint takes 32 samples and at most 16 control points)."""
 
     @staticmethod
-    def forward(fctx, cps, lib_ctx, blocks, slot_stride, nslots):
+    def forward(fctx, cps, lib_ctx, blocks, slot_stride, nslots, precision=mfa.PREC_FP32):
         out = torch.zeros(nslots * slot_stride, device=cps.device, dtype=torch.float32)
         mfa.decode_blocks(lib_ctx, blocks, out, slot_stride, nslots, flags=mfa.DECODE_VALUE_ONLY,
-                          cps=cps.contiguous())
-        fctx.lib = (lib_ctx, blocks, slot_stride, nslots)
+                          cps=cps.contiguous(), precision=precision)
+        fctx.lib = (lib_ctx, blocks, slot_stride, nslots, precision)
         return out
 
     @staticmethod
     def backward(fctx, grad_out):
-        lib_ctx, blocks, slot_stride, nslots = fctx.lib
+        lib_ctx, blocks, slot_stride, nslots, precision = fctx.lib
         grad = torch.empty(blocks.cps_len, device=grad_out.device, dtype=torch.float32)
-        mfa.adjoint_blocks(lib_ctx, blocks, grad_out.contiguous(), slot_stride, nslots, grad)
-        return grad, None, None, None, None
+        mfa.adjoint_blocks(lib_ctx, blocks, grad_out.contiguous(), slot_stride, nslots, grad, precision=precision)
+        return grad, None, None, None, None, None
 
 
-def decode_value(cps, lib_ctx, blocks, slot_stride, nslots):
-    return DecodeValue.apply(cps, lib_ctx, blocks, slot_stride, nslots)
+def decode_value(cps, lib_ctx, blocks, slot_stride, nslots, precision=mfa.PREC_FP32):
+    return DecodeValue.apply(cps, lib_ctx, blocks, slot_stride, nslots, precision)
 
 
 def block_ids(blocks, device="cuda"):

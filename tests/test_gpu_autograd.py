@@ -77,6 +77,37 @@ def test_fused_gradient_equals_autograd(mfa, ctx):
     assert float((G - P.grad).abs().max()) <= 1e-5 * float(P.grad.abs().max())
 
 
+@pytest.mark.parametrize("name", ["split", "bf16"])
+def test_autograd_tensor_core_precisions(mfa, ctx, name):
+    """decode_value with a tensor-core precision: the forward value-only decode and the backward adjoint both
+    on the tensor cores, against the oracle's decode and the oracle's adjoint of the oracle's residual.
+    Tolerances: the value as the decode's (split-BF16 1e-4, BF16 1e-2 of the value range); the gradient as
+    the sum of the decode's and the adjoint's (the residual carries the decode's error into the adjoint)."""
+    from paper_2409_00184_b300.autograd import decode_value
+    prec, tol = {"split": (mfa.PREC_SPLIT_BF16, 1e-4), "bf16": (mfa.PREC_BF16, 1e-2)}[name]
+    bs = synth.random_block_set(12, 503, ncp_choices=(6, 8, 12), nsamp_choices=(32,), degree_choices=(2, 3))
+    blk = mfa.DeviceBlocks(bs)
+    g = synth.rng(503)
+    D = torch.from_numpy(g.uniform(-1, 1, (len(bs), 32 ** 3)).astype(np.float32).ravel()).cuda()
+    P = blk.cps.clone().requires_grad_(True)
+    f = decode_value(P, ctx, blk, 32 ** 3, len(bs), precision=prec)
+    (0.5 * ((f - D) ** 2).sum()).backward()
+    assert ctx.device_status() == 0
+    fh, grad = f.detach().cpu().numpy().reshape(len(bs), -1), P.grad.cpu().numpy()
+    Dn = D.cpu().numpy().reshape(len(bs), 32, 32, 32).astype(np.float64)
+    vmax, gmax = 0.0, 0.0
+    for b in range(len(bs)):
+        kn, deg = bs.block_knots(b), bs.degree[b]
+        fo = odec.decode_block(bs.block_cps(b), kn, deg, bs.nsamp[b])[..., 0]
+        vmax = max(vmax, np.abs(fh[bs.slot[b]].reshape(32, 32, 32) - fo).max() / (fo.max() - fo.min()))
+        want = oadj.adjoint_block(fo - Dn[bs.slot[b]], kn, deg, bs.ncp[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = grad[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        gmax = max(gmax, np.abs(got - want).max() / np.abs(want).max())
+    print(f"{name} autograd: value {vmax:.2e}, gradient {gmax:.2e}")
+    assert vmax <= tol and gmax <= 2 * tol, (vmax, gmax)
+
+
 def test_gradient_descent_fit_config5(mfa, ctx):
     """256^3 Gaussian-mixture+noise field, 512 blocks of 32^3, degree 2, C in {8, 12, 16} by gradient-energy
     terciles; Nesterov gradient descent with per-block step 1/L until max|P - P_LS| / range(P_LS) <= 1e-5,

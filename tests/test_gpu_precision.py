@@ -81,11 +81,11 @@ def test_tensor_core_list_slots_and_shape_checks(mfa, ctx):
         ve, ge = rel_errors(c[m].reshape(32, 32, 32, 4), oracle_decode_set(bs, [b])[0])
         assert ve <= 1e-4 and max(ge) <= 1e-4
     assert np.all(np.isnan(c[2]))
-    # outside the tensor-core path: a value-only decode (host refusal), and a sub-cube whose samples' bands
-    # cover more than 16 control points (clustered knots: a per-block device flag, the other blocks decode)
+    # outside the tensor-core path: the cube layout (host refusal), and a sub-cube whose samples' bands cover
+    # more than 16 control points (clustered knots: a per-block device flag, the other blocks decode)
     with pytest.raises(mfa.MfaError) as e:
-        mfa.decode_blocks(ctx, blk, torch.zeros(3 * 32 ** 3, device="cuda"), 32 ** 3, 3,
-                          precision=mfa.PREC_BF16, flags=mfa.DECODE_VALUE_ONLY)
+        mfa.decode_blocks(ctx, blk, torch.zeros(3 * 32 ** 3 * 4, device="cuda"), 32 ** 3, 3,
+                          precision=mfa.PREC_BF16, flags=mfa.DECODE_CUBES)
     assert e.value.code == mfa.ERR_UNSUPPORTED
     C, p = 24, 2
     uni = synth.clamped_uniform_knots(C, p)
@@ -177,6 +177,26 @@ def test_tensor_core_decode_adaptive_ncp(mfa, ctx):
     ve, ge = rel_errors(got.reshape(len(bs), 32, 32, 32, 4), want)
     print(f"adaptive NCP split-BF16: value {ve:.2e}, gradient {max(ge):.2e}")
     assert ve <= TOL["split"] and max(ge) <= TOL["split"], (ve, ge)
+
+
+@pytest.mark.parametrize("apron", [False, True])
+def test_tensor_core_value_only(mfa, ctx, apron):
+    """MFA_DECODE_VALUE_ONLY on the tensor cores writes f alone (one float per voxel), equal bit for bit to the
+    f of the full decode, in the row and in the apron layout."""
+    bs = synth.random_block_set(10, 610, ncp_choices=(4, 12, 20), degree_choices=(2, 3), nsamp_choices=(16, 32, 40))
+    blk = mfa.DeviceBlocks(bs)
+    S = max(mfa.apron_voxels(int(v)) for v in bs.nsamp.max(axis=1)) if apron else blk.slot_voxels
+    base = mfa.DECODE_APRON if apron else 0
+    full = torch.full((blk.nslots * S * 4,), float("nan"), device="cuda")
+    val = torch.full((blk.nslots * S,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, full, S, blk.nslots, precision=mfa.PREC_SPLIT_BF16, flags=base)
+    mfa.decode_blocks(ctx, blk, val, S, blk.nslots, precision=mfa.PREC_SPLIT_BF16,
+                      flags=base | mfa.DECODE_VALUE_ONLY)
+    assert ctx.device_status() == 0
+    f4 = full.view(blk.nslots, S, 4)[..., 0].cpu().numpy()
+    v = val.view(blk.nslots, S).cpu().numpy()
+    assert np.array_equal(np.isnan(f4), np.isnan(v))
+    assert np.array_equal(f4[~np.isnan(f4)], v[~np.isnan(v)])
 
 
 def test_tensor_core_decode_config1(mfa, ctx):
