@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-frames", action="store_true", help="leave out the adaptive-NCP frames sub-record")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="leave out the per-precision decode sub-record (degree 3, 4096 blocks)")
     ap.add_argument("--layout", choices=["rows", "apron"], default="apron",
                     help="decoded-cache layout of the step: rows ([z][y][x] bricks of 32^3) or apron (slots of "
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
@@ -798,19 +800,14 @@ def run_gd(args):
     return 0
 
 
-def run_precision(args):
-    """Decode precision table: the 512^3 field of the default step at degree 3, 12^3 control points, decoded
-    by the FP32 banded kernel and by the tensor-core kernel in split-BF16, BF16 and FP16. Each variant is
-    timed over K launches (cache 2.15 GB, larger than L2) and checked against the FP64 oracle's decode of
-    the same FP32 control points on sampled voxels."""
+def precision_decode_record(ctx, nf, K, warmup):
+    """Config 4's decode per precision: the nf^3 Gaussian-mixture+noise field at degree 3 with 12^3 control
+    points (the library's least-squares fit), decoded by the FP32 banded kernel and by the tensor-core kernel
+    in split-BF16, BF16 and FP16, each timed over K launches and checked against the FP64 oracle's decode of
+    the same FP32 control points on sampled voxels. Returns the variants and what the caller reuses."""
     from oracle import decode as odec
     from paper_2409_00184_b300 import mfa
-    torch.cuda.set_device(0)
-    ctx = mfa.Context(0)
     seed, p = synth.BASE_SEED + 2, 3
-    nf = args.field
-    if nf < BRICK or nf % BRICK:
-        raise SystemExit("--field must be a positive multiple of 32")
     B, vox = (nf // BRICK) ** 3, BRICK ** 3
     field = synth.gm_noise_field(nf, seed, device="cuda")
     D = synth.blocks_from_field(field, BRICK).contiguous().view(-1)
@@ -835,14 +832,10 @@ def run_precision(args):
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     algo = B * (vox * 16 + NCP ** 3 * 4 + 72)
-    K = args.steps
     variants = {}
-    clocks = ClockSampler(0)
-    clocks.start()
-    n0 = ctx.launch_count()
     for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16),
                        ("fp16", mfa.PREC_FP16)):
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(3, warmup)):
             mfa.decode_blocks(ctx, blk, cache, vox, B, precision=prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -860,6 +853,31 @@ def run_precision(args):
                           "hbm_frac": algo / (ms * 1e-3) / 1e9 / hbm,
                           "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
                           "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm)}
+    return {"variants": variants, "split_vs_fp32_speedup": variants["fp32"]["ms"] / variants["split_bf16"]["ms"],
+            "bs": bs, "blk": blk, "plan": plan, "B": B, "vox": vox, "seed": seed, "hbm": hbm, "peak_src": peak_src,
+            "cache": cache}
+
+
+def run_precision(args):
+    """Decode precision table: the 512^3 field of the default step at degree 3, 12^3 control points, decoded
+    by the FP32 banded kernel and by the tensor-core kernel in split-BF16, BF16 and FP16. Each variant is
+    timed over K launches (cache 2.15 GB, larger than L2) and checked against the FP64 oracle's decode of
+    the same FP32 control points on sampled voxels."""
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    nf = args.field
+    if nf < BRICK or nf % BRICK:
+        raise SystemExit("--field must be a positive multiple of 32")
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    n0 = ctx.launch_count()
+    S = precision_decode_record(ctx, nf, K, args.warmup)
+    variants, bs, blk, plan = S["variants"], S["bs"], S["blk"], S["plan"]
+    B, vox, seed, hbm, peak_src = S["B"], S["vox"], S["seed"], S["hbm"], S["peak_src"]
+    del S["cache"]
     # the fit (without RMSE) and the adjoint of the same blocks in each precision: 4 B/voxel read + C^3 written
     D = synth.blocks_from_field(synth.gm_noise_field(nf, seed, device="cuda"), BRICK).contiguous().view(-1)
     R = torch.empty_like(D).uniform_(-1, 1, generator=torch.Generator(device="cuda").manual_seed(seed))
@@ -1431,6 +1449,19 @@ def main():
         torch.cuda.empty_cache()
         frames = frames_record(args.layout, 32, args.warmup, ctx)
 
+    precision = None
+    if rank == 0 and not args.no_precision:
+        # the decode of the same field at degree 3 in FP32, split-BF16, BF16 and FP16 (20 launches each)
+        torch.cuda.empty_cache()
+        S = precision_decode_record(ctx, N_FIELD, 20, args.warmup)
+        S["plan"].close()
+        precision = {"workload": "512^3 field, 4096 blocks of 32^3, degree 3, 12^3 control points; value+gradient "
+                                 "decode, 20 launches per precision; errors on 12 blocks x 400 voxels against the "
+                                 "FP64 oracle",
+                     "variants": S["variants"], "split_vs_fp32_speedup": S["split_vs_fp32_speedup"]}
+        del S
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": K,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -1440,7 +1471,7 @@ def main():
                                  "no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "frames": frames}
+                "gpu_launches": launches, "clocks": clk, "frames": frames, "precision": precision}
         print(json.dumps(line))
     ctx.close()
     if ws > 1:

@@ -544,17 +544,29 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       }
       wait_mma();
       if (timed_out) break;
+      if (prm.flags & MFA_DECODE_VALUE_ONLY) {
+        // value only (one float per voxel): each lane writes f of its row (k, j), voxel row
+        // (w0_z + k0 + k, w0_y + j), for the 16 voxels of each column half inside the sub-cube
+        float* outf = prm.cache + (int64_t)s_g.slot * prm.slot_stride;
+        const int Rg = 128 * group + 32 * quarter + lane, kl = k0 + (Rg >> 5), j = Rg & 31;
+        const int rows = apron ? s_g.n[1] + 1 : s_g.n[1], pitch = apron ? apron_pitch(s_g.n[0]) : s_g.n[0];
+        float* row = outf + ((int64_t)(s_w0[2] + kl) * rows + s_w0[1] + j) * pitch + s_w0[0];
+        for (int h = 0; h < 2; ++h) {
+          uint32_t f[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 128 * group + 16 * h, f);
+          tmem_ld_wait();
+          if (kl < s_m[2] && j < s_m[1]) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (16 * h + q < s_m[0]) __stcs(row + 16 * h + q, __uint_as_float(f[q]) + s_mid);
+          }
+        }
+      } else
       // readout x: warp group g takes tile g; each warp stages its 32 rows, 8 voxels at a time, and writes
       // the voxels inside the sub-cube: row (k, j) of the tile is voxel row (w0_z + k0 + k, w0_y + j)
       {
         float4* stg = reinterpret_cast<float4*>(sm + L::R1 + warp * 32 * 128);
-        // (f, f_u, f_v, f_w) per voxel, or f alone with MFA_DECODE_VALUE_ONLY
-        const bool vo = (prm.flags & MFA_DECODE_VALUE_ONLY) != 0;
-        float* outv = prm.cache + (int64_t)s_g.slot * prm.slot_stride * (vo ? 1 : 4);
-        auto put_voxel = [&](int64_t voxel, float4 x) {
-          if (vo) __stcs(outv + voxel, x.x);
-          else __stcs(reinterpret_cast<float4*>(outv) + voxel, x);
-        };
+        float4* out = reinterpret_cast<float4*>(prm.cache) + (int64_t)s_g.slot * prm.slot_stride;
 
         for (int h = 0; h < 2; ++h) {
           uint32_t f[16], fu[16], fv[16], fw[16];
@@ -581,13 +593,14 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
                             // ((k0 + k) 33 + j) apron_pitch(32)
                 constexpr int AP = apron_pitch(kN);
                 const int row = apron ? ((k0 + (Rg >> 5)) * (kN + 1) + (Rg & 31)) * AP : k0 * kN * kN + Rg * kN;
-                put_voxel(row + i, stg[rr * 8 + (v ^ (rr & 7))]);
+                __stcs(out + (row + i), stg[rr * 8 + (v ^ (rr & 7))]);
               } else {  // voxel (w0_z + k0 + k, w0_y + j, w0_x + i) when inside the sub-cube; with an apron in
                         // rows of apron_pitch(n_x) and planes of n_y + 1 rows
                 const int kl = k0 + (Rg >> 5), j = Rg & 31;
                 if (kl < s_m[2] && j < s_m[1] && i < s_m[0]) {
                   const int rows = apron ? s_g.n[1] + 1 : s_g.n[1], pitch = apron ? apron_pitch(s_g.n[0]) : s_g.n[0];
-                  put_voxel(((s_w0[2] + kl) * rows + s_w0[1] + j) * pitch + s_w0[0] + i, stg[rr * 8 + (v ^ (rr & 7))]);
+                  __stcs(out + (((s_w0[2] + kl) * rows + s_w0[1] + j) * pitch + s_w0[0] + i),
+                         stg[rr * 8 + (v ^ (rr & 7))]);
                 }
               }
             }
