@@ -118,6 +118,11 @@ typedef struct mfa_ctx mfa_ctx;
 int  mfa_ctx_create(mfa_ctx** out, int device);
 void mfa_ctx_destroy(mfa_ctx* ctx);
 const char* mfa_status_string(int status);
+/* Sizes in bytes of the structs this header declares, for bindings that mirror them:
+ * out[0] mfa_block_desc, out[1] mfa_bounds, out[2] mfa_decode_tiling, out[3] mfa_view,
+ * out[4] mfa_frame_desc. Writes the first min(n, 5) of them (none when out is NULL) and returns
+ * 5, the number of structs. Host only: needs no device and no context. */
+int mfa_abi_struct_sizes(int32_t* out, int32_t n);
 
 /* Synchronise `stream`, copy the device status word to *status and, if `clear`, reset
  * it to 0. Returns MFA_OK, or MFA_ERR_CUDA if the stream reported an error. */

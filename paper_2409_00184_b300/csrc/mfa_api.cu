@@ -64,6 +64,14 @@ void mfa_ctx_destroy(mfa_ctx* ctx) {
   delete ctx;
 }
 
+int mfa_abi_struct_sizes(int32_t* out, int32_t n) {
+  const int32_t sizes[5] = {(int32_t)sizeof(mfa_block_desc), (int32_t)sizeof(mfa_bounds),
+                            (int32_t)sizeof(mfa_decode_tiling), (int32_t)sizeof(mfa_view),
+                            (int32_t)sizeof(mfa_frame_desc)};
+  for (int32_t i = 0; out && i < n && i < 5; ++i) out[i] = sizes[i];
+  return 5;
+}
+
 const char* mfa_status_string(int status) {
   switch (status) {
     case MFA_OK: return "ok";

@@ -62,7 +62,7 @@ DESC_DTYPE = np.dtype({"names": ["degree", "ncp", "nsamp", "slot", "knot_off", "
                        "offsets": [0, 12, 24, 36, 40, 64], "itemsize": 72})
 assert ctypes.sizeof(BlockDesc) == DESC_DTYPE.itemsize == 72
 
-SYMBOLS = ["mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
+SYMBOLS = ["mfa_abi_struct_sizes", "mfa_ctx_create", "mfa_ctx_destroy", "mfa_status_string", "mfa_ctx_device_status",
            "mfa_ctx_launch_count", "mfa_model_bytes", "mfa_decode_blocks", "mfa_basis_tables",
            "mfa_adjoint_blocks", "mfa_encode_plan_create", "mfa_encode_plan_destroy", "mfa_encode_blocks",
            "mfa_raycast", "mfa_ctx_set_decode_tiling", "mfa_ctx_get_decode_tiling", "mfa_encode_blocks_noalloc",
@@ -84,6 +84,7 @@ def _load():
         "mfa_ctx_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int]),
         "mfa_ctx_destroy": (None, [P]),
         "mfa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mfa_abi_struct_sizes": (ctypes.c_int, [P, I32]),
         "mfa_ctx_device_status": (ctypes.c_int, [P, ctypes.POINTER(U32), ctypes.c_int, P]),
         "mfa_ctx_launch_count": (I64, [P]),
         "mfa_ctx_set_decode_tiling": (ctypes.c_int, [P, ctypes.POINTER(Bounds), ctypes.POINTER(DecodeTiling)]),
@@ -138,6 +139,15 @@ def _load():
 
 
 lib = _load()
+
+
+def abi_struct_sizes():
+    """mfa_abi_struct_sizes: the C sizes of mfa_block_desc, mfa_bounds, mfa_decode_tiling, mfa_view and
+    mfa_frame_desc, in that order (host only)."""
+    n = lib.mfa_abi_struct_sizes(None, 0)
+    out = (ctypes.c_int32 * n)()
+    lib.mfa_abi_struct_sizes(ctypes.cast(out, ctypes.c_void_p), n)
+    return list(out)
 
 
 class MfaError(RuntimeError):

@@ -45,3 +45,12 @@ def test_model_bytes_eq2_golden():
     for ncp, deg, size in rows:
         assert mfa.model_bytes(int(ncp), int(deg)) == size
     assert mfa.model_bytes(0, 2) == -1
+
+
+def test_struct_mirrors_match_the_library():
+    """The ctypes structs of the binding have the sizes the library was compiled with (a field added to a
+    C struct without its mirror, or the other way round, fails here)."""
+    import ctypes
+    from paper_2409_00184_b300 import mfa
+    want = [ctypes.sizeof(t) for t in (mfa.BlockDesc, mfa.Bounds, mfa.DecodeTiling, mfa.View, mfa.FrameDesc)]
+    assert mfa.abi_struct_sizes() == want
