@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   __shared__ int s_key_ok;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_pbar;  // the bulk copy of a unit's control points
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, group = warp >> 2;
   float* P = reinterpret_cast<float*>(sm + L::R1);
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   }
   if (tid == 0) {
     mbar_init(&s_bar, 1);
+    mbar_init(&s_pbar, 1);
     fence_mbar_init();
     s_key_ok = 0;
   }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t sbase = smem_addr(sm);
-  uint32_t phase = 0;
+  uint32_t phase = 0, pphase = 0;
   bool timed_out = false;
 
   int count = prm.list ? (prm.count ? *prm.count : prm.list_len) : prm.nblocks;
@@ -363,17 +365,49 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
         put<PREC>(sm + L::Bz + which * kOp64, kmajor_off(n, c, kLBO, kSBO), L::dBz, v);
       }
     }  // !same
-    {  // the window of P: local (c, b, a) at (16 c + b) 16 + a, control (c0_z + c, c0_y + b, c0_x + a)
+    {  // the window of P, control (c0_z + c, c0_y + b, c0_x + a) at Pw[c sz + b sy + a]
     const int x0 = s_c0[0], y0 = s_c0[1], z0 = s_c0[2];
     const int Wx = min(kK, Cx - x0), Wy = min(kK, Cy - y0), Wz = min(kK, Cz - z0);
+    // The block's control points arrive by one bulk copy (TMA) when the copy, widened to 16-byte boundaries,
+    // fits the P area and stays inside the control-point array; then Pw has the block's own strides. Else the
+    // threads load the window into a dense 16 x 16 x 16 box.
+    const int64_t b0 = s_g.cp_off * 4, e0 = (s_g.cp_off + (int64_t)Cx * Cy * Cz) * 4;
+    const int64_t a0 = b0 & ~int64_t(15), a1 = (e0 + 15) & ~int64_t(15);
+    const bool bulk = (reinterpret_cast<uintptr_t>(prm.cps) & 15) == 0 && a1 - a0 <= kPBytes && a1 <= prm.cps_len * 4;
+    const int sy = bulk ? Cx : kK, sz = bulk ? Cx * Cy : kK * kK;
+    const float* Pw = bulk ? P + (b0 - a0) / 4 + ((int64_t)z0 * Cy + y0) * Cx + x0 : P;
     float lo = __int_as_float(0x7f800000), hi = -lo;
-    for (int e = tid; e < kK * kK * kK; e += kThreadsTC) {
-      const int c = e >> 8, b = (e >> 4) & 15, a = e & 15;
-      if (a < Wx && b < Wy && c < Wz) {
-        const float v = __ldg(prm.cps + s_g.cp_off + ((z0 + c) * Cy + y0 + b) * Cx + x0 + a);
-        P[e] = v;
-        lo = fminf(lo, v);
-        hi = fmaxf(hi, v);
+    if (bulk) {
+      if (tid == 0) {
+        fence_async_smem();  // the threads' earlier accesses to the P area come before the copy's writes
+        mbar_arrive_expect_tx(&s_pbar, (uint32_t)(a1 - a0));
+        bulk_load(P, reinterpret_cast<const unsigned char*>(prm.cps) + a0, (uint32_t)(a1 - a0), &s_pbar);
+      }
+      const bool ok = mbar_wait_bounded(&s_pbar, pphase);
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        if (tid == 0) flag(prm.status, MFA_DEV_TIMEOUT);
+        mbar_wait_bounded(&s_pbar, pphase);  // a second bounded wait for the copy still in flight
+        break;
+      }
+      pphase ^= 1;
+      for (int e = tid; e < kK * kK * kK; e += kThreadsTC) {
+        const int c = e >> 8, b = (e >> 4) & 15, a = e & 15;
+        if (a < Wx && b < Wy && c < Wz) {
+          const float v = Pw[c * sz + b * sy + a];
+          lo = fminf(lo, v);
+          hi = fmaxf(hi, v);
+        }
+      }
+    } else {
+      for (int e = tid; e < kK * kK * kK; e += kThreadsTC) {
+        const int c = e >> 8, b = (e >> 4) & 15, a = e & 15;
+        if (a < Wx && b < Wy && c < Wz) {
+          const float v = __ldg(prm.cps + s_g.cp_off + ((z0 + c) * Cy + y0 + b) * Cx + x0 + a);
+          P[e] = v;
+          lo = fminf(lo, v);
+          hi = fmaxf(hi, v);
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -398,12 +432,12 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
       for (int h = 0; h < 2; ++h) {
         const int c = c0 + h;
         if (a < Wx && b < Wy && c < Wz) {
-          const int idx = (c * kK + b) * kK + a;
-          const float p0 = P[idx];
+          const int idx = c * sz + b * sy + a;
+          const float p0 = Pw[idx];
           v0[h] = p0 - mid;
-          if (a + 1 < Wx) vu[h] = dsc[x0 + a] * (P[idx + 1] - p0);
-          if (b + 1 < Wy) vv[h] = dsc[kN + y0 + b] * (P[idx + kK] - p0);
-          if (c + 1 < Wz) vw[h] = dsc[2 * kN + z0 + c] * (P[idx + kK * kK] - p0);
+          if (a + 1 < Wx) vu[h] = dsc[x0 + a] * (Pw[idx + 1] - p0);
+          if (b + 1 < Wy) vv[h] = dsc[kN + y0 + b] * (Pw[idx + sy] - p0);
+          if (c + 1 < Wz) vw[h] = dsc[2 * kN + z0 + c] * (Pw[idx + sz] - p0);
         }
       }
       const uint32_t off = kmajor_off(R, c0, kLBO, kSBO);

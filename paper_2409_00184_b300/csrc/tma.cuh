@@ -78,4 +78,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 1-D bulk copy (TMA) of `bytes` from global `src` to shared `dst`, completing on `bar`; both addresses
+// 16-byte aligned and `bytes` a multiple of 16. The issuing thread arms `bar` with mbar_arrive_expect_tx.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 }  // namespace mfa
