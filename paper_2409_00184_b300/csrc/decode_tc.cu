@@ -369,11 +369,11 @@ __global__ void __launch_bounds__(kThreadsTC, PREC == kSplit ? 1 : 2) decode_tc_
     const int x0 = s_c0[0], y0 = s_c0[1], z0 = s_c0[2];
     const int Wx = min(kK, Cx - x0), Wy = min(kK, Cy - y0), Wz = min(kK, Cz - z0);
     // The block's control points arrive by one bulk copy (TMA) when the copy, widened to 16-byte boundaries,
-    // fits the P area and stays inside the control-point array; then Pw has the block's own strides. Else the
-    // threads load the window into a dense 16 x 16 x 16 box.
+    // fits the R1 area (free until the stage-x operand is written) and stays inside the control-point array;
+    // then Pw has the block's own strides. Else the threads load the window into a dense 16 x 16 x 16 box.
     const int64_t b0 = s_g.cp_off * 4, e0 = (s_g.cp_off + (int64_t)Cx * Cy * Cz) * 4;
     const int64_t a0 = b0 & ~int64_t(15), a1 = (e0 + 15) & ~int64_t(15);
-    const bool bulk = (reinterpret_cast<uintptr_t>(prm.cps) & 15) == 0 && a1 - a0 <= kPBytes && a1 <= prm.cps_len * 4;
+    const bool bulk = (reinterpret_cast<uintptr_t>(prm.cps) & 15) == 0 && a1 - a0 <= L::R1Bytes && a1 <= prm.cps_len * 4;
     const int sy = bulk ? Cx : kK, sz = bulk ? Cx * Cy : kK * kK;
     const float* Pw = bulk ? P + (b0 - a0) / 4 + ((int64_t)z0 * Cy + y0) * Cx + x0 : P;
     float lo = __int_as_float(0x7f800000), hi = -lo;
