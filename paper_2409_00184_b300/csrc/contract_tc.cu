@@ -125,6 +125,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
   __shared__ TcGeom s_g;
   __shared__ float s_kn[3][kKnotMax];
   __shared__ int s_bad;
+  // the key of the B operands in shared memory (fit: the three axis classes; adjoint: knots, degrees and
+  // control-point counts); a block with the same key keeps them
+  __shared__ int64_t s_bkey[9];
+  __shared__ int s_bkey_ok, s_bsame;
   __shared__ float s_lo[kTcThreads / 32], s_hi[kTcThreads / 32];  // fit: per warp, least and greatest sample
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
+    s_bkey_ok = 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -202,11 +207,33 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
         flag(prm.status, bad);
       }
       s_bad = 0;
+      if (s_g.ok) {
+        int64_t key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+          if (prm.mode == kFit) {
+            key[a] = s_g.cls[a];
+          } else {
+            key[a] = s_g.koff[a];
+            key[3 + a] = s_g.p[a];
+            key[6 + a] = s_g.C[a];
+          }
+        }
+        bool same = s_bkey_ok;
+        for (int q = 0; q < 9; ++q) same = same && s_bkey[q] == key[q];
+        s_bsame = same;
+        if (!same) {
+          for (int q = 0; q < 9; ++q) s_bkey[q] = key[q];
+          s_bkey_ok = 0;  // valid once this block's operands are built and its knots checked
+        }
+      }
     }
     __syncthreads();
     if (!s_g.ok || timed_out) break;
     const TcGeom& g = s_g;
-    // ---- B operands: B_a[c][i] = A_a[i][c] for c < C_a, else 0 ----
+    // ---- B operands: B_a[c][i] = A_a[i][c] for c < C_a, else 0 (kept from the previous block when its key
+    //      is the same) ----
+    const bool bsame = s_bsame;
+    if (!bsame) {
     if (prm.mode == kAdjoint) {
       if (tid < 3 * kKnotMax) {
         const int a = tid / kKnotMax, i = tid - a * kKnotMax;
@@ -245,10 +272,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) contract_tc_kernel(ContractPara
       }
       put_one<SPLIT>(sm, kB + a * 2 * kBLo + off32(c, i), kBLo, v);
     }
+    }  // !bsame
     if (prm.mode == kAdjoint && s_bad) {  // (s_bad is read after the barriers above)
       __syncthreads();
       continue;
     }
+    if (tid == 0 && !bsame) s_bkey_ok = 1;  // read by the next block's fetch, after this block's barriers
     // ---- stage x: four batches of 8 planes (256 rows of 32 samples) through the operand region ----
     // Each batch is loaded in two rounds of kF4Round float4 per thread; the first round of the next batch is
     // in flight while the current batch's MMAs run. The fit contracts X - m, m the mid-range of the first
