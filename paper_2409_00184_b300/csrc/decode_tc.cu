@@ -9,9 +9,12 @@
 // clustered knots, sets MFA_DEV_BAD_DESC for that sub-cube). So every MMA has K = 16 (the window, padded);
 // every index is padded to 16 control points and 32 samples, and basis rows are written densely (zero
 // outside each band and for the samples past the sub-cube's end). n is at most 64 per axis. The output is
-// the row layout or the apron layout (MFA_DECODE_APRON). The stage-z operands (P and its differences) do
-// not depend on the slab and are built once per unit; the value chain carries P - m, m the mid-range of the
-// window, and the readout adds m back (the basis functions on the sub-cube sum to 1). One kernel per
+// the row layout or the apron layout (MFA_DECODE_APRON), with or without the gradient. A block's control
+// points arrive by one 1-D bulk copy (TMA) on an mbarrier when the copy, widened to 16-byte boundaries, fits
+// the free operand area and stays inside the control-point array; else the threads load the window. The
+// stage-z operands (P and its differences) do not depend on the slab and are built once per unit; the value
+// chain carries P - m, m the mid-range of the window, and the readout adds m back (the basis functions on
+// the sub-cube sum to 1). One kernel per
 // precision; BF16 and FP16 keep no "lo" operands, which halves the shared memory and lets two CTAs share an
 // SM (2 x 256 TMEM columns). Split-BF16 (one CTA per SM) holds all 512 columns and runs stage z once per
 // unit for all 32 planes (N = 64) into columns 256..511; the slabs then start at stage y. Derivatives use
