@@ -12,7 +12,9 @@
 // share of a batch (coalesced 16-byte loads), splits it into BF16 hi (and lo) parts and writes the stage-x A
 // operand. Stage outputs are read from tensor memory, split again and written transposed as the next stage's
 // A operand (stage y in two halves of 16 planes); the B operands (the three A_a^T, zero beyond C) are built
-// per block. One 32 KB operand region serves every A operand in turn, and a CTA (one warpgroup) holds 128
+// per block, or kept when the previous block of the CTA had the same axis classes (fit) or knots, degrees and
+// control-point counts (adjoint). The fit contracts the samples minus the mid-range of the block's first load
+// round and adds it back to the control points (the fit reproduces constants). One 32 KB operand region serves every A operand in turn, and a CTA (one warpgroup) holds 128
 // tensor-memory columns, so four CTAs share an SM and one's loads and conversions overlap the others' MMAs.
 // One thread issues the MMAs; completion is an mbarrier armed by tcgen05.commit and waited on with a
 // bounded poll that reports MFA_DEV_TIMEOUT.
