@@ -826,7 +826,7 @@ def run_gd(args):
 
 
 def precision_decode_record(ctx, nf, K, warmup):
-    """Config 4's decode per precision: the nf^3 Gaussian-mixture+noise field at degree 3 with 12^3 control
+    """The degree-3 decode per precision: the nf^3 Gaussian-mixture+noise field at degree 3 with 12^3 control
     points (the library's least-squares fit), decoded by the FP32 banded kernel and by the tensor-core kernel
     in split-BF16, BF16 and FP16, each timed over K launches and checked against the FP64 oracle's decode of
     the same FP32 control points on sampled voxels. Returns the variants and what the caller reuses."""

@@ -236,7 +236,7 @@ def marschner_lobb(x, y, z, f_m=6.0, alpha=0.05):
 
 
 def gm_params_field_at(points, seed):
-    """Gaussian-mixture value at arbitrary points (M, 3) in [0, 1]^3, numpy FP64 (config-1 control points)."""
+    """Gaussian-mixture value at arbitrary points (M, 3) in [0, 1]^3, numpy FP64 (the single-block control points)."""
     centers, sigmas, amps = gaussian_mixture_params(seed)
     p = np.asarray(points, dtype=np.float64)
     out = np.zeros(len(p))

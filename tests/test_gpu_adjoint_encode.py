@@ -102,7 +102,7 @@ def test_encode_matches_oracle_least_squares(mfa, ctx, seed, nonuniform):
         assert abs(rm[b] - want_rmse) <= 1e-5 * (Db.max() - Db.min()), (b, rm[b], want_rmse)
 
 
-def test_encode_config2_reduced(mfa, ctx):
+def test_encode_gm_128cubed_c12_degree2(mfa, ctx):
     bs, blocks = gm_blocks_fitted(128, 32, 12, 2, synth.BASE_SEED + 2)
     D = blocks.reshape(len(bs), -1)
     P, rm = _encode(mfa, ctx, bs, D, 32 ** 3)

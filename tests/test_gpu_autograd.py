@@ -108,7 +108,7 @@ def test_autograd_tensor_core_precisions(mfa, ctx, name):
     assert vmax <= tol and gmax <= 2 * tol, (vmax, gmax)
 
 
-def test_gradient_descent_fit_config5(mfa, ctx):
+def test_gradient_descent_fit_256cubed_512_blocks(mfa, ctx):
     """256^3 Gaussian-mixture+noise field, 512 blocks of 32^3, degree 2, C in {8, 12, 16} by gradient-energy
     terciles; Nesterov gradient descent with per-block step 1/L until max|P - P_LS| / range(P_LS) <= 1e-5,
     P_LS the FP64 oracle's least-squares solution, within 2000 steps."""

@@ -3,7 +3,7 @@
 mfa_adjoint_blocks and mfa_encode_blocks_ex with MFA_PREC_SPLIT_BF16 / MFA_PREC_BF16: 32 samples and at most
 16 control points per axis. Tolerances (relative to the largest |output| for the adjoint, to the range of
 the control points for the fit): split-BF16 1e-4, BF16 1e-2 (adjoint) and 5e-2 (fit). Also: gradient descent with the split-BF16
-gradient reaches 1e-4 of the FP64 least-squares solve (config 5's BF16-split variant).
+gradient reaches 1e-4 of the FP64 least-squares solve (256^3 field, 512 blocks, C in {8, 12, 16}).
 """
 
 import numpy as np
@@ -153,8 +153,8 @@ def test_tc_adjoint_skips_a_block_of_another_shape(mfa, ctx):
         assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
 
 
-def test_gradient_descent_split_bf16_config5(mfa, ctx):
-    """Config 5's BF16-split variant: 256^3 field, 512 blocks of 32^3, C in {8, 12, 16} by gradient-energy
+def test_gradient_descent_split_bf16_256cubed_512_blocks(mfa, ctx):
+    """Split-BF16 gradient descent on the 256^3 field, 512 blocks of 32^3, C in {8, 12, 16} by gradient-energy
     terciles; Nesterov descent with the split-BF16 tensor-core adjoint until max|P - P_LS| / range(P_LS) <= 1e-4
     (P_LS the FP64 oracle's least-squares solution)."""
     from paper_2409_00184_b300.autograd import fit_gradient_descent

@@ -80,7 +80,7 @@ def test_value_only(mfa, ctx):
         assert np.abs(f - w).max() / max(w.max() - w.min(), 1e-30) <= TOL_FP32
 
 
-def test_config1_single_block(mfa, ctx):
+def test_single_block_16cp_on_64cubed(mfa, ctx):
     """One degree-2 block, 16^3 clamped uniform control points = Gaussian mixture at the Greville points,
     decoded on a 64^3 grid; compared voxel by voxel."""
     p, C, n = 2, 16, 64
@@ -95,8 +95,8 @@ def test_config1_single_block(mfa, ctx):
     assert ve <= TOL_FP32 and max(ge) <= TOL_FP32, (ve, ge)
 
 
-def test_config2_reduced(mfa, ctx):
-    """Config-2 recipe at 128^3 (64 blocks of 32^3, C = 12, degree 2, oracle least-squares control points)."""
+def test_gm_128cubed_c12_degree2(mfa, ctx):
+    """The 512^3 Gaussian-mixture recipe reduced to 128^3 (64 blocks of 32^3, C = 12, degree 2, oracle least-squares control points)."""
     bs, _ = gm_blocks_fitted(128, 32, 12, 2, synth.BASE_SEED + 2)
     cache = _decode(mfa, ctx, bs)
     want = oracle_decode_set(bs)
@@ -105,8 +105,8 @@ def test_config2_reduced(mfa, ctx):
     assert ve <= TOL_FP32 and max(ge) <= TOL_FP32, (ve, ge)
 
 
-def test_config2_full_size_sampled(mfa, ctx):
-    """Full 512^3 config-2 batch (4096 blocks) decoded in one launch; 96 blocks x 400 voxels checked."""
+def test_gm_512cubed_4096_blocks_sampled(mfa, ctx):
+    """The full 512^3 batch (4096 blocks of 32^3, C = 12, degree 2) decoded in one launch; 96 blocks x 400 voxels checked."""
     bs, _ = gm_blocks_fitted(512, 32, 12, 2, synth.BASE_SEED + 2, device="cuda")
     blk = mfa.DeviceBlocks(bs)
     cache = torch.empty(blk.nslots * blk.slot_voxels * 4, device="cuda")

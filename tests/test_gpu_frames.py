@@ -48,7 +48,7 @@ def _frame_buffers(capacity, nblocks, n, img, device="cuda"):
             torch.zeros(img[1], img[0], 4, device=device))
 
 
-def test_frames_reduced_config3(mfa, ctx):
+def test_frames_flame_128cubed(mfa, ctx):
     """128^3 flame field, 512 bricks of 16^3, C in {4, 6, 8, 12}; two orbit frames through one graph."""
     N, n, p = 128, 16, 2
     bs, B = flame_blockset(N, n, (4, 6, 8, 12), (50, 75, 90), p, synth.BASE_SEED + 3, "cpu")
@@ -94,7 +94,7 @@ def test_frames_reduced_config3(mfa, ctx):
 
 @pytest.mark.parametrize("apron", [False, True])
 def test_frame_graph_tensor_core_precisions(mfa, ctx, apron):
-    """One reduced config-3 frame (128^3 flame field, 512 bricks of 16^3, C in {4, 6, 8, 12}) through frame
+    """One frame of the flame workload reduced to 128^3 (128^3 flame field, 512 bricks of 16^3, C in {4, 6, 8, 12}) through frame
     graphs that decode in split-BF16 and in BF16, against the oracle's Algorithm 4 over its own decode. A
     value error d (relative to the value range) moves a sample's transfer-function entry, and the composite
     weights sum to at most 1, so a pixel moves by about 4 d at most (the steepest opacity bump of the transfer
@@ -136,7 +136,7 @@ def test_frame_graph_tensor_core_precisions(mfa, ctx, apron):
         assert d.max() <= (1e-2 if name == "split" else 1e-1) and (d <= tol).mean() >= share, (name, d.max())
 
 
-def test_frames_full_config3_sampled(mfa, ctx):
+def test_frames_flame_1024cubed_sampled(mfa, ctx):
     """1024^3 flame field, 32768 bricks of 32^3, C in {4..24} by gradient energy, ~6000 visible per frame."""
     N, n, p = 1024, 32, 2
     bs, B = flame_blockset(N, n, synth.FLAME_NCP_CLASSES, synth.FLAME_NCP_PERCENTILES, p, synth.BASE_SEED + 3, "cuda")
@@ -171,7 +171,7 @@ def test_frames_full_config3_sampled(mfa, ctx):
     g.close()
 
 
-def test_frame_full_config3_raycast_sampled_pixels(mfa, ctx):
+def test_frame_flame_1024cubed_raycast_sampled_pixels(mfa, ctx):
     """One frame of the adaptive-NCP workload as it is benchmarked: 1024^3 flame field, 32768 bricks with C in
     {4..24}, ~6600 visible, cost-ordered decode into the apron layout, brick table, apron fill and 1024^2 ray
     cast (O_max = 0.99) replayed from the frame graph; 2000 seeded pixels against the oracle's Algorithm 4
@@ -208,7 +208,7 @@ def test_frame_full_config3_raycast_sampled_pixels(mfa, ctx):
     pix = synth.rng(72).choice(view["width"] * view["height"], 2000, replace=False)
     want = ocast.raycast(voxels, tab.reshape(B, B, B), n, view, tf, pixels=pix)
     d = np.abs(got[pix] - want).max(axis=-1)
-    print(f"config-3 frame, {len(vis)} visible, 2000 pixels: max {d.max():.2e}, within 1e-4: {(d <= 1e-4).mean():.4f},"
+    print(f"1024^3 flame frame, {len(vis)} visible, 2000 pixels: max {d.max():.2e}, within 1e-4: {(d <= 1e-4).mean():.4f},"
           f" lit: {(want[:, 3] > 0).mean():.3f}")
     assert (want[:, 3] > 0).mean() > 0.3
     assert d.max() <= 1e-2 and (d <= 1e-4).mean() >= 0.999

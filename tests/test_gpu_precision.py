@@ -199,8 +199,8 @@ def test_tensor_core_value_only(mfa, ctx, apron):
     assert np.array_equal(f4[~np.isnan(f4)], v[~np.isnan(v)])
 
 
-def test_tensor_core_decode_config1(mfa, ctx):
-    """Config 1 on the tensor cores: one block of 16^3 control points (degree 2, Gaussian-mixture samples)
+def test_tensor_core_decode_single_block_16cp_on_64cubed(mfa, ctx):
+    """On the tensor cores: one block of 16^3 control points (degree 2, Gaussian-mixture samples)
     decoded on a 64^3 grid in split-BF16 (eight 32^3 sub-cubes), every voxel against the oracle."""
     C, p, n = 16, 2, 64
     g = synth.rng(synth.BASE_SEED + 1)
@@ -210,12 +210,12 @@ def test_tensor_core_decode_config1(mfa, ctx):
     got = _decode(mfa, ctx, bs, mfa.PREC_SPLIT_BF16)
     assert ctx.device_status() == 0
     ve, ge = rel_errors(got[0].reshape(n, n, n, 4), oracle_decode_set(bs)[0])
-    print(f"config 1 split-BF16: value {ve:.2e}, gradient {max(ge):.2e}")
+    print(f"one 16^3-control-point block, split-BF16: value {ve:.2e}, gradient {max(ge):.2e}")
     assert ve <= TOL["split"] and max(ge) <= TOL["split"], (ve, ge)
 
 
-def test_config4_full_size_sampled(mfa, ctx):
-    """Config 4: the 512^3 batch (4096 blocks, 12^3 control points) at degree 3, every precision, sampled
+def test_degree3_512cubed_4096_blocks_sampled(mfa, ctx):
+    """The degree-3 512^3 batch (4096 blocks, 12^3 control points) at degree 3, every precision, sampled
     voxels against the oracle; prints max and RMS error of value and gradient per variant."""
     bs, _ = gm_blocks_fitted(512, 32, 12, 3, synth.BASE_SEED + 4, device="cuda")
     blk = mfa.DeviceBlocks(bs)
@@ -232,5 +232,5 @@ def test_config4_full_size_sampled(mfa, ctx):
         got = np.concatenate([c[b][torch.as_tensor((k[:, 0] * 32 + k[:, 1]) * 32 + k[:, 2], device="cuda")]
                              .cpu().numpy() for b, k in picks])
         ve, ge = rel_errors(got, want)
-        print(f"config 4 {name}: value {ve:.2e} gradient {max(ge):.2e}")
+        print(f"degree-3 512^3 {name}: value {ve:.2e} gradient {max(ge):.2e}")
         assert ve <= TOL.get(name, 1e-5) and max(ge) <= TOL.get(name, 1e-5), (name, ve, ge)
