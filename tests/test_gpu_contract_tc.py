@@ -128,6 +128,15 @@ def test_tc_paths_refuse_what_they_do_not_cover(mfa, ctx):
     assert e.value.code == mfa.ERR_UNSUPPORTED
     plan.close()
     assert ctx.device_status() == 0
+    # no blocks: the call returns before any check of the (absent) arrays and launches nothing
+    import ctypes
+    n0 = ctx.launch_count()
+    for prec in (mfa.PREC_SPLIT_BF16, mfa.PREC_BF16):
+        rc = mfa.lib.mfa_adjoint_blocks(ctx.handle, None, 0, None, 0, None, 32 ** 3, 0, None, None, 0,
+                                        ctypes.byref(blk2.bounds), prec,
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == mfa.OK
+    assert ctx.launch_count() == n0
 
 
 def test_tc_adjoint_skips_a_block_of_another_shape(mfa, ctx):

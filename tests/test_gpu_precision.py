@@ -108,6 +108,41 @@ def test_tensor_core_list_slots_and_shape_checks(mfa, ctx):
 
 
 @pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
+def test_tensor_core_decode_empty_and_clamped_counts(mfa, ctx, name):
+    """Empty inputs of the tensor-core decode: no blocks (the call returns before any launch), a device count of
+    0 (the kernel runs and writes nothing), and a device count above the list's length (MFA_DEV_BAD_LIST, and
+    the count is clamped to the list: every listed block is decoded, nothing else)."""
+    import ctypes
+    prec = _prec(mfa, name)
+    bs = synth.random_block_set(4, 611, ncp_choices=(6, 12), nsamp_choices=(32,), degree_choices=(2, 3))
+    blk = mfa.DeviceBlocks(bs)
+    V = blk.slot_voxels
+    cache = torch.full((4 * V * 4,), float("nan"), device="cuda")
+    n0 = ctx.launch_count()
+    rc = mfa.lib.mfa_decode_blocks(ctx.handle, ctypes.c_void_p(blk.desc.data_ptr()), 0, None, 0, None,
+                                   ctypes.c_void_p(blk.knots.data_ptr()), blk.knots.numel(),
+                                   ctypes.c_void_p(blk.cps.data_ptr()), blk.cps.numel(),
+                                   ctypes.c_void_p(cache.data_ptr()), V, 4, ctypes.byref(blk.bounds), prec, 0,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == mfa.OK and ctx.launch_count() == n0
+    lst = torch.tensor([2, 0, 3, 1], dtype=torch.int32, device="cuda")
+    mfa.decode_blocks(ctx, blk, cache, V, 4, precision=prec, list_=lst,
+                      count=torch.tensor([0], dtype=torch.int32, device="cuda"), flags=mfa.DECODE_LIST_SLOTS)
+    assert ctx.launch_count() > n0 and ctx.device_status() == 0
+    assert torch.isnan(cache).all()
+    lst3 = lst[:3].contiguous()
+    mfa.decode_blocks(ctx, blk, cache, V, 4, precision=prec, list_=lst3,
+                      count=torch.tensor([9], dtype=torch.int32, device="cuda"), flags=mfa.DECODE_LIST_SLOTS)
+    assert ctx.device_status() == mfa.DEV_BAD_LIST
+    c = cache.view(4, V, 4).cpu().numpy()
+    want = oracle_decode_set(bs, [2, 0, 3])
+    for m in range(3):
+        ve, ge = rel_errors(c[m, : 32 ** 3].reshape(32, 32, 32, 4), want[m])
+        assert ve <= TOL[name] and max(ge) <= TOL[name], (m, ve, ge)
+    assert np.all(np.isnan(c[3]))
+
+
+@pytest.mark.parametrize("name", ["split", "bf16", "fp16"])
 def test_tensor_core_decode_any_sample_count(mfa, ctx, name):
     """Sample counts other than 32 (2 .. 64 per axis, anisotropic, non-uniform knots): a block of n samples is
     decoded as ceil(n/32)^3 sub-cubes whose rows past n are zero and never stored."""
