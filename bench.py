@@ -71,8 +71,9 @@ def parse():
                          "34 x 33 x 33 whose x, y, z = 32 planes repeat the neighbouring bricks, filled after the "
                          "decode)")
     ap.add_argument("--field", type=int, default=N_FIELD,
-                    help="edge of the synthetic field of the precision workload (a multiple of 32; default 512, "
-                         "the quoted configuration; smaller fields make small profiler captures)")
+                    help="edge of the synthetic field of the step and precision workloads (a multiple of 32; "
+                         "default 512, the quoted configuration; smaller fields make small profiler captures, and "
+                         "the step then needs --no-check --no-cpu-baseline)")
     ap.add_argument("--workload", choices=["step", "frames", "gd", "precision", "ncp", "lod", "direct", "outofcore",
                                            "lodrender"],
                     default="step",
@@ -172,13 +173,13 @@ def src_sha(name):
 
 
 class Workload:
-    def __init__(self, mfa, ctx, seed, layout="rows"):
+    def __init__(self, mfa, ctx, seed, layout="rows", nf=N_FIELD):
         self.mfa, self.ctx = mfa, ctx
-        B = (N_FIELD // BRICK) ** 3
+        B = (nf // BRICK) ** 3
         self.B, self.vox = B, BRICK ** 3
         self.apron = layout == "apron"
         self.stride = mfa.apron_voxels(BRICK) if self.apron else self.vox  # cache slot stride (voxels)
-        field = synth.gm_noise_field(N_FIELD, seed, device="cuda")
+        field = synth.gm_noise_field(nf, seed, device="cuda")
         self.D = synth.blocks_from_field(field, BRICK).contiguous().view(B, self.vox)
         del field
         zero = np.zeros((NCP, NCP, NCP))
@@ -186,7 +187,7 @@ class Workload:
         self.blk = mfa.DeviceBlocks(self.bs)
         self.plan = mfa.EncodePlan(ctx, self.blk)
         self.cache = torch.empty(B * self.stride * 4, device="cuda")
-        nb = N_FIELD // BRICK
+        nb = nf // BRICK
         self.table = torch.arange(B, dtype=torch.int32, device="cuda").view(nb, nb, nb)
         self.tf = torch.from_numpy(synth.transfer_function(seed)).cuda()
         self.view = synth.default_view(IMG, IMG)
@@ -1331,6 +1332,12 @@ def main():
         return run_outofcore(args) if rank == 0 else 0
     if args.workload == "lodrender":
         return run_lodrender(args) if rank == 0 else 0
+    if args.field != N_FIELD and not (args.no_check and args.no_cpu_baseline):
+        # the oracle comparisons and baselines of the step are written for the 512^3 field; a smaller field
+        # serves profiler captures of the same kernels
+        raise SystemExit("--field other than 512 for the step: add --no-check --no-cpu-baseline")
+    if args.field % BRICK or args.field < 2 * BRICK:
+        raise SystemExit("--field: a multiple of 32, at least 64")
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -1338,7 +1345,7 @@ def main():
     from paper_2409_00184_b300 import mfa
     ctx = mfa.Context(local)
     seed = synth.BASE_SEED + 2 + rank
-    w = Workload(mfa, ctx, seed, args.layout)
+    w = Workload(mfa, ctx, seed, args.layout, args.field)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -1406,7 +1413,7 @@ def main():
     dom = max(names, key=lambda n: per[n])
     src = {"encode": "contract3.cu", "decode": "decode_fp32.cu", "fill": "apron.cu", "raycast": "raycast.cu",
            "adjoint": "contract3.cu"}[dom]
-    tr = TRAFFIC.get((dom, args.layout))
+    tr = TRAFFIC.get((dom, args.layout)) if args.field == N_FIELD else None  # taken on the 512^3 step
     traffic = tr["bytes"] if tr and tr["src_sha"] == src_sha(src) else None
     achieved = algo[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -1491,8 +1498,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": K,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "layout": args.layout, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
-                           "l2": f"inputs larger than L2 (512 MB samples, {w.cache.numel() * 4 / 1e9:.2f} GB cache); "
+                "config": {"workload": WORKLOAD if args.field == N_FIELD else
+                           f"{args.field}^3 field, {w.B} micro-blocks (profiling case of: {WORKLOAD})",
+                           "layout": args.layout, "blocks": w.B, "voxels_per_step": voxels, "image": [IMG, IMG],
+                           "l2": f"inputs larger than L2 ({w.D.numel() * 4 / 2 ** 20:.0f} MiB samples, "
+                                 f"{w.cache.numel() * 4 / 1e9:.2f} GB cache); "
                                  "no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "max_err": err, "cpu_baseline": cpu, "e2e": e2e,
