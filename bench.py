@@ -878,7 +878,9 @@ def precision_decode_record(ctx, nf, K, warmup):
         variants[name] = {"ms": ms, "Gvoxel_s": B * vox / (ms * 1e-3) / 1e9, "GB_s": algo / (ms * 1e-3) / 1e9,
                           "hbm_frac": algo / (ms * 1e-3) / 1e9 / hbm,
                           "value_err": float(np.abs(got[:, 0] - want[:, 0]).max() / vr),
-                          "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm)}
+                          "grad_err": float(np.abs(got[:, 1:] - want[:, 1:]).max() / gm),
+                          "value_rms": float(np.sqrt(np.mean((got[:, 0] - want[:, 0]) ** 2)) / vr),
+                          "grad_rms": float(np.sqrt(np.mean((got[:, 1:] - want[:, 1:]) ** 2)) / gm)}
     return {"variants": variants, "split_vs_fp32_speedup": variants["fp32"]["ms"] / variants["split_bf16"]["ms"],
             "bs": bs, "blk": blk, "plan": plan, "B": B, "vox": vox, "seed": seed, "hbm": hbm, "peak_src": peak_src,
             "cache": cache}
@@ -907,12 +909,29 @@ def run_precision(args):
     # the fit (without RMSE) and the adjoint of the same blocks in each precision: 4 B/voxel read + C^3 written
     D = synth.blocks_from_field(synth.gm_noise_field(nf, seed, device="cuda"), BRICK).contiguous().view(-1)
     R = torch.empty_like(D).uniform_(-1, 1, generator=torch.Generator(device="cuda").manual_seed(seed))
-    P_tmp = torch.empty(blk.cps_len, device="cuda")
+    P_fit = torch.empty(blk.cps_len, device="cuda")
+    G_adj = torch.empty(blk.cps_len, device="cuda")
     c_algo = B * (vox * 4 + NCP ** 3 * 4 + 72)
+    # the FP64 oracle's fit and adjoint of 8 sampled blocks (outside any timed region)
+    from oracle import adjoint as oadj
+    from oracle import encode as oenc
+    knots = tuple(np.float32(synth.clamped_uniform_knots(NCP, 3)).astype(np.float64) for _ in range(3))
+    cpick = synth.rng(seed + 11).choice(B, min(B, 8), replace=False)
+    Dh, Rh = D.view(B, BRICK, BRICK, BRICK), R.view(B, BRICK, BRICK, BRICK)
+    want_fit = [oenc.fit_separable(Dh[int(b)].double().cpu().numpy(), knots, (3, 3, 3)).ravel() for b in cpick]
+    want_adj = [oadj.adjoint_block(Rh[int(b)].double().cpu().numpy(), knots, (3, 3, 3), (NCP,) * 3).ravel()
+                for b in cpick]
+
+    def contraction_err(out, want, fit):
+        got = out.view(B, NCP ** 3)[torch.as_tensor(cpick, device=out.device)].double().cpu().numpy()
+        w = np.stack(want)
+        scale = (w.max() - w.min()) if fit else np.abs(w).max()
+        return float(np.abs(got - w).max() / scale)
+
     contraction = {}
     for name, prec in (("fp32", mfa.PREC_FP32), ("split_bf16", mfa.PREC_SPLIT_BF16), ("bf16", mfa.PREC_BF16)):
-        for what, fn in (("fit", lambda: mfa.encode_blocks(ctx, plan, D, vox, B, P_tmp, precision=prec)),
-                         ("adjoint", lambda: mfa.adjoint_blocks(ctx, blk, R, vox, B, P_tmp, precision=prec))):
+        for what, fn in (("fit", lambda: mfa.encode_blocks(ctx, plan, D, vox, B, P_fit, precision=prec)),
+                         ("adjoint", lambda: mfa.adjoint_blocks(ctx, blk, R, vox, B, G_adj, precision=prec))):
             for _ in range(max(3, args.warmup)):
                 fn()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -923,8 +942,9 @@ def run_precision(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
+            err = contraction_err(P_fit, want_fit, True) if what == "fit" else contraction_err(G_adj, want_adj, False)
             contraction[f"{what}_{name}"] = {"ms": ms, "GB_s": c_algo / (ms * 1e-3) / 1e9,
-                                             "hbm_frac": c_algo / (ms * 1e-3) / 1e9 / hbm}
+                                             "hbm_frac": c_algo / (ms * 1e-3) / 1e9 / hbm, "err": err}
     if ctx.device_status():
         raise RuntimeError("device status after the contractions")
     launches = ctx.launch_count() - n0
@@ -942,7 +962,9 @@ def run_precision(args):
                                    "12^3 control points (library LS fit); value+gradient decode per precision",
                        "l2": f"cache {B * vox * 16 / 1e9:.2f} GB" + (", larger than L2; no flush" if B * vox * 16 > 126e6
                                                                       else ", smaller than L2"),
-                       "error_sample": "12 blocks x 400 voxels; value: max|df|/range(f), grad: max|dg|/max|g|"},
+                       "error_sample": "decode: 12 blocks x 400 voxels; value: max (and RMS) |df|/range(f), grad: "
+                                       "max (and RMS) |dg|/max|g|; contraction: 8 blocks, fit max|dP|/range(P), "
+                                       "adjoint max|dG|/max|G|, against the FP64 oracle's fit and adjoint"},
             "roofline": {"kernel": "decode_tc (split-BF16)", "bound": "hbm", "achieved": sp["GB_s"], "peak": hbm,
                          "unit": "GB/s", "frac": sp["hbm_frac"], "traffic": None,
                          "peak_source": f"{peak_src} hbm_gbs (copy, read+write)"},
