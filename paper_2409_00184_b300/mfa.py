@@ -161,14 +161,29 @@ def _check(code, what):
         raise MfaError(code, what)
 
 
-def _ptr(t):
+F32, F64, I32, U8 = torch.float32, torch.float64, torch.int32, torch.uint8
+
+
+def _ptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None stays None). With dtype, the tensor must hold that
+    element type: the library reads and writes it with that width, and the element counts checked against
+    the call's extents assume it."""
     if t is None:
         return None
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected a {dtype} tensor, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _tf(tf):
+    """Pointer and entry count of a transfer function: a float32 CUDA tensor of shape (n, 4) (RGBA)."""
+    if tf.dim() != 2 or tf.shape[1] != 4:
+        raise ValueError("tf: float32 tensor of shape (n, 4)")
+    return _ptr(tf, F32), tf.shape[0]
 
 
 def _stream(stream):
@@ -317,9 +332,9 @@ def decode_blocks(ctx, blocks, cache, slot_stride, nslots, precision=PREC_FP32, 
     _need(cache, nslots * slot_stride * width, "cache")
     _need(cps, blocks.cps_len, "cps")
     _check(lib.mfa_decode_blocks(ctx.handle, _ptr(blocks.desc), blocks.n,
-                                 _ptr(list_), 0 if list_ is None else list_.numel(), _ptr(count),
-                                 _ptr(blocks.knots), blocks.knots.numel(), _ptr(cps), cps.numel(),
-                                 _ptr(cache), slot_stride, nslots, ctypes.byref(bounds or blocks.bounds),
+                                 _ptr(list_, I32), 0 if list_ is None else list_.numel(), _ptr(count, I32),
+                                 _ptr(blocks.knots), blocks.knots.numel(), _ptr(cps, F32), cps.numel(),
+                                 _ptr(cache, F32), slot_stride, nslots, ctypes.byref(bounds or blocks.bounds),
                                  precision, flags, _stream(stream)), "mfa_decode_blocks")
 
 
@@ -341,18 +356,20 @@ def decode_compare_blocks(ctx, blocks, cache, slot_stride, nslots, data, data_st
         if rmse.dtype != torch.float64:
             raise ValueError("rmse: float64 tensor")
         _need(rmse, list_.numel() if list_ is not None else blocks.n, "rmse")
-    _check(lib.mfa_decode_compare_blocks(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(list_),
-                                         0 if list_ is None else list_.numel(), _ptr(count), _ptr(blocks.knots),
-                                         blocks.knots.numel(), _ptr(cps), cps.numel(), _ptr(cache), slot_stride,
-                                         nslots, ctypes.byref(bounds or blocks.bounds), flags, _ptr(data), data_stride,
-                                         _ptr(residual), _ptr(rmse), _stream(stream)), "mfa_decode_compare_blocks")
+    _check(lib.mfa_decode_compare_blocks(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(list_, I32),
+                                         0 if list_ is None else list_.numel(), _ptr(count, I32), _ptr(blocks.knots),
+                                         blocks.knots.numel(), _ptr(cps, F32), cps.numel(), _ptr(cache, F32),
+                                         slot_stride, nslots, ctypes.byref(bounds or blocks.bounds), flags,
+                                         _ptr(data, F32), data_stride, _ptr(residual, F32), _ptr(rmse, F64),
+                                         _stream(stream)), "mfa_decode_compare_blocks")
 
 
 def basis_tables(ctx, desc_one, knots, stream=None):
     """mfa_basis_tables for one descriptor (uint8 CUDA tensor of 72 bytes): (span (3, 64), basis (3, 64, 2, 4))."""
     span = torch.zeros(3 * MAX_NSAMP, dtype=torch.int32, device=knots.device)
     basis = torch.zeros(3 * MAX_NSAMP * 2 * 4, dtype=torch.float32, device=knots.device)
-    _check(lib.mfa_basis_tables(ctx.handle, _ptr(desc_one), _ptr(knots), knots.numel(), _ptr(span), _ptr(basis),
+    _check(lib.mfa_basis_tables(ctx.handle, _ptr(desc_one, U8), _ptr(knots, F32), knots.numel(), _ptr(span),
+                                _ptr(basis),
                                 _stream(stream)), "mfa_basis_tables")
     return span.view(3, MAX_NSAMP), basis.view(3, MAX_NSAMP, 2, 4)
 
@@ -365,7 +382,8 @@ def adjoint_blocks(ctx, blocks, residual, slot_stride, nslots, grad, cps=None, p
     if cps is not None:
         _need(cps, blocks.cps_len, "cps")
     _check(lib.mfa_adjoint_blocks(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
-                                  _ptr(residual), slot_stride, nslots, _ptr(cps), _ptr(grad), grad.numel(),
+                                  _ptr(residual, F32), slot_stride, nslots, _ptr(cps, F32), _ptr(grad, F32),
+                                  grad.numel(),
                                   ctypes.byref(bounds or blocks.bounds), precision, _stream(stream)),
            "mfa_adjoint_blocks")
 
@@ -403,11 +421,12 @@ def encode_blocks(ctx, plan, data, slot_stride, nslots, cps_out, rmse=None, stre
     if rmse is not None:
         _need(rmse, plan.nblocks, "rmse")
     if precision == PREC_FP32:
-        _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
-                                     _ptr(rmse), _stream(stream)), "mfa_encode_blocks")
+        _check(lib.mfa_encode_blocks(ctx.handle, plan.handle, _ptr(data, F32), slot_stride, nslots,
+                                     _ptr(cps_out, F32), _ptr(rmse, F64), _stream(stream)), "mfa_encode_blocks")
     else:
-        _check(lib.mfa_encode_blocks_ex(ctx.handle, plan.handle, _ptr(data), slot_stride, nslots, _ptr(cps_out),
-                                        _ptr(rmse), precision, _stream(stream)), "mfa_encode_blocks_ex")
+        _check(lib.mfa_encode_blocks_ex(ctx.handle, plan.handle, _ptr(data, F32), slot_stride, nslots,
+                                        _ptr(cps_out, F32), _ptr(rmse, F64), precision, _stream(stream)),
+               "mfa_encode_blocks_ex")
 
 
 def encode_blocks_noalloc(blocks, data, slot_stride, nslots, cps_out, rmse=None, stream=None):
@@ -420,7 +439,8 @@ def encode_blocks_noalloc(blocks, data, slot_stride, nslots, cps_out, rmse=None,
     desc = np.ascontiguousarray(blocks.host_desc)
     rc = lib.mfa_encode_blocks_noalloc(desc.ctypes.data_as(ctypes.c_void_p), blocks.n,
                                        blocks.host_knots.ctypes.data_as(ctypes.c_void_p), blocks.host_knots.size,
-                                       _ptr(data), slot_stride, nslots, _ptr(cps_out), blocks.cps_len, _ptr(rmse),
+                                       _ptr(data, F32), slot_stride, nslots, _ptr(cps_out, F32), blocks.cps_len,
+                                       _ptr(rmse, F64),
                                        _stream(stream))
     if rc == ERR_CAPACITY:
         raise MfaError(rc, "mfa_encode_blocks_noalloc: the batch's tables exceed the fixed 2 MiB scratch")
@@ -439,7 +459,8 @@ def select_ncp(ctx, errors, ncps, bound, out=None, stream=None):
         out = torch.empty(nb, dtype=torch.int32, device=errors.device)
     _need(out, nb, "out")
     h = (ctypes.c_int32 * ncand)(*[int(c) for c in ncps])
-    _check(lib.mfa_select_ncp(ctx.handle, _ptr(errors), ncand, h, nb, float(bound), _ptr(out), _stream(stream)),
+    _check(lib.mfa_select_ncp(ctx.handle, _ptr(errors, F64), ncand, h, nb, float(bound), _ptr(out, I32),
+                              _stream(stream)),
            "mfa_select_ncp")
     return out
 
@@ -465,7 +486,8 @@ def lod_gather(ctx, field, n, stride, ids=None, nblocks=None, out=None, stream=N
     dims = (ctypes.c_int32 * 3)(Nx, Ny, Nz)
     if count == 0:
         return out
-    _check(lib.mfa_lod_gather_ex(ctx.handle, _ptr(field), dims, n, stride, _ptr(ids), count, _ptr(out), n ** 3,
+    _check(lib.mfa_lod_gather_ex(ctx.handle, _ptr(field, F32), dims, n, stride, _ptr(ids, I32), count,
+                                 _ptr(out, F32), n ** 3,
                                  LOD_SHARED_BOUNDARY if shared else 0, _stream(stream)), "mfa_lod_gather_ex")
     return out
 
@@ -479,7 +501,7 @@ def lod_select(ctx, eye, fine_blocks, n, levels, ranges=(0.8, 1.6, 2.4), table=N
     e = (ctypes.c_float * 3)(*[float(x) for x in eye])
     r = (ctypes.c_float * max(1, len(ranges)))(*[float(x) for x in ranges])
     _check(lib.mfa_lod_select(ctx.handle, ctypes.byref(e), fine_blocks, n, levels, r if levels > 1 else None,
-                              _ptr(table), _stream(stream)), "mfa_lod_select")
+                              _ptr(table, I32), _stream(stream)), "mfa_lod_select")
     return table
 
 
@@ -490,9 +512,10 @@ def raycast_lod(ctx, blocks, table, fine_blocks, n, levels, view, tf, image, cps
     _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
     _need(table, fine_blocks ** 3, "table")
     v = make_view(view)
+    tfp, tfn = _tf(tf)
     _check(lib.mfa_raycast_lod(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
-                               _ptr(cps), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table), fine_blocks, n, levels,
-                               ctypes.byref(v), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+                               _ptr(cps, F32), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table, I32),
+                               fine_blocks, n, levels, ctypes.byref(v), tfp, tfn, _ptr(image, F32), _stream(stream)),
            "mfa_raycast_lod")
 
 
@@ -588,9 +611,10 @@ def raycast_direct(ctx, blocks, table, brick_n, view, tf, image, cps=None, strea
     _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
     v = make_view(view)
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
+    tfp, tfn = _tf(tf)
     _check(lib.mfa_raycast_direct(ctx.handle, _ptr(blocks.desc), blocks.n, _ptr(blocks.knots), blocks.knots.numel(),
-                                  _ptr(cps), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table), dims, brick_n,
-                                  ctypes.byref(v), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+                                  _ptr(cps, F32), cps.numel(), ctypes.byref(blocks.bounds), _ptr(table, I32), dims,
+                                  brick_n, ctypes.byref(v), tfp, tfn, _ptr(image, F32), _stream(stream)),
            "mfa_raycast_direct")
 
 
@@ -603,15 +627,17 @@ def raycast(ctx, cache, slot_stride, nslots, table, brick_n, view, tf, image, st
     _need(cache, nslots * slot_stride * 4, "cache")
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
     vw = make_view(view)
+    tfp, tfn = _tf(tf)
     if cubes or apron or count_sectors:
         flags = ((RAYCAST_CUBES if cubes else 0) | (RAYCAST_APRON if apron else 0) |
                  (RAYCAST_COUNT_SECTORS if count_sectors else 0))
-        _check(lib.mfa_raycast_ex(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
-                                  brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), flags,
+        _check(lib.mfa_raycast_ex(ctx.handle, _ptr(cache, F32), slot_stride, nslots, _ptr(table, I32),
+                                  ctypes.byref(dims), brick_n, ctypes.byref(vw), tfp, tfn, _ptr(image, F32), flags,
                                   _stream(stream)), "mfa_raycast_ex")
     else:
-        _check(lib.mfa_raycast(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
-                               brick_n, ctypes.byref(vw), _ptr(tf), tf.shape[0], _ptr(image), _stream(stream)),
+        _check(lib.mfa_raycast(ctx.handle, _ptr(cache, F32), slot_stride, nslots, _ptr(table, I32),
+                               ctypes.byref(dims), brick_n, ctypes.byref(vw), tfp, tfn, _ptr(image, F32),
+                               _stream(stream)),
                "mfa_raycast")
 
 
@@ -621,7 +647,7 @@ def fill_aprons(ctx, cache, slot_stride, nslots, table, brick_n, stream=None):
     Bz, By, Bx = table.shape
     _need(cache, nslots * slot_stride * 4, "cache")
     dims = (ctypes.c_int32 * 3)(Bx, By, Bz)
-    _check(lib.mfa_fill_aprons(ctx.handle, _ptr(cache), slot_stride, nslots, _ptr(table), ctypes.byref(dims),
+    _check(lib.mfa_fill_aprons(ctx.handle, _ptr(cache, F32), slot_stride, nslots, _ptr(table, I32), ctypes.byref(dims),
                                brick_n, _stream(stream)), "mfa_fill_aprons")
 
 
@@ -641,10 +667,10 @@ class FrameGraph:
         self._view = None
         fd = FrameDesc()
         fd.d_desc, fd.nblocks = _ptr(blocks.desc), blocks.n
-        fd.d_list, fd.list_capacity, fd.d_count = _ptr(list_buf), cap, _ptr(count_buf)
+        fd.d_list, fd.list_capacity, fd.d_count = _ptr(list_buf, I32), cap, _ptr(count_buf, I32)
         fd.d_knots, fd.knots_len = _ptr(blocks.knots), blocks.knots.numel()
-        fd.d_cps, fd.cps_len = _ptr(blocks.cps), blocks.cps.numel()
-        fd.d_cache, fd.slot_stride_voxels = _ptr(cache), slot_stride
+        fd.d_cps, fd.cps_len = _ptr(blocks.cps, F32), blocks.cps.numel()
+        fd.d_cache, fd.slot_stride_voxels = _ptr(cache, F32), slot_stride
         fd.bounds = blocks.bounds
         fd.precision = precision
         if view is not None:
@@ -652,11 +678,12 @@ class FrameGraph:
             _need(table, blocks.n, "table")
             _need(image, int(view["width"]) * int(view["height"]) * 4, "image")
             self._view = make_view(view)
-            fd.d_brick_table = _ptr(table)
+            fd.d_brick_table = _ptr(table, I32)
             fd.brick_dims = (ctypes.c_int32 * 3)(*brick_dims)
             fd.brick_n = brick_n
             fd.view = ctypes.cast(ctypes.pointer(self._view), ctypes.c_void_p)
-            fd.d_tf, fd.tf_n, fd.d_image = _ptr(tf), tf.shape[0], _ptr(image)
+            fd.d_tf, fd.tf_n = _tf(tf)
+            fd.d_image = _ptr(image, F32)
         fd.flags = flags
         h = ctypes.c_void_p()
         _check(lib.mfa_frame_graph_create(ctx.handle, ctypes.byref(h), ctypes.byref(fd)), "mfa_frame_graph_create")

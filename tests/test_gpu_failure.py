@@ -68,3 +68,31 @@ def test_host_device_copies_round_trip():
     assert mfa.lib.mfa_copy_to_device(None, ctypes.c_void_p(h.data_ptr()), 4, None) == mfa.ERR_INVALID_ARG
     assert mfa.lib.mfa_copy_to_host(ctypes.c_void_p(back.data_ptr()), ctypes.c_void_p(d.data_ptr()), -1,
                                     None) == mfa.ERR_INVALID_ARG
+
+
+def test_binding_refuses_tensors_of_another_element_type(mfa, ctx):
+    """The binding checks each tensor's element type before a call: a byte tensor as the cache would pass an
+    element-count check yet be a quarter of the bytes the decode writes. Nothing is launched."""
+    bs = synth.random_block_set(2, 811, ncp_choices=(4,), nsamp_choices=(8,), degree_choices=(2,))
+    blk = mfa.DeviceBlocks(bs)
+    n0 = ctx.launch_count()
+    V = blk.slot_voxels
+    with pytest.raises(ValueError):
+        mfa.decode_blocks(ctx, blk, torch.zeros(2 * V * 4, dtype=torch.uint8, device="cuda"), V, 2)
+    with pytest.raises(ValueError):
+        mfa.decode_blocks(ctx, blk, torch.zeros(2 * V * 4, device="cuda"), V, 2,
+                          list_=torch.zeros(2, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        mfa.adjoint_blocks(ctx, blk, torch.zeros(2 * V, dtype=torch.float64, device="cuda"), V, 2,
+                           torch.zeros(blk.cps_len, device="cuda"))
+    table = torch.zeros(1, 1, 2, dtype=torch.int32, device="cuda")
+    view = synth.default_view(width=8, height=8)
+    tf = torch.from_numpy(synth.transfer_function(1)).cuda()
+    cache = torch.zeros(2 * V * 4, device="cuda")
+    with pytest.raises(ValueError):  # a transfer function must be (n, 4)
+        mfa.raycast(ctx, cache, V, 2, table, 8, view, tf.view(-1), torch.zeros(8, 8, 4, device="cuda"))
+    with pytest.raises(ValueError):
+        mfa.raycast(ctx, cache, V, 2, table.long(), 8, view, tf, torch.zeros(8, 8, 4, device="cuda"))
+    with pytest.raises(ValueError):
+        mfa.raycast(ctx, cache, V, 2, table, 8, view, tf, torch.zeros(8, 8, 4, dtype=torch.float64, device="cuda"))
+    assert ctx.launch_count() == n0 and ctx.device_status() == 0
