@@ -171,7 +171,9 @@ int mfa_copy_to_host(void* h_dst, const void* d_src, int64_t bytes, void* stream
  * corresponding factor. Selection: if d_list is NULL every block 0..nblocks-1 is decoded;
  * otherwise the items d_list[0 .. count) where count = *d_count (device int32, read by
  * the kernel, so the call can be replayed from a CUDA graph) or list_len if d_count is
- * NULL; count must be <= list_len. Destination: slot desc.slot, or slot m for item m
+ * NULL; count must be <= list_len (a larger or negative *d_count sets MFA_DEV_BAD_LIST and is
+ * clamped to 0 .. list_len; a count of 0 decodes nothing; with no blocks, or an empty list and
+ * no d_count, nothing is enqueued). Destination: slot desc.slot, or slot m for item m
  * with MFA_DECODE_LIST_SLOTS. Output per voxel: 4 floats (f, f_u, f_v, f_w), or 1 float
  * with MFA_DECODE_VALUE_ONLY, at d_cache + (slot*slot_stride_voxels + voxel)*width.
  * d_cache must be 16-byte aligned. knots_len / cps_len are the array lengths (floats),
