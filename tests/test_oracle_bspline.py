@@ -88,3 +88,18 @@ def test_sample_params_are_fp32_quotients():
         u = bspline.sample_params(n)
         assert u[0] == 0.0 and u[-1] == 1.0
         assert np.all(u == (np.arange(n, dtype=np.float32) / np.float32(n - 1)).astype(np.float64))
+
+
+@pytest.mark.parametrize("t,p", _knot_cases())
+def test_degree0_indicators_cover_each_parameter_once(t, p):
+    """Degree 0: every parameter in [t_0, t_end] lies in exactly one half-open knot interval; empty
+    intervals (repeated knots) hold none, and the right end belongs to the last non-empty interval."""
+    u = np.concatenate([[0.0, 1.0], t, synth.rng(5).uniform(0, 1, 200)])
+    N0 = bspline.degree0(t, u)
+    assert N0.shape == (len(u), len(t) - 1)
+    assert np.all((N0 == 0) | (N0 == 1)) and np.all(N0.sum(axis=1) == 1)
+    empty = np.diff(t) == 0
+    assert np.all(N0[:, empty] == 0)
+    for r, x in enumerate(u):
+        i = int(np.argmax(N0[r]))
+        assert t[i] <= x and (x < t[i + 1] or (x == t[-1] and t[i] < t[i + 1] == t[-1]))

@@ -192,3 +192,16 @@ def test_evaluate_points_multi_matches_per_block():
     for b in range(4):
         sel = which == b
         assert np.array_equal(got[sel], decode.evaluate_points(Ps[b], knots, degrees, uvw[sel]))
+
+
+def test_grid_params_order_and_corners():
+    """Sample parameters of a block: x fastest, then y, then z; endpoints 0 and 1 on every axis; each
+    parameter i/(n-1) rounded to FP32 (the reading both sides take)."""
+    nsamp = (3, 4, 5)
+    G = decode.grid_params(nsamp)
+    assert G.shape == (60, 3)
+    assert np.array_equal(G[0], [0, 0, 0]) and np.array_equal(G[-1], [1, 1, 1])
+    third = float(np.float32(1 / 3))
+    assert np.array_equal(G[1], [0.5, 0, 0]) and np.array_equal(G[3], [0, third, 0]) and G[12][2] == 0.25
+    k, j, i = 2, 1, 2
+    assert np.array_equal(G[(k * 4 + j) * 3 + i], [np.float32(i / 2), np.float32(j / 3), np.float32(k / 4)])

@@ -207,3 +207,20 @@ def test_fit_separable_batch_matches_per_block_and_dense():
         Pd = encode.fit_dense(D[b], knots, degrees)
         assert np.max(np.abs(Pb[b] - Ps)) < 1e-12
         assert np.max(np.abs(Pb[b] - Pd)) < 1e-10
+
+
+@pytest.mark.parametrize("C,p,n", [(4, 2, 8), (12, 2, 32), (16, 3, 32), (24, 3, 64), (5, 1, 13)])
+def test_collocation_rows_and_pseudo_inverse(C, p, n):
+    """The collocation matrix has one row per sample that sums to 1 with at most p + 1 contiguous nonzeros,
+    and the pseudo-inverse from the normal equations is a left inverse equal to the SVD-based one."""
+    t = synth.clamped_uniform_knots(C, p)
+    N = encode.collocation(t, p, n)
+    assert N.shape == (n, C)
+    assert np.max(np.abs(N.sum(axis=1) - 1.0)) < 1e-14
+    for row in N:
+        nz = np.nonzero(row)[0]
+        assert len(nz) <= p + 1 and np.all(np.diff(nz) == 1)
+    A = encode.pseudo_inverse(N)
+    assert A.shape == (C, n)
+    assert np.max(np.abs(A @ N - np.eye(C))) < 1e-10
+    assert np.max(np.abs(A - np.linalg.pinv(N))) < 1e-9 * max(1.0, np.abs(A).max())

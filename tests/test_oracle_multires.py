@@ -209,3 +209,14 @@ def test_ssim_against_per_window_sums_and_closed_forms():
     rgba = g.uniform(0, 1, (16, 14, 4))
     per = [multires.ssim(rgba[..., k], rgba[..., k] * 0.9) for k in range(4)]
     assert abs(multires.ssim(rgba, rgba * 0.9) - np.mean(per)) < 1e-12
+
+
+def test_ssim_gaussian_window():
+    """The structural-similarity window: symmetric, normalised, peaked at the centre, with the variance of
+    the sampled Gaussian (sigma^2 = 2.25 up to the truncation at +-5 taps)."""
+    w = multires.gaussian_window()
+    x = np.arange(11) - 5.0
+    assert len(w) == 11 and abs(w.sum() - 1.0) < 1e-15 and np.allclose(w, w[::-1], rtol=0, atol=0)
+    assert np.argmax(w) == 5 and np.all(np.diff(w[:6]) > 0)
+    var = float((w * x * x).sum())
+    assert 2.2 < var < 2.25

@@ -332,3 +332,25 @@ def test_decoded_nodes_equal_block_decodes():
     got = voxels(slot, iz, iy, ix)
     want = np.stack([full[s][z, y, x] for s, z, y, x in zip(slot, iz, iy, ix)]).astype(np.float64)
     assert np.array_equal(got, want)
+
+
+def test_camera_frame_is_orthonormal_and_oriented():
+    """The camera frame: unit forward towards the target, right = forward x up and up = right x forward
+    orthonormal (so right x up = -forward), up on the world up's side, and tan of half the field of view."""
+    g = synth.rng(21)
+    for _ in range(20):
+        eye = g.uniform(-3, 3, 3)
+        tgt = g.uniform(-0.5, 0.5, 3)
+        view = synth.default_view(width=int(g.integers(8, 64)), height=int(g.integers(8, 64)),
+                                  eye=tuple(eye), target=tuple(tgt), fov_y_deg=float(g.uniform(10, 90)))
+        e, fwd, right, up, tan_w, tan_h = (np.asarray(x, np.float64) for x in raycast.camera_frame(view))
+        d = np.float32(tgt).astype(np.float64) - np.float32(eye).astype(np.float64)
+        assert np.allclose(fwd, d / np.linalg.norm(d), atol=1e-6)
+        for v in (fwd, right, up):
+            assert abs(np.linalg.norm(v) - 1.0) < 1e-6
+        assert abs(fwd @ right) < 1e-6 and abs(fwd @ up) < 1e-6 and abs(right @ up) < 1e-6
+        assert np.allclose(np.cross(right, up), -fwd, atol=1e-6)
+        upw = np.asarray(view["up"], np.float64)
+        assert up @ upw > 0 and abs(np.linalg.det(np.stack([upw, fwd, up]))) < 1e-6
+        assert abs(tan_h - np.tan(np.radians(view["fov_y_deg"]) / 2)) < 1e-6 * max(1.0, tan_h)
+        assert abs(tan_w - tan_h * view["width"] / view["height"]) < 1e-6 * max(1.0, tan_w)
