@@ -25,9 +25,9 @@ namespace mfa {
 namespace {
 
 constexpr int kApronThreads = 256;
-constexpr int kBatch = 8;
+constexpr int kBatch = 13;  // 256 x 13 >= 3169: a 32^3 brick's apron in one round of loads
 
-__global__ void __launch_bounds__(kApronThreads) apron_fill_kernel(ApronParams prm) {
+__global__ void __launch_bounds__(kApronThreads, 3) apron_fill_kernel(ApronParams prm) {
   __shared__ int s_nb[8];  // slot of the brick at offset (e & 1, (e >> 1) & 1, e >> 2)
   const int brick = blockIdx.x;
   const int B0 = prm.B[0], B1 = prm.B[1], B2 = prm.B[2];
