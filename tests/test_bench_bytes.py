@@ -29,3 +29,16 @@ def test_decode_and_contraction_bytes_per_block():
     assert b["adjoint"] == vox * 4 + cp * 4 + 72
     # the step's 4096 blocks of 32^3 at C = 12: 24.2 bytes per voxel through the decode
     assert abs(bench.algorithmic_bytes(4096, True)["decode"] / (4096 * vox) - 24.2) < 0.05
+
+
+def test_reduced_step_field_is_for_profiling_only():
+    """A step on another field than 512^3 needs the oracle checks and baselines off (they are written for the
+    512^3 field), and the field must be a multiple of 32 of at least 64; both refusals come before any GPU
+    work."""
+    import subprocess
+    run = lambda *a: subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *a], capture_output=True,
+                                    text=True, cwd=ROOT, timeout=300)
+    r = run("--field", "384")
+    assert r.returncode != 0 and "--no-check --no-cpu-baseline" in r.stderr
+    r = run("--field", "100", "--no-check", "--no-cpu-baseline")
+    assert r.returncode != 0 and "multiple of 32" in r.stderr
