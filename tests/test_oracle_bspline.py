@@ -103,3 +103,50 @@ def test_degree0_indicators_cover_each_parameter_once(t, p):
     for r, x in enumerate(u):
         i = int(np.argmax(N0[r]))
         assert t[i] <= x and (x < t[i + 1] or (x == t[-1] and t[i] < t[i + 1] == t[-1]))
+
+
+def _clamped_with_repeats(data):
+    """A clamped knot vector for a random degree p and control-point count C whose interior knots sit on a
+    coarse grid, each grid point taken up to p times (so the basis stays continuous and knots repeat)."""
+    from hypothesis import strategies as st
+    p = data.draw(st.integers(1, 3))
+    C = data.draw(st.integers(p + 1, 16))
+    need = C - p - 1
+    lo = max(2, -(-need // p) + 1)  # enough grid points for multiplicities up to p
+    grid = data.draw(st.integers(lo, max(lo, need // 2 + 2)))
+    counts = [0] * (grid - 1)
+    interior = []
+    while len(interior) < need:
+        i = data.draw(st.integers(0, grid - 2))
+        while counts[i] == p:  # the next grid point that is not yet at multiplicity p
+            i = (i + 1) % (grid - 1)
+        counts[i] += 1
+        interior.append((i + 1) / grid)
+    return np.array([0.0] * (p + 1) + sorted(interior) + [1.0] * (p + 1)), p
+
+
+def test_basis_properties_with_repeated_interior_knots():
+    """For clamped knot vectors with repeated interior knots: partition of unity, nonnegativity, at most
+    p + 1 contiguous nonzero functions starting at the span minus p, derivatives summing to 0, and linear
+    precision (the Greville abscissae as control points reproduce u exactly)."""
+    from hypothesis import HealthCheck, given, settings
+    from hypothesis import strategies as st
+
+    @settings(max_examples=150, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+    @given(st.data())
+    def check(data):
+        t, p = _clamped_with_repeats(data)
+        C = len(t) - p - 1
+        u = np.concatenate([[0.0, 1.0], np.unique(t), synth.rng(len(t)).uniform(0, 1, 40)])
+        N, dN = bspline.basis(t, p, u), bspline.basis_deriv(t, p, u)
+        s = bspline.find_span(t, p, u)
+        assert np.max(np.abs(N.sum(axis=1) - 1.0)) < 1e-13
+        assert N.min() >= 0.0
+        assert np.max(np.abs(dN.sum(axis=1))) < 1e-9 * max(1.0, np.abs(dN).max())
+        for r in range(len(u)):
+            nz = np.nonzero(N[r])[0]
+            assert len(nz) <= p + 1 and (len(nz) == 0 or (nz[0] >= s[r] - p and nz[-1] <= s[r]))
+        greville = np.array([t[i + 1: i + p + 1].sum() / p for i in range(C)])
+        assert np.max(np.abs(N @ greville - u)) < 1e-13
+
+    check()
