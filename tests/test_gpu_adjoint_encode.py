@@ -172,3 +172,42 @@ def test_decode_compare_fuses_residual_and_rmse(mfa, ctx, flags_name):
         want = encode.rmse(rb.block_cps(b), g, rb.block_knots(b), tuple(rb.degree[b]))
         assert abs(got[m] - want) <= 1e-5 * max(1.0, float(np.abs(g).max())), (m, b)
     assert got[4] == 0.0  # beyond the device count: zeroed, not decoded
+
+
+def test_repeated_interior_knots_adjoint_and_fit(mfa, ctx):
+    """Knot vectors with repeated interior knots (multiplicity up to p, so spans skip empty intervals and a
+    band can move by several control points between samples): the adjoint and the least-squares fit (with its
+    RMSE pass, and without it on the z-first kernel where the shapes allow) against the FP64 oracle."""
+    from gpu_util import repeated_knot_set
+    bs = repeated_knot_set(10, 341, nsamp_choices=(13, 32))
+    blk = mfa.DeviceBlocks(bs)
+    R, stride = _grids(bs, 342)
+    grad = torch.full((blk.cps_len,), float("nan"), device="cuda")
+    mfa.adjoint_blocks(ctx, blk, torch.from_numpy(R.ravel()).cuda(), stride, len(bs), grad)
+    assert ctx.device_status() == 0
+    G = grad.cpu().numpy()
+    for b in range(len(bs)):
+        want = oadj.adjoint_block(_block_grid(R, bs, b), bs.block_knots(b), bs.degree[b], bs.ncp[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = G[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max(), b
+    # the fit, on 32 samples per axis (every span of these knots holds samples: a well-posed fit)
+    fb = repeated_knot_set(8, 343, nsamp_choices=(32,))
+    D, stride = _grids(fb, 344)
+    P, rm = _encode(mfa, ctx, fb, D, stride)
+    fblk = mfa.DeviceBlocks(fb)
+    plan = mfa.EncodePlan(ctx, fblk)
+    Pz = torch.full((fblk.cps_len,), float("nan"), device="cuda")
+    mfa.encode_blocks(ctx, plan, torch.from_numpy(np.ascontiguousarray(D).ravel()).cuda(), stride, len(fb), Pz)
+    assert ctx.device_status() == 0
+    plan.close()
+    Pz = Pz.cpu().numpy()
+    for b in range(len(fb)):
+        Db = _block_grid(D, fb, b)
+        want = encode.fit_separable(Db, fb.block_knots(b), fb.degree[b])
+        Cx, Cy, Cz = fb.ncp[b]
+        for got in (P, Pz):
+            g = got[fb.cp_off[b]: fb.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+            assert np.abs(g - want).max() <= 1e-5 * max(1.0, np.abs(want).max()), b
+        want_rmse = encode.rmse(want, Db, fb.block_knots(b), fb.degree[b])
+        assert abs(rm[b] - want_rmse) <= 1e-5 * (Db.max() - Db.min()), (b, rm[b], want_rmse)

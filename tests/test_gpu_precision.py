@@ -269,3 +269,20 @@ def test_degree3_512cubed_4096_blocks_sampled(mfa, ctx):
         ve, ge = rel_errors(got, want)
         print(f"degree-3 512^3 {name}: value {ve:.2e} gradient {max(ge):.2e}")
         assert ve <= TOL.get(name, 1e-5) and max(ge) <= TOL.get(name, 1e-5), (name, ve, ge)
+
+
+@pytest.mark.parametrize("name", ["fp32", "split", "bf16"])
+def test_decode_with_repeated_interior_knots(mfa, ctx, name):
+    """Knot vectors with repeated interior knots (multiplicity up to p): the FP32 decode and the tensor-core
+    decode against the oracle, with sample counts from 13 to 64."""
+    from gpu_util import TOL_FP32, repeated_knot_set
+    bs = repeated_knot_set(10, 351, nsamp_choices=(13, 32, 64))
+    prec = mfa.PREC_FP32 if name == "fp32" else _prec(mfa, name)
+    got = _decode(mfa, ctx, bs, prec)
+    assert ctx.device_status() == 0
+    want = oracle_decode_set(bs)
+    tol = TOL_FP32 if name == "fp32" else TOL[name]
+    for b in range(len(bs)):
+        nx, ny, nz = bs.nsamp[b]
+        ve, ge = rel_errors(got[bs.slot[b], : nx * ny * nz].reshape(nz, ny, nx, 4), want[b])
+        assert ve <= tol and max(ge) <= tol, (b, ve, ge)
