@@ -319,6 +319,8 @@ typedef struct mfa_encode_plan mfa_encode_plan;
 int  mfa_encode_plan_create(mfa_ctx* ctx, mfa_encode_plan** out,
                             const mfa_block_desc* h_desc, int32_t nblocks,
                             const float* h_knots, int64_t knots_len, int64_t cps_len);
+/* Frees the plan's device tables with cudaFree, which waits for the device's pending work first, so a plan
+ * may be destroyed right after the fits that use it have been enqueued (at the cost of that wait). */
 void mfa_encode_plan_destroy(mfa_encode_plan* plan);
 int  mfa_encode_blocks(mfa_ctx* ctx, const mfa_encode_plan* plan,
                        const float* d_data, int64_t slot_stride_voxels, int64_t nslots,
