@@ -97,7 +97,9 @@ def cross_level_encode(ctx, field, n, degree, bound, levels, encode=True, search
     to the finest: the blocks of the coarsest level, and at every finer level the blocks whose parent
     block is complex, are searched over NCP in [degree + 2, n] (Eq. 4 on the RMSE of each fit); a searched
     block is simple when its NCP* is degree + 2, complex otherwise (no candidate below the bound counts
-    as complex and is encoded with NCP = n). Blocks that are not searched take NCP = degree + 1.
+    as complex and is encoded with NCP = n). Blocks that are not searched take NCP = degree + 1. The
+    library fits at most MAX_NCP control points per axis, so for n > MAX_NCP the search stops there and a
+    block with no candidate below the bound takes MAX_NCP.
     With `encode`, every level is then fitted with its per-block NCP in one batched call. With
     `search_all`, every block of every level is searched (in-level adaptive encoding alone, the baseline
     that Algorithm 1 speeds up).
@@ -126,7 +128,7 @@ def cross_level_encode(ctx, field, n, degree, bound, levels, encode=True, search
             sel, _ = search_ncp(ctx, D.view(-1), n, degree, bound, candidates=cands, keep_errors=False,
                                 stream=stream)
             sel = sel.cpu().numpy()
-            ncp[search] = np.where(sel > 0, sel, n)
+            ncp[search] = np.where(sel > 0, sel, cands[-1])  # n, or the library's maximum below it
             cplx[search] = sel != degree + 2
         rec = {"level": lvl, "stride": s, "blocks_per_axis": B, "ncp": ncp, "complex": cplx,
                "searched": np.isin(np.arange(nb), search), "fits": len(search) * len(cands)}
