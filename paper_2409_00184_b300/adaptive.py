@@ -109,6 +109,7 @@ def cross_level_encode(ctx, field, n, degree, bound, levels, encode=True, search
     holding the control points) and rmse (float64 CUDA tensor)."""
     Nz, Ny, Nx = field.shape
     cands = list(range(degree + 2, min(n, mfa.MAX_NCP) + 1))
+    fallback = min(n, mfa.MAX_NCP)  # NCP of a block with no candidate below the bound
     out, parent_complex, parent_B = [], None, None
     for lvl in range(levels - 1, -1, -1):
         s = 2 ** lvl
@@ -128,7 +129,7 @@ def cross_level_encode(ctx, field, n, degree, bound, levels, encode=True, search
             sel, _ = search_ncp(ctx, D.view(-1), n, degree, bound, candidates=cands, keep_errors=False,
                                 stream=stream)
             sel = sel.cpu().numpy()
-            ncp[search] = np.where(sel > 0, sel, cands[-1])  # n, or the library's maximum below it
+            ncp[search] = np.where(sel > 0, sel, fallback)
             cplx[search] = sel != degree + 2
         rec = {"level": lvl, "stride": s, "blocks_per_axis": B, "ncp": ncp, "complex": cplx,
                "searched": np.isin(np.arange(nb), search), "fits": len(search) * len(cands)}
