@@ -65,7 +65,8 @@ class OutOfCoreRenderer:
         self.table_host.fill_(-1)
         self.table_host.view(-1)[torch.from_numpy(visible.astype(np.int64))] = torch.arange(len(visible),
                                                                                             dtype=torch.int32)
-        self.table.copy_(self.table_host, non_blocking=True)
+        with torch.cuda.stream(stream):  # ordered before the fill and the ray cast that read it
+            self.table.copy_(self.table_host, non_blocking=True)
         caching_ns = time.perf_counter_ns() - t0
         S, nv = self.stride, len(visible)
         mfa.decode_blocks(self.ctx, self.batch, self.slots, S, nv, bounds=self.batch.bounds,
