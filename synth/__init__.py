@@ -357,6 +357,37 @@ def make_block_set(ncp, degree, nsamp, cps_list, knots_list=None, slots=None, or
     return BlockSet(degree, ncp, nsamp, knot_off, cp_off, slot, origin, pool.array(), cps, meta or {})
 
 
+# Clamped knot vectors whose interior knots repeat (multiplicity up to p), as (C, p, interior knots): spans jump
+# over the empty intervals, so a sample's band can move by more than one control point from its neighbour's.
+REPEATED_KNOT_AXES = [
+    (8, 2, [1 / 4, 1 / 4, 1 / 2, 3 / 4, 3 / 4]),
+    (10, 3, [1 / 4, 1 / 4, 1 / 2, 1 / 2, 1 / 2, 3 / 4]),
+    (6, 1, [1 / 5, 2 / 5, 3 / 5, 4 / 5]),
+    (12, 2, [1 / 8, 1 / 4, 1 / 4, 3 / 8, 1 / 2, 1 / 2, 5 / 8, 3 / 4, 7 / 8]),
+    (7, 3, [3 / 8, 3 / 8, 5 / 8]),
+]
+
+
+def repeated_knots(axis):
+    """Full clamped knot vector of REPEATED_KNOT_AXES[axis] (float64)."""
+    C, p, inner = REPEATED_KNOT_AXES[axis]
+    return np.array([0.0] * (p + 1) + list(inner) + [1.0] * (p + 1))
+
+
+def repeated_knot_set(nblocks, seed, nsamp_choices=(32,)):
+    """Blocks whose three axes each take one of REPEATED_KNOT_AXES (seeded), control points U[-1, 1]."""
+    g = rng(seed)
+    ncp, deg, ns, cps, kn = [], [], [], [], []
+    for _ in range(nblocks):
+        axes = [int(i) for i in g.integers(0, len(REPEATED_KNOT_AXES), 3)]
+        ncp.append([REPEATED_KNOT_AXES[a][0] for a in axes])
+        deg.append([REPEATED_KNOT_AXES[a][1] for a in axes])
+        ns.append([int(g.choice(nsamp_choices)) for _ in range(3)])
+        kn.append([repeated_knots(a) for a in axes])
+        cps.append(g.uniform(-1, 1, size=(ncp[-1][2], ncp[-1][1], ncp[-1][0])))
+    return make_block_set(ncp, deg, ns, cps, kn)
+
+
 def random_block_set(B, seed, ncp_choices=(4, 6, 8, 12), degree_choices=(1, 2, 3), nsamp_choices=(5, 8, 13, 32),
                      nonuniform=False, anisotropic=True, min_gap=0.02):
     """Small mixed batch for parity tests: random per-axis (C, p, n) with p+1 <= C <= n, random CPs in [-1, 1]."""

@@ -68,26 +68,5 @@ def node_groups(bs, slots_of=None):
     return groups
 
 
-# Knot vectors whose interior knots repeat (multiplicity up to p): spans jump over the empty intervals, so a
-# sample's band can move by more than one control point from the previous sample's. (C, p, interior knots)
-REPEATED_KNOT_AXES = [
-    (8, 2, [1 / 4, 1 / 4, 1 / 2, 3 / 4, 3 / 4]),
-    (10, 3, [1 / 4, 1 / 4, 1 / 2, 1 / 2, 1 / 2, 3 / 4]),
-    (6, 1, [1 / 5, 2 / 5, 3 / 5, 4 / 5]),
-    (12, 2, [1 / 8, 1 / 4, 1 / 4, 3 / 8, 1 / 2, 1 / 2, 5 / 8, 3 / 4, 7 / 8]),
-    (7, 3, [3 / 8, 3 / 8, 5 / 8]),
-]
 
-
-def repeated_knot_set(nblocks, seed, nsamp_choices=(32,)):
-    """Blocks whose three axes each take one of REPEATED_KNOT_AXES (seeded), control points U[-1, 1]."""
-    g = synth.rng(seed)
-    ncp, deg, ns, cps, kn = [], [], [], [], []
-    for _ in range(nblocks):
-        axes = [REPEATED_KNOT_AXES[int(i)] for i in g.integers(0, len(REPEATED_KNOT_AXES), 3)]
-        ncp.append([a[0] for a in axes])
-        deg.append([a[1] for a in axes])
-        ns.append([int(g.choice(nsamp_choices)) for _ in range(3)])
-        kn.append([np.array([0.0] * (p + 1) + list(t) + [1.0] * (p + 1)) for _, p, t in axes])
-        cps.append(g.uniform(-1, 1, size=(ncp[-1][2], ncp[-1][1], ncp[-1][0])))
-    return synth.make_block_set(ncp, deg, ns, cps, kn)
+repeated_knot_set = synth.repeated_knot_set

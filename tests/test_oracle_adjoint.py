@@ -37,3 +37,15 @@ def test_gradient_of_squared_residual_matches_finite_differences():
         E[idx] = h
         fd = (loss(P + E) - loss(P - E)) / (2 * h)
         assert abs(fd - G[idx]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_dot_product_identity_with_repeated_knots():
+    """<decode(P), R> = <P, adjoint(R)> on blocks whose knot vectors repeat interior knots."""
+    bs = synth.repeated_knot_set(4, 45, nsamp_choices=(9, 13))
+    g = synth.rng(45)
+    for b in range(len(bs)):
+        P, knots, deg, nsamp = bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b]
+        R = g.uniform(-1, 1, (nsamp[2], nsamp[1], nsamp[0]))
+        lhs = np.sum(decode.decode_block(P, knots, deg, nsamp)[..., 0] * R)
+        rhs = np.sum(P * adjoint.adjoint_block(R, knots, deg, bs.ncp[b]))
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))

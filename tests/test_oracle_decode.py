@@ -205,3 +205,18 @@ def test_grid_params_order_and_corners():
     assert np.array_equal(G[1], [0.5, 0, 0]) and np.array_equal(G[3], [0, third, 0]) and G[12][2] == 0.25
     k, j, i = 2, 1, 2
     assert np.array_equal(G[(k * 4 + j) * 3 + i], [np.float32(i / 2), np.float32(j / 3), np.float32(k / 4)])
+
+
+@pytest.mark.parametrize("axes", [(0, 1, 2), (3, 4, 0), (1, 1, 4), (2, 3, 1)])
+def test_polynomial_reproduction_with_repeated_knots(axes):
+    """Marsden's identity on knot vectors with repeated interior knots (multiplicity up to p): every polynomial
+    of degree <= p per axis is reproduced exactly, value and gradient."""
+    knots = tuple(synth.repeated_knots(a) for a in axes)
+    degrees = tuple(synth.REPEATED_KNOT_AXES[a][1] for a in axes)
+    ncp = tuple(synth.REPEATED_KNOT_AXES[a][0] for a in axes)
+    g = synth.rng(71)
+    coef = g.uniform(-1, 1, size=(degrees[2] + 1, degrees[1] + 1, degrees[0] + 1))
+    P = poly_cps(coef, knots, degrees, ncp)
+    inner = np.unique(np.concatenate(knots))
+    uvw = np.concatenate([g.uniform(0, 1, (200, 3)), np.stack([inner] * 3, axis=1)])
+    assert np.max(np.abs(decode.evaluate_points(P, knots, degrees, uvw) - poly_eval(coef, uvw))) < 1e-11

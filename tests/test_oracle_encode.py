@@ -224,3 +224,22 @@ def test_collocation_rows_and_pseudo_inverse(C, p, n):
     assert A.shape == (C, n)
     assert np.max(np.abs(A @ N - np.eye(C))) < 1e-10
     assert np.max(np.abs(A - np.linalg.pinv(N))) < 1e-9 * max(1.0, np.abs(A).max())
+
+
+@pytest.mark.parametrize("axes,nsamp", [((2, 4, 0), (11, 12, 13)), ((0, 2, 4), (13, 9, 10))])
+def test_fit_with_repeated_knots(axes, nsamp):
+    """Knot vectors with repeated interior knots: the separable fit equals the dense least squares, its
+    residual is orthogonal to the basis, and polynomial data of degree <= p is fitted exactly."""
+    knots = tuple(synth.repeated_knots(a) for a in axes)
+    degrees = tuple(synth.REPEATED_KNOT_AXES[a][1] for a in axes)
+    ncp = tuple(synth.REPEATED_KNOT_AXES[a][0] for a in axes)
+    g = synth.rng(73)
+    D = g.uniform(-1, 1, (nsamp[2], nsamp[1], nsamp[0]))
+    Ps, Pd = encode.fit_separable(D, knots, degrees), encode.fit_dense(D, knots, degrees)
+    assert np.max(np.abs(Ps - Pd)) < 1e-10 * max(1.0, np.abs(Pd).max())
+    G = adjoint.adjoint_block(encode.residual(Ps, D, knots, degrees), knots, degrees, ncp)
+    assert np.max(np.abs(G)) < 1e-11
+    coef = g.uniform(-1, 1, (degrees[2] + 1, degrees[1] + 1, degrees[0] + 1))
+    P_true = poly_cps(coef, knots, degrees, ncp)
+    Dp = decode.decode_block(P_true, knots, degrees, nsamp)[..., 0]
+    assert np.max(np.abs(encode.fit_separable(Dp, knots, degrees) - P_true)) < 1e-10
