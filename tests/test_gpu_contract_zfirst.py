@@ -129,3 +129,32 @@ def test_zfirst_skips_blocks_that_fail_their_checks(mfa, ctx):
         want = oadj.adjoint_block(_grid(R, bs, b), bs.block_knots(b), bs.degree[b], bs.ncp[b])
         assert np.abs(_cps(G, bs, b) - want).max() <= 1e-5 * np.abs(want).max(), b
     assert ctx.device_status() == 0
+
+
+def test_zfirst_adjoint_at_the_step_size_sampled():
+    """The adjoint as the 512^3 step launches it: 4096 blocks of 32^3, C = 12, degree 2, on the z-first kernel
+    (one CTA per SM, about 28 blocks each, so the set-up buffers rotate many times), over the step's own
+    synthetic field as the residual; 18 sampled blocks (the first and last among them) against the FP64
+    oracle's adjoint."""
+    from paper_2409_00184_b300 import mfa
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0)
+    N, n, C, p = 512, 32, 12, 2
+    field = synth.gm_noise_field(N, synth.BASE_SEED + 2, device="cuda")
+    R = synth.blocks_from_field(field, n).contiguous().view(-1)
+    del field
+    B = (N // n) ** 3
+    bs = synth.make_block_set([(C,) * 3] * B, [(p,) * 3] * B, [(n,) * 3] * B, [np.zeros((C, C, C))] * B)
+    blk = mfa.DeviceBlocks(bs)
+    grad = torch.full((blk.cps_len,), float("nan"), device="cuda")
+    mfa.adjoint_blocks(ctx, blk, R, n ** 3, B, grad)
+    assert ctx.device_status() == 0
+    G = grad.view(B, C ** 3)
+    assert bool(torch.isfinite(G).all())
+    pick = sorted(set(synth.rng(5).choice(B, 16, replace=False).tolist()) | {0, B - 1})
+    Rv = R.view(B, n, n, n)
+    for b in pick:
+        want = oadj.adjoint_block(Rv[b].double().cpu().numpy(), bs.block_knots(b), bs.degree[b], bs.ncp[b])
+        got = G[b].double().cpu().numpy().reshape(C, C, C)
+        assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max(), b
+    ctx.close()
