@@ -211,3 +211,45 @@ def test_repeated_interior_knots_adjoint_and_fit(mfa, ctx):
             assert np.abs(g - want).max() <= 1e-5 * max(1.0, np.abs(want).max()), b
         want_rmse = encode.rmse(want, Db, fb.block_knots(b), fb.degree[b])
         assert abs(rm[b] - want_rmse) <= 1e-5 * (Db.max() - Db.min()), (b, rm[b], want_rmse)
+
+
+def test_smallest_blocks_decode_adjoint_fit(mfa, ctx):
+    """The smallest blocks the library takes: 2 or 3 samples per axis with C = p + 1 <= n control points
+    (degree 1 or 2, a single Bezier span). The FP32 decode, the adjoint and the least-squares fit (with
+    C = n the fit interpolates the samples) against the FP64 oracle."""
+    specs = [((2, 2, 2), (1, 1, 1), (2, 2, 2)), ((3, 3, 3), (2, 2, 2), (3, 3, 3)), ((2, 3, 2), (1, 2, 1), (3, 3, 2)),
+             ((2, 2, 3), (1, 1, 2), (2, 3, 3))]
+    g = synth.rng(361)
+    ncp, deg, ns, cps = [], [], [], []
+    for C, p, n in specs * 2:
+        ncp.append(C), deg.append(p), ns.append(n)
+        cps.append(g.uniform(-1, 1, (C[2], C[1], C[0])))
+    bs = synth.make_block_set(ncp, deg, ns, cps)
+    blk = mfa.DeviceBlocks(bs)
+    V = blk.slot_voxels
+    cache = torch.full((len(bs) * V * 4,), float("nan"), device="cuda")
+    mfa.decode_blocks(ctx, blk, cache, V, len(bs))
+    R, stride = _grids(bs, 362)
+    grad = torch.full((blk.cps_len,), float("nan"), device="cuda")
+    mfa.adjoint_blocks(ctx, blk, torch.from_numpy(R.ravel()).cuda(), stride, len(bs), grad)
+    assert ctx.device_status() == 0
+    c = cache.view(len(bs), V, 4).cpu().numpy()
+    G = grad.cpu().numpy()
+    for b in range(len(bs)):
+        nx, ny, nz = bs.nsamp[b]
+        Cx, Cy, Cz = bs.ncp[b]
+        want = decode.decode_block(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b])
+        got = c[bs.slot[b], : nx * ny * nz].reshape(nz, ny, nx, 4)
+        assert np.abs(got - want).max() <= 1e-5 * max(1.0, np.abs(want).max()), b
+        gw = oadj.adjoint_block(_block_grid(R, bs, b), bs.block_knots(b), bs.degree[b], bs.ncp[b])
+        gg = G[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(gg - gw).max() <= 1e-5 * max(1e-30, np.abs(gw).max()), b
+    D, stride = _grids(bs, 363)
+    P, rm = _encode(mfa, ctx, bs, D, stride)
+    for b in range(len(bs)):
+        Db = _block_grid(D, bs, b)
+        want = encode.fit_separable(Db, bs.block_knots(b), bs.degree[b])
+        Cx, Cy, Cz = bs.ncp[b]
+        got = P[bs.cp_off[b]: bs.cp_off[b] + Cx * Cy * Cz].reshape(Cz, Cy, Cx)
+        assert np.abs(got - want).max() <= 1e-5 * max(1.0, np.abs(want).max()), b
+        assert abs(rm[b] - encode.rmse(want, Db, bs.block_knots(b), bs.degree[b])) <= 1e-5 * (Db.max() - Db.min())
