@@ -237,3 +237,40 @@ def test_autotuner_installs_a_tiling_and_keeps_parity(mfa, ctx, tmp_path):
         want = odec.decode_block(bs.block_cps(b), bs.block_knots(b), bs.degree[b], bs.nsamp[b])
         ve, ge = rel_errors(c[bs.slot[b], : nx * ny * nz].reshape(nz, ny, nx, 4), want)
         assert ve <= TOL_FP32 and max(ge) <= TOL_FP32
+
+
+def test_frame_with_no_visible_blocks(mfa, ctx):
+    """A frame whose visible list is empty (count 0, e.g. the camera looks away from the volume): the replayed
+    graph decodes nothing, the brick table holds no brick, and the image is the oracle's render of a volume of
+    absent bricks (their nodes read as zero). The same graph then renders a frame with visible blocks, which
+    maps exactly those blocks."""
+    N, n, p = 64, 16, 2
+    bs, B = flame_blockset(N, n, (4, 6), (50,), p, synth.BASE_SEED + 5, "cpu")
+    blk = mfa.DeviceBlocks(bs)
+    cap = len(bs)
+    lst, cnt, cache, table, image = _frame_buffers(cap, len(bs), n, (24, 16))
+    tf = torch.from_numpy(synth.transfer_function(synth.BASE_SEED + 3)).cuda()
+    view = synth.orbit_view(0, width=24, height=16)
+    g = mfa.FrameGraph(ctx, blk, lst, cnt, cache, n ** 3, sort=True, table=table,
+                       brick_dims=(B, B, B), brick_n=n, view=view, tf=tf, image=image)
+    image.fill_(float("nan"))
+    table.fill_(7)
+    cnt.fill_(0)
+    g.launch()
+    assert ctx.device_status() == 0
+    assert bool((table == -1).all())
+    assert bool(torch.isnan(cache).all())  # nothing decoded
+    want = ocast.raycast(np.zeros((1, n, n, n, 4), np.float32), np.full((B, B, B), -1, np.int32), n, view,
+                         tf.cpu().numpy())
+    assert np.abs(image.cpu().numpy() - want).max() <= 1e-6
+    vis = np.array([3, 0, 5], dtype=np.int32)
+    lst[:3] = torch.from_numpy(vis).cuda()
+    cnt.fill_(3)
+    g.launch()
+    assert ctx.device_status() == 0
+    order = lst[:3].cpu().numpy()
+    assert sorted(order.tolist()) == sorted(vis.tolist())
+    tab = np.full(len(bs), -1, np.int32)
+    tab[order] = np.arange(3, dtype=np.int32)
+    assert np.array_equal(table.cpu().numpy(), tab)
+    g.close()
