@@ -463,7 +463,12 @@ int mfa_selftest_wait_timeout(mfa_ctx* ctx, int32_t polls, void* stream);
  * decoded cache of bricks of brick_n^3 voxels. d_brick_table[(bz*By + by)*Bx + bx] is the
  * slot of brick (bx, by, bz) or -1 if absent (its nodes read as zero); brick_dims =
  * {Bx, By, Bz}. The volume of B_a*brick_n nodes per axis maps onto [-1, 1]^3. The
- * transfer function is tf_n RGBA float entries over [vmin, vmax]. */
+ * transfer function is tf_n RGBA float entries over [vmin, vmax]. MFA_ERR_INVALID_ARG for null
+ * pointers, d_cache / d_tf / d_image not 16-byte aligned, brick_n < 2, slot_stride_voxels below
+ * brick_n^3, brick_dims[a] < 1 or brick_dims[a]*brick_n > 2^20, tf_n < 2, an image side outside
+ * 1 .. 16384, a field of view outside (0, 180) degrees, step_voxels <= 0, vmax <= vmin, eye equal to
+ * target or up parallel to the view direction, or a step so small that a ray would exceed 2^24
+ * samples; MFA_ERR_CAPACITY for tf_n > 1024. */
 int mfa_raycast(mfa_ctx* ctx,
                 const float* d_cache, int64_t slot_stride_voxels, int64_t nslots,
                 const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
