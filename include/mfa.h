@@ -523,7 +523,8 @@ int mfa_fill_aprons(mfa_ctx* ctx, float* d_cache, int64_t slot_stride_voxels, in
  * gaps of several axes meet), as trilinear interpolation of a decoded cache would be there.
  * Descriptors, knots and control points as for mfa_decode_blocks (bounds: the batch's maxima,
  * max_nsamp >= brick_n); a block that fails its checks reads as absent and sets its status bit.
- * Samples marched add to MFA_STAT_RAY_SAMPLES. */
+ * Samples marched add to MFA_STAT_RAY_SAMPLES. The view, transfer function, image and brick grid are
+ * checked as in mfa_raycast (slot strides aside), and the model arrays as in mfa_decode_blocks. */
 int mfa_raycast_direct(mfa_ctx* ctx, const mfa_block_desc* d_desc, int32_t nblocks, const float* d_knots,
                        int64_t knots_len, const float* d_cps, int64_t cps_len, const mfa_bounds* bounds,
                        const int32_t* d_brick_table, const int32_t brick_dims[3], int32_t brick_n,
