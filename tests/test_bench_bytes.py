@@ -42,3 +42,23 @@ def test_reduced_step_field_is_for_profiling_only():
     assert r.returncode != 0 and "--no-check --no-cpu-baseline" in r.stderr
     r = run("--field", "100", "--no-check", "--no-cpu-baseline")
     assert r.returncode != 0 and "multiple of 32" in r.stderr
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
+    """The clock record of a timed region: median SM clock, the maximum clock, and every throttle reason
+    that was Active in any sample (here hw_slowdown in one row and sw_power_cap in another), from
+    nvidia-smi's CSV rows (a stand-in script prints three samples, then waits to be stopped)."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    rows = ["0, 2032, 2032, 800.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2032, 1100.2, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2032, 2032, 900.0, 0x8, Active, Not Active, Not Active, Not Active"]
+    fake.write_text("#!/bin/sh\n" + "".join(f"echo '{r}'\n" for r in rows) + "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ.get('PATH', '')}")
+    s = bench.ClockSampler(0)
+    s.start()
+    time.sleep(0.5)
+    r = s.stop()
+    assert r["samples"] == 3 and r["sm_mhz"] == 2032.0 and r["sm_max_mhz"] == 2032.0
+    assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
