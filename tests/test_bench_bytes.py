@@ -62,3 +62,15 @@ def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
     r = s.stop()
     assert r["samples"] == 3 and r["sm_mhz"] == 2032.0 and r["sm_max_mhz"] == 2032.0
     assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_rejection_rule():
+    """A timed region is measured again when a hardware or thermal slowdown was active, or when the SM clock
+    sat well below its maximum with no reason (a leftover clock lock); sw_power_cap alone is kept."""
+    ok = {"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1900.0, reasons=["sw_power_cap"]))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))  # locked low, no reason given
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
