@@ -54,3 +54,33 @@ def test_struct_mirrors_match_the_library():
     from paper_2409_00184_b300 import mfa
     want = [ctypes.sizeof(t) for t in (mfa.BlockDesc, mfa.Bounds, mfa.DecodeTiling, mfa.View, mfa.FrameDesc)]
     assert mfa.abi_struct_sizes() == want
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The package (binding, autograd, adaptive encoding, out-of-core sequencing, build) and the library
+    sources name no oracle module: every result of the product path comes from the CUDA library. The oracle
+    and the library share no source either (the oracle is plain numpy)."""
+    pkg = os.path.join(ROOT, "paper_2409_00184_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\b(import|from)\s+oracle\b|oracle\.", src), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2409_00184_b300" not in src and "libmfa" not in src, f
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """With libmfa.so missing the binding raises ImportError: there is no CPU or framework fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2409_00184_b300"
+    pkg.mkdir()
+    for f in ("__init__.py", "mfa.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2409_00184_b300", f), pkg / f)
+    r = subprocess.run([sys.executable, "-c", "import paper_2409_00184_b300.mfa"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "ImportError" in r.stderr and "no fallback" in r.stderr
