@@ -70,6 +70,9 @@ def test_product_code_never_reaches_the_oracle():
         if f.endswith(".py"):
             src = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2409_00184_b300" not in src and "libmfa" not in src, f
+    # the seeded input generators serve both sides and import neither
+    src = open(os.path.join(ROOT, "synth", "__init__.py")).read()
+    assert not re.search(r"\b(import|from)\s+(oracle|paper_2409_00184_b300)\b", src)
 
 
 def test_binding_refuses_to_load_without_the_library(tmp_path):
