@@ -87,3 +87,29 @@ def test_binding_refuses_to_load_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", "import paper_2409_00184_b300.mfa"], cwd=tmp_path,
                        capture_output=True, text=True, timeout=300)
     assert r.returncode != 0 and "ImportError" in r.stderr and "no fallback" in r.stderr
+
+
+def _undocumented(lines):
+    """Functions whose declaration is not reached, walking up without crossing a blank line, from the end of
+    a comment block (their own, or the one opening their group of declarations and flag defines)."""
+    out = []
+    for i, line in enumerate(lines):
+        m = re.match(r"\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(mfa_[a-z_0-9]+)\s*\(", line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            out.append(m.group(1))
+    return out
+
+
+def test_every_entry_point_is_documented():
+    """Every function include/mfa.h declares sits under a comment (its own, or one shared with the
+    declarations right after it), which states what it computes, its arguments and its errors."""
+    probe = ["/* a */", "int mfa_a(int x);", "", "int mfa_b(int y);", "/* c, d */", "int mfa_c(void);",
+             "#define X 1", "int mfa_d(void);"]
+    assert _undocumented(probe) == ["mfa_b"]  # the check itself
+    lines = open(os.path.join(ROOT, "include", "mfa.h")).read().splitlines()
+    assert not _undocumented(lines), _undocumented(lines)
